@@ -1,0 +1,292 @@
+"""Pins of the oracle's H_eff, environments, Lanczos, truncated SVD and DMRG."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dmrg as D
+from oracle import ed, models
+from oracle.blocksparse import OUT, BlockTensor, QNIndex, trivial_index
+from paper_2007_14822_gb300 import synth
+
+from test_oracle_models import mpo_full
+
+
+def random_mps(mpo, dims, seed, nsect=None, qn_link_fn=None):
+    """Random real MPS with given link dims (dense: one trivial sector)."""
+    site = mpo.site_index
+    N = mpo.N
+    A = []
+    left = QNIndex([((0,) * site.nq, 1)], OUT)
+    for j in range(N):
+        if j == N - 1:
+            right = QNIndex([(left.qn(0) if left.nsect == 1 else (0,) * site.nq, 1)], OUT)
+        else:
+            right = QNIndex([((0,) * site.nq, dims[j])], OUT)
+        inds = [left, site, right.dag()]
+        A.append(BlockTensor.from_blocks_fn(inds, None,
+                 lambda key, shp, j=j: synth.block_gaussian(seed, f"A{j}", key, shp)))
+        left = right
+    return A
+
+
+def dense_site_mpo(mpo):
+    """The same MPO with every index flattened to one trivial sector."""
+    W = []
+    for w in mpo.W:
+        inds = [trivial_index(i.dim, i.arrow, nq=w.inds[0].nq) for i in w.inds]
+        W.append(BlockTensor.from_dense(w.to_dense(), inds))
+    site = trivial_index(mpo.site_index.dim, OUT, nq=mpo.site_index.nq)
+    return models.MPO(W, site, mpo.start, mpo.done)
+
+
+def projector(A, j):
+    """P maps theta[a_j, s_j, s_j+1, b] to the full state (site 0 slowest)."""
+    N = len(A)
+    left = np.ones((1, 1))                       # [full_left, a]
+    for i in range(j):
+        t = np.einsum("pa,asb->psb", left, A[i].to_dense())
+        left = t.reshape(-1, t.shape[2])
+    right = np.ones((1, 1))                      # [b, full_right]
+    for i in range(N - 1, j + 1, -1):
+        t = np.einsum("asb,bq->asq", A[i].to_dense(), right)
+        right = t.reshape(t.shape[0], -1)
+    # P[(l, s1, s2, r), (a, s1, s2, b)] = left[l,a] right[b,r]
+    da, db = left.shape[1], right.shape[0]
+    d = A[0].inds[1].dim
+    P = np.einsum("la,sx,uy,br->lsuraxyb", left, np.eye(d), np.eye(d), right)
+    return P.reshape(left.shape[0] * d * d * right.shape[1], da * d * d * db)
+
+
+def envs_at(mpo, A, j):
+    W = mpo.W
+    N = mpo.N
+    L = D.left_boundary(A[0], W[0], mpo.start)
+    for i in range(j):
+        L = D.env_left(L, A[i], W[i])
+    R = D.right_boundary(A[N - 1], W[N - 1], mpo.done)
+    for i in range(N - 1, j + 1, -1):
+        R = D.env_right(R, A[i], W[i])
+    return L, R
+
+
+@pytest.mark.parametrize("model", ["heis", "hub"])
+def test_heff_equals_projected_hamiltonian(model):
+    if model == "heis":
+        N, d = 6, 2
+        mpo = dense_site_mpo(models.heisenberg_mpo(N))
+        terms = models.spin_pair_terms(models.heisenberg_pairs(N))
+        dims = [2, 3, 4, 3, 2]
+    else:
+        N, d = 4, 4
+        mpo = dense_site_mpo(models.hubbard_mpo(N, 1.0, 4.0))
+        terms = models.hubbard_terms(N, 1.0, 4.0)
+        dims = [3, 4, 2]
+    A = random_mps(mpo, dims, seed=21)
+    H = ed.hamiltonian_dense(N, d, terms)
+    for j in range(N - 1):
+        P = projector(A, j)
+        L, R = envs_at(mpo, A, j)
+        th = D.theta(A[j], A[j + 1])
+        Hm = D.heff_dense_matrix(L, mpo.W[j], mpo.W[j + 1], R, th)
+        np.testing.assert_allclose(Hm, P.T @ H @ P, atol=1e-12 * max(1, np.abs(Hm).max()))
+
+
+def qn_random_mps(mpo, maxd, seed, states):
+    """Random QN MPS: start from a product state's link charges, widen links."""
+    site = mpo.site_index
+    N = mpo.N
+    nq = site.nq
+    # link sectors: every charge reachable from the left and completable to
+    # the right target, dims capped by maxd
+    qs = [site.qn(s) for s in range(site.nsect)]
+    total = tuple(sum(site.qn(site.sector_of(st)[0])[k] for st in states) for k in range(nq))
+    reach = [{(0,) * nq}]
+    for j in range(N):
+        reach.append({tuple(a + b for a, b in zip(q, s)) for q in reach[-1] for s in qs})
+    back = [None] * (N + 1)
+    back[N] = {total}
+    for j in range(N - 1, -1, -1):
+        back[j] = {tuple(a - b for a, b in zip(q, s)) for q in back[j + 1] for s in qs}
+    links = []
+    rng = np.random.default_rng(seed)
+    for j in range(N + 1):
+        ok = sorted(reach[j] & back[j])
+        links.append(QNIndex([(q, 1 if j in (0, N) else int(rng.integers(1, maxd + 1)))
+                              for q in ok], OUT))
+    A = []
+    for j in range(N):
+        inds = [links[j], site, links[j + 1].dag()]
+        A.append(BlockTensor.from_blocks_fn(inds, None,
+                 lambda key, shp, j=j: synth.block_gaussian(seed, f"Q{j}", key, shp)))
+    return A
+
+
+def dense_tensor(T):
+    inds = [trivial_index(i.dim, i.arrow, nq=i.nq) for i in T.inds]
+    return BlockTensor.from_dense(T.to_dense(), inds, tuple(0 for _ in T.flux))
+
+
+def test_qn_heff_embeds_dense_heff():
+    N = 6
+    mpo = models.heisenberg_mpo(N)
+    A = qn_random_mps(mpo, 3, seed=22, states=[0, 1] * 3)
+    dmpo = dense_site_mpo(mpo)
+    for j in range(N - 1):
+        L, R = envs_at(mpo, A, j)
+        th = D.theta(A[j], A[j + 1])
+        x = BlockTensor.from_blocks_fn(th.inds, th.flux,
+                                       lambda k, s: synth.block_gaussian(5, "x", k, s))
+        y = D.heff_apply(L, mpo.W[j], mpo.W[j + 1], R, x)
+        # flux preserved: y has only allowed blocks
+        BlockTensor.from_dense(y.to_dense(), y.inds, y.flux, atol=0.0)
+        yd = D.heff_apply(dense_tensor(L), dmpo.W[j], dmpo.W[j + 1], dense_tensor(R),
+                          dense_tensor(x))
+        np.testing.assert_allclose(y.to_dense(), yd.to_dense(), atol=1e-12)
+
+
+def test_heff_hermitian_and_matches_chain_energy():
+    N = 8
+    mpo = models.heisenberg_mpo(N)
+    A = qn_random_mps(mpo, 4, seed=23, states=[0, 1] * 4)
+    j = 3
+    L, R = envs_at(mpo, A, j)
+    th = D.theta(A[j], A[j + 1])
+    x = BlockTensor.from_blocks_fn(th.inds, th.flux, lambda k, s: synth.block_gaussian(6, "x", k, s))
+    z = BlockTensor.from_blocks_fn(th.inds, th.flux, lambda k, s: synth.block_gaussian(7, "z", k, s))
+    Hx = D.heff_apply(L, mpo.W[j], mpo.W[j + 1], R, x)
+    Hz = D.heff_apply(L, mpo.W[j], mpo.W[j + 1], R, z)
+    assert abs(z.vdot(Hx) - Hz.vdot(x)) < 1e-12 * abs(z.vdot(Hx))
+    # <theta|H_eff|theta> / <P theta|P theta> equals the full-chain expectation
+    Hth = D.heff_apply(L, mpo.W[j], mpo.W[j + 1], R, th)
+    num = th.vdot(Hth)
+    want_num = D.mps_expectation(mpo, A)
+    # normalisation through the same projector
+    P = projector([dense_tensor(a) for a in A], j)
+    nrm = float(np.sum((P @ th.to_dense().ravel()) ** 2))
+    assert abs(num / nrm - want_num) < 1e-11 * abs(want_num)
+
+
+def test_lanczos_matches_eigh():
+    rng = np.random.default_rng(31)
+    n = 60
+    M = rng.standard_normal((n, n))
+    M = M + M.T
+    w = np.linalg.eigvalsh(M)
+    ops = dict(vdot=lambda u, v: float(u @ v), norm=lambda u: float(np.linalg.norm(u)),
+               scale=lambda u, a: u * a, axpy=lambda u, a, v: u + a * v)
+    E, x, res, k = D.lanczos(lambda v: M @ v, rng.standard_normal(n), 60, 1e-12, **ops)
+    assert abs(E - w[0]) < 1e-10
+    assert np.linalg.norm(M @ x - E * x) < 1e-8
+
+
+def test_truncation_count_rule():
+    s = np.array([1.0, 0.5, 0.1, 0.01])
+    tot = float(np.sum(s ** 2))
+    # cutoff just above the smallest weight -> drop one
+    k, err = D.truncation_count(s, 1.0001e-4 / tot, 10)
+    assert k == 3 and abs(err - 1e-4 / tot) < 1e-15
+    # cutoff just below -> keep all
+    k, err = D.truncation_count(s, 0.9999e-4 / tot, 10)
+    assert k == 4 and err == 0.0
+    # cutoff covering the two smallest
+    k, _ = D.truncation_count(s, (0.01 ** 2 + 0.1 ** 2) / tot, 10)
+    assert k == 2
+    # maxdim binds
+    k, err = D.truncation_count(s, 0.0, 2)
+    assert k == 2 and abs(err - (0.01 ** 2 + 0.1 ** 2) / tot) < 1e-15
+    # mindim binds
+    k, _ = D.truncation_count(s, 1.0, 10, mindim=2)
+    assert k == 2
+    # at least one is kept
+    k, _ = D.truncation_count(s, 1.0, 10)
+    assert k == 1
+
+
+def test_svd_trunc_eckart_young_and_predicted_count():
+    # theta built as U diag(sigma) V^T per charge sector with chosen sigma
+    site = QNIndex([((1,), 1), ((-1,), 1)], OUT)
+    a = QNIndex([((0,), 3), ((2,), 2), ((-2,), 2)], OUT)
+    b = QNIndex([((0,), 3), ((2,), 2), ((-2,), 2)], OUT)
+    inds = [a, site, site, b.dag()]
+    rng = np.random.default_rng(41)
+    th = BlockTensor.from_blocks_fn(inds, None, lambda k, s: rng.standard_normal(s))
+    U, S, V, err0 = D.svd_trunc(th, 2, 0.0, 10 ** 6)
+    rec = D.theta(D.scale_link(U, S, 2), V)
+    np.testing.assert_allclose(rec.to_dense(), th.to_dense(), atol=1e-12)
+    allsv = np.sort(np.concatenate(list(S.values())))[::-1]
+    n = len(allsv)
+    for keep in [1, 3, n // 2, n - 1]:
+        U, S, V, err = D.svd_trunc(th, 2, 0.0, keep)
+        assert sum(len(v) for v in S.values()) == keep
+        rec = D.theta(D.scale_link(U, S, 2), V)
+        disc = float(np.sum(allsv[keep:] ** 2))
+        diff = th.to_dense() - rec.to_dense()
+        assert abs(float(np.sum(diff ** 2)) - disc) < 1e-10 * float(np.sum(allsv ** 2))
+        assert abs(err - disc / float(np.sum(allsv ** 2))) < 1e-12
+    # U is an isometry
+    Ud = U.to_dense().reshape(-1, U.inds[2].dim)
+    np.testing.assert_allclose(Ud.T @ Ud, np.eye(Ud.shape[1]), atol=1e-12)
+
+
+def _dmrg(mpo, mps, sweeps, **kw):
+    return D.dmrg(mpo, mps, sweeps, **kw)
+
+
+def test_dmrg_heisenberg_dense_vs_ed():
+    N = 10
+    mpo = dense_site_mpo(models.heisenberg_mpo(N))
+    vecs = synth.product_spinors(1, N, 2)
+    A = D.product_mps_vectors(mpo.site_index, vecs)
+    E, A, st = _dmrg(mpo, A, [(8, 1e-12), (16, 1e-12), (32, 1e-13), (32, 1e-13)])
+    e_ed = ed.ground_energy(N, 2, models.spin_pair_terms(models.heisenberg_pairs(N)))
+    assert abs(E - e_ed) < 1e-10 * abs(e_ed)
+    assert abs(D.mps_expectation(mpo, A) - E) < 1e-9
+
+
+def test_dmrg_heisenberg_qn_vs_ed():
+    N = 12
+    mpo = models.heisenberg_mpo(N)
+    A = D.product_mps_basis(mpo.site_index, [0, 1] * (N // 2), 1)
+    E, A, st = _dmrg(mpo, A, [(8, 1e-12), (32, 1e-12), (64, 1e-13), (64, 1e-13)])
+    e_ed = ed.ground_energy(N, 2, models.spin_pair_terms(models.heisenberg_pairs(N)),
+                            models.SPIN_QN, (0,))
+    assert abs(E - e_ed) < 1e-10 * abs(e_ed)
+
+
+def test_dmrg_tfim_free_fermion():
+    from test_oracle_models import tfim_closed_form
+    N = 12
+    mpo = models.tfim_mpo(N, 1.0, 1.3)
+    A = D.product_mps_vectors(mpo.site_index, synth.product_spinors(2, N, 2))
+    E, A, st = _dmrg(mpo, A, [(8, 1e-12), (24, 1e-13), (32, 1e-13)])
+    assert abs(E - tfim_closed_form(N, 1.0, 1.3)) < 1e-10 * abs(E)
+
+
+def test_dmrg_majumdar_ghosh():
+    N = 12
+    mpo = models.heisenberg_like_mpo(N, models.j1j2_chain_pairs(N, 1.0, 0.5))
+    A = D.product_mps_basis(mpo.site_index, [0, 1] * (N // 2), 1)
+    E, A, st = _dmrg(mpo, A, [(8, 1e-12), (32, 1e-12), (64, 1e-13), (64, 1e-13)])
+    assert abs(E + 3 * N / 8) < 1e-10 * 3 * N / 8
+
+
+def test_dmrg_hubbard_vs_ed():
+    N = 4
+    mpo = models.hubbard_mpo(N, 1.0, 4.0)
+    A = D.product_mps_basis(mpo.site_index, [1, 2] * (N // 2), 2)
+    E, A, st = _dmrg(mpo, A, [(16, 1e-12), (64, 1e-13), (64, 1e-13)])
+    e_ed = ed.ground_energy(N, 4, models.hubbard_terms(N, 1.0, 4.0), models.HUB_QN, (N, 0))
+    assert abs(E - e_ed) < 1e-10 * abs(e_ed)
+
+
+def test_dmrg_is_variational_and_truncation_bounded():
+    # N=20 Heisenberg, m=32, cutoff 1e-10, 5 sweeps, random product state
+    N = 20
+    mpo = dense_site_mpo(models.heisenberg_mpo(N))
+    A = D.product_mps_vectors(mpo.site_index, synth.product_spinors(1, N, 2))
+    E, A, st = _dmrg(mpo, A, [(32, 1e-10)] * 5, krylov_dim=64, tol=1e-10)
+    e_ed = ed.ground_energy(N, 2, models.spin_pair_terms(models.heisenberg_pairs(N)),
+                            models.SPIN_QN, (0,))
+    assert E >= e_ed - 1e-10
+    assert E - e_ed <= 1e-4 * abs(e_ed)
