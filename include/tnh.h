@@ -1,0 +1,257 @@
+/*
+ * tnh.h -- C ABI of the GB300 two-site DMRG effective-Hamiltonian library.
+ *
+ * The library computes the hot path of two-site DMRG as described in the
+ * ITensor paper (arXiv:2007.14822): the labelled tensor contraction over
+ * shared indices (Sec. 4, Sec. 9.1), on dense and QN block-sparse storage
+ * (Sec. 6, Sec. 8, Sec. 9.2), the effective-Hamiltonian product H_eff . psi
+ * that the eigensolver applies at every bond (Sec. 7.2), the environment
+ * update, the truncated SVD with cutoff and maxdim (Sec. 5) and the sweep
+ * driver dmrg(H, psi0, sweeps) (Sec. 7.2).
+ *
+ * Conventions shared by every entry point
+ *   - Real float64 data, row-major, rightmost index fastest.
+ *   - Tensor data pointers are DEVICE pointers owned by the caller; all
+ *     metadata (indices, block lists) are HOST pointers read during the call
+ *     and not retained.
+ *   - Every call is asynchronous on the context's stream unless documented
+ *     otherwise; calls that must read a result on the host (a kept dimension,
+ *     an energy) synchronise that stream and say so.
+ *   - No exception crosses the ABI. Every call returns a tnh_status; the text
+ *     of the last error of a context is returned by tnh_last_error().
+ *   - Nothing falls back to the CPU: when the device or the kernels are not
+ *     usable the call fails with TNH_ERR_CUDA.
+ */
+#ifndef TNH_H
+#define TNH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TNH_OK = 0,
+    TNH_ERR_ARG = 1,        /* null pointer, bad enum, bad size            */
+    TNH_ERR_LABEL = 2,      /* labels do not pair up as a contraction needs */
+    TNH_ERR_ARROW = 3,      /* contracted QN indices with equal arrows     */
+    TNH_ERR_FLUX = 4,       /* a stored block violates the tensor's flux   */
+    TNH_ERR_SHAPE = 5,      /* sector dims / block offsets inconsistent    */
+    TNH_ERR_OOM = 6,        /* device allocation failed                    */
+    TNH_ERR_CUDA = 7,       /* CUDA runtime / launch error                 */
+    TNH_ERR_TIMEOUT = 8,    /* a bounded device wait gave up               */
+    TNH_ERR_NUMERIC = 9,    /* NaN/Inf or Lanczos breakdown at start       */
+    TNH_ERR_NOT_CONVERGED = 10
+} tnh_status;
+
+/* Arithmetic used by the contractions.
+ *   TNH_FP64    plain float64 on the CUDA cores (the reference GPU path).
+ *   TNH_BF16x6  each float64 operand split into three bfloat16 parts
+ *               x = hi + mid + lo; six tensor-core products (hh, hm, mh,
+ *               hl, lh, mm) accumulated in float32 (tcgen05, sm_103a).
+ *   TNH_BF16x3  two-part split, three products (hh, hm, mh).
+ *   TNH_BF16    one bfloat16 part, one product.
+ * The split modes are the "lower precision" storage the paper mentions in
+ * Sec. 6; their measured error against float64 is reported by the tests. */
+typedef enum {
+    TNH_FP64 = 0,
+    TNH_BF16x6 = 1,
+    TNH_BF16x3 = 2,
+    TNH_BF16 = 3
+} tnh_precision;
+
+typedef struct tnh_ctx tnh_ctx;
+typedef struct tnh_heff tnh_heff;
+typedef struct tnh_svd tnh_svd;
+
+/* A QN index (Sec. 3, Sec. 8.2).
+ *   label     integer the contraction matches; equal labels are summed
+ *             (it stands for the Index id + prime level of Sec. 3).
+ *   nsect     number of sectors (>= 1); a dense index has one sector.
+ *   nq        number of integer charges in a QN (0..4).
+ *   qn        host [nsect * nq] charges, sector-major.
+ *   sect_dim  host [nsect] sector dimensions (>= 1).
+ *   arrow     +1 Out (charges added to the flux), -1 In (subtracted). */
+typedef struct {
+    int64_t label;
+    int32_t nsect;
+    int32_t nq;
+    const int32_t* qn;
+    const int32_t* sect_dim;
+    int32_t arrow;
+} tnh_index;
+
+/* A block-sparse tensor (Sec. 6 "Block sparse storage", Sec. 9.2).
+ *   rank        number of indices (0..8).
+ *   inds        host [rank].
+ *   nblocks     number of stored blocks; each block is a dense row-major
+ *               array of the sector dimensions it selects.
+ *   block_sect  host [nblocks * rank] sector number of each index.
+ *   block_off   host [nblocks] element offset of each block in data.
+ *   data        DEVICE float64 pointer (caller-owned).
+ *   size        number of float64 elements behind data (bounds check).
+ * A dense tensor is one block with one sector per index. Every block must
+ * have the same flux (sum of arrow * charge); otherwise TNH_ERR_FLUX. */
+typedef struct {
+    int32_t rank;
+    const tnh_index* inds;
+    int32_t nblocks;
+    const int32_t* block_sect;
+    const int64_t* block_off;
+    double* data;
+    int64_t size;
+} tnh_tensor;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` using `stream` (a cudaStream_t,
+ * NULL for the legacy default stream). The library keeps the stream handle;
+ * the caller keeps ownership of the stream. */
+tnh_status tnh_create(tnh_ctx** ctx, int device, void* stream);
+void tnh_destroy(tnh_ctx* ctx);
+/* Text of the last error raised on `ctx` (or of the last context-free error
+ * when ctx is NULL). Valid until the next call on the same context. */
+const char* tnh_last_error(const tnh_ctx* ctx);
+/* Block until all work queued by the context has finished. */
+tnh_status tnh_sync(tnh_ctx* ctx);
+
+/* ---- layout helper (host only, no device work) ------------------------- */
+
+/* Enumerate the blocks of a tensor with the given indices and flux (Sec. 8.3:
+ * only blocks whose flux equals the tensor's flux are stored), in
+ * lexicographic order of the sector tuple, packed contiguously.
+ *   flux        host [nq] (ignored when nq == 0).
+ *   nblocks     out: number of allowed blocks.
+ *   block_sect  out host [*nblocks * rank] or NULL to only count.
+ *   block_off   out host [*nblocks] or NULL.
+ *   total       out: number of elements of the packed storage.
+ * Call once with NULL buffers to size them, then again to fill them. */
+tnh_status tnh_layout(int32_t rank, const tnh_index* inds, const int32_t* flux,
+                      int32_t* nblocks, int32_t* block_sect, int64_t* block_off,
+                      int64_t* total);
+
+/* ---- labelled contraction (Sec. 4, Sec. 9.1, Sec. 9.4) ------------------ */
+
+/* C = A * B. Indices of A and B with equal labels are summed; they must
+ * have the same sectors and opposite arrows (TNH_ERR_ARROW, Sec. 8.3). Every
+ * other label must appear exactly once in C (TNH_ERR_LABEL), in any order;
+ * C's blocks are given by the caller (tnh_layout) and every C block not
+ * reached by a block pair is set to zero. A block-sparse product is the set
+ * of dense block-pair products whose contracted sectors agree; pairs landing
+ * on the same C block are summed (Sec. 9.4). Asynchronous. */
+tnh_status tnh_contract(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
+                        tnh_tensor* C, tnh_precision prec);
+
+/* ---- effective Hamiltonian (Sec. 7.2) ---------------------------------- */
+
+/* Plan y = H_eff . psi with
+ *   y[a',s1',s2',b'] = sum L[a,w,a'] W1[w,w1,s1,s1'] W2[w1,w2,s2,s2']
+ *                          R[b,w2,b'] psi[a,s1,s2,b]
+ *   L   [a, w, a']        left environment  (a In, w Out, a' Out)
+ *   W1  [w, w1, s1, s1']  MPO tensor of site 1 (w In, w1 Out, s In, s' Out)
+ *   W2  [w1, w2, s2, s2'] MPO tensor of site 2
+ *   R   [b, w2, b']       right environment (b Out, w In, b' In)
+ *   psi [a, s1, s2, b]    layout of the two-site state (data ignored).
+ * Labels are taken from the position, not from the index labels. L, R and
+ * the W's are read during the call (the plan keeps packed copies; the
+ * caller may free them afterwards). Synchronises the context's stream. */
+tnh_status tnh_heff_plan(tnh_ctx* ctx, const tnh_tensor* L, const tnh_tensor* W1,
+                         const tnh_tensor* W2, const tnh_tensor* R,
+                         const tnh_tensor* psi, tnh_precision prec, tnh_heff** plan);
+/* y = H_eff . x; x and y are DEVICE float64 vectors in the psi layout of the
+ * plan (they must not alias). Asynchronous on the plan's context stream. */
+tnh_status tnh_heff_apply(tnh_heff* plan, const double* x, double* y);
+/* Same product in another precision than the plan's (FP64 is always
+ * available; a split mode is available when the plan was made with it). */
+tnh_status tnh_heff_apply_prec(tnh_heff* plan, tnh_precision prec,
+                               const double* x, double* y);
+/* Algorithmic flops of one product: 2 M N K summed over every block GEMM of
+ * the contraction chain (split-precision extra products not counted). */
+tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops);
+/* Number of float64 elements of the psi layout. */
+tnh_status tnh_heff_size(const tnh_heff* plan, int64_t* n);
+void tnh_heff_free(tnh_heff* plan);
+
+/* Lowest eigenpair of H_eff by Lanczos with full reorthogonalisation
+ * (Gram-Schmidt applied twice), starting from psi (DEVICE, overwritten by the
+ * normalised Ritz vector). Matvecs run in the plan's precision; the Krylov
+ * vectors, dot products, tridiagonal eigensolve and the final energy
+ * E = <psi|H psi> and residual |H psi - E psi| run in float64 on the device
+ * (the final product is an FP64 H_eff). Stops when the Ritz residual
+ * estimate falls below tol * max(1, |E|) or after krylov_dim matvecs.
+ * Synchronises the context's stream once per iteration. */
+tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol,
+                        double* energy, double* resid, int32_t* matvecs);
+
+/* ---- environment update ------------------------------------------------ */
+
+/* dir = +1: E_out[b,w',b'] = sum E[a,w,a'] A[a,s,b] W[w,w',s,s'] A[a',s',b']
+ * dir = -1: E_out[a,w,a'] = sum A[a,s,b] W[w,w',s,s'] A[a',s',b'] E[b,w',b']
+ * A [a, s, b] is an MPS tensor (a Out, s Out, b In); its bra copy has the
+ * arrows reversed (real data). E_out's blocks are given by the caller.
+ * Asynchronous. */
+tnh_status tnh_env_update(tnh_ctx* ctx, int32_t dir, const tnh_tensor* E,
+                          const tnh_tensor* A, const tnh_tensor* W,
+                          tnh_tensor* E_out, tnh_precision prec);
+
+/* ---- truncated SVD (Sec. 5) --------------------------------------------- */
+
+/* Factorise T with its first nrow indices as rows: blocks are grouped by
+ * their row charge (each group is one dense matrix, as a combiner groups
+ * equal-QN sectors, Sec. 4), every group is factorised by a float64
+ * one-sided Jacobi SVD on the device, the singular values of all groups are
+ * pooled and truncated: the squares are summed from the smallest upward while
+ * their share of the total stays <= cutoff, at most maxdim and at least
+ * max(mindim, 1) values are kept (Sec. 5). Ties are ordered by group, then
+ * position. Synchronises the stream (the kept count sizes the results). */
+tnh_status tnh_svd_trunc(tnh_ctx* ctx, const tnh_tensor* T, int32_t nrow, double cutoff,
+                         int32_t maxdim, int32_t mindim, tnh_svd** out);
+/* Shape of the result: the new link index has nsect sectors (charges in
+ * ascending order, qn [nsect * nq], sect_dim [nsect]); pass NULL arrays to
+ * only read nsect. truncerr is the discarded share of sum s^2. */
+tnh_status tnh_svd_info(const tnh_svd* svd, int32_t* nsect, int32_t* nq, int32_t* qn,
+                        int32_t* sect_dim, double* truncerr);
+/* Copy the factors: U [rows..., c] (c In) and V [c, cols...] (c Out) with
+ * caller-given layouts (DEVICE data), S DEVICE [sum of sect_dim] in sector
+ * order, descending inside a sector. T = U diag(S) V up to the truncation. */
+tnh_status tnh_svd_get(tnh_svd* svd, tnh_tensor* U, double* S, tnh_tensor* V);
+void tnh_svd_free(tnh_svd* svd);
+
+/* ---- two-site DMRG sweeps (Sec. 7.2) ------------------------------------ */
+
+typedef struct {
+    int32_t nsweep;
+    const int32_t* maxdim;   /* host [nsweep] */
+    const double* cutoff;    /* host [nsweep] */
+    int32_t mindim;
+    int32_t krylov_dim;      /* max Lanczos matvecs per bond */
+    double lanczos_tol;
+    int32_t precision;       /* tnh_precision of the Lanczos matvecs */
+    int32_t env_precision;   /* tnh_precision of theta and the environments */
+} tnh_sweep_params;
+
+typedef struct {
+    int32_t sweep;
+    double energy;           /* eigenvalue at the last bond of the sweep */
+    double resid;            /* its FP64 residual */
+    double truncerr;         /* largest truncation error of the sweep */
+    int32_t maxlink;         /* largest MPS link dimension after the sweep */
+    int64_t matvecs;
+    double seconds;
+} tnh_sweep_stat;
+
+/* Run the sweeps on the MPS (right-orthogonal from site 1 on; a normalised
+ * product state is) with MPO tensors W[j] [wl, wr, s, s'] (same arrows as
+ * above). start/done are the MPO link states selected by the left and right
+ * boundaries. A sweep is a left-to-right pass over the bonds followed by a
+ * right-to-left pass; energy is the eigenvalue at the last bond. The final
+ * MPS stays on the device inside the context (tnh_dmrg_mps_*). Synchronous. */
+tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, int64_t start,
+                    int64_t done, const tnh_tensor* mps, const tnh_sweep_params* p,
+                    double* energy, tnh_sweep_stat* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNH_H */

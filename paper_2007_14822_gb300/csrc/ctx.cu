@@ -1,0 +1,258 @@
+// Context, error handling, index/tensor parsing and the layout helper.
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "tnh_internal.h"
+#include "tnh_guard.h"
+
+namespace tnh {
+
+std::string strf(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return buf;
+}
+
+thread_local std::string g_last_error;
+
+void set_error(Ctx* ctx, const std::string& m) {
+    if (ctx) ctx->err = m;
+    g_last_error = m;
+}
+
+void DevBuf::alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        TNH_FAIL(e == cudaErrorMemoryAllocation ? TNH_ERR_OOM : TNH_ERR_CUDA,
+                 "cudaMalloc(%zu): %s", n, cudaGetErrorString(e));
+    }
+    bytes = n;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+void Workspace::ensure(DevBuf& buf, size_t bytes) {
+    if (buf.bytes < bytes) buf.alloc(bytes);
+}
+
+int planes_of(tnh_precision p) {
+    switch (p) {
+        case TNH_BF16x6: return 3;
+        case TNH_BF16x3: return 2;
+        case TNH_BF16: return 1;
+        default: return 0;
+    }
+}
+
+void Index::finish() {
+    off.assign(nsect, 0);
+    total = 0;
+    for (int s = 0; s < nsect; ++s) { off[s] = total; total += dim[s]; }
+}
+
+Index parse_index(const tnh_index& in, const char* what) {
+    TNH_REQUIRE(in.nsect >= 1, TNH_ERR_ARG, "%s: index with nsect=%d", what, in.nsect);
+    TNH_REQUIRE(in.nq >= 0 && in.nq <= 4, TNH_ERR_ARG, "%s: nq=%d out of 0..4", what, in.nq);
+    TNH_REQUIRE(in.sect_dim != nullptr, TNH_ERR_ARG, "%s: sect_dim is NULL", what);
+    TNH_REQUIRE(in.nq == 0 || in.qn != nullptr, TNH_ERR_ARG, "%s: qn is NULL", what);
+    TNH_REQUIRE(in.arrow == 1 || in.arrow == -1, TNH_ERR_ARG, "%s: arrow must be +1/-1", what);
+    Index r;
+    r.label = in.label;
+    r.nsect = in.nsect;
+    r.nq = in.nq;
+    r.arrow = in.arrow;
+    r.dim.assign(in.sect_dim, in.sect_dim + in.nsect);
+    if (in.nq) r.qn.assign(in.qn, in.qn + (size_t)in.nsect * in.nq);
+    for (int d : r.dim) TNH_REQUIRE(d >= 1, TNH_ERR_SHAPE, "%s: sector dim %d < 1", what, d);
+    r.finish();
+    return r;
+}
+
+std::vector<int> block_flux(const std::vector<Index>& inds, const int* key, int nq) {
+    std::vector<int> f(nq, 0);
+    for (size_t i = 0; i < inds.size(); ++i)
+        for (int k = 0; k < nq; ++k) f[k] += inds[i].arrow * inds[i].q(key[i], k);
+    return f;
+}
+
+int64_t Layout::packed_total() const {
+    int64_t t = 0;
+    for (int b = 0; b < nblocks(); ++b) t += belems(b);
+    return t;
+}
+
+void Layout::build_lookup() {
+    lookup.clear();
+    for (int b = 0; b < nblocks(); ++b) lookup[key(b)] = b;
+}
+
+Layout parse_tensor(const tnh_tensor* t, const char* what, bool need_data) {
+    TNH_REQUIRE(t != nullptr, TNH_ERR_ARG, "%s: tensor is NULL", what);
+    TNH_REQUIRE(t->rank >= 0 && t->rank <= kMaxDims, TNH_ERR_ARG, "%s: rank %d", what, t->rank);
+    TNH_REQUIRE(t->rank == 0 || t->inds != nullptr, TNH_ERR_ARG, "%s: inds NULL", what);
+    TNH_REQUIRE(t->nblocks >= 0, TNH_ERR_ARG, "%s: nblocks %d", what, t->nblocks);
+    Layout L;
+    for (int i = 0; i < t->rank; ++i) L.inds.push_back(parse_index(t->inds[i], what));
+    int nq = L.inds.empty() ? 0 : L.inds[0].nq;
+    for (auto& ix : L.inds)
+        TNH_REQUIRE(ix.nq == nq, TNH_ERR_ARG, "%s: indices disagree on nq", what);
+    if (t->nblocks) {
+        TNH_REQUIRE(t->rank == 0 || t->block_sect, TNH_ERR_ARG, "%s: block_sect NULL", what);
+        TNH_REQUIRE(t->block_off, TNH_ERR_ARG, "%s: block_off NULL", what);
+    }
+    L.sect.assign(t->block_sect, t->block_sect + (size_t)t->nblocks * t->rank);
+    L.off.assign(t->block_off, t->block_off + t->nblocks);
+    L.data = t->data;
+    L.size = t->size;
+    if (need_data) TNH_REQUIRE(L.data != nullptr || t->nblocks == 0, TNH_ERR_ARG, "%s: data NULL", what);
+    L.flux.assign(nq, 0);
+    for (int b = 0; b < t->nblocks; ++b) {
+        for (int i = 0; i < t->rank; ++i) {
+            int s = L.sect[(size_t)b * t->rank + i];
+            TNH_REQUIRE(s >= 0 && s < L.inds[i].nsect, TNH_ERR_SHAPE,
+                        "%s: block %d sector %d of index %d out of range", what, b, s, i);
+        }
+        auto f = block_flux(L.inds, &L.sect[(size_t)b * t->rank], nq);
+        if (b == 0) L.flux = f;
+        TNH_REQUIRE(f == L.flux, TNH_ERR_FLUX, "%s: block %d has a different flux", what, b);
+        TNH_REQUIRE(L.off[b] >= 0 && L.off[b] + L.belems(b) <= t->size, TNH_ERR_SHAPE,
+                    "%s: block %d [%lld, +%lld) outside size %lld", what, b,
+                    (long long)L.off[b], (long long)L.belems(b), (long long)t->size);
+    }
+    L.build_lookup();
+    TNH_REQUIRE((int)L.lookup.size() == t->nblocks, TNH_ERR_SHAPE, "%s: repeated block", what);
+    return L;
+}
+
+Layout make_layout(const std::vector<Index>& inds, const std::vector<int>& flux) {
+    Layout L;
+    L.inds = inds;
+    L.flux = flux;
+    int r = (int)inds.size();
+    int nq = (int)flux.size();
+    std::vector<int> key(r, 0);
+    int64_t off = 0;
+    // odometer over all sector tuples, lexicographic (last index fastest)
+    while (true) {
+        if (block_flux(inds, key.data(), nq) == flux) {
+            L.sect.insert(L.sect.end(), key.begin(), key.end());
+            L.off.push_back(off);
+            int64_t n = 1;
+            for (int i = 0; i < r; ++i) n *= inds[i].dim[key[i]];
+            off += n;
+        }
+        int i = r - 1;
+        while (i >= 0 && ++key[i] == inds[i].nsect) { key[i] = 0; --i; }
+        if (i < 0) break;
+    }
+    L.size = off;
+    L.build_lookup();
+    return L;
+}
+
+void make_chunks(const std::vector<Piece>& pieces, std::vector<Chunk>& chunks, int per_chunk) {
+    chunks.clear();
+    for (int p = 0; p < (int)pieces.size(); ++p) {
+        int64_t n = (int64_t)pieces[p].rows * pieces[p].cols;
+        for (int64_t s = 0; s < n; s += per_chunk)
+            chunks.push_back(Chunk{p, (int)s, (int)std::min<int64_t>(per_chunk, n - s)});
+    }
+}
+
+void check_device_flag(Ctx* ctx) {
+    int h[4] = {0, 0, 0, 0};
+    CUDA_CHECK(cudaMemcpyAsync(h, ctx->d_flag.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (h[0]) {
+        CUDA_CHECK(cudaMemsetAsync(ctx->d_flag.p, 0, sizeof h, ctx->stream));
+        TNH_FAIL(TNH_ERR_TIMEOUT, "device wait gave up (code %d, site %d, block %d)", h[0], h[1], h[2]);
+    }
+}
+
+}  // namespace tnh
+
+using namespace tnh;
+
+extern "C" {
+
+tnh_status tnh_create(tnh_ctx** out, int device, void* stream) {
+    return guard(nullptr, [&] {
+        TNH_REQUIRE(out != nullptr, TNH_ERR_ARG, "tnh_create: out is NULL");
+        int n = 0;
+        CUDA_CHECK(cudaGetDeviceCount(&n));
+        TNH_REQUIRE(device >= 0 && device < n, TNH_ERR_ARG, "tnh_create: device %d of %d", device, n);
+        CUDA_CHECK(cudaSetDevice(device));
+        int major = 0, minor = 0;
+        CUDA_CHECK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
+        CUDA_CHECK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device));
+        TNH_REQUIRE(major == 10 && minor == 3, TNH_ERR_CUDA,
+                    "tnh_create: device %d is sm_%d%d; this library is built for sm_103a only",
+                    device, major, minor);
+        auto* c = new Ctx();
+        c->device = device;
+        c->stream = (cudaStream_t)stream;
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+        try {
+            c->d_flag.alloc(16);
+            CUDA_CHECK(cudaMemsetAsync(c->d_flag.p, 0, 16, c->stream));
+        } catch (...) {
+            delete c;
+            throw;
+        }
+        *out = reinterpret_cast<tnh_ctx*>(c);
+    });
+}
+
+void tnh_destroy(tnh_ctx* ctx) {
+    if (!ctx) return;
+    auto* c = reinterpret_cast<Ctx*>(ctx);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+const char* tnh_last_error(const tnh_ctx* ctx) {
+    if (ctx) return reinterpret_cast<const Ctx*>(ctx)->err.c_str();
+    return g_last_error.c_str();
+}
+
+tnh_status tnh_sync(tnh_ctx* ctx) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c, TNH_ERR_ARG, "tnh_sync: ctx NULL");
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        check_device_flag(c);
+    });
+}
+
+tnh_status tnh_layout(int32_t rank, const tnh_index* inds, const int32_t* flux, int32_t* nblocks,
+                      int32_t* block_sect, int64_t* block_off, int64_t* total) {
+    return guard(nullptr, [&] {
+        TNH_REQUIRE(rank >= 0 && rank <= kMaxDims, TNH_ERR_ARG, "tnh_layout: rank %d", rank);
+        TNH_REQUIRE(nblocks && total, TNH_ERR_ARG, "tnh_layout: NULL output");
+        std::vector<Index> ix;
+        for (int i = 0; i < rank; ++i) ix.push_back(parse_index(inds[i], "tnh_layout"));
+        int nq = ix.empty() ? 0 : ix[0].nq;
+        std::vector<int> f(nq, 0);
+        for (int k = 0; k < nq; ++k) f[k] = flux ? flux[k] : 0;
+        Layout L = make_layout(ix, f);
+        *nblocks = L.nblocks();
+        *total = L.size;
+        if (block_sect) std::copy(L.sect.begin(), L.sect.end(), block_sect);
+        if (block_off) std::copy(L.off.begin(), L.off.end(), block_off);
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// Grouped split-bfloat16 GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// C_t[M][ldc] (float64) = sum over products (p, q) of A_t^(p) * B_t^(q)^T,
+// where A^(0..P-1) / B^(0..P-1) are the bfloat16 parts of the float64
+// operands (x = hi + mid + lo). P = 3 keeps the six products
+// hh, hm, mh, hl, lh, mm; P = 2 keeps hh, hm, mh; P = 1 keeps hh.
+//
+// Persistent warp-specialised kernel, one CTA per SM, 128 x 128 output tiles:
+//   warp 0      producer: bulk-copies the P A-tiles and P B-tiles of one
+//               64-wide K block into a shared-memory stage (TMA engine,
+//               mbarrier complete_tx); operands arrive pre-tiled and
+//               pre-swizzled from the packer, one 16 KB copy per tile.
+//   warp 1      MMA issuer: one thread issues tcgen05.mma (M=128, N=128,
+//               K=16) into tensor memory; hh goes to its own accumulator,
+//               the cross products to a second one, so the large partial
+//               sums are not rounded once per small cross term.
+//   warps 2..9  epilogue (two warps per TMEM lane quarter, 64 columns each). The tensor core accumulates one K chunk (128
+//               for the three-part split) at a time; the epilogue adds every
+//               chunk's two accumulators into float32 registers (round to
+//               nearest) and stores float64 at the end of the tile. The
+//               tensor-core accumulation error grows linearly with the
+//               number of MMAs accumulated, so short chunks bound it.
+//               Two accumulator pairs (512 TMEM columns) let the epilogue of
+//               one chunk overlap the MMAs of the next.
+// Every wait is bounded (ptx::mbar_wait); a timeout sets the device error flag.
+#include <cuda_bf16.h>
+
+#include "ptx.cuh"
+#include "tnh_internal.h"
+
+namespace tnh {
+
+namespace {
+
+constexpr int kTileBytes = kTcTileM * kTcTileK * 2;   // 16384, A and B tiles alike
+constexpr int kThreads = 320;   // producer, MMA, 8 epilogue warps
+constexpr int kEpiWarps = 8;
+
+template <int P>
+struct TcCfg {
+    static constexpr int kStages = P == 3 ? 2 : (P == 2 ? 3 : 6);
+    static constexpr int kNumProd = P == 3 ? 6 : (P == 2 ? 3 : 1);
+    static constexpr int kStageBytes = 2 * P * kTileBytes;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+    // k-blocks (of 64) accumulated on the tensor core before the epilogue
+    // folds the partial sum into registers
+    static constexpr int kChunk = P == 3 ? 2 : (P == 2 ? 4 : 8);
+};
+
+// products (a-part, b-part); the first one is hh
+__constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
+__constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
+
+__device__ __forceinline__ int find_task(const GemmTask* __restrict__ tasks, int ntasks, int tile) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_kernel(const GemmTask* __restrict__ tasks, int ntasks, int total_tiles,
+                   const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, double* __restrict__ C,
+                   int* err) {
+    using Cfg = TcCfg<P>;
+    constexpr int S = Cfg::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;                               // [S][P] tiles
+    uint8_t* sB = smem + S * P * kTileBytes;          // [S][P] tiles
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + S * P * kTileBytes);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* fin = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&tfull[b], 1);
+            ptx::mbar_init(&tempty[b], kEpiWarps);
+        }
+        ptx::mbar_init(fin, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(tmem_slot, 512);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+                const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+                const int local = tile - t.tile0;
+                const int mi = local / t.nt, ni = local - mi * t.nt;
+                const uint16_t* a = A + (t.a_base + (int64_t)mi * t.kt) * P * kTcTileElems;
+                const uint16_t* b = B + (t.b_base + (int64_t)ni * t.kt) * P * kTcTileElems;
+                for (int kb = 0; kb < t.kt; ++kb) {
+                    if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, err, 1)) { ok = false; break; }
+                    ptx::mbar_expect_tx(&full[stage], 2 * P * kTileBytes);
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        ptx::bulk_g2s(sA + (stage * P + p) * kTileBytes,
+                                      a + ((int64_t)kb * P + p) * kTcTileElems, kTileBytes, &full[stage]);
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        ptx::bulk_g2s(sB + (stage * P + p) * kTileBytes,
+                                      b + ((int64_t)kb * P + p) * kTcTileElems, kTileBytes, &full[stage]);
+                    if (++stage == S) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (!ok) __nanosleep(20000);   // let copies already in flight land
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            constexpr uint32_t idesc = ptx::idesc_bf16_f32(kTcTileM, kTcTileN);
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int it = 0;
+            for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+                const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+                for (int k0 = 0; ok && k0 < t.kt; k0 += Cfg::kChunk, ++it) {
+                    const int k1 = min(t.kt, k0 + Cfg::kChunk);
+                    const int buf = it & 1;
+                    const uint32_t tph = (uint32_t)(it >> 1) & 1u;
+                    if (!ptx::mbar_wait(&tempty[buf], tph ^ 1u, err, 2)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t d_hh = tmem + buf * 256, d_x = tmem + buf * 256 + 128;
+                    for (int kb = k0; kb < k1; ++kb) {
+                        if (!ptx::mbar_wait(&full[stage], phase, err, 3)) { ok = false; break; }
+                        ptx::tc_fence_after();
+                        const uint32_t a0 = ptx::smem_u32(sA + stage * P * kTileBytes);
+                        const uint32_t b0 = ptx::smem_u32(sB + stage * P * kTileBytes);
+#pragma unroll
+                        for (int kk = 0; kk < kTcTileK / 16; ++kk) {
+#pragma unroll
+                            for (int j = 0; j < Cfg::kNumProd; ++j) {
+                                const uint64_t ad =
+                                    ptx::sw128_kmajor_desc(a0 + kProdA[j] * kTileBytes + kk * 32);
+                                const uint64_t bd =
+                                    ptx::sw128_kmajor_desc(b0 + kProdB[j] * kTileBytes + kk * 32);
+                                const bool first = (kb == k0 && kk == 0);
+                                const uint32_t acc = j == 0 ? !first : (!first || j > 1);
+                                ptx::mma_bf16(j == 0 ? d_hh : d_x, ad, bd, idesc, acc);
+                            }
+                        }
+                        ptx::mma_commit(&empty[stage]);
+                        if (++stage == S) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    ptx::mma_commit(&tfull[buf]);
+                }
+            }
+            // every MMA issued above completes before the tensor memory is freed
+            ptx::mma_commit(fin);
+            ptx::mbar_wait(fin, 0, err, 4, /*watch_flag=*/false);
+        }
+    } else {
+        // ---------------- epilogue: warp w owns TMEM lane quarter (w % 4) and
+        // the column half (w - 2) / 4 of the tile
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        constexpr int kCols = kTcTileN / 2;
+        int it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+            const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+            const int local = tile - t.tile0;
+            const int mi = local / t.nt, ni = local - mi * t.nt;
+            float acc[kCols];
+#pragma unroll
+            for (int j = 0; j < kCols; ++j) acc[j] = 0.0f;
+            for (int k0 = 0; k0 < t.kt; k0 += Cfg::kChunk, ++it) {
+                const int buf = it & 1;
+                const uint32_t tph = (uint32_t)(it >> 1) & 1u;
+                if (!ptx::mbar_wait(&tfull[buf], tph, err, 5)) { ok = false; break; }
+                ptx::tc_fence_after();
+                const uint32_t row_addr = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + half * kCols;
+#pragma unroll
+                for (int c0 = 0; c0 < kCols; c0 += 32) {
+                    uint32_t rh[32], rx[32];
+                    ptx::tmem_ld32(row_addr + c0, rh);
+                    if (P > 1) ptx::tmem_ld32(row_addr + 128 + c0, rx);
+                    ptx::tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float v = __uint_as_float(rh[j]);
+                        if (P > 1) v += __uint_as_float(rx[j]);
+                        acc[c0 + j] += v;
+                    }
+                }
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&tempty[buf]);
+            }
+            if (!ok) break;
+            const int m = mi * kTcTileM + q * 32 + lane;
+            if (m < t.M) {
+                double* crow = C + t.c_base + (int64_t)m * t.ldc;
+                const int n0 = ni * kTcTileN + half * kCols;
+#pragma unroll
+                for (int j = 0; j < kCols; ++j)
+                    if (n0 + j < t.N) crow[n0 + j] = (double)acc[j];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+template <int P>
+void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A, const uint16_t* B,
+              double* C, int num_sms, int* err, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        CUDA_CHECK(cudaFuncSetAttribute(gemm_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        TcCfg<P>::kSmem));
+        configured = true;
+    }
+    int grid = std::min(total_tiles, num_sms > 0 ? num_sms : 148);
+    gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err);
+}
+
+}  // namespace
+
+void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A, const uint16_t* B,
+                    double* C, int planes, int num_sms, int* err, cudaStream_t s) {
+    if (total_tiles == 0) return;
+    if (planes == 3)
+        launch_p<3>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s);
+    else if (planes == 2)
+        launch_p<2>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s);
+    else
+        launch_p<1>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s);
+}
+
+}  // namespace tnh

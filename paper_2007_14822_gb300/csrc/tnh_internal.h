@@ -1,0 +1,222 @@
+// Internal declarations shared by the translation units of libtnh.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tnh.h"
+
+namespace tnh {
+
+// ------------------------------------------------------------------ errors
+struct Error : public std::exception {
+    tnh_status code;
+    std::string msg;
+    Error(tnh_status c, std::string m) : code(c), msg(std::move(m)) {}
+    const char* what() const noexcept override { return msg.c_str(); }
+};
+
+std::string strf(const char* fmt, ...);
+
+#define TNH_FAIL(code, ...) throw ::tnh::Error((code), ::tnh::strf(__VA_ARGS__))
+#define TNH_REQUIRE(cond, code, ...) \
+    do { if (!(cond)) TNH_FAIL(code, __VA_ARGS__); } while (0)
+#define CUDA_CHECK(x)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (x);                                                      \
+        if (e_ != cudaSuccess)                                                     \
+            TNH_FAIL(e_ == cudaErrorMemoryAllocation ? TNH_ERR_OOM : TNH_ERR_CUDA, \
+                     "%s: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------- device memory
+// Owning device buffer (cudaMalloc / cudaFree; freed on destruction).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t n) { alloc(n); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t n);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
+    DevBuf b(std::max<size_t>(v.size() * sizeof(T), 16));
+    if (!v.empty())
+        CUDA_CHECK(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T),
+                                   cudaMemcpyHostToDevice, s));
+    return b;
+}
+
+// ------------------------------------------------------------- structures
+struct Index {
+    int64_t label = 0;
+    int nsect = 0, nq = 0, arrow = 1;
+    std::vector<int> qn;    // nsect * nq
+    std::vector<int> dim;   // nsect
+    std::vector<int64_t> off;
+    int64_t total = 0;
+    void finish();
+    int q(int s, int k) const { return qn[(size_t)s * nq + k]; }
+    bool same_space(const Index& o) const { return nq == o.nq && qn == o.qn && dim == o.dim; }
+    Index dag() const { Index r = *this; r.arrow = -arrow; return r; }
+    Index relabel(int64_t l) const { Index r = *this; r.label = l; return r; }
+};
+
+// Host view of a block-sparse tensor: indices + block table + device data.
+struct Layout {
+    std::vector<Index> inds;
+    std::vector<int> sect;      // nblocks * rank
+    std::vector<int64_t> off;   // nblocks
+    std::vector<int> flux;      // nq
+    double* data = nullptr;
+    int64_t size = 0;
+    std::map<std::vector<int>, int> lookup;
+    int rank() const { return (int)inds.size(); }
+    int nblocks() const { return (int)off.size(); }
+    int nq() const { return inds.empty() ? (int)flux.size() : inds[0].nq; }
+    std::vector<int> key(int b) const {
+        return std::vector<int>(sect.begin() + (size_t)b * rank(), sect.begin() + (size_t)(b + 1) * rank());
+    }
+    int bdim(int b, int i) const { return inds[i].dim[sect[(size_t)b * rank() + i]]; }
+    int64_t belems(int b) const {
+        int64_t n = 1;
+        for (int i = 0; i < rank(); ++i) n *= bdim(b, i);
+        return n;
+    }
+    int64_t packed_total() const;
+    void build_lookup();
+    int find(const std::vector<int>& k) const {
+        auto it = lookup.find(k);
+        return it == lookup.end() ? -1 : it->second;
+    }
+};
+
+Index parse_index(const tnh_index& in, const char* what);
+Layout parse_tensor(const tnh_tensor* t, const char* what, bool need_data = true);
+// Allowed blocks of the given indices at the given flux, lexicographic, packed.
+Layout make_layout(const std::vector<Index>& inds, const std::vector<int>& flux);
+std::vector<int> block_flux(const std::vector<Index>& inds, const int* key, int nq);
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    DevBuf d_flag;    // int[4]: [0] device error code written by bounded waits
+};
+
+// Check the device error flag (synchronises); throws TNH_ERR_TIMEOUT if set.
+void check_device_flag(Ctx* ctx);
+
+// -------------------------------------------------------- pack / unpack
+// A piece copies a strided sub-tensor (row dims then col dims) into a 2-D
+// region of a task matrix, or back.
+constexpr int kMaxDims = 8;
+struct Piece {
+    int64_t src_off;          // element offset in the strided tensor
+    int64_t strides[kMaxDims];
+    int dims[kMaxDims];
+    int nr, nc;               // number of row / col dims
+    int rows, cols;           // products of the dims
+    int task;                 // task whose matrix receives / provides it
+    int row0, col0;           // position inside that task matrix
+};
+struct Chunk {
+    int piece;
+    int start;                // first element (row-major over rows x cols)
+    int count;
+};
+void make_chunks(const std::vector<Piece>& pieces, std::vector<Chunk>& chunks, int per_chunk = 4096);
+
+// Operand formats
+enum class Fmt { F64, BF16T };  // plain float64 [rows][ld] / bf16 split tiles
+
+// Task geometry of one packed operand (per task).
+struct OpGeom {
+    int64_t base;   // F64: element offset; BF16T: tile offset
+    int ld;         // F64: row pitch (padded K); BF16T: tiles along K
+};
+
+void launch_pack_f64(const Piece* d_pieces, const Chunk* d_chunks, int nchunks,
+                     const OpGeom* d_geom, const double* src, double* dst, cudaStream_t s);
+void launch_pack_bf16(const Piece* d_pieces, const Chunk* d_chunks, int nchunks,
+                      const OpGeom* d_geom, const double* src, uint16_t* dst, int planes,
+                      cudaStream_t s);
+// Ct region of task -> strided destination (overwrite).
+void launch_unpack(const Piece* d_pieces, const Chunk* d_chunks, int nchunks,
+                   const int64_t* d_cbase, const int* d_ldc, const double* Ct, double* dst,
+                   cudaStream_t s);
+
+// ---------------------------------------------------------------- GEMMs
+// C_t[M][ldc] = A_t[M][K] * B_t[N][K]^T for every task t (both K-major).
+struct GemmTask {
+    int M, N, K;
+    int mt, nt, kt;          // tiles along M, N, K for the launch's tile shape
+    int64_t a_base, b_base;  // F64: element offsets; BF16T: tile offsets
+    int lda, ldb;            // F64 only: padded K pitch
+    int64_t c_base;
+    int ldc;
+    int tile0;               // prefix sum of mt * nt
+};
+void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, int total_tiles, const double* A,
+                     const double* B, double* C, cudaStream_t s);
+// tcgen05 split-bf16 GEMM; planes in {1,2,3}; err is a device int flag.
+void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A,
+                    const uint16_t* B, double* C, int planes, int num_sms, int* err,
+                    cudaStream_t s);
+constexpr int kF64TileM = 64, kF64TileN = 64, kF64TileK = 16;
+constexpr int kTcTileM = 128, kTcTileN = 128, kTcTileK = 64;
+constexpr int kTcTileElems = kTcTileM * kTcTileK;   // 8192 bf16 per plane tile
+
+int planes_of(tnh_precision p);
+
+// ------------------------------------------------------ contraction plan
+struct ContractPlan {
+    // host
+    std::vector<GemmTask> tasks_f64, tasks_tc;
+    std::vector<Piece> packA, packB, unpackC;
+    std::vector<int64_t> cbase;
+    std::vector<int> ldc;
+    int ntiles_f64 = 0, ntiles_tc = 0;
+    int64_t a_elems_f64 = 0, b_elems_f64 = 0, a_tiles = 0, b_tiles = 0, c_elems = 0;
+    int64_t c_total = 0;  // elements of the output tensor
+    double flops = 0.0;
+    // device
+    DevBuf d_packA, d_packB, d_unpack, d_chA, d_chB, d_chC;
+    int nchA = 0, nchB = 0, nchC = 0;
+    DevBuf d_geomA_f64, d_geomB_f64, d_geomA_tc, d_geomB_tc;
+    DevBuf d_tasks_f64, d_tasks_tc, d_cbase, d_ldc;
+};
+
+// Label-matched plan for C = A * B (validates labels and arrows).
+std::unique_ptr<ContractPlan> plan_contract(const Layout& A, const Layout& B, const Layout& C,
+                                            cudaStream_t s);
+// Workspace big enough for one execution of the plan in a precision.
+struct Workspace {
+    DevBuf a, b, c;
+    void ensure(DevBuf& buf, size_t bytes);
+};
+// Execute: C.data = A.data * B.data (pack, GEMM, unpack).
+void run_contract(Ctx* ctx, const ContractPlan& P, const double* A, const double* B, double* C,
+                  tnh_precision prec, Workspace& ws);
+
+}  // namespace tnh

@@ -1,0 +1,69 @@
+"""The C-ABI library: it builds, loads without a GPU, exports every symbol the
+header declares, and its host-only layout helper agrees with the oracle."""
+import re
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_14822_gb300 import build, tnh
+    build.build()
+    return tnh.lib()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "tnh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tnh_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_match_header(lib):
+    from paper_2007_14822_gb300 import tnh
+    out = subprocess.run(["nm", "-D", "--defined-only", tnh.LIB_PATH], capture_output=True, text=True).stdout
+    exported = sorted(set(re.findall(r" T (tnh_[a-z_0-9]+)$", out, flags=re.M)))
+    declared = header_functions()
+    assert declared == exported
+    assert sorted(tnh.SYMBOLS) == declared
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_layout_matches_oracle(lib):
+    from oracle.blocksparse import QNIndex, allowed_blocks
+    from paper_2007_14822_gb300 import tnh
+    rng = np.random.default_rng(3)
+    for trial in range(5):
+        inds = []
+        for r in range(4):
+            ns = int(rng.integers(1, 5))
+            inds.append(tnh.Index([((int(q), int(q) % 3), int(rng.integers(1, 4))) for q in range(-ns // 2, ns - ns // 2)],
+                                  +1 if rng.random() < 0.5 else -1))
+        flux = (int(rng.integers(-1, 2)), int(rng.integers(0, 2)))
+        blocks, offs, total = tnh.layout(inds, flux)
+        want = allowed_blocks([QNIndex(i.sectors, i.arrow) for i in inds], flux)
+        assert blocks == want
+        sizes = [int(np.prod([inds[i].sectors[s][1] for i, s in enumerate(b)])) for b in blocks]
+        assert offs == list(np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)) if blocks else offs == []
+        assert total == sum(sizes)
+
+
+def test_layout_paper_block_sparse_example(lib):
+    # Sec. 9.2 example: blockdims ([2,2],[2,3]), nonzero blocks (1,2),(2,1)
+    from paper_2007_14822_gb300 import tnh
+    i1 = tnh.Index([((0,), 2), ((1,), 2)])
+    i2 = tnh.Index([((0,), 2), ((1,), 3)])
+    blocks, offs, total = tnh.layout([i1, i2], (1,))
+    assert [tuple(k + 1 for k in b) for b in blocks] == [(1, 2), (2, 1)]
+    assert total == 10
+
+
+def test_layout_rejects_bad_index(lib):
+    from paper_2007_14822_gb300 import tnh
+    with pytest.raises(tnh.TnhError):
+        tnh.layout([tnh.Index([((0,), 0)])], (0,))

@@ -1,0 +1,169 @@
+"""GPU parity of the labelled contraction, H_eff, the environment update and the
+eigensolver against the FP64 oracle (calls go through the C ABI)."""
+import numpy as np
+import pytest
+
+import helpers as H
+from oracle import dmrg as D
+from oracle.blocksparse import BlockTensor, contract as ocontract
+
+pytestmark = pytest.mark.gpu
+
+# tolerances (relative, norm-wise over the whole output)
+TOL = {"fp64": 1e-12, "bf16x6": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2007_14822_gb300 import build, tnh
+    assert torch.cuda.is_available()
+    build.build()
+    c = tnh.Context(0)
+    yield c
+    c.close()
+
+
+def prec(name):
+    from paper_2007_14822_gb300 import tnh
+    return tnh.PRECISION[name]
+
+
+# ------------------------------------------------------------ contraction
+def _qn_index(rng, ns, arrow, label, maxd=4):
+    from paper_2007_14822_gb300.tnh import Index
+    return Index([((q,), int(rng.integers(1, maxd + 1))) for q in range(-(ns // 2), ns - ns // 2)],
+                 arrow, label)
+
+
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_contract_block_sparse(ctx, p):
+    from paper_2007_14822_gb300.tnh import Tensor
+    rng = np.random.default_rng(5)
+    for trial in range(4):
+        i = _qn_index(rng, 3, +1, 1)
+        j = _qn_index(rng, 4, +1, 2)
+        k = _qn_index(rng, 3, +1, 3)
+        l = _qn_index(rng, 2, +1, 4)
+        A, Ao = H.random_pair([i, j, k], (0,), 10 + trial, "A")
+        B, Bo = H.random_pair([k.dag(), l, j.dag()], (1,), 10 + trial, "B")
+        # output in a permuted order: (l, i)
+        Cd = Tensor([l, i], (1,))
+        ctx.contract(A, B, Cd, prec(p))
+        want = ocontract(Ao.relabel([1, 2, 3]), Bo.relabel([3, 4, 2]), out_labels=[4, 1])
+        got = H.to_oracle(Cd)
+        assert H.rel_err(got, want) < TOL[p] * 10
+
+
+def test_contract_outer_and_full(ctx):
+    from paper_2007_14822_gb300.tnh import Index, Tensor
+    a = Index.dense(5, +1, 1)
+    b = Index.dense(7, +1, 2)
+    A, Ao = H.random_pair([a], (0,), 1, "a")
+    B, Bo = H.random_pair([b], (0,), 1, "b")
+    C = Tensor([b, a], (0,))
+    ctx.contract(A, B, C)
+    np.testing.assert_allclose(C.data.cpu().numpy().reshape(7, 5),
+                               np.outer(Bo.to_dense(), Ao.to_dense()), rtol=1e-14)
+    B2, B2o = H.random_pair([a.dag()], (0,), 2, "c")
+    S = Tensor([], (0,))
+    ctx.contract(A, B2, S)
+    assert abs(S.data.cpu().item() - float(Ao.to_dense() @ B2o.to_dense())) < 1e-13
+
+
+def test_contract_rejects_equal_arrows(ctx):
+    from paper_2007_14822_gb300.tnh import Index, Tensor, TnhError
+    a = Index([((0,), 2), ((1,), 3)], +1, 1)
+    A, _ = H.random_pair([a], (0,), 1, "x")
+    B, _ = H.random_pair([a], (0,), 2, "y")
+    with pytest.raises(TnhError) as e:
+        ctx.contract(A, B, Tensor([], (0,)))
+    assert e.value.code == 3
+
+
+# ------------------------------------------------------------------ H_eff
+def _heff_case(ctx, m, nsect, p, seed=7, maxd=None):
+    d = H.heff_inputs(m, None, seed, nsect=nsect, maxd=maxd)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    import torch
+    y = torch.zeros_like(d["psi"].data)
+    plan.apply(d["psi"].data, y)
+    ytens = d["psi"].with_inds(d["psi"].inds)
+    ytens.data = y
+    got = H.to_oracle(ytens)
+    want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    return H.rel_err(got, want), plan
+
+
+@pytest.mark.parametrize("m", [1, 3, 24, 130])
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_heff_dense(ctx, m, p):
+    err, plan = _heff_case(ctx, m, 1, p)
+    assert err < TOL[p], err
+    # algorithmic flops: S1+S4 = 4 w d^2 m^3, S2+S3 = 4 w^2 d^3 m^2 (MPO counted dense)
+    w, dd = 5, 2
+    assert plan.flops == pytest.approx(4 * w * dd * dd * m ** 3 + 4 * w * w * dd ** 3 * m * m)
+
+
+@pytest.mark.parametrize("m,nsect,maxd", [(12, 5, 4), (64, 9, 16), (300, 15, 60)])
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_heff_qn(ctx, m, nsect, maxd, p):
+    err, _ = _heff_case(ctx, m, nsect, p, maxd=maxd)
+    assert err < TOL[p], err
+
+
+def test_heff_config2_full_size(ctx):
+    # dense m=256, w=5, d=2: L/R (256,5,256), psi (256,2,2,256), Gaussian, seeded
+    for p in ("fp64", "bf16x6"):
+        err, _ = _heff_case(ctx, 256, 1, p, seed=2)
+        assert err < TOL[p], (p, err)
+
+
+@pytest.mark.parametrize("p,tol", [("bf16x3", 1e-3), ("bf16", 2e-2)])
+def test_heff_low_precision_modes_error_bounded(ctx, p, tol):
+    err, _ = _heff_case(ctx, 64, 1, p)
+    assert err < tol, err
+
+
+# ------------------------------------------------------------ environments
+@pytest.mark.parametrize("direction", [1, -1])
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("nsect", [1, 7])
+def test_env_update(ctx, direction, p, nsect):
+    from paper_2007_14822_gb300.tnh import Tensor
+    m = 40
+    d = H.heff_inputs(m, None, 9, nsect=nsect, maxd=12)
+    a = d["psi"].inds[0]
+    s = d["psi"].inds[1]
+    # MPS tensor A[a, s, b] with b = a-link shifted by one site
+    A, Ao = H.random_pair([a, s, a.dag()], None, 11, "A")
+    if direction == 1:
+        E, Eo = d["L"], d["Lo"]
+        out = Tensor(list(d["L"].inds), (0,))
+        ctx.env_update(1, E, A, d["W"], out, prec(p))
+        want = D.env_left(Eo, Ao, d["Wo"])
+    else:
+        E, Eo = d["R"], d["Ro"]
+        out = Tensor(list(d["R"].inds), (0,))
+        ctx.env_update(-1, E, A, d["W"], out, prec(p))
+        want = D.env_right(Eo, Ao, d["Wo"])
+    err = H.rel_err(H.to_oracle(out), want)
+    assert err < TOL[p], err
+
+
+# -------------------------------------------------------------- eigsolve
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_eigsolve_dense(ctx, p):
+    m = 20
+    d = H.heff_inputs(m, None, 13, nsect=1, symmetric=True)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    Hm = D.heff_dense_matrix(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    assert np.abs(Hm - Hm.T).max() < 1e-10 * np.abs(Hm).max()
+    w, v = np.linalg.eigh(Hm)
+    psi = d["psi"].data.clone()
+    E, r, k = plan.eigsolve(psi, krylov_dim=200, tol=1e-10 if p == "fp64" else 1e-6)
+    scale = abs(w[0])
+    assert abs(E - w[0]) < 1e-9 * scale, (E, w[0])
+    x = psi.cpu().numpy()
+    ov = abs(float(x @ v[:, 0]))
+    assert ov > 1 - (1e-10 if p == "fp64" else 1e-7)

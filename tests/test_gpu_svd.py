@@ -1,0 +1,94 @@
+"""GPU truncated SVD (batched one-sided Jacobi, FP64) against the oracle's
+LAPACK SVD and the Eckart-Young identity."""
+import numpy as np
+import pytest
+
+import helpers as H
+from oracle import dmrg as D
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2007_14822_gb300 import build, tnh
+    build.build()
+    c = tnh.Context(0)
+    yield c
+    c.close()
+
+
+def theta_inputs(m, nsect, maxd, seed):
+    from paper_2007_14822_gb300 import models as pm
+    a = H.link_index(m, nsect, maxd, +1)
+    s = pm.site_index(pm.SPIN_QN, qn=nsect > 1)
+    return H.random_pair([a, s, s, a.dag()], None, seed, "theta")
+
+
+def factor(ctx, T, cutoff, maxdim, mindim=1):
+    svd = ctx.svd_trunc(T, 2, cutoff, maxdim, mindim)
+    U, S, V = svd.factors()
+    Uo, Vo = H.to_oracle(U), H.to_oracle(V)
+    s = S.cpu().numpy()
+    Sd, pos = {}, 0
+    for q, dim in svd.sectors:
+        Sd[q] = s[pos:pos + dim]
+        pos += dim
+    return svd, Uo, Sd, Vo, s
+
+
+@pytest.mark.parametrize("m,nsect,maxd", [(1, 1, 1), (5, 1, 5), (24, 7, 6), (40, 1, 40), (96, 11, 20)])
+def test_svd_full_rank_matches_oracle(ctx, m, nsect, maxd):
+    T, To = theta_inputs(m, nsect, maxd, 3)
+    svd, Uo, Sd, Vo, s = factor(ctx, T, 0.0, 10 ** 6)
+    _, So, _, _ = D.svd_trunc(To, 2, 0.0, 10 ** 6)
+    want = np.sort(np.concatenate(list(So.values())))[::-1]
+    got = np.sort(s)[::-1]
+    assert got.shape == want.shape
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-13 * want[0])
+    # every sector is descending and the factors reproduce theta
+    for v in Sd.values():
+        assert np.all(np.diff(v) <= 0)
+    rec = D.theta(D.scale_link(Uo, Sd, 2), Vo)
+    assert H.rel_err(rec, To) < 1e-12
+    Ud = Uo.to_dense().reshape(-1, Uo.inds[2].dim)
+    np.testing.assert_allclose(Ud.T @ Ud, np.eye(Ud.shape[1]), atol=1e-12)
+    Vd = Vo.to_dense().reshape(Vo.inds[0].dim, -1)
+    np.testing.assert_allclose(Vd @ Vd.T, np.eye(Vd.shape[0]), atol=1e-12)
+
+
+@pytest.mark.parametrize("keep", [1, 7, 30])
+def test_svd_truncation_matches_oracle(ctx, keep):
+    T, To = theta_inputs(48, 9, 10, 4)
+    svd, Uo, Sd, Vo, s = factor(ctx, T, 0.0, keep)
+    Uw, Sw, Vw, errw = D.svd_trunc(To, 2, 0.0, keep)
+    assert svd.kept == keep
+    assert [d for _, d in svd.sectors] == [len(v) for _, v in sorted(Sw.items())]
+    assert abs(svd.truncerr - errw) < 1e-12
+    rec = D.theta(D.scale_link(Uo, Sd, 2), Vo)
+    disc = float(np.sum((rec.to_dense() - To.to_dense()) ** 2)) / To.norm() ** 2
+    assert abs(disc - errw) < 1e-11
+
+
+def test_svd_cutoff_rule(ctx):
+    T, To = theta_inputs(48, 9, 10, 5)
+    _, So, _, _ = D.svd_trunc(To, 2, 0.0, 10 ** 6)
+    sv = np.sort(np.concatenate(list(So.values())))[::-1]
+    tot = float(np.sum(sv ** 2))
+    tail = np.cumsum((sv ** 2)[::-1])[::-1] / tot
+    for k in (5, 20, 40):
+        cutoff = 0.5 * (tail[k] + tail[k - 1])      # strictly between two tails
+        svd = ctx.svd_trunc(T, 2, cutoff, 10 ** 6)
+        assert svd.kept == k
+        svd = ctx.svd_trunc(T, 2, cutoff, k - 2)    # maxdim binds
+        assert svd.kept == k - 2
+
+
+def test_svd_config2_size(ctx):
+    # theta of the dense m=256, d=2 workload: a 512 x 512 matrix
+    T, To = theta_inputs(256, 1, 256, 6)
+    svd, Uo, Sd, Vo, s = factor(ctx, T, 1e-10, 256)
+    Uw, Sw, Vw, errw = D.svd_trunc(To, 2, 1e-10, 256)
+    want = np.concatenate(list(Sw.values()))
+    np.testing.assert_allclose(np.sort(s)[::-1], np.sort(want)[::-1], rtol=1e-11, atol=1e-12 * want.max())
+    assert abs(svd.truncerr - errw) < 1e-12
