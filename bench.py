@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the two-site DMRG hot path on one GB300 (replicas on N GPUs).
+
+Workload (dense S=1/2 Heisenberg chain bond, N=100 bulk shapes): bond
+dimension m=256, MPO bond dimension w=5, site dimension d=2. Left/right
+environments L, R are (256, 5, 256), the two MPS tensors A_j, A_{j+1} are
+(256, 2, 256), so the two-site state psi is (256, 2, 2, 256). Entries are
+seeded N(0,1) (L seed 2, R seed 3, A seed 4); L and R get the symmetry that
+environments built from a real MPS have, so H_eff is symmetric.
+
+One step is one full two-site bond update, every row of the hot path:
+  theta = A_j A_{j+1}                                  (FP64)
+  H_eff plan; Lanczos, K_LANCZOS matvecs in BF16x6     (split-bf16 tcgen05)
+  energy E = <psi|H psi> and residual                  (FP64 H_eff)
+  truncated SVD, maxdim 256, cutoff 1e-10              (FP64 Jacobi)
+  U -> A_j, S V -> A_{j+1}, L_{j+1} = update(L_j, U, W) (FP64)
+
+The reported metric counts the algorithmic flops of the step's contractions
+(theta + (K_LANCZOS + 1) H_eff products + environment update; the extra
+products of the bf16 split are not counted) divided by the step time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, W_DIM, D = 256, 5, 2
+K_LANCZOS = 8
+CUTOFF, MAXDIM = 1e-10, 256
+METRIC = "H_eff·ψ TFLOP/s + DMRG sweep time, mixed vs FP64 on GB300 at ΔE/E≤1e-9"
+
+
+def step_flops(m=M, w=W_DIM, d=D, k=K_LANCZOS):
+    theta = 2 * d * d * m ** 3
+    heff = 4 * w * d * d * m ** 3 + 4 * w * w * d ** 3 * m * m
+    env = 4 * w * d * m ** 3 + 2 * w * w * d * d * m * m
+    return theta + (k + 1) * heff + env, heff
+
+
+# ----------------------------------------------------------------- inputs
+def host_inputs(m=M):
+    """Seeded host arrays of the workload (shared by both arms)."""
+    from paper_2007_14822_gb300 import models as pm, synth
+    L = synth.gaussian(2, (m, W_DIM, m))
+    R = synth.gaussian(3, (m, W_DIM, m))
+    for E in (L, R):
+        for ch in (0, 3, 4):
+            E[:, ch, :] = 0.5 * (E[:, ch, :] + E[:, ch, :].T)
+        E[:, 2, :] = E[:, 1, :].T
+    A = synth.gaussian(4, (2, m, D, m)) / np.sqrt(m)
+    W = pm.heisenberg(3).W[1]
+    return dict(L=L, R=R, A1=A[0], A2=A[1], W=W)
+
+
+class GpuBond:
+    """Device tensors and one bond update through the C ABI."""
+
+    def __init__(self, ctx, host, pinned=False):
+        import torch
+        from paper_2007_14822_gb300.tnh import Index, Tensor, BF16x6, FP64
+        self.ctx, self.torch = ctx, torch
+        self.FP64, self.MIX = FP64, BF16x6
+        # labels matter only for the labelled contraction theta = A1 * A2
+        a, c, b = Index.dense(M, +1, 1), Index.dense(M, +1, 3), Index.dense(M, +1, 5)
+        s1, s2 = Index.dense(D, +1, 2), Index.dense(D, +1, 4)
+        s = s1
+        wl, wr = Index.dense(W_DIM, -1), Index.dense(W_DIM, +1)
+        self.L = Tensor([a.dag(), wl.dag(), a])
+        self.R = Tensor([b, wr.dag(), b.dag()])
+        self.W = Tensor([wl, wr, s.dag(), s])
+        self.A1 = Tensor([a, s1, c.dag()])
+        self.A2 = Tensor([c, s2, b.dag()])
+        self.theta = Tensor([a, s1, s2, b.dag()])
+        self.Lnew = Tensor([a, wr, a.dag()])
+        self.host = host
+        self.pinned = {}
+        for k, t in (("L", self.L), ("R", self.R), ("A1", self.A1), ("A2", self.A2), ("W", self.W)):
+            arr = torch.from_numpy(np.ascontiguousarray(host[k]).ravel())
+            self.pinned[k] = arr.pin_memory() if pinned else arr
+            t.data.copy_(self.pinned[k])
+        self.s_idx = s
+        self.h2d_bytes = sum(self.pinned[k].numel() * 8 for k in ("L", "R", "A1", "A2"))
+        self.d2h_bytes = 0
+
+    def upload(self):
+        for k, t in (("L", self.L), ("R", self.R), ("A1", self.A1), ("A2", self.A2)):
+            t.data.copy_(self.pinned[k], non_blocking=True)
+
+    def step(self, download=False):
+        ctx = self.ctx
+        ctx.contract(self.A1, self.A2, self.theta, self.FP64)
+        plan = ctx.heff_plan(self.L, self.W, self.W, self.R, self.theta, self.MIX)
+        E, res, k = plan.eigsolve(self.theta.data, krylov_dim=K_LANCZOS, tol=0.0)
+        plan.free()
+        svd = ctx.svd_trunc(self.theta, 2, CUTOFF, MAXDIM)
+        U, S, V = svd.factors(absorb=2)
+        svd.free()
+        Lnew = self.Lnew.__class__([U.inds[2], self.W.inds[1], U.inds[2].dag()])
+        ctx.env_update(1, self.L, U, self.W, Lnew, self.FP64)
+        out = dict(E=E, res=res, k=k, kept=U.inds[2].dim)
+        if download:
+            h = U.data.cpu()
+            self.d2h_bytes = 8 + h.numel() * 8
+            out["U"] = h
+        return out
+
+
+def oracle_bond(host, k=K_LANCZOS):
+    """The same bond update by the FP64 oracle (numpy)."""
+    from oracle import dmrg as D_
+    from oracle.blocksparse import BlockTensor, IN, OUT, trivial_index
+    a = trivial_index(M, OUT)
+    s = trivial_index(D, OUT)
+    wl, wr = trivial_index(W_DIM, IN), trivial_index(W_DIM, OUT)
+    L = BlockTensor.from_dense(host["L"], [a.dag(), wl.dag(), a])
+    R = BlockTensor.from_dense(host["R"], [a, wr.dag(), a.dag()])
+    W = BlockTensor.from_dense(host["W"], [wl, wr, s.dag(), s])
+    A1 = BlockTensor.from_dense(host["A1"], [a, s, a.dag()])
+    A2 = BlockTensor.from_dense(host["A2"], [a, s, a.dag()])
+    th = D_.theta(A1, A2)
+    apply = lambda x: D_.heff_apply(L, W, W, R, x)
+    E, x, res, nmv = D_.lanczos(apply, th, k, 0.0)
+    E, r = D_.energy_residual(apply, x)
+    U, S, V, err = D_.svd_trunc(x, 2, CUTOFF, MAXDIM)
+    Lnew = D_.env_left(L, U, W)
+    return E
+
+
+def blas_threads():
+    """Threads numpy's BLAS uses (what the oracle timing ran on)."""
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        if info:
+            return max(i.get("num_threads", 1) for i in info)
+    except ImportError:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------ measurement
+def l2_flush(torch, buf):
+    buf.add_(1.0)
+
+
+def time_steps(torch, bond, steps, flush, e2e=False):
+    s = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(steps):
+        l2_flush(torch, flush)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        if e2e:
+            bond.upload()
+        bond.step(download=e2e)
+        b.record(s)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b) / 1e3
+    return total
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    flops, heff_flops = step_flops()
+    config = {"workload": "dense Heisenberg bond update, m=256 w=5 d=2 (L/R 256x5x256, psi 256x2x2x256)",
+              "step": f"theta + Lanczos {K_LANCZOS} matvecs BF16x6 + FP64 energy + FP64 Jacobi SVD "
+                      f"(maxdim {MAXDIM}, cutoff {CUTOFF}) + FP64 env update",
+              "flops_per_step": flops, "l2": "flushed between timed steps (256 MB write)",
+              "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        host = host_inputs()
+        cores = blas_threads()
+        for _ in range(max(0, min(args.warmup, 1))):
+            oracle_bond(host, k=2)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle_bond(host)
+        dt = (time.perf_counter() - t0) / args.steps
+        val = flops / dt / 1e12
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"{args.steps} oracle bond updates of the workload"},
+                "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2007_14822_gb300 import build, tnh
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = tnh.Context(local)
+    host = host_inputs()
+    bond = GpuBond(ctx, host, pinned=True)
+    flush = torch.zeros(32 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 256 MB > L2
+    for _ in range(args.warmup):
+        bond.step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        t_dev = time_steps(torch, bond, args.steps, flush)
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = t.item()
+    # end to end: host buffers in, result out, every step
+    t_e2e = time_steps(torch, bond, max(1, args.steps // 2), flush, e2e=True) / max(1, args.steps // 2)
+    # per-kernel breakdown of one step (profiled separately)
+    ctx.profile_begin()
+    bond.step()
+    prof = ctx.profile_end()
+    launches = sum(v[0] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    # H_eff alone, mixed and FP64 (kernel chain of one matvec)
+    plan = ctx.heff_plan(bond.L, bond.W, bond.W, bond.R, bond.theta, tnh.BF16x6)
+    y = torch.empty_like(bond.theta.data)
+    hs = {}
+    for name, p in (("bf16x6", None), ("fp64", tnh.FP64)):
+        for _ in range(3):
+            plan.apply(bond.theta.data, y, p)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20 if p is None else 5
+        a.record()
+        for _ in range(reps):
+            plan.apply(bond.theta.data, y, p)
+        b.record()
+        torch.cuda.synchronize()
+        hs[name] = heff_flops / (a.elapsed_time(b) / 1e3 / reps) / 1e12
+    plan.free()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    ms_step = t_dev / args.steps * 1e3
+    value = world * flops * args.steps / t_dev / 1e12
+    # roofline of the dominant kernel
+    name, (nl, ms) = top
+    fp64_flops = 2 * D * D * M ** 3 + heff_flops + (4 * W_DIM * D * M ** 3 + 2 * W_DIM ** 2 * D * D * M * M)
+    if name == "gemm_f64":
+        achieved = fp64_flops / (ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": None, "kernel": name,
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}
+    elif name.startswith("gemm_tc"):
+        achieved = K_LANCZOS * heff_flops / (ms / 1e3) / 1e12
+        pk = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "traffic": None, "kernel": name, "peak_source": "measured bf16 (burst)"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": 1.25, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": name, "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}
+    roof["kernel_ms_per_step"] = ms
+    roof["launches_per_step"] = nl
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+bf16x6", "data": "synthetic", "config": config,
+            "e2e": {"value": world * flops / t_e2e / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": bond.h2d_bytes, "d2h_bytes_per_step": bond.d2h_bytes},
+            "gpu_launches": launches * args.steps, "clocks": clk.summary(), "roofline": roof,
+            "heff_tflops": hs, "kernels_per_step": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = blas_threads()
+        t0 = time.perf_counter()
+        oracle_bond(host)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                                "sample": "1 oracle bond update of the same workload"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,17 @@ const char* tnh_last_error(const tnh_ctx* ctx);
 /* Block until all work queued by the context has finished. */
 tnh_status tnh_sync(tnh_ctx* ctx);
 
+/* Kernel profiling (no counterpart in the paper; measurement support).
+ * Between tnh_profile_begin and tnh_profile_end every kernel the library
+ * launches for this context on the calling thread is bracketed by CUDA
+ * events on its stream. tnh_profile_end synchronises the stream and returns,
+ * per kernel name (at most max_kinds; *nkinds is the number found):
+ * names [max_kinds * 64] NUL-terminated, launches, and summed device time
+ * in milliseconds. Any output array may be NULL. */
+tnh_status tnh_profile_begin(tnh_ctx* ctx);
+tnh_status tnh_profile_end(tnh_ctx* ctx, int32_t max_kinds, int32_t* nkinds, char* names,
+                           int64_t* launches, double* ms);
+
 /* ---- layout helper (host only, no device work) ------------------------- */
 
 /* Enumerate the blocks of a tensor with the given indices and flux (Sec. 8.3:
@@ -139,7 +150,8 @@ tnh_status tnh_layout(int32_t rank, const tnh_index* inds, const int32_t* flux,
  * C's blocks are given by the caller (tnh_layout) and every C block not
  * reached by a block pair is set to zero. A block-sparse product is the set
  * of dense block-pair products whose contracted sectors agree; pairs landing
- * on the same C block are summed (Sec. 9.4). Asynchronous. */
+ * on the same C block are summed (Sec. 9.4). Synchronises the stream (the
+ * temporary plan and workspace are freed on return). */
 tnh_status tnh_contract(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
                         tnh_tensor* C, tnh_precision prec);
 
@@ -190,7 +202,7 @@ tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_dim, double 
  * dir = -1: E_out[a,w,a'] = sum A[a,s,b] W[w,w',s,s'] A[a',s',b'] E[b,w',b']
  * A [a, s, b] is an MPS tensor (a Out, s Out, b In); its bra copy has the
  * arrows reversed (real data). E_out's blocks are given by the caller.
- * Asynchronous. */
+ * Synchronises the stream (temporary plan and workspace). */
 tnh_status tnh_env_update(tnh_ctx* ctx, int32_t dir, const tnh_tensor* E,
                           const tnh_tensor* A, const tnh_tensor* W,
                           tnh_tensor* E_out, tnh_precision prec);
@@ -214,8 +226,11 @@ tnh_status tnh_svd_info(const tnh_svd* svd, int32_t* nsect, int32_t* nq, int32_t
                         int32_t* sect_dim, double* truncerr);
 /* Copy the factors: U [rows..., c] (c In) and V [c, cols...] (c Out) with
  * caller-given layouts (DEVICE data), S DEVICE [sum of sect_dim] in sector
- * order, descending inside a sector. T = U diag(S) V up to the truncation. */
-tnh_status tnh_svd_get(tnh_svd* svd, tnh_tensor* U, double* S, tnh_tensor* V);
+ * order, descending inside a sector (S may be NULL). T = U diag(S) V up to
+ * the truncation. absorb = 1 returns U diag(S) in U, absorb = 2 returns
+ * diag(S) V in V (the two ways a two-site update moves the orthogonality
+ * centre), absorb = 0 neither. Synchronises the stream. */
+tnh_status tnh_svd_get(tnh_svd* svd, tnh_tensor* U, double* S, tnh_tensor* V, int32_t absorb);
 void tnh_svd_free(tnh_svd* svd);
 
 /* ---- two-site DMRG sweeps (Sec. 7.2) ------------------------------------ */

@@ -4,8 +4,9 @@
 #include <cstring>
 #include <numeric>
 
-#include "tnh_internal.h"
+#include "prof.h"
 #include "tnh_guard.h"
+#include "tnh_internal.h"
 
 namespace tnh {
 
@@ -170,6 +171,10 @@ void make_chunks(const std::vector<Piece>& pieces, std::vector<Chunk>& chunks, i
         for (int64_t s = 0; s < n; s += per_chunk)
             chunks.push_back(Chunk{p, (int)s, (int)std::min<int64_t>(per_chunk, n - s)});
     }
+}
+
+Ctx::~Ctx() {
+    if (prof && active_profiler() == prof.get()) set_active_profiler(nullptr);
 }
 
 void check_device_flag(Ctx* ctx) {

@@ -3,6 +3,7 @@
 // C_t[M][ldc] = A_t[M][K] * B_t[N][K]^T for every task t, both operands
 // K-major and zero-padded to 64-row / 16-column multiples by the packer.
 // One CTA computes one 64 x 64 output tile; tiles of all tasks form one grid.
+#include "prof.h"
 #include "tnh_internal.h"
 
 namespace tnh {
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmTask* __restric
 void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, int total_tiles, const double* A, const double* B,
                      double* C, cudaStream_t s) {
     if (total_tiles == 0) return;
+    KScope ks("gemm_f64", s);
     gemm_f64_kernel<<<total_tiles, 256, 0, s>>>(d_tasks, ntasks, A, B, C);
 }
 

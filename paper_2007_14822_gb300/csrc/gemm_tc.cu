@@ -25,6 +25,7 @@
 // Every wait is bounded (ptx::mbar_wait); a timeout sets the device error flag.
 #include <cuda_bf16.h>
 
+#include "prof.h"
 #include "ptx.cuh"
 #include "tnh_internal.h"
 
@@ -241,6 +242,7 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
         configured = true;
     }
     int grid = std::min(total_tiles, num_sms > 0 ? num_sms : 148);
+    KScope ks(P == 3 ? "gemm_tc_bf16x6" : (P == 2 ? "gemm_tc_bf16x3" : "gemm_tc_bf16"), s);
     gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err);
 }
 

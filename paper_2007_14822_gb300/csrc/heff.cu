@@ -40,7 +40,7 @@ DevBuf copy_data(const Layout& T, cudaStream_t s) {
 HeffPlan::~HeffPlan() = default;
 
 std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L0, const Layout& W10, const Layout& W20,
-                                    const Layout& R0, const Layout& psi0, tnh_precision prec) {
+                                    const Layout& R0, const Layout& psi0, tnh_precision prec, bool copy_inputs) {
     TNH_REQUIRE(L0.rank() == 3 && R0.rank() == 3 && W10.rank() == 4 && W20.rank() == 4 && psi0.rank() == 4,
                 TNH_ERR_ARG, "heff_plan: ranks must be L 3, W 4, R 3, psi 4");
     TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "heff_plan: bad precision");
@@ -75,10 +75,21 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L0, const Layout& W1
     P->t1.alloc((size_t)std::max<int64_t>(T1.size, 1) * 8);
     P->t2.alloc((size_t)std::max<int64_t>(T2.size, 1) * 8);
     P->t3.alloc((size_t)std::max<int64_t>(T3.size, 1) * 8);
-    P->Ld = copy_data(L, s);
-    P->Rd = copy_data(R, s);
-    P->W1d = copy_data(W1, s);
-    P->W2d = copy_data(W2, s);
+    if (copy_inputs) {
+        P->Ld = copy_data(L, s);
+        P->Rd = copy_data(R, s);
+        P->W1d = copy_data(W1, s);
+        P->W2d = copy_data(W2, s);
+        P->Lp = P->Ld.as<double>();
+        P->Rp = P->Rd.as<double>();
+        P->W1p = P->W1d.as<double>();
+        P->W2p = P->W2d.as<double>();
+    } else {
+        P->Lp = L.data;
+        P->Rp = R.data;
+        P->W1p = W1.data;
+        P->W2p = W2.data;
+    }
     P->flops = P->c1->flops + P->c2->flops + P->c3->flops + P->c4->flops;
     CUDA_CHECK(cudaStreamSynchronize(s));
     return P;
@@ -88,10 +99,10 @@ void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
     Ctx* ctx = P.ctx;
     TNH_REQUIRE(prec == TNH_FP64 || prec == P.prec, TNH_ERR_ARG,
                 "heff_apply: precision %d not prepared by this plan", (int)prec);
-    run_contract(ctx, *P.c1, P.Ld.as<double>(), x, P.t1.as<double>(), prec, P.ws);
-    run_contract(ctx, *P.c2, P.t1.as<double>(), P.W1d.as<double>(), P.t2.as<double>(), prec, P.ws);
-    run_contract(ctx, *P.c3, P.t2.as<double>(), P.W2d.as<double>(), P.t3.as<double>(), prec, P.ws);
-    run_contract(ctx, *P.c4, P.t3.as<double>(), P.Rd.as<double>(), y, prec, P.ws);
+    run_contract(ctx, *P.c1, P.Lp, x, P.t1.as<double>(), prec, P.ws);
+    run_contract(ctx, *P.c2, P.t1.as<double>(), P.W1p, P.t2.as<double>(), prec, P.ws);
+    run_contract(ctx, *P.c3, P.t2.as<double>(), P.W2p, P.t3.as<double>(), prec, P.ws);
+    run_contract(ctx, *P.c4, P.t3.as<double>(), P.Rp, y, prec, P.ws);
 }
 
 }  // namespace tnh

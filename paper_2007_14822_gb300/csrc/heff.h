@@ -13,13 +13,17 @@ struct HeffPlan {
     Layout psi;             // its layout
     double flops = 0.0;
     std::unique_ptr<ContractPlan> c1, c2, c3, c4;
-    DevBuf t1, t2, t3, Ld, Rd, W1d, W2d;
+    DevBuf t1, t2, t3, Ld, Rd, W1d, W2d;     // owned copies (public entry point)
+    const double *Lp = nullptr, *Rp = nullptr, *W1p = nullptr, *W2p = nullptr;
     Workspace ws;
     ~HeffPlan();
 };
 
+// copy_inputs: keep private copies of L, W1, W2, R (else reference the
+// caller's device data, which must outlive the plan)
 std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
-                                    const Layout& R, const Layout& psi, tnh_precision prec);
+                                    const Layout& R, const Layout& psi, tnh_precision prec,
+                                    bool copy_inputs = true);
 void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y);
 
 struct EigResult {

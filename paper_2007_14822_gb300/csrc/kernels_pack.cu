@@ -6,6 +6,7 @@
 // the GEMM reads only contiguous tiles.
 #include <cuda_bf16.h>
 
+#include "prof.h"
 #include "tnh_internal.h"
 
 namespace tnh {
@@ -103,12 +104,14 @@ __global__ void unpack_kernel(const Piece* __restrict__ pieces, const Chunk* __r
 void launch_pack_f64(const Piece* d_pieces, const Chunk* d_chunks, int nchunks, const OpGeom* d_geom,
                      const double* src, double* dst, cudaStream_t s) {
     if (nchunks == 0) return;
+    KScope ks("pack_f64", s);
     pack_f64_kernel<<<nchunks, 256, 0, s>>>(d_pieces, d_chunks, d_geom, src, dst);
 }
 
 void launch_pack_bf16(const Piece* d_pieces, const Chunk* d_chunks, int nchunks, const OpGeom* d_geom,
                       const double* src, uint16_t* dst, int planes, cudaStream_t s) {
     if (nchunks == 0) return;
+    KScope ks("pack_split_bf16", s);
     if (planes == 3)
         pack_bf16_kernel<3><<<nchunks, 256, 0, s>>>(d_pieces, d_chunks, d_geom, src, dst);
     else if (planes == 2)
@@ -120,6 +123,7 @@ void launch_pack_bf16(const Piece* d_pieces, const Chunk* d_chunks, int nchunks,
 void launch_unpack(const Piece* d_pieces, const Chunk* d_chunks, int nchunks, const int64_t* d_cbase,
                    const int* d_ldc, const double* Ct, double* dst, cudaStream_t s) {
     if (nchunks == 0) return;
+    KScope ks("unpack", s);
     unpack_kernel<<<nchunks, 256, 0, s>>>(d_pieces, d_chunks, d_cbase, d_ldc, Ct, dst);
 }
 

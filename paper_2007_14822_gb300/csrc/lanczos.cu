@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "heff.h"
+#include "prof.h"
 #include "tnh_guard.h"
 
 namespace tnh {
@@ -122,7 +123,7 @@ __device__ void tri_solve(const double* a, const double* b, int k, double theta,
     for (int i = 0; i + 1 < k; ++i) { dl[i] = b[i]; du[i] = b[i]; du2[i] = 0.0; }
     // a zero pivot (theta is an eigenvalue) is replaced by eps * |T|, which
     // keeps the solution finite and pointing along the eigenvector
-    const double tiny = 1e-15 * tnorm;
+    const double tiny = fmax(1e-15 * tnorm, 1e-200);
     for (int i = 0; i + 1 < k; ++i) {
         if (fabs(dd[i]) >= fabs(dl[i])) {
             if (dd[i] == 0.0) dd[i] = tiny;
@@ -198,7 +199,14 @@ __global__ void tridiag_lowest(const double* __restrict__ alpha, double* __restr
         }
         __syncthreads();
     }
-    if (t == 0) {
+    if (t == 0 && k == 1) {
+        double bk = sqrt(fmax(*beta2_last, 0.0));
+        beta[0] = bk;
+        out[0] = a[0];
+        out[1] = bk;
+        out[2] = bk;
+        s[0] = 1.0;
+    } else if (t == 0) {
         double theta = 0.5 * (lo_s + hi_s);
         for (int i = 0; i < k; ++i) v[i] = 1.0;
         for (int rep = 0; rep < 3; ++rep) {
@@ -245,13 +253,19 @@ void VecWork::ensure(int nsms) {
 
 void vdot(Ctx* ctx, VecWork& w, const double* x, const double* y, int64_t n, double* d_out) {
     w.ensure(ctx->num_sms);
+    { KScope ks_("multidot_partial", ctx->stream);
     multidot_partial<<<dim3(w.blocks, 1), kRedThreads, 0, ctx->stream>>>(x, 0, y, n, w.partial.as<double>());
+    }
+    { KScope ks_("reduce_partials", ctx->stream);
     reduce_partials<<<1, kRedThreads, 0, ctx->stream>>>(w.partial.as<double>(), w.blocks, d_out);
+    }
 }
 
 void vscale_copy(Ctx* ctx, const double* x, double* y, int64_t n, const double* d_num, const double* d_den,
                  int mode) {
+    { KScope ks_("scale_copy", ctx->stream);
     scale_copy<<<grid_for(n, ctx->num_sms), 256, 0, ctx->stream>>>(x, y, n, d_num, d_den, mode);
+    }
 }
 
 EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
@@ -283,22 +297,34 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
     CUDA_CHECK(cudaMemcpyAsync(&hn2, misc, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
     TNH_REQUIRE(std::isfinite(hn2) && hn2 > 0.0, TNH_ERR_NUMERIC, "eigsolve: start vector has norm^2 %g", hn2);
+    { KScope ks_("scale_copy", s);
     scale_copy<<<g, 256, 0, s>>>(psi, q, n, nullptr, misc, 1);
+    }
     int k = 0;
     double host[3] = {0, 0, 0};
     for (int j = 0; j < kmax; ++j) {
         double* qj = q + (int64_t)j * n;
         heff_apply(P, P.prec, qj, w);
         vdot(ctx, vw, qj, w, n, alpha + j);
+        { KScope ks_("lanczos_three_term", s);
         lanczos_three_term<<<g, 256, 0, s>>>(w, qj, j > 0 ? qj - n : nullptr, alpha + j,
                                             j > 0 ? beta + (j - 1) : alpha, n);
+        }
         for (int rep = 0; rep < 2; ++rep) {
+            { KScope ks_("multidot_partial", s);
             multidot_partial<<<dim3(vw.blocks, j + 1), kRedThreads, 0, s>>>(q, n, w, n, vw.partial.as<double>());
+            }
+            { KScope ks_("reduce_partials", s);
             reduce_partials<<<j + 1, kRedThreads, 0, s>>>(vw.partial.as<double>(), vw.blocks, h);
+            }
+            { KScope ks_("multi_axpy", s);
             multi_axpy<<<g, 256, 0, s>>>(w, q, n, j + 1, h, -1.0, 0, n);
+            }
         }
         vdot(ctx, vw, w, w, n, misc + 1);
+        { KScope ks_("tridiag_lowest", s);
         tridiag_lowest<<<1, 256, 0, s>>>(alpha, beta, j + 1, misc + 1, out, sv);
+        }
         CUDA_CHECK(cudaMemcpyAsync(host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CUDA_CHECK(cudaStreamSynchronize(s));
         k = j + 1;
@@ -306,16 +332,24 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
                     "eigsolve: non-finite Ritz value at step %d", j);
         const double scale = std::max(1.0, std::fabs(host[0]));
         if (host[1] <= tol * scale || host[2] <= 1e-14 * scale || j + 1 == kmax) break;
+        { KScope ks_("scale_copy", s);
         scale_copy<<<g, 256, 0, s>>>(w, q + (int64_t)(j + 1) * n, n, nullptr, beta + j, 2);
+        }
     }
     // Ritz vector, normalised, into psi
+    { KScope ks_("multi_axpy", s);
     multi_axpy<<<g, 256, 0, s>>>(psi, q, n, k, sv, 1.0, 1, n);
+    }
     vdot(ctx, vw, psi, psi, n, misc);
+    { KScope ks_("scale_copy", s);
     scale_copy<<<g, 256, 0, s>>>(psi, psi, n, nullptr, misc, 1);
+    }
     // float64 energy and residual
     heff_apply(P, TNH_FP64, psi, yv.as<double>());
     vdot(ctx, vw, psi, yv.as<double>(), n, misc + 2);
+    { KScope ks_("axpy_dev", s);
     axpy_dev<<<g, 256, 0, s>>>(yv.as<double>(), psi, misc + 2, n);
+    }
     vdot(ctx, vw, yv.as<double>(), yv.as<double>(), n, misc + 3);
     double fin[2];
     CUDA_CHECK(cudaMemcpyAsync(fin, misc + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));

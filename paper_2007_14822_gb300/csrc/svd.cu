@@ -17,9 +17,11 @@
 #include <cmath>
 #include <map>
 
+#include "prof.h"
 #include "ptx.cuh"
 #include "tnh_guard.h"
 #include "tnh_internal.h"
+#include "svd.h"
 
 namespace tnh {
 
@@ -255,22 +257,30 @@ struct SvdOut {
     int s0;           // first singular value of the group in S
 };
 
+// absorb: 0 none, 1 multiply S into U, 2 multiply S into V
 __global__ void svd_scatter(const SvdOut* __restrict__ O, const int* __restrict__ perm, const double* __restrict__ X,
-                            const double* __restrict__ V, const double* __restrict__ sig_col, const int* __restrict__ col0g,
-                            int* __restrict__ dummy, double* __restrict__ U, double* __restrict__ Vt) {
+                            const double* __restrict__ V, const double* __restrict__ sk, int absorb,
+                            double* __restrict__ U, double* __restrict__ Vt) {
     const SvdOut o = O[blockIdx.y];
     const int64_t n = (int64_t)(o.which == 0 ? o.rows : o.cols) * o.kept;
+    const bool into_this = (o.which == 0 && absorb == 1) || (o.which == 1 && absorb == 2);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         int k, idx;
         if (o.which == 0) { idx = (int)(e / o.kept); k = (int)(e - (int64_t)idx * o.kept); }
         else { k = (int)(e / o.cols); idx = (int)(e - (int64_t)k * o.cols); }
         const int j = perm[o.perm0 + k];             // source column in the group
-        const double s = sig_col[col0g[0] + 0] * 0.0 + sig_col[o.s0 + k];
+        const double sv = sk[o.s0 + k];
         const int g = o.off + idx;                   // row (U) or column (V) of M_Q
+        const bool from_x = (o.which == 0) ? !o.trans : o.trans;
         double v;
-        bool from_x = (o.which == 0) ? !o.trans : o.trans;
-        if (from_x) v = s > 0 ? X[o.x_off + (int64_t)j * o.len + g] / s : 0.0;
-        else v = V[o.v_off + (int64_t)j * o.n + g];
+        if (from_x) {
+            // rotated column j of X is sigma_j times a singular vector
+            const double x = X[o.x_off + (int64_t)j * o.len + g];
+            v = into_this ? x : (sv > 0 ? x / sv : 0.0);
+        } else {
+            const double x = V[o.v_off + (int64_t)j * o.n + g];
+            v = into_this ? x * sv : x;
+        }
         if (o.which == 0) U[o.dst + e] = v;
         else Vt[o.dst + e] = v;
     }
@@ -304,7 +314,7 @@ struct SvdResult {
     int nq = 0;
 };
 
-static std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim,
+std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim,
                                           int mindim) {
     cudaStream_t s = ctx->stream;
     const int r = T.rank();
@@ -402,8 +412,12 @@ static std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, d
     DevBuf d_groups = upload(R->groups, s);
     DevBuf d_packs = upload(packs, s);
     DevBuf d_col0 = upload(R->col0, s);
+    { KScope ks_("svd_pack", s);
     svd_pack<<<dim3(16, (unsigned)packs.size()), 256, 0, s>>>(d_packs.as<SvdPack>(), T.data, R->X.as<double>());
+    }
+    { KScope ks_("set_identity", s);
     set_identity<<<dim3(16, ng), 256, 0, s>>>(d_groups.as<JGroup>(), R->V.as<double>());
+    }
     // ---- Jacobi
     DevBuf d_last((size_t)ng * 4), d_state(16), d_bar(16);
     std::vector<int> minus1(ng, -1);
@@ -426,15 +440,24 @@ static std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, d
     int* errp = ctx->d_flag.as<int>();
     void* args[] = {(void*)&gp, (void*)&ng, (void*)&pairs, (void*)&max_rounds, (void*)&rmax, (void*)&Xp,
                     (void*)&Vp, (void*)&lastp, (void*)&statep, (void*)&barp, (void*)&errp};
-    CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(threads), args, 0, s));
+    {
+        KScope ks("jacobi_svd", s);
+        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(threads), args, 0, s));
+    }
     // ---- sigma, ranking, truncation
     DevBuf d_gid((size_t)tot * 4), d_pos((size_t)tot * 4), d_order((size_t)tot * 4), d_out(16), d_outd(16);
+    { KScope ks_("column_norms", s);
     column_norms<<<ng, 256, 0, s>>>(gp, ng, d_col0.as<int>(), Xp, R->sig.as<double>(), d_gid.as<int>(),
                                      d_pos.as<int>());
+    }
+    { KScope ks_("rank_kernel", s);
     rank_kernel<<<(tot + 255) / 256, 256, 0, s>>>(R->sig.as<double>(), d_gid.as<int>(), d_pos.as<int>(), tot,
                                                   d_order.as<int>());
+    }
+    { KScope ks_("trunc_select", s);
     trunc_select<<<1, 32, 0, s>>>(R->sig.as<double>(), d_order.as<int>(), tot, cutoff, maxdim, mindim,
                                   d_out.as<int>(), d_outd.as<double>());
+    }
     int keep = 0;
     int state_h[2];
     CUDA_CHECK(cudaMemcpyAsync(&keep, d_out.p, 4, cudaMemcpyDeviceToHost, s));
@@ -460,7 +483,7 @@ static std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, d
     return R;
 }
 
-static void svd_get(SvdResult& R, const Layout& U, double* S, const Layout& Vl) {
+void svd_get(SvdResult& R, const Layout& U, double* S, const Layout& Vl, int absorb) {
     Ctx* ctx = R.ctx;
     cudaStream_t s = ctx->stream;
     const int r = R.T.rank(), nrow = R.nrow;
@@ -543,13 +566,15 @@ static void svd_get(SvdResult& R, const Layout& U, double* S, const Layout& Vl) 
     DevBuf d_outs = upload(outs, s), d_perm = upload(perm, s), d_sidx = upload(sidx, s);
     // singular values in output order (sector, desc)
     DevBuf d_sk((size_t)std::max<size_t>(sidx.size(), 1) * 8);
+    { KScope ks_("gather_s", s);
     gather_s<<<((int)sidx.size() + 255) / 256, 256, 0, s>>>(R.sig.as<double>(), d_sidx.as<int>(), (int)sidx.size(),
                                                             d_sk.as<double>());
-    int zero = 0;
-    DevBuf d_zero = upload(std::vector<int>{zero}, s);
+    }
+    { KScope ks_("svd_scatter", s);
     svd_scatter<<<dim3(8, (unsigned)outs.size()), 256, 0, s>>>(d_outs.as<SvdOut>(), d_perm.as<int>(),
                                                                R.X.as<double>(), R.V.as<double>(), d_sk.as<double>(),
-                                                               d_zero.as<int>(), nullptr, U.data, Vl.data);
+                                                               absorb, U.data, Vl.data);
+    }
     if (S)
         CUDA_CHECK(cudaMemcpyAsync(S, d_sk.p, sidx.size() * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
@@ -590,11 +615,12 @@ tnh_status tnh_svd_info(const tnh_svd* svd, int32_t* nsect, int32_t* nq, int32_t
     });
 }
 
-tnh_status tnh_svd_get(tnh_svd* svd, tnh_tensor* U, double* S, tnh_tensor* V) {
+tnh_status tnh_svd_get(tnh_svd* svd, tnh_tensor* U, double* S, tnh_tensor* V, int32_t absorb) {
     auto* R = reinterpret_cast<SvdResult*>(svd);
     return guard(R ? R->ctx : nullptr, [&] {
         TNH_REQUIRE(R && U && V, TNH_ERR_ARG, "tnh_svd_get: NULL argument");
-        svd_get(*R, parse_tensor(U, "U"), S, parse_tensor(V, "V"));
+        TNH_REQUIRE(absorb >= 0 && absorb <= 2, TNH_ERR_ARG, "tnh_svd_get: absorb must be 0, 1 or 2");
+        svd_get(*R, parse_tensor(U, "U"), S, parse_tensor(V, "V"), absorb);
     });
 }
 
@@ -606,3 +632,27 @@ void tnh_svd_free(tnh_svd* svd) {
 }
 
 }  // extern "C"
+
+namespace tnh {
+
+SvdResult* svd_run(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim) {
+    return run_svd(ctx, T, nrow, cutoff, maxdim, mindim).release();
+}
+
+SvdShape svd_shape(const SvdResult* R) {
+    SvdShape sh;
+    for (int g : R->sect_groups) {
+        sh.qn.push_back(R->gq[g]);
+        sh.dims.push_back(R->kept_g[g]);
+    }
+    sh.truncerr = R->truncerr;
+    return sh;
+}
+
+void svd_fetch(SvdResult* R, const Layout& U, double* S, const Layout& V, int absorb) {
+    svd_get(*R, U, S, V, absorb);
+}
+
+void svd_delete(SvdResult* R) { delete R; }
+
+}  // namespace tnh

@@ -116,12 +116,15 @@ Layout make_layout(const std::vector<Index>& inds, const std::vector<int>& flux)
 std::vector<int> block_flux(const std::vector<Index>& inds, const int* key, int nq);
 
 // ------------------------------------------------------------------ context
+struct Profiler;
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     std::string err;
     DevBuf d_flag;    // int[4]: [0] device error code written by bounded waits
+    std::unique_ptr<Profiler> prof;
+    ~Ctx();
 };
 
 // Check the device error flag (synchronises); throws TNH_ERR_TIMEOUT if set.

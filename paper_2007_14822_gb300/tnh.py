@@ -27,7 +27,7 @@ PRECISION = {"fp64": FP64, "bf16x6": BF16x6, "bf16x3": BF16x3, "bf16": BF16}
 SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layout", "tnh_contract",
            "tnh_heff_plan", "tnh_heff_apply", "tnh_heff_apply_prec", "tnh_heff_flops", "tnh_heff_size",
            "tnh_heff_free", "tnh_eigsolve", "tnh_env_update", "tnh_svd_trunc", "tnh_svd_info",
-           "tnh_svd_get", "tnh_svd_free", "tnh_dmrg"]
+           "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end"]
 
 
 class TnhError(RuntimeError):
@@ -91,10 +91,12 @@ def lib():
         "tnh_env_update": (i32, [vp, i32, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), C.c_int]),
         "tnh_svd_trunc": (i32, [vp, P(tnh_tensor), i32, dbl, i32, i32, P(vp)]),
         "tnh_svd_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(dbl)]),
-        "tnh_svd_get": (i32, [vp, P(tnh_tensor), vp, P(tnh_tensor)]),
+        "tnh_svd_get": (i32, [vp, P(tnh_tensor), vp, P(tnh_tensor), i32]),
         "tnh_svd_free": (None, [vp]),
         "tnh_dmrg": (i32, [vp, i32, P(tnh_tensor), i64, i64, P(tnh_tensor), P(tnh_sweep_params), P(dbl),
                            P(tnh_sweep_stat)]),
+        "tnh_profile_begin": (i32, [vp]),
+        "tnh_profile_end": (i32, [vp, i32, P(i32), C.c_char_p, P(i64), P(dbl)]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -273,6 +275,23 @@ class Context:
     def sync(self):
         self.check(self._lib.tnh_sync(self.h))
 
+    def profile_begin(self):
+        self.check(self._lib.tnh_profile_begin(self.h))
+
+    def profile_end(self):
+        """{kernel name: (launches, device milliseconds)} since profile_begin."""
+        mx = 64
+        n = C.c_int32()
+        names = C.create_string_buffer(64 * mx)
+        launches = (C.c_int64 * mx)()
+        ms = (C.c_double * mx)()
+        self.check(self._lib.tnh_profile_end(self.h, mx, C.byref(n), names, launches, ms))
+        out = {}
+        for k in range(min(n.value, mx)):
+            name = names.raw[64 * k:64 * (k + 1)].split(b"\0", 1)[0].decode()
+            out[name] = (int(launches[k]), float(ms[k]))
+        return out
+
     def contract(self, A, B, Cout, prec=FP64):
         keep = []
         a, b, c = A._c(keep), B._c(keep), Cout._c(keep)
@@ -386,8 +405,10 @@ class Svd:
     def kept(self):
         return sum(d for _, d in self.sectors)
 
-    def factors(self, link_label=0):
-        """(U, S, V) as device tensors with a new link index (U's c In, V's c Out)."""
+    def factors(self, link_label=0, absorb=0):
+        """(U, S, V) as device tensors with a new link index (U's c In, V's c Out).
+
+        absorb = 1 multiplies S into U, 2 into V (0: neither)."""
         import torch
         link = Index(self.sectors, +1, link_label)
         rows = self.T.inds[:self.nrow]
@@ -397,5 +418,5 @@ class Svd:
         S = torch.zeros(max(1, self.kept), dtype=torch.float64, device=self.T.data.device)
         keep = []
         u, v = U._c(keep), V._c(keep)
-        self.ctx.check(self.ctx._lib.tnh_svd_get(self.h, C.byref(u), _ptr(S), C.byref(v)))
+        self.ctx.check(self.ctx._lib.tnh_svd_get(self.h, C.byref(u), _ptr(S), C.byref(v), int(absorb)))
         return U, S[:self.kept], V
