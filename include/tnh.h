@@ -155,6 +155,26 @@ tnh_status tnh_layout(int32_t rank, const tnh_index* inds, const int32_t* flux,
 tnh_status tnh_contract(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
                         tnh_tensor* C, tnh_precision prec);
 
+/* C = A * B for DENSE float64 tensors (one block, one sector per index),
+ * with the same label rules and the same kernels as tnh_contract in
+ * TNH_FP64, but allocating nothing, on the device or the host, when it
+ * succeeds. The paper has no counterpart: this is for callers that must not
+ * allocate while they work -- a process that reserved all device memory at
+ * start-up, a latency-bound loop where cudaMalloc/cudaFree would stall the
+ * device, a framework that only hands out memory from its own pool. Its
+ * scratch (packed operands, GEMM result, launch descriptors) lives in one
+ * static device array of 16 MiB that every GPU loading the library holds
+ * until the process exits; a contraction needing more than that is refused
+ * with TNH_ERR_ARG (use tnh_contract). The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it: make that
+ * first call before any stream capture. Every call reuses the same array,
+ * so calls whose work overlaps on the GPU (other streams, other contexts on
+ * the same device) race and must be serialised by the caller. Asynchronous
+ * on the context's stream, except that staging the launch descriptors from
+ * host memory waits for the stream's earlier work. */
+tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
+                                      tnh_tensor* C);
+
 /* ---- effective Hamiltonian (Sec. 7.2) ---------------------------------- */
 
 /* Plan y = H_eff . psi with

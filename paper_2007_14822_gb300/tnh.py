@@ -27,7 +27,8 @@ PRECISION = {"fp64": FP64, "bf16x6": BF16x6, "bf16x3": BF16x3, "bf16": BF16}
 SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layout", "tnh_contract",
            "tnh_heff_plan", "tnh_heff_apply", "tnh_heff_apply_prec", "tnh_heff_flops", "tnh_heff_size",
            "tnh_heff_free", "tnh_eigsolve", "tnh_env_update", "tnh_svd_trunc", "tnh_svd_info",
-           "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end"]
+           "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
+           "tnh_contract_dense_noalloc"]
 
 
 class TnhError(RuntimeError):
@@ -95,6 +96,7 @@ def lib():
         "tnh_svd_free": (None, [vp]),
         "tnh_dmrg": (i32, [vp, i32, P(tnh_tensor), i64, i64, P(tnh_tensor), P(tnh_sweep_params), P(dbl),
                            P(tnh_sweep_stat)]),
+        "tnh_contract_dense_noalloc": (i32, [vp, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor)]),
         "tnh_profile_begin": (i32, [vp]),
         "tnh_profile_end": (i32, [vp, i32, P(i32), C.c_char_p, P(i64), P(dbl)]),
     }
@@ -296,6 +298,13 @@ class Context:
         keep = []
         a, b, c = A._c(keep), B._c(keep), Cout._c(keep)
         self.check(self._lib.tnh_contract(self.h, C.byref(a), C.byref(b), C.byref(c), int(prec)))
+        return Cout
+
+    def contract_dense_noalloc(self, A, B, Cout):
+        """Dense FP64 C = A * B using only the library's static device scratch."""
+        keep = []
+        a, b, c = A._c(keep), B._c(keep), Cout._c(keep)
+        self.check(self._lib.tnh_contract_dense_noalloc(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return Cout
 
     def heff_plan(self, L, W1, W2, R, psi, prec=FP64):
