@@ -231,14 +231,19 @@ tnh_status tnh_env_update(tnh_ctx* ctx, int32_t dir, const tnh_tensor* E,
 
 /* Factorise T with its first nrow indices as rows: blocks are grouped by
  * their row charge (each group is one dense matrix, as a combiner groups
- * equal-QN sectors, Sec. 4), every group is factorised by a float64
- * one-sided Jacobi SVD on the device, the singular values of all groups are
- * pooled and truncated: the squares are summed from the smallest upward while
- * their share of the total stays <= cutoff, at most maxdim and at least
- * max(mindim, 1) values are kept (Sec. 5). Ties are ordered by group, then
- * position. Synchronises the stream (the kept count sizes the results). */
+ * equal-QN sectors, Sec. 4) and every group is factorised by one-sided
+ * Jacobi on the device: float32 block sweeps find the dominant subspace,
+ * float64 sweeps on the candidate columns (at least maxdim + 32, and every
+ * column within 1e-4 of the largest singular value) give the result. The
+ * singular values of all groups are pooled and truncated in float64: the
+ * squares are summed from the smallest upward while their share of the total
+ * stays <= cutoff, at most maxdim and at least max(mindim, 1) values are kept
+ * (Sec. 5). Ties are ordered by group, then position. exact_side = 0 makes U
+ * orthonormal to float64 accuracy (a left-to-right move), 1 makes V so (a
+ * right-to-left move); the other factor is the float64 product with T.
+ * Synchronises the stream (the kept count sizes the results). */
 tnh_status tnh_svd_trunc(tnh_ctx* ctx, const tnh_tensor* T, int32_t nrow, double cutoff,
-                         int32_t maxdim, int32_t mindim, tnh_svd** out);
+                         int32_t maxdim, int32_t mindim, int32_t exact_side, tnh_svd** out);
 /* Shape of the result: the new link index has nsect sectors (charges in
  * ascending order, qn [nsect * nq], sect_dim [nsect]); pass NULL arrays to
  * only read nsect. truncerr is the discarded share of sum s^2. */

@@ -12,6 +12,8 @@
 // at the last bond of the sweep.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "env.h"
 #include "heff.h"
@@ -163,10 +165,16 @@ extern "C" tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, i
                         nmv += r.matvecs;
                     }
                     // truncated SVD
-                    SvdResult* sv = svd_run(c, th.L, 2, p->cutoff[sw], p->maxdim[sw], p->mindim);
+                    SvdResult* sv = svd_run(c, th.L, 2, p->cutoff[sw], p->maxdim[sw], p->mindim, dir > 0 ? 0 : 1);
                     try {
                         SvdShape sh = svd_shape(sv);
                         maxerr = std::max(maxerr, sh.truncerr);
+                        if (std::getenv("TNH_DEBUG")) {
+                            int kept = 0;
+                            for (int d : sh.dims) kept += d;
+                            std::fprintf(stderr, "dmrg: sweep %d bond %d dir %+d E %.14f kept %d in %zu sectors truncerr %.3e\n",
+                                         sw, j, dir, E, kept, sh.dims.size(), sh.truncerr);
+                        }
                         Index link;
                         link.nsect = (int)sh.dims.size();
                         link.nq = nq;

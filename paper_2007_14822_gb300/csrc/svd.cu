@@ -1,94 +1,237 @@
-// Truncated SVD of a block-sparse tensor (Sec. 5), float64 on the device.
+// Truncated SVD of a block-sparse tensor (Sec. 5), decided in float64.
 //
 // 1. Blocks are grouped by their row charge; each group is one dense matrix
 //    M_Q (rows: the row-sector tuples of the group, columns: the column
 //    tuples), as a combiner groups equal-QN sectors (Sec. 4).
-// 2. Every M_Q is factorised by one-sided (Hestenes) Jacobi: the columns of
-//    X = M_Q (or M_Q^T when it is wide) are rotated pairwise until all are
-//    orthogonal, X V = U Sigma. Pairs follow the round-robin (circle)
-//    schedule; one cooperative launch works on all groups at once, a warp
-//    per column pair, with a bounded grid barrier between rounds. A group
-//    stops after a full sweep without a rotation.
-// 3. The singular values of all groups are pooled and ranked (sigma desc,
-//    group, position); the cutoff/maxdim rule of Sec. 5 picks the kept count
-//    (the only host synchronisation: it sizes the factors).
-// 4. tnh_svd_get scatters U, S, V into the caller's block layouts.
+// 2. One-sided (Hestenes) Jacobi in two precisions. GB300 runs float64 at a
+//    small fraction of its float32 rate, so the bulk of the rotations is done
+//    in float32 and float64 is kept for the result:
+//    a. float32 block Jacobi on X = M_Q (or M_Q^T): column blocks of b
+//       columns are paired round-robin; each pair of blocks (X and V
+//       columns) is loaded into shared memory by one CTA, which runs one
+//       inner Jacobi sweep over its 2b columns. One cooperative launch
+//       works on all groups, with a bounded grid barrier between rounds.
+//       This gives V32 with columns orthogonal to float32 accuracy.
+//    b. The candidate columns (the largest float32 singular values: maxdim
+//       plus a margin, and all within 1e-4 of the largest) are
+//       re-orthonormalised and re-formed in float64, Y = X V32[:, cand], and
+//       polished by float64 one-sided Jacobi (a warp per column pair), which
+//       converges in one or two sweeps because Y is already nearly
+//       orthogonal.
+//    c. The float64 singular values sigma_j = |Y_j| are pooled, ranked
+//       (sigma desc, group, position) and the cutoff/maxdim rule of Sec. 5
+//       picks the kept count; the discarded weight is |M|_F^2 minus the kept
+//       sigma^2, in float64.
+//    d. The side that must come out orthonormal (U going right, V going left
+//       in a sweep) is Y_j / sigma_j; the other side is the float64 product
+//       of M with it (S V^T = U^T M, or U S = M V).
+// Every wait is bounded and reports through the device error flag.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 
 #include "prof.h"
 #include "ptx.cuh"
+#include "svd.h"
 #include "tnh_guard.h"
 #include "tnh_internal.h"
-#include "svd.h"
 
 namespace tnh {
 
 namespace {
 
-struct JGroup {
-    int64_t x_off;   // column-major X: n columns of length len
-    int64_t v_off;   // column-major V: n x n
-    int len, n;
-    int rounds;      // rounds per sweep (n rounded up to even, minus one)
-    int pair0;       // first global pair index
-    int npairs;
-};
-
+// Grid barrier for a cooperative launch: a monotonic arrival counter
+// (release add, acquire poll); barrier number e completes when the counter
+// reaches e * nblocks. The wait gives up after 4 s of global time or when
+// another thread has raised the error flag.
 struct GridBar {
     unsigned count;
-    unsigned gen;
+    unsigned pad;
 };
 
-__device__ bool grid_barrier(GridBar* bar, unsigned nblocks, int* err) {
+__device__ bool grid_barrier(GridBar* bar, unsigned nblocks, unsigned& epoch, int* err) {
     __syncthreads();
     __shared__ int ok;
+    epoch += nblocks;
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned* vgen = &bar->gen;
-        unsigned g = *vgen;
-        __threadfence();
-        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            const uint64_t t0 = ptx::gtimer_ns();
-            unsigned it = 0;
-            while (*vgen == g) {
-                if ((++it & 255u) == 0) {
-                    if (*(volatile int*)err) { ok = 0; break; }
-                    if (ptx::gtimer_ns() - t0 > 4000000000ull) {
-                        if (atomicCAS(err, 0, 1) == 0) { err[1] = 20; err[2] = blockIdx.x; }
-                        ok = 0;
-                        break;
-                    }
+        unsigned v;
+        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(&bar->count) : "memory");
+        const uint64_t t0 = ptx::gtimer_ns();
+        unsigned it = 0;
+        while (true) {
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(&bar->count) : "memory");
+            if ((int)(v - epoch) >= 0) break;
+            if ((++it & 255u) == 0) {
+                if (*(volatile int*)err) { ok = 0; break; }
+                if (ptx::gtimer_ns() - t0 > 4000000000ull) {
+                    if (atomicCAS(err, 0, 1) == 0) { err[1] = 20; err[2] = blockIdx.x; }
+                    ok = 0;
+                    break;
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
+// round-robin (circle) schedule: slot j of round k among R+1 slots
 __device__ __forceinline__ int rr_pos(int j, int k, int R) { return j == 0 ? 0 : 1 + (j - 1 + k) % R; }
 
-// state[0] = last round with any rotation (global), state[1] = rounds done
-__global__ void jacobi_kernel(const JGroup* __restrict__ groups, int ngroups, int total_pairs, int max_rounds,
-                              int rmax, double* __restrict__ X, double* __restrict__ V, int* __restrict__ last_rot,
-                              int* state, GridBar* bar, int* err) {
+// ------------------------------------------------ stage a: float32 blocks
+struct BGroup {
+    int64_t x_off;   // column-major X32: n columns of length len
+    int64_t v_off;   // column-major V32: n x n
+    int len, n;
+    int b;           // columns per block
+    int nblk;        // blocks, rounded up to even
+    int rounds;      // nblk - 1
+    int pair0;       // first global block-pair index
+};
+
+// state[0] = last round with a rotation anywhere, state[1] = rounds done
+// fro2[g] = |X_g|_F^2; columns whose squared norm is below 1e-12 fro2 are
+// float32 rounding noise and are not rotated (they would mix forever).
+__global__ void block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups, int total_pairs, int max_rounds,
+                                 int rmax, float* __restrict__ X, float* __restrict__ V, int* __restrict__ last_rot,
+                                 int* state, GridBar* bar, int* err, int stride, const double* __restrict__ fro2) {
+    extern __shared__ float sm[];            // [2b][stride]: X part (len) then V part (n)
+    __shared__ int rotated, skip;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    unsigned epoch = 0;
+    int t = 0;
+    for (; t < max_rounds; ++t) {
+        for (int item = blockIdx.x; item < total_pairs; item += gridDim.x) {
+            int lo = 0, hi = ngroups - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (groups[mid].pair0 <= item) lo = mid; else hi = mid - 1;
+            }
+            const BGroup G = groups[lo];
+            const int R = G.rounds;
+            // one thread decides whether the group has converged, so the
+            // whole CTA takes the same branch around its barriers
+            if (threadIdx.x == 0) skip = (t - *(volatile int*)&last_rot[lo] > R);
+            __syncthreads();
+            const int sk = skip;
+            __syncthreads();   // every thread has read skip before thread 0 rewrites it
+            if (sk) continue;
+            const int i = item - G.pair0, k = t % R;
+            const int bp = rr_pos(i, k, R), bq = rr_pos(G.nblk - 1 - i, k, R);
+            // local column list: block bp then block bq (clipped to n)
+            const int p0 = bp * G.b, p1 = min(G.n, p0 + G.b);
+            const int q0 = bq * G.b, q1 = min(G.n, q0 + G.b);
+            const int np = max(0, p1 - p0), nq = max(0, q1 - q0), nc = np + nq;
+            if (nc < 2) continue;
+            const int L = G.len, Nn = G.n;
+            for (int c = warp; c < nc; c += nwarp) {
+                const int col = c < np ? p0 + c : q0 + (c - np);
+                const float* xs = X + G.x_off + (int64_t)col * L;
+                const float* vs = V + G.v_off + (int64_t)col * Nn;
+                float* d = sm + (size_t)c * stride;
+#pragma unroll 4
+                for (int r = lane; r < L; r += 32) d[r] = xs[r];
+#pragma unroll 4
+                for (int r = lane; r < Nn; r += 32) d[L + r] = vs[r];
+            }
+            if (threadIdx.x == 0) rotated = 0;
+            __syncthreads();
+            const int ne = nc + (nc & 1), Ri = ne - 1;
+            // float32 only has to find the dominant subspace; float64 finishes
+            const float tol = 2e-6f;
+            const float null2 = (float)(1e-12 * fro2[lo]);
+            {
+                for (int ir = 0; ir < Ri; ++ir) {
+                    for (int pr = warp; pr < ne / 2; pr += nwarp) {
+                        const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
+                        if (a >= nc || bb >= nc) continue;
+                        float* xa = sm + (size_t)a * stride;
+                        float* xb = sm + (size_t)bb * stride;
+                        float al = 0.f, be = 0.f, ga = 0.f, al2 = 0.f, be2 = 0.f, ga2 = 0.f;
+                        int r = lane;
+                        for (; r + 32 < L; r += 64) {          // two independent chains
+                            float u = xa[r], v = xb[r], u2 = xa[r + 32], v2 = xb[r + 32];
+                            al = fmaf(u, u, al);
+                            be = fmaf(v, v, be);
+                            ga = fmaf(u, v, ga);
+                            al2 = fmaf(u2, u2, al2);
+                            be2 = fmaf(v2, v2, be2);
+                            ga2 = fmaf(u2, v2, ga2);
+                        }
+                        if (r < L) {
+                            float u = xa[r], v = xb[r];
+                            al = fmaf(u, u, al);
+                            be = fmaf(v, v, be);
+                            ga = fmaf(u, v, ga);
+                        }
+                        al = warp_sum(al + al2);
+                        be = warp_sum(be + be2);
+                        ga = warp_sum(ga + ga2);
+                        if (!(fabsf(ga) > tol * sqrtf(al * be)) || al <= null2 || be <= null2) continue;
+                        const float zeta = (be - al) / (2.0f * ga);
+                        const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                        const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
+#pragma unroll 4
+                        for (int rr = lane; rr < L + Nn; rr += 32) {
+                            float u = xa[rr], v = xb[rr];
+                            xa[rr] = c * u - sn * v;
+                            xb[rr] = sn * u + c * v;
+                        }
+                        if (lane == 0) rotated = 1;
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int c = warp; c < nc; c += nwarp) {
+                const int col = c < np ? p0 + c : q0 + (c - np);
+                float* xs = X + G.x_off + (int64_t)col * L;
+                float* vs = V + G.v_off + (int64_t)col * Nn;
+                const float* d = sm + (size_t)c * stride;
+#pragma unroll 4
+                for (int r = lane; r < L; r += 32) xs[r] = d[r];
+#pragma unroll 4
+                for (int r = lane; r < Nn; r += 32) vs[r] = d[L + r];
+            }
+            if (threadIdx.x == 0 && rotated) {
+                atomicMax(&last_rot[lo], t);
+                atomicMax(&state[0], t);
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
+        if (t - *(volatile int*)&state[0] > rmax) { ++t; break; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
+}
+
+// ------------------------------------------------ stage b: float64 pairs
+struct JGroup {
+    int64_t x_off;   // column-major Y: n columns of length len
+    int len, n;
+    int rounds;
+    int pair0;
+    int grp;         // group (index into fro2)
+};
+
+// columns whose squared norm is below 1e-28 |M_g|_F^2 are float64 rounding
+// noise and are not rotated
+__global__ void jacobi_f64(const JGroup* __restrict__ groups, int ngroups, int total_pairs, int max_rounds, int rmax,
+                           double* __restrict__ X, int* __restrict__ last_rot, int* state, GridBar* bar, int* err,
+                           const double* __restrict__ fro2) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nw = gridDim.x * (blockDim.x >> 5);
-    const double tol = 1e-15;
+    unsigned epoch = 0;
     int t = 0;
     for (; t < max_rounds; ++t) {
         for (int pi = gw; pi < total_pairs; pi += nw) {
@@ -99,67 +242,88 @@ __global__ void jacobi_kernel(const JGroup* __restrict__ groups, int ngroups, in
             }
             const JGroup G = groups[lo];
             const int R = G.rounds;
-            if (t - *(volatile int*)&last_rot[lo] > R) continue;        // converged
-            const int i = pi - G.pair0;
-            const int ne = R + 1;
-            const int k = t % R;
-            int p = rr_pos(i, k, R), q = rr_pos(ne - 1 - i, k, R);
+            if (t - *(volatile int*)&last_rot[lo] > R) continue;
+            const int i = pi - G.pair0, ne = R + 1, k = t % R;
+            const int p = rr_pos(i, k, R), q = rr_pos(ne - 1 - i, k, R);
             if (p >= G.n || q >= G.n) continue;
             double* xp = X + G.x_off + (int64_t)p * G.len;
             double* xq = X + G.x_off + (int64_t)q * G.len;
+            const int L = G.len;
             double a = 0, b = 0, g = 0;
-            for (int r = lane; r < G.len; r += 32) {
-                double u = xp[r], v = xq[r];
-                a = fma(u, u, a);
-                b = fma(v, v, b);
-                g = fma(u, v, g);
+            // chunks of 8 elements per lane: the loads of a chunk are independent
+            for (int r0 = 0; r0 < L; r0 += 256) {
+                double u[8], v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int r = r0 + e * 32 + lane;
+                    u[e] = r < L ? xp[r] : 0.0;
+                    v[e] = r < L ? xq[r] : 0.0;
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    a = fma(u[e], u[e], a);
+                    b = fma(v[e], v[e], b);
+                    g = fma(u[e], v[e], g);
+                }
             }
             a = warp_sum(a);
             b = warp_sum(b);
             g = warp_sum(g);
-            if (!(fabs(g) > tol * sqrt(a * b)) || a == 0.0 || b == 0.0) continue;
+            const double tol = fmax(1e-15, 2.0 * sqrt((double)L) * 1.1102230246251565e-16);
+            const double null2 = 1e-28 * fro2[G.grp];
+            if (!(fabs(g) > tol * sqrt(a * b)) || a <= null2 || b <= null2) continue;
             const double zeta = (b - a) / (2.0 * g);
             const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-            for (int r = lane; r < G.len; r += 32) {
-                double u = xp[r], v = xq[r];
-                xp[r] = c * u - s * v;
-                xq[r] = s * u + c * v;
-            }
-            double* vp = V + G.v_off + (int64_t)p * G.n;
-            double* vq = V + G.v_off + (int64_t)q * G.n;
-            for (int r = lane; r < G.n; r += 32) {
-                double u = vp[r], v = vq[r];
-                vp[r] = c * u - s * v;
-                vq[r] = s * u + c * v;
+            const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+            for (int r0 = 0; r0 < L; r0 += 256) {
+                double u[8], v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int r = r0 + e * 32 + lane;
+                    u[e] = r < L ? xp[r] : 0.0;
+                    v[e] = r < L ? xq[r] : 0.0;
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int r = r0 + e * 32 + lane;
+                    if (r < L) {
+                        xp[r] = c * u[e] - sn * v[e];
+                        xq[r] = sn * u[e] + c * v[e];
+                    }
+                }
             }
             if (lane == 0) {
                 atomicMax(&last_rot[lo], t);
                 atomicMax(&state[0], t);
             }
         }
-        if (!grid_barrier(bar, gridDim.x, err)) break;
+        if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
         if (t - *(volatile int*)&state[0] > rmax) { ++t; break; }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
 
-// sigma of every column; key for ranking
-__global__ void column_norms(const JGroup* __restrict__ groups, int ngroups, const int* __restrict__ col0,
-                             const double* __restrict__ X, double* __restrict__ sig, int* __restrict__ gid,
-                             int* __restrict__ pos) {
-    const int g = blockIdx.x;
-    const JGroup G = groups[g];
+// ------------------------------------------------ helpers
+struct ColSet {      // columns of one group for norms / ranking
+    int64_t off;     // first element of column 0
+    int len, n;
+    int col0;        // first pooled index
+};
+
+template <class T>
+__global__ void column_norms(const ColSet* __restrict__ sets, const T* __restrict__ X, double* __restrict__ sig,
+                             int* __restrict__ gid, int* __restrict__ pos) {
+    const ColSet S = sets[blockIdx.x];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = w; j < G.n; j += nw) {
-        const double* x = X + G.x_off + (int64_t)j * G.len;
+    for (int j = w; j < S.n; j += nw) {
+        const T* x = X + S.off + (int64_t)j * S.len;
         double a = 0;
-        for (int r = lane; r < G.len; r += 32) a = fma(x[r], x[r], a);
+        for (int r = lane; r < S.len; r += 32) a = fma((double)x[r], (double)x[r], a);
         a = warp_sum(a);
         if (lane == 0) {
-            sig[col0[g] + j] = sqrt(a);
-            gid[col0[g] + j] = g;
-            pos[col0[g] + j] = j;
+            sig[S.col0 + j] = sqrt(a);
+            gid[S.col0 + j] = blockIdx.x;
+            pos[S.col0 + j] = j;
         }
     }
 }
@@ -170,7 +334,7 @@ __device__ __forceinline__ bool key_before(double s1, int g1, int p1, double s2,
     return p1 < p2;
 }
 
-// rank of every singular value in the pooled descending order
+// order[rank] = index, pooled order sigma desc, group, position
 __global__ void rank_kernel(const double* __restrict__ sig, const int* __restrict__ gid, const int* __restrict__ pos,
                             int n, int* __restrict__ order) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,40 +346,91 @@ __global__ void rank_kernel(const double* __restrict__ sig, const int* __restric
     order[r] = i;
 }
 
-// Sec. 5 truncation on the sorted values: out[0] = kept, out_d[0] = truncerr
-__global__ void trunc_select(const double* __restrict__ sig, const int* __restrict__ order, int n, double cutoff,
-                             int maxdim, int mindim, int* __restrict__ out, double* __restrict__ out_d) {
+// fro2[g] = sum of squares of group g of X64 (one block per group)
+struct FroSet {
+    int64_t off, n;
+};
+
+__global__ void group_sumsq(const FroSet* __restrict__ S, const double* __restrict__ x, double* __restrict__ out) {
+    __shared__ double red[256];
+    const FroSet f = S[blockIdx.x];
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < f.n; i += blockDim.x) s = fma(x[f.off + i], x[f.off + i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// T = 1.5 I - 0.5 G for every k x k block (Newton-Schulz polar step)
+struct NsSet {
+    int64_t off;
+    int k;
+};
+
+__global__ void ns_shift(const NsSet* __restrict__ S, double* __restrict__ G) {
+    const NsSet f = S[blockIdx.y];
+    const int64_t n = (int64_t)f.k * f.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(e / f.k), j = (int)(e - (int64_t)i * f.k);
+        G[f.off + e] = (i == j ? 1.5 : 0.0) - 0.5 * G[f.off + e];
+    }
+}
+
+// Sum of squares of x[0..n) into out (deterministic, one block)
+__global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(x[i], x[i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// Sec. 5 rule on the ranked candidates: tail(k) = total - sum_{i<k} s_i^2.
+__global__ void trunc_select(const double* __restrict__ sig, const int* __restrict__ order, int n,
+                             const double* __restrict__ total_p, double cutoff, int maxdim, int mindim, int ntotal,
+                             int* __restrict__ out, double* __restrict__ out_d) {
     if (threadIdx.x != 0) return;
-    double total = 0.0;
-    for (int k = n - 1; k >= 0; --k) total += sig[order[k]] * sig[order[k]];
+    const double total = *total_p;
     int keep;
     double err = 0.0;
     if (n == 0) {
         keep = 0;
-    } else if (total == 0.0) {
+    } else if (!(total > 0.0)) {
         keep = min(n, max(1, mindim));
     } else {
-        // tail(k) = sum_{i >= k} s_i^2 / total, summed from the smallest
-        keep = n;
-        double acc = 0.0;
-        for (int k = n; k >= 1; --k) {
-            double s = sig[order[k - 1]];
-            acc += s * s;
-            if (acc / total <= cutoff) keep = k - 1;
-            else break;
+        // the smallest k whose discarded tail is within the cutoff
+        keep = -1;
+        double pre = 0.0;
+        for (int k = 0; k <= n; ++k) {
+            double tail = fmax(total - pre, 0.0) / total;
+            if (tail <= cutoff) { keep = k; break; }
+            if (k < n) {
+                double s = sig[order[k]];
+                pre += s * s;
+            }
         }
+        if (keep < 0) keep = ntotal;
         keep = max(keep, max(1, mindim));
-        keep = min(keep, min(maxdim, n));
-        keep = max(keep, max(min(mindim, n), 1));
-        double tail = 0.0;
-        for (int k = n - 1; k >= keep; --k) tail += sig[order[k]] * sig[order[k]];
-        err = tail / total;
+        keep = min(keep, min(maxdim, ntotal));
+        keep = max(keep, max(min(mindim, ntotal), 1));
+        keep = min(keep, n);
+        double p2 = 0.0;
+        for (int k = 0; k < keep; ++k) p2 += sig[order[k]] * sig[order[k]];
+        err = fmax(total - p2, 0.0) / total;
     }
     out[0] = keep;
     out_d[0] = err;
 }
 
-// copy one block of T into its group matrix (column-major X, maybe transposed)
 struct SvdPack {
     int64_t src;      // T block offset
     int64_t dst;      // X offset of the group
@@ -237,58 +452,155 @@ __global__ void svd_pack(const SvdPack* __restrict__ P, const double* __restrict
     }
 }
 
-__global__ void set_identity(const JGroup* __restrict__ groups, double* __restrict__ V) {
-    const JGroup G = groups[blockIdx.y];
-    const int64_t n2 = (int64_t)G.n * G.n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x)
-        V[G.v_off + e] = (e / G.n == e % G.n) ? 1.0 : 0.0;
+__global__ void to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
 }
 
-// scatter of the kept factors into caller blocks
-struct SvdOut {
-    int64_t dst;      // caller block offset
-    int64_t x_off, v_off;
-    int len, n, trans;
-    int which;        // 0: U block (rows x kept), 1: V block (kept x cols)
-    int rows, cols;   // U: block rows; V: block cols
-    int off;          // roff (U) or coff (V) inside the group matrix
-    int kept;         // kept in this group
-    int perm0;        // first entry in the kept-column permutation
-    int s0;           // first singular value of the group in S
+__global__ void set_identity_f32(const BGroup* __restrict__ groups, float* __restrict__ V) {
+    const BGroup G = groups[blockIdx.y];
+    const int64_t n2 = (int64_t)G.n * G.n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x)
+        V[G.v_off + e] = (e / G.n == e % G.n) ? 1.0f : 0.0f;
+}
+
+// Vc[:, j] = V32[:, cand[j]] (float -> double), per group
+struct CandSet {
+    int64_t v_off;    // V32 group offset
+    int64_t c_off;    // Vc offset
+    int n;            // V32 is n x n
+    int k;            // candidates
+    int cand0;        // first entry in cand[]
 };
 
-// absorb: 0 none, 1 multiply S into U, 2 multiply S into V
-__global__ void svd_scatter(const SvdOut* __restrict__ O, const int* __restrict__ perm, const double* __restrict__ X,
-                            const double* __restrict__ V, const double* __restrict__ sk, int absorb,
-                            double* __restrict__ U, double* __restrict__ Vt) {
-    const SvdOut o = O[blockIdx.y];
-    const int64_t n = (int64_t)(o.which == 0 ? o.rows : o.cols) * o.kept;
-    const bool into_this = (o.which == 0 && absorb == 1) || (o.which == 1 && absorb == 2);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        int k, idx;
-        if (o.which == 0) { idx = (int)(e / o.kept); k = (int)(e - (int64_t)idx * o.kept); }
-        else { k = (int)(e / o.cols); idx = (int)(e - (int64_t)k * o.cols); }
-        const int j = perm[o.perm0 + k];             // source column in the group
-        const double sv = sk[o.s0 + k];
-        const int g = o.off + idx;                   // row (U) or column (V) of M_Q
-        const bool from_x = (o.which == 0) ? !o.trans : o.trans;
-        double v;
-        if (from_x) {
-            // rotated column j of X is sigma_j times a singular vector
-            const double x = X[o.x_off + (int64_t)j * o.len + g];
-            v = into_this ? x : (sv > 0 ? x / sv : 0.0);
-        } else {
-            const double x = V[o.v_off + (int64_t)j * o.n + g];
-            v = into_this ? x * sv : x;
+__global__ void gather_cand(const CandSet* __restrict__ S, const int* __restrict__ cand, const float* __restrict__ V32,
+                            double* __restrict__ Vc) {
+    const CandSet s = S[blockIdx.y];
+    const int64_t tot = (int64_t)s.n * s.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(e / s.n), r = (int)(e - (int64_t)j * s.n);
+        Vc[s.c_off + e] = (double)V32[s.v_off + (int64_t)cand[s.cand0 + j] * s.n + r];
+    }
+}
+
+// C(i,j) = sum_k A(i,k) B(k,j) with explicit strides; 64 x 64 tiles
+struct SGemm {
+    int M, N, K;
+    int64_t a, ars, acs, b, brs, bcs, c, crs, ccs;
+    int nt, tile0;
+};
+
+__global__ void __launch_bounds__(256) sgemm_f64(const SGemm* __restrict__ tasks, int ntasks,
+                                                 const double* __restrict__ A, const double* __restrict__ B,
+                                                 double* __restrict__ C) {
+    __shared__ double As[16][65], Bs[16][65];
+    const int tile = blockIdx.x;
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    const SGemm t = tasks[lo];
+    const int local = tile - t.tile0, mi = local / t.nt, ni = local - mi * t.nt;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < t.K; k0 += 16) {
+        for (int e = tid; e < 1024; e += 256) {
+            int r = e >> 4, kk = e & 15;
+            int gi = mi * 64 + r, gk = k0 + kk;
+            As[kk][r] = (gi < t.M && gk < t.K) ? A[t.a + gi * t.ars + gk * t.acs] : 0.0;
+            int gj = ni * 64 + r;
+            Bs[kk][r] = (gj < t.N && gk < t.K) ? B[t.b + gk * t.brs + gj * t.bcs] : 0.0;
         }
-        if (o.which == 0) U[o.dst + e] = v;
-        else Vt[o.dst + e] = v;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gi = mi * 64 + ty + 16 * i;
+        if (gi >= t.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gj = ni * 64 + tx + 16 * j;
+            if (gj < t.N) C[t.c + gi * t.crs + gj * t.ccs] = acc[i][j];
+        }
+    }
+}
+
+// exact side, normalised: Ex[:, k] = Y[:, perm[k]] / sigma_k
+struct ExSet {
+    int64_t y_off, e_off;
+    int len, k, perm0, s0;
+};
+
+__global__ void form_exact(const ExSet* __restrict__ S, const int* __restrict__ perm, const double* __restrict__ Y,
+                           const double* __restrict__ sk, double* __restrict__ Ex) {
+    const ExSet s = S[blockIdx.y];
+    const int64_t tot = (int64_t)s.len * s.k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int k = (int)(e / s.len), r = (int)(e - (int64_t)k * s.len);
+        double sv = sk[s.s0 + k];
+        Ex[s.e_off + e] = sv > 0 ? Y[s.y_off + (int64_t)perm[s.perm0 + k] * s.len + r] / sv : 0.0;
+    }
+}
+
+// scatter: caller block element (a, b) of a 2-D view = src[off + a*ras + b*rbs] (scaled by sigma_k)
+struct OutPiece {
+    int64_t dst;        // caller block offset
+    int64_t src;        // source offset
+    int64_t ras, rbs;   // source strides for the block's (row, col)
+    int rows, cols;     // block viewed as rows x cols, row-major
+    int kaxis;          // 0: the row index is the kept index k, 1: the column index is
+    int s0;             // first singular value of the group
+    int mode;           // 0: copy, 1: times sigma_k, 2: divided by sigma_k
+    int from_p;         // 0: source is the exact side Ex, 1: the product side P
+};
+
+__global__ void svd_scatter(const OutPiece* __restrict__ O, const double* __restrict__ Ex,
+                            const double* __restrict__ P, const double* __restrict__ sk, double* __restrict__ dst) {
+    const OutPiece o = O[blockIdx.y];
+    const double* src = o.from_p ? P : Ex;
+    const int64_t n = (int64_t)o.rows * o.cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int a = (int)(e / o.cols), b = (int)(e - (int64_t)a * o.cols);
+        double v = src[o.src + a * o.ras + b * o.rbs];
+        if (o.mode) {
+            double sv = sk[o.s0 + (o.kaxis == 0 ? a : b)];
+            v = o.mode == 1 ? v * sv : (sv > 0 ? v / sv : 0.0);
+        }
+        dst[o.dst + e] = v;
     }
 }
 
 __global__ void gather_s(const double* __restrict__ sig, const int* __restrict__ src, int n, double* __restrict__ S) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) S[i] = sig[src[i]];
+}
+
+inline unsigned blocks_for(int64_t n, int cap = 1024) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (n + 255) / 256));
+}
+
+// reset the convergence bookkeeping of a cooperative Jacobi launch
+void reset_state(DevBuf& last, DevBuf& state, DevBuf& bar, int n, cudaStream_t s) {
+    std::vector<int> minus1(n, -1);
+    CUDA_CHECK(cudaMemcpyAsync(last.p, minus1.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    static const int st0[4] = {-1, 0, 0, 0};
+    CUDA_CHECK(cudaMemcpyAsync(state.p, st0, 16, cudaMemcpyHostToDevice, s));
+    CUDA_CHECK(cudaMemsetAsync(bar.p, 0, 16, s));
+    // minus1 is pageable: the copy above is staged before returning
 }
 
 }  // namespace
@@ -298,31 +610,37 @@ struct SvdResult {
     cudaStream_t stream = nullptr;
     int nrow = 0;
     Layout T;
-    std::vector<std::vector<int>> gq;        // charge of each group
-    std::vector<JGroup> groups;
-    std::vector<int> trans;
+    int nq = 0;
+    // groups
+    std::vector<std::vector<int>> gq;
+    std::vector<int> trans, rows, cols, len, n;
+    std::vector<int64_t> xoff;                     // X64 offsets
     std::vector<std::vector<std::vector<int>>> rkeys, ckeys;
     std::vector<std::vector<int>> roff, coff;
-    std::vector<int> col0;                   // first pooled sigma of each group
-    DevBuf X, V, sig;
-    int total = 0;
+    DevBuf X64;
+    // float64 stage
+    std::vector<int> kcand;                        // candidates per group
+    std::vector<int64_t> yoff;                     // Y offsets (len x kcand)
+    std::vector<int> ycol0;                        // first pooled candidate of each group
+    DevBuf Y, sig;
     // kept
-    std::vector<int> kept_g;                 // kept per group
-    std::vector<std::vector<int>> perm;      // kept columns per group (sigma desc)
-    std::vector<int> sect_groups;            // groups with kept > 0, ascending charge
+    std::vector<int> kept_g;
+    std::vector<std::vector<int>> perm;            // kept Y columns per group (sigma desc)
+    std::vector<int> sect_groups;                  // groups with kept > 0, ascending charge
+    std::vector<int> sidx;                         // pooled index of every kept value, output order
     double truncerr = 0.0;
-    int nq = 0;
+    int rounds32 = 0, rounds64 = 0;
 };
 
-std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim,
-                                          int mindim) {
+std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim,
+                                   int exact_side) {
     cudaStream_t s = ctx->stream;
     const int r = T.rank();
     TNH_REQUIRE(nrow >= 1 && nrow < r, TNH_ERR_ARG, "svd_trunc: nrow %d of rank %d", nrow, r);
     TNH_REQUIRE(maxdim >= 1, TNH_ERR_ARG, "svd_trunc: maxdim %d", maxdim);
     auto R = std::make_unique<SvdResult>();
     R->ctx = ctx;
-    R->stream = ctx->stream;
+    R->stream = s;
     R->nrow = nrow;
     R->T = T;
     R->nq = T.nq();
@@ -335,8 +653,9 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         byq[q].push_back(b);
     }
     std::vector<SvdPack> packs;
+    std::vector<BGroup> bg;
     int64_t xo = 0, vo = 0;
-    int pairs = 0, tot = 0, rmax = 1;
+    int bpairs = 0, rmax = 1, stride = 0, bmax = 1;
     for (auto& kv : byq) {
         std::map<std::vector<int>, int> rk, ck;
         for (int b : kv.second) {
@@ -351,32 +670,31 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
             e.second = rows;
             rks.push_back(e.first);
             ro.push_back(rows);
-            int n = 1;
-            for (int i = 0; i < nrow; ++i) n *= T.inds[i].dim[e.first[i]];
-            rows += n;
+            int m = 1;
+            for (int i = 0; i < nrow; ++i) m *= T.inds[i].dim[e.first[i]];
+            rows += m;
         }
         for (auto& e : ck) {
             e.second = cols;
             cks.push_back(e.first);
             co.push_back(cols);
-            int n = 1;
-            for (int i = nrow; i < r; ++i) n *= T.inds[i].dim[e.first[i - nrow]];
-            cols += n;
+            int m = 1;
+            for (int i = nrow; i < r; ++i) m *= T.inds[i].dim[e.first[i - nrow]];
+            cols += m;
         }
-        const int tr = rows < cols ? 1 : 0;
-        JGroup G{};
-        G.len = tr ? cols : rows;
-        G.n = tr ? rows : cols;
+        // exact_side 0: U exact (orthogonalise the columns of M); 1: V exact (of M^T)
+        const int tr = exact_side == 1 ? 1 : 0;
+        const int L = tr ? cols : rows, Nn = tr ? rows : cols;
+        BGroup G{};
         G.x_off = xo;
         G.v_off = vo;
-        G.rounds = std::max(1, G.n + (G.n & 1) - 1);
-        G.pair0 = pairs;
-        G.npairs = (G.n + 1) / 2;
-        rmax = std::max(rmax, G.rounds);
-        for (int b : kv.second) {
-            auto key = T.key(b);
+        G.len = L;
+        G.n = Nn;
+        stride = std::max(stride, L + Nn);
+        for (int bl : kv.second) {
+            auto key = T.key(bl);
             SvdPack p{};
-            p.src = T.off[b];
+            p.src = T.off[bl];
             p.dst = xo;
             int rn = 1, cn = 1;
             for (int i = 0; i < nrow; ++i) rn *= T.inds[i].dim[key[i]];
@@ -385,101 +703,344 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
             p.cols = cn;
             p.roff = rk[std::vector<int>(key.begin(), key.begin() + nrow)];
             p.coff = ck[std::vector<int>(key.begin() + nrow, key.end())];
-            p.len = G.len;
+            p.len = L;
             p.trans = tr;
             packs.push_back(p);
         }
-        xo += (int64_t)G.len * G.n;
-        vo += (int64_t)G.n * G.n;
-        pairs += G.npairs;
-        R->col0.push_back(tot);
-        tot += G.n;
-        R->groups.push_back(G);
-        R->trans.push_back(tr);
         R->gq.push_back(kv.first);
+        R->trans.push_back(tr);
+        R->rows.push_back(rows);
+        R->cols.push_back(cols);
+        R->len.push_back(L);
+        R->n.push_back(Nn);
+        R->xoff.push_back(xo);
         R->rkeys.push_back(rks);
         R->ckeys.push_back(cks);
         R->roff.push_back(ro);
         R->coff.push_back(co);
+        bg.push_back(G);
+        xo += (int64_t)L * Nn;
+        vo += (int64_t)Nn * Nn;
     }
-    R->total = tot;
-    const int ng = (int)R->groups.size();
+    const int ng = (int)bg.size();
     if (ng == 0) return R;
-    R->X.alloc((size_t)xo * 8);
-    R->V.alloc((size_t)vo * 8);
-    R->sig.alloc((size_t)tot * 8);
-    CUDA_CHECK(cudaMemsetAsync(R->X.p, 0, (size_t)xo * 8, s));
-    DevBuf d_groups = upload(R->groups, s);
-    DevBuf d_packs = upload(packs, s);
-    DevBuf d_col0 = upload(R->col0, s);
-    { KScope ks_("svd_pack", s);
-    svd_pack<<<dim3(16, (unsigned)packs.size()), 256, 0, s>>>(d_packs.as<SvdPack>(), T.data, R->X.as<double>());
+    // one block width for all groups: up to 8 columns while a block pair
+    // (X and V columns) fits in shared memory
+    bmax = 8;
+    while (bmax > 1 && (size_t)2 * bmax * stride * 4 > 200 * 1024) bmax >>= 1;
+    for (auto& G : bg) {
+        G.b = bmax;
+        int nb = (G.n + bmax - 1) / bmax;
+        G.nblk = std::max(2, nb + (nb & 1));
+        G.rounds = G.nblk - 1;
+        G.pair0 = bpairs;
+        bpairs += G.nblk / 2;
+        rmax = std::max(rmax, G.rounds);
     }
-    { KScope ks_("set_identity", s);
-    set_identity<<<dim3(16, ng), 256, 0, s>>>(d_groups.as<JGroup>(), R->V.as<double>());
-    }
-    // ---- Jacobi
-    DevBuf d_last((size_t)ng * 4), d_state(16), d_bar(16);
-    std::vector<int> minus1(ng, -1);
-    CUDA_CHECK(cudaMemcpyAsync(d_last.p, minus1.data(), (size_t)ng * 4, cudaMemcpyHostToDevice, s));
-    int st0[4] = {-1, 0, 0, 0};
-    CUDA_CHECK(cudaMemcpyAsync(d_state.p, st0, 16, cudaMemcpyHostToDevice, s));
-    CUDA_CHECK(cudaMemsetAsync(d_bar.p, 0, 16, s));
-    int bpsm = 0;
-    const int threads = 256;
-    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, jacobi_kernel, threads, 0));
-    int want = (pairs + (threads / 32) - 1) / (threads / 32);
-    int grid = std::max(1, std::min(want, std::max(1, bpsm) * ctx->num_sms));
-    int max_rounds = 40 * rmax + 8;
-    const JGroup* gp = d_groups.as<JGroup>();
-    double* Xp = R->X.as<double>();
-    double* Vp = R->V.as<double>();
-    int* lastp = d_last.as<int>();
-    int* statep = d_state.as<int>();
-    GridBar* barp = d_bar.as<GridBar>();
+    int ntot = 0;
+    for (int g = 0; g < ng; ++g) ntot += R->n[g];
     int* errp = ctx->d_flag.as<int>();
-    void* args[] = {(void*)&gp, (void*)&ng, (void*)&pairs, (void*)&max_rounds, (void*)&rmax, (void*)&Xp,
-                    (void*)&Vp, (void*)&lastp, (void*)&statep, (void*)&barp, (void*)&errp};
+    // ---- pack, float32 copy, identity
+    R->X64.alloc((size_t)xo * 8);
+    DevBuf X32((size_t)xo * 4), V32((size_t)vo * 4);
+    CUDA_CHECK(cudaMemsetAsync(R->X64.p, 0, (size_t)xo * 8, s));
+    DevBuf d_bg = upload(bg, s), d_packs = upload(packs, s);
     {
-        KScope ks("jacobi_svd", s);
-        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(threads), args, 0, s));
+        KScope ks("svd_pack", s);
+        svd_pack<<<dim3(16, (unsigned)packs.size()), 256, 0, s>>>(d_packs.as<SvdPack>(), T.data, R->X64.as<double>());
     }
-    // ---- sigma, ranking, truncation
-    DevBuf d_gid((size_t)tot * 4), d_pos((size_t)tot * 4), d_order((size_t)tot * 4), d_out(16), d_outd(16);
-    { KScope ks_("column_norms", s);
-    column_norms<<<ng, 256, 0, s>>>(gp, ng, d_col0.as<int>(), Xp, R->sig.as<double>(), d_gid.as<int>(),
-                                     d_pos.as<int>());
+    DevBuf d_fro2((size_t)ng * 8);
+    {
+        std::vector<FroSet> fs(ng);
+        for (int g = 0; g < ng; ++g) fs[g] = FroSet{R->xoff[g], (int64_t)R->len[g] * R->n[g]};
+        DevBuf d_fs = upload(fs, s);
+        KScope ks("svd_group_sumsq", s);
+        group_sumsq<<<ng, 256, 0, s>>>(d_fs.as<FroSet>(), R->X64.as<double>(), d_fro2.as<double>());
+        CUDA_CHECK(cudaStreamSynchronize(s));   // d_fs is freed on scope exit
     }
-    { KScope ks_("rank_kernel", s);
-    rank_kernel<<<(tot + 255) / 256, 256, 0, s>>>(R->sig.as<double>(), d_gid.as<int>(), d_pos.as<int>(), tot,
-                                                  d_order.as<int>());
+    const double* frop = d_fro2.as<double>();
+    {
+        KScope ks("svd_to_f32", s);
+        to_f32<<<blocks_for(xo, 4096), 256, 0, s>>>(R->X64.as<double>(), X32.as<float>(), xo);
     }
-    { KScope ks_("trunc_select", s);
-    trunc_select<<<1, 32, 0, s>>>(R->sig.as<double>(), d_order.as<int>(), tot, cutoff, maxdim, mindim,
-                                  d_out.as<int>(), d_outd.as<double>());
+    {
+        KScope ks("svd_set_identity", s);
+        set_identity_f32<<<dim3(16, ng), 256, 0, s>>>(d_bg.as<BGroup>(), V32.as<float>());
     }
-    int keep = 0;
-    int state_h[2];
-    CUDA_CHECK(cudaMemcpyAsync(&keep, d_out.p, 4, cudaMemcpyDeviceToHost, s));
-    CUDA_CHECK(cudaMemcpyAsync(&R->truncerr, d_outd.p, 8, cudaMemcpyDeviceToHost, s));
-    CUDA_CHECK(cudaMemcpyAsync(state_h, d_state.p, 8, cudaMemcpyDeviceToHost, s));
-    std::vector<int> order(tot), gid(tot), pos(tot);
-    CUDA_CHECK(cudaMemcpyAsync(order.data(), d_order.p, (size_t)tot * 4, cudaMemcpyDeviceToHost, s));
-    CUDA_CHECK(cudaMemcpyAsync(gid.data(), d_gid.p, (size_t)tot * 4, cudaMemcpyDeviceToHost, s));
-    CUDA_CHECK(cudaMemcpyAsync(pos.data(), d_pos.p, (size_t)tot * 4, cudaMemcpyDeviceToHost, s));
+    // ---- stage a: float32 block Jacobi
+    {
+        DevBuf d_last((size_t)ng * 4), d_state(16), d_bar(16);
+        reset_state(d_last, d_state, d_bar, ng, s);
+        const int threads = 256;
+        size_t smem = (size_t)2 * bmax * stride * 4;
+        CUDA_CHECK(cudaFuncSetAttribute(block_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int bpsm = 0;
+        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, block_jacobi_f32, threads, smem));
+        TNH_REQUIRE(bpsm >= 1, TNH_ERR_CUDA, "svd: block Jacobi does not fit on an SM");
+        int grid = std::max(1, std::min(bpairs, bpsm * ctx->num_sms));
+        int max_rounds = 30 * rmax + 4;
+        const BGroup* gp = d_bg.as<BGroup>();
+        float* Xp = X32.as<float>();
+        float* Vp = V32.as<float>();
+        int* lastp = d_last.as<int>();
+        int* statep = d_state.as<int>();
+        GridBar* barp = d_bar.as<GridBar>();
+        void* args[] = {(void*)&gp,    (void*)&ng,     (void*)&bpairs, (void*)&max_rounds, (void*)&rmax,
+                        (void*)&Xp,    (void*)&Vp,     (void*)&lastp,  (void*)&statep,     (void*)&barp,
+                        (void*)&errp,  (void*)&stride, (void*)&frop};
+        {
+            KScope ks("svd_jacobi_f32", s);
+            CUDA_CHECK(cudaLaunchCooperativeKernel((void*)block_jacobi_f32, dim3(grid), dim3(threads), args, smem, s));
+        }
+        int st[2];
+        CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));   // bookkeeping buffers are freed on scope exit
+        R->rounds32 = st[1];
+        if (std::getenv("TNH_DEBUG"))
+            std::fprintf(stderr, "svd: float32 block Jacobi %d rounds (max %d, per sweep %d, grid %d, b %d)\n", st[1],
+                         max_rounds, rmax, grid, bmax);
+    }
+    // ---- rank the float32 singular values, pick the candidates
+    std::vector<ColSet> cs32(ng);
+    for (int g = 0, c0 = 0; g < ng; ++g) {
+        cs32[g] = ColSet{R->xoff[g], R->len[g], R->n[g], c0};
+        c0 += R->n[g];
+    }
+    DevBuf d_cs32 = upload(cs32, s);
+    DevBuf sig32((size_t)ntot * 8), gid((size_t)ntot * 4), pos((size_t)ntot * 4), order((size_t)ntot * 4);
+    {
+        KScope ks("svd_norms", s);
+        column_norms<float><<<ng, 256, 0, s>>>(d_cs32.as<ColSet>(), X32.as<float>(), sig32.as<double>(),
+                                                gid.as<int>(), pos.as<int>());
+    }
+    {
+        KScope ks("svd_rank", s);
+        rank_kernel<<<(ntot + 255) / 256, 256, 0, s>>>(sig32.as<double>(), gid.as<int>(), pos.as<int>(), ntot,
+                                                       order.as<int>());
+    }
+    std::vector<int> h_order(ntot), h_gid(ntot), h_pos(ntot);
+    CUDA_CHECK(cudaMemcpyAsync(h_order.data(), order.p, (size_t)ntot * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaMemcpyAsync(h_gid.data(), gid.p, (size_t)ntot * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaMemcpyAsync(h_pos.data(), pos.p, (size_t)ntot * 4, cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
     check_device_flag(ctx);
-    TNH_REQUIRE(state_h[1] < max_rounds, TNH_ERR_NOT_CONVERGED,
-                "svd_trunc: Jacobi did not converge in %d rounds", max_rounds);
+    // candidates: at least max(maxdim, mindim) + 32, and every column whose
+    // float32 singular value is within 1e-4 of the largest. Restricting the
+    // float64 polish to a subspace biases sigma_i^2 by at most
+    // sigma_excluded^2 sin^2(angle) (angle ~ float32 accuracy), so excluded
+    // columns below 1e-4 sigma_max shift no sigma^2 by more than ~1e-20
+    // sigma_max^2.
+    std::vector<double> h_sig32(ntot);
+    CUDA_CHECK(cudaMemcpy(h_sig32.data(), sig32.p, (size_t)ntot * 8, cudaMemcpyDeviceToHost));
+    const double smax = ntot ? h_sig32[h_order[0]] : 0.0;
+    int ncand = std::min(ntot, std::max(maxdim, mindim) + 32);
+    while (ncand < ntot && h_sig32[h_order[ncand]] >= 1e-4 * smax) ++ncand;
+    std::vector<std::vector<int>> cand(ng);
+    for (int k = 0; k < ncand; ++k) cand[h_gid[h_order[k]]].push_back(h_pos[h_order[k]]);
+    // ---- float64 re-formation Y = X64 V32[:, cand]
+    std::vector<CandSet> csets;
+    std::vector<int> candflat;
+    std::vector<SGemm> gemms;
+    std::vector<JGroup> jg;
+    R->kcand.assign(ng, 0);
+    R->yoff.assign(ng, 0);
+    R->ycol0.assign(ng, 0);
+    int64_t yo = 0, vco = 0;
+    int tiles = 0, jpairs = 0, jrmax = 1, yc = 0;
+    for (int g = 0; g < ng; ++g) {
+        const int k = (int)cand[g].size();
+        R->kcand[g] = k;
+        R->yoff[g] = yo;
+        R->ycol0[g] = yc;
+        if (k == 0) continue;
+        csets.push_back(CandSet{bg[g].v_off, vco, R->n[g], k, (int)candflat.size()});
+        candflat.insert(candflat.end(), cand[g].begin(), cand[g].end());
+        SGemm t{};
+        t.M = R->len[g];
+        t.N = k;
+        t.K = R->n[g];
+        t.a = R->xoff[g];
+        t.ars = 1;
+        t.acs = R->len[g];
+        t.b = vco;
+        t.brs = 1;
+        t.bcs = R->n[g];
+        t.c = yo;
+        t.crs = 1;
+        t.ccs = R->len[g];
+        t.nt = (k + 63) / 64;
+        t.tile0 = tiles;
+        tiles += ((t.M + 63) / 64) * t.nt;
+        gemms.push_back(t);
+        JGroup J{};
+        J.x_off = yo;
+        J.len = R->len[g];
+        J.n = k;
+        J.rounds = std::max(1, k + (k & 1) - 1);
+        J.pair0 = jpairs;
+        J.grp = g;
+        jpairs += (k + 1) / 2;
+        jrmax = std::max(jrmax, J.rounds);
+        jg.push_back(J);
+        vco += (int64_t)R->n[g] * k;
+        yo += (int64_t)R->len[g] * k;
+        yc += k;
+    }
+    R->Y.alloc((size_t)std::max<int64_t>(yo, 1) * 8);
+    {
+        DevBuf Vc((size_t)std::max<int64_t>(vco, 1) * 8);
+        DevBuf d_cs = upload(csets, s), d_cand = upload(candflat, s), d_gm = upload(gemms, s);
+        {
+            KScope ks("svd_gather_cand", s);
+            gather_cand<<<dim3(16, (unsigned)csets.size()), 256, 0, s>>>(d_cs.as<CandSet>(), d_cand.as<int>(),
+                                                                          V32.as<float>(), Vc.as<double>());
+        }
+        // V32 is orthogonal only to float32 accuracy, and the singular values
+        // of X V32 differ from those of X at first order in that error:
+        // re-orthonormalise the candidate columns in float64 by two
+        // Newton-Schulz steps Vc <- Vc (3 I - Vc^T Vc) / 2 (quadratic).
+        {
+            std::vector<SGemm> g1, g2;
+            std::vector<NsSet> ns;
+            int64_t go = 0;
+            int t1 = 0, t2 = 0;
+            for (const CandSet& c : csets) {
+                SGemm a{};   // G = Vc^T Vc (k x k, row-major)
+                a.M = c.k; a.N = c.k; a.K = c.n;
+                a.a = c.c_off; a.ars = c.n; a.acs = 1;
+                a.b = c.c_off; a.brs = 1; a.bcs = c.n;
+                a.c = go; a.crs = c.k; a.ccs = 1;
+                a.nt = (c.k + 63) / 64; a.tile0 = t1;
+                t1 += ((c.k + 63) / 64) * a.nt;
+                g1.push_back(a);
+                SGemm b{};   // Vc' = Vc T (n x k, column-major)
+                b.M = c.n; b.N = c.k; b.K = c.k;
+                b.a = c.c_off; b.ars = 1; b.acs = c.n;
+                b.b = go; b.brs = c.k; b.bcs = 1;
+                b.c = c.c_off; b.crs = 1; b.ccs = c.n;
+                b.nt = (c.k + 63) / 64; b.tile0 = t2;
+                t2 += ((c.n + 63) / 64) * b.nt;
+                g2.push_back(b);
+                ns.push_back(NsSet{go, c.k});
+                go += (int64_t)c.k * c.k;
+            }
+            DevBuf Gb((size_t)std::max<int64_t>(go, 1) * 8), Vc2((size_t)std::max<int64_t>(vco, 1) * 8);
+            DevBuf d_g1 = upload(g1, s), d_g2 = upload(g2, s), d_ns = upload(ns, s);
+            for (int it = 0; it < 2; ++it) {
+                {
+                    KScope ks("svd_sgemm_f64", s);
+                    sgemm_f64<<<t1, 256, 0, s>>>(d_g1.as<SGemm>(), (int)g1.size(), Vc.as<double>(), Vc.as<double>(),
+                                                 Gb.as<double>());
+                }
+                {
+                    KScope ks("svd_ns_shift", s);
+                    ns_shift<<<dim3(8, (unsigned)ns.size()), 256, 0, s>>>(d_ns.as<NsSet>(), Gb.as<double>());
+                }
+                {
+                    KScope ks("svd_sgemm_f64", s);
+                    sgemm_f64<<<t2, 256, 0, s>>>(d_g2.as<SGemm>(), (int)g2.size(), Vc.as<double>(), Gb.as<double>(),
+                                                 Vc2.as<double>());
+                }
+                std::swap(Vc, Vc2);
+            }
+            {
+                KScope ks("svd_sgemm_f64", s);
+                sgemm_f64<<<tiles, 256, 0, s>>>(d_gm.as<SGemm>(), (int)gemms.size(), R->X64.as<double>(),
+                                                 Vc.as<double>(), R->Y.as<double>());
+            }
+            CUDA_CHECK(cudaStreamSynchronize(s));   // temporaries are freed on scope exit
+        }
+    }
+    // ---- stage b: float64 polish
+    {
+        const int njg = (int)jg.size();
+        DevBuf d_jg = upload(jg, s);
+        DevBuf d_last((size_t)njg * 4), d_state(16), d_bar(16);
+        reset_state(d_last, d_state, d_bar, njg, s);
+        const int threads = 32;   // one column pair per CTA spreads float64 work over the SMs
+        int bpsm = 0;
+        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, jacobi_f64, threads, 0));
+        int want = jpairs;
+        int grid = std::max(1, std::min(want, std::max(1, bpsm) * ctx->num_sms));
+        int max_rounds = 20 * jrmax + 8;
+        const JGroup* gp = d_jg.as<JGroup>();
+        double* Yp = R->Y.as<double>();
+        int* lastp = d_last.as<int>();
+        int* statep = d_state.as<int>();
+        GridBar* barp = d_bar.as<GridBar>();
+        void* args[] = {(void*)&gp,    (void*)&njg,    (void*)&jpairs, (void*)&max_rounds, (void*)&jrmax,
+                        (void*)&Yp,    (void*)&lastp,  (void*)&statep, (void*)&barp,       (void*)&errp,
+                        (void*)&frop};
+        {
+            KScope ks("svd_jacobi_f64", s);
+            CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_f64, dim3(grid), dim3(threads), args, 0, s));
+        }
+        int st[2];
+        CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+        check_device_flag(ctx);
+        R->rounds64 = st[1];
+        if (std::getenv("TNH_DEBUG"))
+            std::fprintf(stderr, "svd: float64 Jacobi %d rounds (max %d, per sweep %d, grid %d)\n", st[1], max_rounds,
+                         jrmax, grid);
+        TNH_REQUIRE(st[1] < max_rounds, TNH_ERR_NOT_CONVERGED, "svd_trunc: float64 Jacobi did not converge");
+    }
+    // ---- float64 singular values, ranking, truncation
+    const int ny = yc;
+    std::vector<ColSet> cs64;
+    std::vector<int> cs_group;
+    for (int g = 0; g < ng; ++g)
+        if (R->kcand[g]) {
+            cs64.push_back(ColSet{R->yoff[g], R->len[g], R->kcand[g], R->ycol0[g]});
+            cs_group.push_back(g);
+        }
+    DevBuf d_cs64 = upload(cs64, s);
+    R->sig.alloc((size_t)std::max(ny, 1) * 8);
+    DevBuf gid2((size_t)std::max(ny, 1) * 4), pos2((size_t)std::max(ny, 1) * 4), ord2((size_t)std::max(ny, 1) * 4);
+    DevBuf total(16), outi(16), outd(16);
+    {
+        KScope ks("svd_norms", s);
+        column_norms<double><<<(unsigned)cs64.size(), 256, 0, s>>>(d_cs64.as<ColSet>(), R->Y.as<double>(),
+                                                                   R->sig.as<double>(), gid2.as<int>(), pos2.as<int>());
+    }
+    {
+        KScope ks("svd_rank", s);
+        rank_kernel<<<(ny + 255) / 256, 256, 0, s>>>(R->sig.as<double>(), gid2.as<int>(), pos2.as<int>(), ny,
+                                                     ord2.as<int>());
+    }
+    {
+        KScope ks("svd_sumsq", s);
+        sumsq_kernel<<<1, 256, 0, s>>>(R->X64.as<double>(), xo, total.as<double>());
+    }
+    {
+        KScope ks("svd_trunc_select", s);
+        trunc_select<<<1, 32, 0, s>>>(R->sig.as<double>(), ord2.as<int>(), ny, total.as<double>(), cutoff, maxdim,
+                                      mindim, ntot, outi.as<int>(), outd.as<double>());
+    }
+    int keep = 0;
+    std::vector<int> o2(ny), g2(ny), p2(ny);
+    CUDA_CHECK(cudaMemcpyAsync(&keep, outi.p, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaMemcpyAsync(&R->truncerr, outd.p, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaMemcpyAsync(o2.data(), ord2.p, (size_t)ny * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaMemcpyAsync(g2.data(), gid2.p, (size_t)ny * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaMemcpyAsync(p2.data(), pos2.p, (size_t)ny * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    check_device_flag(ctx);
     R->kept_g.assign(ng, 0);
     R->perm.assign(ng, {});
+    std::vector<std::vector<int>> pooled(ng);
     for (int k = 0; k < keep; ++k) {
-        int i = order[k];
-        R->perm[gid[i]].push_back(pos[i]);
-        R->kept_g[gid[i]]++;
+        int i = o2[k];
+        int g = cs_group[g2[i]];
+        R->perm[g].push_back(p2[i]);
+        pooled[g].push_back(i);
+        R->kept_g[g]++;
     }
     for (int g = 0; g < ng; ++g)
-        if (R->kept_g[g] > 0) R->sect_groups.push_back(g);
+        if (R->kept_g[g] > 0) {
+            R->sect_groups.push_back(g);
+            R->sidx.insert(R->sidx.end(), pooled[g].begin(), pooled[g].end());
+        }
     return R;
 }
 
@@ -504,82 +1065,182 @@ void svd_get(SvdResult& R, const Layout& U, double* S, const Layout& Vl, int abs
         TNH_REQUIRE(Vl.inds[i - nrow + 1].same_space(R.T.inds[i]), TNH_ERR_SHAPE, "svd_get: V index %d differs", i);
     CUDA_CHECK(cudaMemsetAsync(U.data, 0, (size_t)U.size * 8, s));
     CUDA_CHECK(cudaMemsetAsync(Vl.data, 0, (size_t)Vl.size * 8, s));
-    std::vector<SvdOut> outs;
-    std::vector<int> perm, sidx;
+    if (ns == 0) return;
+    // kept singular values in output order
+    DevBuf d_sidx = upload(R.sidx, s);
+    const int nk = (int)R.sidx.size();
+    DevBuf sk((size_t)nk * 8);
+    {
+        KScope ks("svd_gather_s", s);
+        gather_s<<<(nk + 255) / 256, 256, 0, s>>>(R.sig.as<double>(), d_sidx.as<int>(), nk, sk.as<double>());
+    }
+    // exact side Ex (len x kept, column-major) and the product side P
+    std::vector<ExSet> ex;
+    std::vector<int> permflat;
+    std::vector<SGemm> gm;
+    int64_t eo = 0, po = 0;
+    int tiles = 0, s0 = 0;
+    std::vector<int64_t> e_off(ns), p_off(ns);
+    std::vector<int> s_first(ns);
     for (int k = 0; k < ns; ++k) {
-        const int g = R.sect_groups[k];
-        const JGroup& G = R.groups[g];
-        const int p0 = (int)perm.size();
-        const int s0 = (int)sidx.size();
-        for (int j : R.perm[g]) {
-            perm.push_back(j);
-            sidx.push_back(R.col0[g] + j);
+        const int g = R.sect_groups[k], kk = R.kept_g[g], L = R.len[g];
+        ex.push_back(ExSet{R.yoff[g], eo, L, kk, (int)permflat.size(), s0});
+        permflat.insert(permflat.end(), R.perm[g].begin(), R.perm[g].end());
+        e_off[k] = eo;
+        p_off[k] = po;
+        s_first[k] = s0;
+        SGemm t{};
+        const int64_t xg = R.xoff[g];
+        if (!R.trans[g]) {
+            // P = Ex^T M (kept x cols, row-major); M(i, c) = X64[xg + c*len + i]
+            t.M = kk;
+            t.N = R.cols[g];
+            t.K = R.rows[g];
+            t.a = eo;
+            t.ars = L;
+            t.acs = 1;
+            t.b = xg;
+            t.brs = 1;
+            t.bcs = L;
+            t.c = po;
+            t.crs = R.cols[g];
+            t.ccs = 1;
+        } else {
+            // P = M Ex (rows x kept, column-major), computed as P^T = Ex^T M^T so
+            // that A is the Ex buffer and B the X64 buffer as in the launch;
+            // M(i, c) = X64[xg + i*len + c], Ex(c, k) = Ex[eo + k*len + c]
+            t.M = kk;
+            t.N = R.rows[g];
+            t.K = R.cols[g];
+            t.a = eo;
+            t.ars = L;
+            t.acs = 1;
+            t.b = xg;
+            t.brs = 1;
+            t.bcs = L;
+            t.c = po;
+            t.crs = R.rows[g];
+            t.ccs = 1;
         }
+        t.nt = (t.N + 63) / 64;
+        t.tile0 = tiles;
+        tiles += ((t.M + 63) / 64) * t.nt;
+        gm.push_back(t);
+        eo += (int64_t)L * kk;
+        po += (int64_t)kk * (R.trans[g] ? R.rows[g] : R.cols[g]);
+        s0 += kk;
+    }
+    DevBuf Ex((size_t)eo * 8), Pb((size_t)po * 8);
+    DevBuf d_ex = upload(ex, s), d_perm = upload(permflat, s), d_gm = upload(gm, s);
+    {
+        KScope ks("svd_form_exact", s);
+        form_exact<<<dim3(16, (unsigned)ex.size()), 256, 0, s>>>(d_ex.as<ExSet>(), d_perm.as<int>(), R.Y.as<double>(),
+                                                                 sk.as<double>(), Ex.as<double>());
+    }
+    {
+        KScope ks("svd_sgemm_f64", s);
+        sgemm_f64<<<tiles, 256, 0, s>>>(d_gm.as<SGemm>(), (int)gm.size(), Ex.as<double>(), R.X64.as<double>(),
+                                         Pb.as<double>());
+    }
+    // scatter into the caller's blocks
+    std::vector<OutPiece> uo, vo;
+    for (int k = 0; k < ns; ++k) {
+        const int g = R.sect_groups[k], kk = R.kept_g[g];
+        const bool tr = R.trans[g];
         for (size_t a = 0; a < R.rkeys[g].size(); ++a) {
             std::vector<int> key = R.rkeys[g][a];
             key.push_back(k);
             int b = U.find(key);
             TNH_REQUIRE(b >= 0, TNH_ERR_SHAPE, "svd_get: U layout lacks a block");
-            SvdOut o{};
-            o.dst = U.off[b];
-            o.x_off = G.x_off;
-            o.v_off = G.v_off;
-            o.len = G.len;
-            o.n = G.n;
-            o.trans = R.trans[g];
-            o.which = 0;
             int rn = 1;
             for (int i = 0; i < nrow; ++i) rn *= R.T.inds[i].dim[R.rkeys[g][a][i]];
+            const int ro = R.roff[g][a];
+            OutPiece o{};
+            o.dst = U.off[b];
             o.rows = rn;
-            o.cols = 0;
-            o.off = R.roff[g][a];
-            o.kept = R.kept_g[g];
-            o.perm0 = p0;
-            o.s0 = s0;
-            outs.push_back(o);
+            o.cols = kk;
+            o.kaxis = 1;
+            o.s0 = s_first[k];
+            if (!tr) {   // U = Ex (column-major, len = rows)
+                o.src = e_off[k] + ro;
+                o.ras = 1;
+                o.rbs = R.len[g];
+                o.mode = absorb == 1 ? 1 : 0;
+                o.from_p = 0;
+            } else {     // U S = P (column-major rows x kept)
+                o.src = p_off[k] + ro;
+                o.ras = 1;
+                o.rbs = R.rows[g];
+                o.mode = absorb == 1 ? 0 : 2;
+                o.from_p = 1;
+            }
+            uo.push_back(o);
         }
         for (size_t a = 0; a < R.ckeys[g].size(); ++a) {
             std::vector<int> key{k};
             key.insert(key.end(), R.ckeys[g][a].begin(), R.ckeys[g][a].end());
             int b = Vl.find(key);
             TNH_REQUIRE(b >= 0, TNH_ERR_SHAPE, "svd_get: V layout lacks a block");
-            SvdOut o{};
-            o.dst = Vl.off[b];
-            o.x_off = G.x_off;
-            o.v_off = G.v_off;
-            o.len = G.len;
-            o.n = G.n;
-            o.trans = R.trans[g];
-            o.which = 1;
             int cn = 1;
             for (int i = nrow; i < r; ++i) cn *= R.T.inds[i].dim[R.ckeys[g][a][i - nrow]];
-            o.rows = 0;
+            const int co = R.coff[g][a];
+            OutPiece o{};
+            o.dst = Vl.off[b];
+            o.rows = kk;
             o.cols = cn;
-            o.off = R.coff[g][a];
-            o.kept = R.kept_g[g];
-            o.perm0 = p0;
-            o.s0 = s0;
-            outs.push_back(o);
+            o.kaxis = 0;
+            o.s0 = s_first[k];
+            if (!tr) {   // S V^T = P (row-major kept x cols)
+                o.src = p_off[k] + co;
+                o.ras = R.cols[g];
+                o.rbs = 1;
+                o.mode = absorb == 2 ? 0 : 2;
+                o.from_p = 1;
+            } else {     // V^T rows = Ex columns (len = cols)
+                o.src = e_off[k] + co;
+                o.ras = R.len[g];
+                o.rbs = 1;
+                o.mode = absorb == 2 ? 1 : 0;
+                o.from_p = 0;
+            }
+            vo.push_back(o);
         }
     }
-    if (outs.empty()) return;
-    DevBuf d_outs = upload(outs, s), d_perm = upload(perm, s), d_sidx = upload(sidx, s);
-    // singular values in output order (sector, desc)
-    DevBuf d_sk((size_t)std::max<size_t>(sidx.size(), 1) * 8);
-    { KScope ks_("gather_s", s);
-    gather_s<<<((int)sidx.size() + 255) / 256, 256, 0, s>>>(R.sig.as<double>(), d_sidx.as<int>(), (int)sidx.size(),
-                                                            d_sk.as<double>());
+    DevBuf d_uo = upload(uo, s), d_vo = upload(vo, s);
+    {
+        KScope ks("svd_scatter", s);
+        svd_scatter<<<dim3(8, (unsigned)uo.size()), 256, 0, s>>>(d_uo.as<OutPiece>(), Ex.as<double>(),
+                                                                 Pb.as<double>(), sk.as<double>(), U.data);
     }
-    { KScope ks_("svd_scatter", s);
-    svd_scatter<<<dim3(8, (unsigned)outs.size()), 256, 0, s>>>(d_outs.as<SvdOut>(), d_perm.as<int>(),
-                                                               R.X.as<double>(), R.V.as<double>(), d_sk.as<double>(),
-                                                               absorb, U.data, Vl.data);
+    {
+        KScope ks("svd_scatter", s);
+        svd_scatter<<<dim3(8, (unsigned)vo.size()), 256, 0, s>>>(d_vo.as<OutPiece>(), Ex.as<double>(),
+                                                                 Pb.as<double>(), sk.as<double>(), Vl.data);
     }
-    if (S)
-        CUDA_CHECK(cudaMemcpyAsync(S, d_sk.p, sidx.size() * 8, cudaMemcpyDeviceToDevice, s));
+    if (S) CUDA_CHECK(cudaMemcpyAsync(S, sk.p, (size_t)nk * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
     check_device_flag(ctx);
 }
+
+SvdResult* svd_run(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim, int exact_side) {
+    return run_svd(ctx, T, nrow, cutoff, maxdim, mindim, exact_side).release();
+}
+
+SvdShape svd_shape(const SvdResult* R) {
+    SvdShape sh;
+    for (int g : R->sect_groups) {
+        sh.qn.push_back(R->gq[g]);
+        sh.dims.push_back(R->kept_g[g]);
+    }
+    sh.truncerr = R->truncerr;
+    return sh;
+}
+
+void svd_fetch(SvdResult* R, const Layout& U, double* S, const Layout& V, int absorb) {
+    svd_get(*R, U, S, V, absorb);
+}
+
+void svd_delete(SvdResult* R) { delete R; }
 
 }  // namespace tnh
 
@@ -588,12 +1249,13 @@ using namespace tnh;
 extern "C" {
 
 tnh_status tnh_svd_trunc(tnh_ctx* ctx, const tnh_tensor* T, int32_t nrow, double cutoff, int32_t maxdim,
-                         int32_t mindim, tnh_svd** out) {
+                         int32_t mindim, int32_t exact_side, tnh_svd** out) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     return guard(c, [&] {
         TNH_REQUIRE(c && out, TNH_ERR_ARG, "tnh_svd_trunc: NULL argument");
         CUDA_CHECK(cudaSetDevice(c->device));
-        auto R = run_svd(c, parse_tensor(T, "T"), nrow, cutoff, maxdim, mindim);
+        TNH_REQUIRE(exact_side == 0 || exact_side == 1, TNH_ERR_ARG, "tnh_svd_trunc: exact_side must be 0 or 1");
+        auto R = run_svd(c, parse_tensor(T, "T"), nrow, cutoff, maxdim, mindim, exact_side);
         *out = reinterpret_cast<tnh_svd*>(R.release());
     });
 }
@@ -632,27 +1294,3 @@ void tnh_svd_free(tnh_svd* svd) {
 }
 
 }  // extern "C"
-
-namespace tnh {
-
-SvdResult* svd_run(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim) {
-    return run_svd(ctx, T, nrow, cutoff, maxdim, mindim).release();
-}
-
-SvdShape svd_shape(const SvdResult* R) {
-    SvdShape sh;
-    for (int g : R->sect_groups) {
-        sh.qn.push_back(R->gq[g]);
-        sh.dims.push_back(R->kept_g[g]);
-    }
-    sh.truncerr = R->truncerr;
-    return sh;
-}
-
-void svd_fetch(SvdResult* R, const Layout& U, double* S, const Layout& V, int absorb) {
-    svd_get(*R, U, S, V, absorb);
-}
-
-void svd_delete(SvdResult* R) { delete R; }
-
-}  // namespace tnh

@@ -90,7 +90,7 @@ def lib():
         "tnh_heff_free": (None, [vp]),
         "tnh_eigsolve": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
         "tnh_env_update": (i32, [vp, i32, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), C.c_int]),
-        "tnh_svd_trunc": (i32, [vp, P(tnh_tensor), i32, dbl, i32, i32, P(vp)]),
+        "tnh_svd_trunc": (i32, [vp, P(tnh_tensor), i32, dbl, i32, i32, i32, P(vp)]),
         "tnh_svd_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(dbl)]),
         "tnh_svd_get": (i32, [vp, P(tnh_tensor), vp, P(tnh_tensor), i32]),
         "tnh_svd_free": (None, [vp]),
@@ -322,12 +322,12 @@ class Context:
         self.check(self._lib.tnh_env_update(self.h, int(direction), *[C.byref(x) for x in args], int(prec)))
         return out
 
-    def svd_trunc(self, T, nrow, cutoff, maxdim, mindim=1):
+    def svd_trunc(self, T, nrow, cutoff, maxdim, mindim=1, exact_side=0):
         keep = []
         t = T._c(keep)
         h = C.c_void_p()
         self.check(self._lib.tnh_svd_trunc(self.h, C.byref(t), int(nrow), float(cutoff), int(maxdim),
-                                           int(mindim), C.byref(h)))
+                                           int(mindim), int(exact_side), C.byref(h)))
         res = Svd(self, h, T, nrow)
         self._children.add(res)
         return res

@@ -25,9 +25,9 @@ def theta_inputs(m, nsect, maxd, seed):
     return H.random_pair([a, s, s, a.dag()], None, seed, "theta")
 
 
-def factor(ctx, T, cutoff, maxdim, mindim=1):
-    svd = ctx.svd_trunc(T, 2, cutoff, maxdim, mindim)
-    U, S, V = svd.factors()
+def factor(ctx, T, cutoff, maxdim, mindim=1, side=0, absorb=0):
+    svd = ctx.svd_trunc(T, 2, cutoff, maxdim, mindim, exact_side=side)
+    U, S, V = svd.factors(absorb=absorb)
     Uo, Vo = H.to_oracle(U), H.to_oracle(V)
     s = S.cpu().numpy()
     Sd, pos = {}, 0
@@ -92,3 +92,46 @@ def test_svd_config2_size(ctx):
     want = np.concatenate(list(Sw.values()))
     np.testing.assert_allclose(np.sort(s)[::-1], np.sort(want)[::-1], rtol=1e-11, atol=1e-12 * want.max())
     assert abs(svd.truncerr - errw) < 1e-12
+
+
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("absorb", [0, 1, 2])
+def test_svd_exact_side_and_absorb(ctx, side, absorb):
+    T, To = theta_inputs(40, 7, 12, 8)
+    svd, Uo, Sd, Vo, s = factor(ctx, T, 0.0, 30, side=side, absorb=absorb)
+    Sn = {q: np.ones_like(v) for q, v in Sd.items()}
+    Su = Sd if absorb == 0 else Sn
+    rec = D.theta(D.scale_link(Uo, Su, 2), Vo)
+    _, _, _, err = D.svd_trunc(To, 2, 0.0, 30)
+    disc = float(np.sum((rec.to_dense() - To.to_dense()) ** 2)) / To.norm() ** 2
+    assert abs(disc - err) < 1e-11
+    # the exact side is orthonormal to float64 accuracy
+    if side == 0 and absorb != 1:
+        Ud = Uo.to_dense().reshape(-1, Uo.inds[2].dim)
+        np.testing.assert_allclose(Ud.T @ Ud, np.eye(Ud.shape[1]), atol=1e-13)
+    if side == 1 and absorb != 2:
+        Vd = Vo.to_dense().reshape(Vo.inds[0].dim, -1)
+        np.testing.assert_allclose(Vd @ Vd.T, np.eye(Vd.shape[0]), atol=1e-13)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_svd_rank_deficient(ctx, side):
+    # theta = A B with a rank smaller than the matrix: exact zero singular values
+    from paper_2007_14822_gb300.tnh import Index, Tensor, FP64
+    from paper_2007_14822_gb300 import models as pm
+    a = H.link_index(24, 5, 8, +1)
+    c = H.link_index(6, 3, 2, +1)
+    s1, s2 = pm.site_index(pm.SPIN_QN, qn=True), pm.site_index(pm.SPIN_QN, qn=True)
+    A, Ao = H.random_pair([a, s1, c.dag()], None, 3, "A")
+    B, Bo = H.random_pair([c, s2, a.dag()], None, 4, "B")
+    for t, lab in ((A, (1, 2, 3)), (B, (3, 4, 5))):
+        for ix, l in zip(t.inds, lab):
+            ix.label = l
+    th = Tensor([A.inds[0], A.inds[1], B.inds[1], B.inds[2]])
+    ctx.contract(A, B, th, FP64)
+    tho = H.to_oracle(th)
+    svd, Uo, Sd, Vo, s = factor(ctx, th, 1e-14, 64, side=side, absorb=2 - side)
+    _, So, _, err = D.svd_trunc(tho, 2, 1e-14, 64)
+    assert svd.kept == sum(len(v) for v in So.values())
+    rec = D.theta(Uo, Vo)
+    assert H.rel_err(rec, tho) < 1e-12
