@@ -263,6 +263,31 @@ std::unique_ptr<ContractPlan> plan_contract(const Layout& A, const Layout& B, co
     return P;
 }
 
+double contract_flops(const Layout& A, const Layout& B) {
+    // the block pairs plan_contract would form: contracted sectors equal
+    std::vector<int> ia, ib;
+    for (int i = 0; i < A.rank(); ++i)
+        for (int j = 0; j < B.rank(); ++j)
+            if (A.inds[i].label == B.inds[j].label) { ia.push_back(i); ib.push_back(j); }
+    std::map<std::vector<int>, std::vector<int>> bmap;
+    for (int b = 0; b < B.nblocks(); ++b) {
+        std::vector<int> k;
+        for (int j : ib) k.push_back(B.sect[(size_t)b * B.rank() + j]);
+        bmap[k].push_back(b);
+    }
+    double f = 0.0;
+    for (int a = 0; a < A.nblocks(); ++a) {
+        std::vector<int> k;
+        double K = 1.0;
+        for (int i : ia) { k.push_back(A.sect[(size_t)a * A.rank() + i]); K *= A.bdim(a, i); }
+        auto it = bmap.find(k);
+        if (it == bmap.end()) continue;
+        const double M = (double)A.belems(a) / K;
+        for (int b : it->second) f += 2.0 * M * ((double)B.belems(b) / K) * K;
+    }
+    return f;
+}
+
 void run_contract(Ctx* ctx, const ContractPlan& P, const double* A, const double* B, double* C,
                   tnh_precision prec, Workspace& ws) {
     cudaStream_t s = ctx->stream;

@@ -158,7 +158,7 @@ extern "C" tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, i
                     }
                     // eigensolver
                     {
-                        auto P = make_heff(c, Ls[j].L, W[j], W[j + 1], Rs[j + 2].L, th.L, prec, false);
+                        auto P = make_heff(c, Ls[j].L, W[j], W[j + 1], Rs[j + 2].L, th.L, prec);
                         EigResult r = eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
                         E = r.energy;
                         resid = r.resid;

@@ -1,0 +1,299 @@
+// Tile gather: build GEMM operand tiles from weighted sums of strided
+// sub-blocks.
+//
+// One CTA owns one 128-row x 64-column tile of a GEMM operand (K-major).
+// The tile is assembled in shared memory from its segments; a segment is a
+// rectangle of the tile whose every element is
+//     sum_j coef_j * src[off_j + r * rs_j + c * cs_j]
+// (r, c relative to the segment). Elements covered by no segment are zero,
+// so the tile is written whole and no operand buffer needs clearing.
+//
+// Uses in the effective-Hamiltonian plan: packing L and R (once per plan)
+// and psi (every application) into GEMM operands, one term per segment: a
+// transposing, format-converting copy whose reads run along the unit-stride
+// direction.
+//
+// In the split formats all arithmetic is float32 (the operands end up as
+// three bfloat16 parts, 24 significant bits); the float64 format keeps
+// float64 arithmetic.
+//
+// The fused S2+S3 step (w12_kernel below) works per cell instead: the
+// inputs of one (a'-sector, b-sector) pair are staged once and every output
+// sub-block is a weighted sum of them, weights = nonzero entries of the
+// two-site MPO product W1*W2 (Sec. 7.2).
+//
+// Output formats: float64 rows (pitch ld) for the FP64 GEMM, or the split
+// bfloat16 swizzled tiles (x = hi + mid + lo) of the tcgen05 GEMM.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "gather.h"
+#include "prof.h"
+
+namespace tnh {
+
+namespace {
+
+constexpr int kPitch = kGatherCols + 1;   // padded smem row (doubles)
+constexpr int kSmemBytes = kGatherRows * kPitch * 8;
+
+// x = hi + mid + lo, each part rounded to nearest bfloat16; float32
+// arithmetic (exact residuals), the float64 units of this GPU being scarce
+template <int P>
+__device__ __forceinline__ void split_bf16(float x, uint16_t* part) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    part[0] = __bfloat16_as_ushort(hi);
+    if (P > 1) {
+        const float r1 = x - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        part[1] = __bfloat16_as_ushort(mid);
+        if (P > 2) part[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(mid)));
+    }
+}
+
+// float64 rows: float64 arithmetic; split-bfloat16 tiles: float32
+template <bool kF64>
+struct Acc { using T = float; };
+template <>
+struct Acc<true> { using T = double; };
+
+template <bool kF64>
+__device__ __forceinline__ typename Acc<kF64>::T coef_of(const GatherTerm& g) {
+    if constexpr (kF64) return g.coef; else return g.coef32;
+}
+
+template <class SrcT, bool kF64, int P>
+__global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restrict__ tiles,
+                                                     const GatherSeg* __restrict__ segs,
+                                                     const GatherTerm* __restrict__ terms,
+                                                     const OpGeom* __restrict__ geom,
+                                                     const SrcT* __restrict__ src, void* __restrict__ dst) {
+    using AccT = typename Acc<kF64>::T;
+    extern __shared__ double tile_raw[];
+    AccT* tile_s = reinterpret_cast<AccT*>(tile_raw);
+    const GatherTile T = tiles[blockIdx.x];
+    for (int e = threadIdx.x; e < kGatherRows * kPitch; e += blockDim.x) tile_s[e] = AccT(0);
+    __syncthreads();
+    for (int si = T.seg0; si < T.seg1; ++si) {
+        const GatherSeg S = segs[si];
+        const int n = S.nr * S.nc;
+        const bool cfast = terms[S.t0].cs == 1;
+        if (S.t1 - S.t0 == 1) {
+            // one term (a copy): eight independent loads in flight per thread
+            const GatherTerm g = terms[S.t0];
+            const AccT cf = coef_of<kF64>(g);
+            for (int e0 = threadIdx.x; e0 < n; e0 += 8 * blockDim.x) {
+                AccT v[8];
+                int pos[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    int r = 0, c = 0;
+                    if (e < n) {
+                        if (cfast) { r = e / S.nc; c = e - r * S.nc; }
+                        else { c = e / S.nr; r = e - c * S.nr; }
+                    }
+                    pos[u] = e < n ? (S.r0 + r) * kPitch + S.c0 + c : -1;
+                    v[u] = e < n ? cf * (AccT)src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs] : AccT(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (pos[u] >= 0) tile_s[pos[u]] = v[u];
+            }
+            continue;
+        }
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            int r, c;
+            if (cfast) { r = e / S.nc; c = e - r * S.nc; }
+            else { c = e / S.nr; r = e - c * S.nr; }
+            AccT v = AccT(0);
+            for (int j = S.t0; j < S.t1; ++j) {
+                const GatherTerm& g = terms[j];
+                v += coef_of<kF64>(g) * (AccT)src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs];
+            }
+            tile_s[(S.r0 + r) * kPitch + S.c0 + c] = v;
+        }
+    }
+    __syncthreads();
+    const OpGeom G = geom[T.task];
+    if constexpr (kF64) {
+        double* d = static_cast<double*>(dst) + G.base + (int64_t)T.mi * kGatherRows * G.ld +
+                    (int64_t)T.ki * kGatherCols;
+        for (int e = threadIdx.x; e < kGatherRows * kGatherCols; e += blockDim.x) {
+            const int r = e / kGatherCols, c = e - r * kGatherCols;
+            d[(int64_t)r * G.ld + c] = tile_s[r * kPitch + c];
+        }
+    } else {
+        // tile (mi, ki) of a [mt][kt] grid of P-plane 128 x 64 tiles; the
+        // 16-byte chunk j of row r holds k-group j ^ (r & 7) (128-byte swizzle)
+        uint16_t* d = static_cast<uint16_t*>(dst) +
+                      (G.base + (int64_t)T.mi * G.ld + T.ki) * (int64_t)(P * kTcTileElems);
+        for (int ci = threadIdx.x; ci < kGatherRows * 8; ci += blockDim.x) {
+            const int r = ci >> 3, j = ci & 7;
+            const int kg = j ^ (r & 7);
+            const float* v = tile_s + r * kPitch + kg * 8;
+            uint32_t w[3][4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                uint16_t a[3], b[3];
+                split_bf16<P>(v[2 * h], a);
+                split_bf16<P>(v[2 * h + 1], b);
+#pragma unroll
+                for (int p = 0; p < P; ++p) w[p][h] = (uint32_t)a[p] | ((uint32_t)b[p] << 16);
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                *reinterpret_cast<uint4*>(d + p * kTcTileElems + ci * 8) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        }
+    }
+}
+
+// Offset of element (row, k) inside a 128 x 64 bfloat16 operand tile in the
+// 128-byte-swizzled K-major layout of the tcgen05 shared-memory descriptor.
+__device__ __forceinline__ int swz(int row, int k) {
+    return row * 64 + ((((k >> 3) ^ (row & 7))) << 3) + (k & 7);
+}
+
+template <class SrcT, bool kF64, int P>
+__global__ void __launch_bounds__(kW12Elems) w12_kernel(const W12Cta* __restrict__ ctas,
+                                                        const W12Cell* __restrict__ cells,
+                                                        const W12In* __restrict__ ins,
+                                                        const W12Out* __restrict__ outs,
+                                                        const W12Term* __restrict__ terms,
+                                                        const OpGeom* __restrict__ geom,
+                                                        const SrcT* __restrict__ src, void* __restrict__ dst) {
+    extern __shared__ unsigned char w12_smem[];
+    SrcT* in_s = reinterpret_cast<SrcT*>(w12_smem);   // [nin][kW12Elems], one column per thread
+    const W12Cta T = ctas[blockIdx.x];
+    const W12Cell C = cells[T.cell];
+    const int tid = threadIdx.x;
+    const int e = T.e0 + tid;
+    const bool live = e < C.Da * C.Db;
+    const int r = live ? e / C.Db : 0, c = live ? e - r * C.Db : 0;
+    // stage: every input once (independent loads, four at a time)
+    int i = 0;
+    for (; i + 4 <= C.nin; i += 4) {
+        SrcT v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const W12In in = ins[C.in0 + i + u];
+            v[u] = live ? src[in.base + (int64_t)r * in.ld + c] : SrcT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) in_s[(i + u) * kW12Elems + tid] = v[u];
+    }
+    for (; i < C.nin; ++i) {
+        const W12In in = ins[C.in0 + i];
+        in_s[i * kW12Elems + tid] = live ? src[in.base + (int64_t)r * in.ld + c] : SrcT(0);
+    }
+    if (!live) return;   // each thread reads back only its own column: no barrier
+    using AccT = typename Acc<kF64>::T;
+    for (int o = 0; o < C.nout; ++o) {
+        const W12Out O = outs[C.out0 + o];
+        AccT v = AccT(0);
+        for (int j = O.t0; j < O.t1; ++j) {
+            const W12Term t = terms[j];
+            if constexpr (kF64) v += t.coef * (AccT)in_s[t.in * kW12Elems + tid];
+            else v += t.coef32 * (AccT)in_s[t.in * kW12Elems + tid];
+        }
+        const OpGeom G = geom[O.task];
+        const int row = O.row0 + r, col = O.col0 + c;
+        if constexpr (kF64) {
+            static_cast<double*>(dst)[G.base + (int64_t)row * G.ld + col] = v;
+        } else {
+            uint16_t* d = static_cast<uint16_t*>(dst) +
+                          (G.base + (int64_t)(row >> 7) * G.ld + (col >> 6)) * (int64_t)(P * kTcTileElems) +
+                          swz(row & 127, col & 63);
+            uint16_t part[3];
+            split_bf16<P>(v, part);
+#pragma unroll
+            for (int p = 0; p < P; ++p) d[p * kTcTileElems] = part[p];
+        }
+    }
+}
+
+template <class SrcT, bool kF64, int P>
+void launch_w12_one(const W12Job& J, const OpGeom* geom, const SrcT* src, void* dst, cudaStream_t s) {
+    const int smem = std::max(J.max_in, 1) * kW12Elems * (int)sizeof(SrcT);
+    static int configured = 0;
+    if (smem > configured) {
+        CUDA_CHECK(cudaFuncSetAttribute(w12_kernel<SrcT, kF64, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        smem));
+        configured = smem;
+    }
+    w12_kernel<SrcT, kF64, P><<<(int)J.ctas.size(), kW12Elems, smem, s>>>(
+        J.d_ctas.as<W12Cta>(), J.d_cells.as<W12Cell>(), J.d_ins.as<W12In>(), J.d_outs.as<W12Out>(),
+        J.d_terms.as<W12Term>(), geom, src, dst);
+}
+
+template <class SrcT>
+void launch_w12_t(const W12Job& J, const OpGeom* geom, const SrcT* src, void* dst, int planes, cudaStream_t s) {
+    if (J.ctas.empty()) return;
+    KScope ks("heff_w12", s);
+    if (planes == 0) launch_w12_one<SrcT, true, 1>(J, geom, src, dst, s);
+    else if (planes == 1) launch_w12_one<SrcT, false, 1>(J, geom, src, dst, s);
+    else if (planes == 2) launch_w12_one<SrcT, false, 2>(J, geom, src, dst, s);
+    else launch_w12_one<SrcT, false, 3>(J, geom, src, dst, s);
+}
+
+template <class SrcT, bool kF64, int P>
+void launch_one(const GatherJob& J, const OpGeom* geom, const SrcT* src, void* dst, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        CUDA_CHECK(cudaFuncSetAttribute(gather_kernel<SrcT, kF64, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemBytes));
+        configured = true;
+    }
+    gather_kernel<SrcT, kF64, P><<<J.ntiles, 256, kSmemBytes, s>>>(
+        J.d_tiles.as<GatherTile>(), J.d_segs.as<GatherSeg>(), J.d_terms.as<GatherTerm>(), geom, src, dst);
+}
+
+template <class SrcT>
+void launch_t(const GatherJob& J, const OpGeom* geom, const SrcT* src, void* dst, int planes, cudaStream_t s) {
+    if (planes == 0) launch_one<SrcT, true, 1>(J, geom, src, dst, s);
+    else if (planes == 1) launch_one<SrcT, false, 1>(J, geom, src, dst, s);
+    else if (planes == 2) launch_one<SrcT, false, 2>(J, geom, src, dst, s);
+    else launch_one<SrcT, false, 3>(J, geom, src, dst, s);
+}
+
+}  // namespace
+
+void W12Job::upload_all(cudaStream_t s) {
+    d_cells = upload(cells, s);
+    d_ins = upload(ins, s);
+    d_outs = upload(outs, s);
+    d_terms = upload(terms, s);
+    d_ctas = upload(ctas, s);
+}
+
+void launch_w12(const W12Job& J, const OpGeom* d_geom, const double* src, void* dst, int planes, cudaStream_t s) {
+    launch_w12_t<double>(J, d_geom, src, dst, planes, s);
+}
+
+void launch_w12(const W12Job& J, const OpGeom* d_geom, const float* src, void* dst, int planes, cudaStream_t s) {
+    launch_w12_t<float>(J, d_geom, src, dst, planes, s);
+}
+
+void GatherJob::upload_all(cudaStream_t s) {
+    ntiles = (int)tiles.size();
+    d_tiles = upload(tiles, s);
+    d_segs = upload(segs, s);
+    d_terms = upload(terms, s);
+}
+
+void launch_gather(const GatherJob& J, const OpGeom* d_geom, const double* src, void* dst, int planes,
+                   cudaStream_t s, const char* name) {
+    if (J.ntiles == 0) return;
+    KScope ks(name, s);
+    launch_t<double>(J, d_geom, src, dst, planes, s);
+}
+
+void launch_gather(const GatherJob& J, const OpGeom* d_geom, const float* src, void* dst, int planes,
+                   cudaStream_t s, const char* name) {
+    if (J.ntiles == 0) return;
+    KScope ks(name, s);
+    launch_t<float>(J, d_geom, src, dst, planes, s);
+}
+
+}  // namespace tnh

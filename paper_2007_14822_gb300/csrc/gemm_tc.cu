@@ -1,6 +1,6 @@
 // Grouped split-bfloat16 GEMM on the 5th-generation tensor cores (tcgen05).
 //
-// C_t[M][ldc] (float64) = sum over products (p, q) of A_t^(p) * B_t^(q)^T,
+// C_t[M][ldc] (float64, or float32 per task) = sum over products (p, q) of A_t^(p) * B_t^(q)^T,
 // where A^(0..P-1) / B^(0..P-1) are the bfloat16 parts of the float64
 // operands (x = hi + mid + lo). P = 3 keeps the six products
 // hh, hm, mh, hl, lh, mm; P = 2 keeps hh, hm, mh; P = 1 keeps hh.
@@ -65,7 +65,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const GemmTask* __restrict__ tasks, int ntasks, int total_tiles,
                    const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, double* __restrict__ C,
-                   int* err) {
+                   int* err, const int64_t* __restrict__ row_off) {
     using Cfg = TcCfg<P>;
     constexpr int S = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
@@ -217,11 +217,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             const int m = mi * kTcTileM + q * 32 + lane;
             if (m < t.M) {
-                double* crow = C + t.c_base + (int64_t)m * t.ldc;
+                // each lane stores its own row: 16-byte vectors where aligned
+                const int64_t rb = t.use_roff ? row_off[t.roff + m] : t.c_base + (int64_t)m * t.ldc;
                 const int n0 = ni * kTcTileN + half * kCols;
+                const int nv = t.N - n0;
+                if (t.c_f32) {
+                    float* crow = reinterpret_cast<float*>(C) + rb + n0;
+                    if (nv >= kCols && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
 #pragma unroll
-                for (int j = 0; j < kCols; ++j)
-                    if (n0 + j < t.N) crow[n0 + j] = (double)acc[j];
+                        for (int j = 0; j < kCols; j += 4)
+                            *reinterpret_cast<float4*>(crow + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < kCols; ++j)
+                            if (j < nv) crow[j] = acc[j];
+                    }
+                } else {
+                    double* crow = C + rb + n0;
+                    if (nv >= kCols && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
+#pragma unroll
+                        for (int j = 0; j < kCols; j += 2)
+                            *reinterpret_cast<double2*>(crow + j) = make_double2((double)acc[j], (double)acc[j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < kCols; ++j)
+                            if (j < nv) crow[j] = (double)acc[j];
+                    }
+                }
             }
         }
     }
@@ -234,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int P>
 void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A, const uint16_t* B,
-              double* C, int num_sms, int* err, cudaStream_t s) {
+              double* C, int num_sms, int* err, cudaStream_t s, const int64_t* row_off) {
     static bool configured = false;
     if (!configured) {
         CUDA_CHECK(cudaFuncSetAttribute(gemm_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -243,20 +265,20 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
     }
     int grid = std::min(total_tiles, num_sms > 0 ? num_sms : 148);
     KScope ks(P == 3 ? "gemm_tc_bf16x6" : (P == 2 ? "gemm_tc_bf16x3" : "gemm_tc_bf16"), s);
-    gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err);
+    gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err, row_off);
 }
 
 }  // namespace
 
 void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A, const uint16_t* B,
-                    double* C, int planes, int num_sms, int* err, cudaStream_t s) {
+                    double* C, int planes, int num_sms, int* err, cudaStream_t s, const int64_t* row_off) {
     if (total_tiles == 0) return;
     if (planes == 3)
-        launch_p<3>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s);
+        launch_p<3>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
     else if (planes == 2)
-        launch_p<2>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s);
+        launch_p<2>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
     else
-        launch_p<1>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s);
+        launch_p<1>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
 }
 
 }  // namespace tnh

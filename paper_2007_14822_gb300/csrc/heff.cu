@@ -3,9 +3,34 @@
 //   y[a',s1',s2',b'] = sum L[a,w,a'] W1[w,w1,s1,s1'] W2[w1,w2,s2,s2']
 //                          R[b,w2,b'] x[a,s1,s2,b]
 //
-// evaluated as four labelled contractions S1 (sum a), S2 (sum w, s1),
-// S3 (sum w1, s2), S4 (sum w2, b), each a grouped block-pair GEMM.
+// One application is four launches on the plan's stream:
+//   1. gather  x -> operand B of S1 (split-bfloat16 tiles or float64 rows)
+//   2. S1      T1[(w,a'), (s1,s2,b)] = sum_a L[a,w,a'] x[a,s1,s2,b]: a grouped
+//              GEMM with one task per a-sector (Sec. 9.4: blocks whose
+//              contracted sectors agree)
+//   3. MPO     T3[(s1',s2',a'), (w2,b)] = sum W12[w,s1,s2; w2,s1',s2'] T1:
+//              the contractions with W1 and W2 (S2, S3) fused into one pass
+//              through the two-site MPO product W12 = sum_w1 W1 W2; one CTA
+//              stages the T1 sub-blocks of an (a'-sector, b-sector) pair once
+//              and writes every T3 sub-block of that pair, directly as
+//              operand A of S4
+//   4. S4      y[(s1',s2',a'), b'] = sum_(w2,b) T3 R[b,w2,b']: a grouped GEMM
+//              with one task per b'-sector whose epilogue writes every row
+//              to its place in psi's block layout
+// L and R are packed into GEMM operands when the plan is made: they are the
+// same for every application of the Lanczos iteration. The plan keeps no
+// reference to the caller's L, W1, W2, R.
+//
+// In the split-bfloat16 modes the tensor cores accumulate in float32, T1 is
+// stored in float32 and the packing and MPO-step arithmetic is float32 (the
+// operands are three bfloat16 parts: 24 significant bits). An FP64 plan uses
+// the FP64 GEMM throughout. A split-mode plan can also apply in FP64 (for the
+// final energy and residual), so it keeps the float64 operands of L and R too.
 #include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
 
 #include "heff.h"
 #include "tnh_guard.h"
@@ -15,6 +40,9 @@ namespace tnh {
 namespace {
 
 enum : int64_t { La = 1, Lw = 2, Lap = 3, Ls1 = 4, Ls2 = 5, Lb = 6, Lw1 = 7, Ls1p = 8, Lw2 = 9, Ls2p = 10, Lbp = 11 };
+
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+int64_t cdiv(int64_t x, int64_t m) { return (x + m - 1) / m; }
 
 Layout with_labels(Layout T, std::initializer_list<int64_t> labels) {
     int i = 0;
@@ -28,69 +56,481 @@ std::vector<int> add_flux(const std::vector<int>& a, const std::vector<int>& b) 
     return r;
 }
 
-DevBuf copy_data(const Layout& T, cudaStream_t s) {
-    DevBuf b((size_t)std::max<int64_t>(T.size, 1) * sizeof(double));
-    if (T.size) CUDA_CHECK(cudaMemcpyAsync(b.p, T.data, (size_t)T.size * sizeof(double),
-                                           cudaMemcpyDeviceToDevice, s));
-    return b;
+void check_pair(const Index& a, const Index& b, const char* what) {
+    TNH_REQUIRE(a.same_space(b), TNH_ERR_SHAPE, "heff_plan: %s: the two indices have different sectors", what);
+    TNH_REQUIRE(a.arrow != b.arrow, TNH_ERR_ARROW, "heff_plan: %s: contracted indices have equal arrows", what);
+}
+
+// sector of element e of an index and its position inside the sector
+std::pair<int, int> locate(const Index& ix, int64_t e) {
+    int s = 0;
+    while (s + 1 < ix.nsect && e >= ix.off[s + 1]) ++s;
+    return {s, (int)(e - ix.off[s])};
+}
+
+std::vector<double> to_host(const Layout& T, cudaStream_t s) {
+    std::vector<double> h((size_t)T.size);
+    if (T.size) {
+        CUDA_CHECK(cudaMemcpyAsync(h.data(), T.data, (size_t)T.size * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+    }
+    return h;
+}
+
+// Nonzero entries of a rank-4 MPO tensor, global element numbers per index.
+struct MpoEntry {
+    int l, r, s, sp;
+    double v;
+};
+std::vector<MpoEntry> mpo_entries(const Layout& W, cudaStream_t s) {
+    std::vector<double> h = to_host(W, s);
+    std::vector<MpoEntry> out;
+    for (int b = 0; b < W.nblocks(); ++b) {
+        int d[4];
+        int64_t o[4];
+        for (int i = 0; i < 4; ++i) {
+            d[i] = W.bdim(b, i);
+            o[i] = W.inds[i].off[W.sect[(size_t)b * 4 + i]];
+        }
+        int64_t e = W.off[b];
+        for (int i0 = 0; i0 < d[0]; ++i0)
+            for (int i1 = 0; i1 < d[1]; ++i1)
+                for (int i2 = 0; i2 < d[2]; ++i2)
+                    for (int i3 = 0; i3 < d[3]; ++i3, ++e)
+                        if (h[(size_t)e] != 0.0)
+                            out.push_back({(int)(o[0] + i0), (int)(o[1] + i1), (int)(o[2] + i2), (int)(o[3] + i3),
+                                           h[(size_t)e]});
+    }
+    return out;
+}
+
+// Collects the segments of one gather job and orders them by tile.
+struct JobBuilder {
+    struct Task { int64_t tile0; int mt, kt; };
+    struct Pending { int64_t tile; GatherSeg s; };
+    std::vector<Task> tasks;
+    std::vector<Pending> segs;
+    std::vector<GatherTerm> terms;
+    int64_t ntiles = 0;
+
+    void task(int64_t rows, int64_t K) {
+        Task t{ntiles, (int)cdiv(rows, kGatherRows), (int)cdiv(K, kGatherCols)};
+        tasks.push_back(t);
+        ntiles += (int64_t)t.mt * t.kt;
+    }
+    // rows [row0, row0+nr) x cols [col0, col0+nc) of task t: element (r, c)
+    // is sum over terms of coef * src[off + r rs + c cs]
+    void rect(int t, int64_t row0, int64_t col0, int64_t nr, int64_t nc, const std::vector<GatherTerm>& tm) {
+        if (tm.empty() || nr <= 0 || nc <= 0) return;
+        const Task& T = tasks[t];
+        for (int64_t R = row0; R < row0 + nr;) {
+            const int64_t mi = R / kGatherRows, Re = std::min(row0 + nr, (mi + 1) * kGatherRows);
+            for (int64_t Cc = col0; Cc < col0 + nc;) {
+                const int64_t ki = Cc / kGatherCols, Ce = std::min(col0 + nc, (ki + 1) * kGatherCols);
+                GatherSeg s{(int)(R - mi * kGatherRows), (int)(Cc - ki * kGatherCols), (int)(Re - R), (int)(Ce - Cc),
+                            (int)terms.size(), 0};
+                for (const GatherTerm& g : tm)
+                    terms.push_back({g.coef, g.off + (R - row0) * g.rs + (Cc - col0) * g.cs, g.rs, g.cs, g.coef32});
+                s.t1 = (int)terms.size();
+                segs.push_back({T.tile0 + mi * T.kt + ki, s});
+                Cc = Ce;
+            }
+            R = Re;
+        }
+    }
+    void finish(GatherJob& J, cudaStream_t s) {
+        std::stable_sort(segs.begin(), segs.end(), [](const Pending& a, const Pending& b) { return a.tile < b.tile; });
+        TNH_REQUIRE(terms.size() < (size_t)INT32_MAX && ntiles < INT32_MAX, TNH_ERR_SHAPE,
+                    "heff_plan: gather job too large");
+        J.tiles.clear();
+        J.segs.clear();
+        J.terms.clear();
+        J.terms.reserve(terms.size());
+        size_t k = 0;
+        for (int t = 0; t < (int)tasks.size(); ++t) {
+            for (int mi = 0; mi < tasks[t].mt; ++mi)
+                for (int ki = 0; ki < tasks[t].kt; ++ki) {
+                    const int64_t id = tasks[t].tile0 + (int64_t)mi * tasks[t].kt + ki;
+                    GatherTile g{t, mi, ki, (int)J.segs.size(), 0};
+                    for (; k < segs.size() && segs[k].tile == id; ++k) {
+                        GatherSeg sg = segs[k].s;
+                        const int t0 = (int)J.terms.size();
+                        for (int j = sg.t0; j < sg.t1; ++j) J.terms.push_back(terms[(size_t)j]);
+                        sg.t0 = t0;
+                        sg.t1 = (int)J.terms.size();
+                        J.segs.push_back(sg);
+                    }
+                    g.seg1 = (int)J.segs.size();
+                    J.tiles.push_back(g);
+                }
+        }
+        J.upload_all(s);
+    }
+};
+
+// Collects the outputs of the fused S2+S3 step per cell (a'-sector, b-sector)
+// and splits cells whose outputs need more than kW12MaxIn inputs.
+struct CellBuilder {
+    struct Term { int64_t base, ld; double coef; };
+    struct Out { int task; int64_t row0, col0; std::vector<Term> terms; };
+    struct Cell { int Da = 0, Db = 0; std::vector<Out> outs; };
+    std::map<std::pair<int, int>, Cell> cells;
+
+    void add(int Ap, int B, int Da, int Db, int task, int64_t row0, int64_t col0, std::vector<Term> tm) {
+        if (tm.empty()) return;
+        Cell& c = cells[{Ap, B}];
+        c.Da = Da;
+        c.Db = Db;
+        c.outs.push_back({task, row0, col0, std::move(tm)});
+    }
+    void finish(W12Job& J, cudaStream_t s) {
+        J = W12Job();
+        for (auto& kv : cells) {
+            Cell& c = kv.second;
+            size_t o = 0;
+            while (o < c.outs.size()) {
+                std::map<int64_t, int> local;   // input base -> index in the group
+                std::vector<int64_t> lds;
+                W12Cell cell{(int)J.ins.size(), 0, (int)J.outs.size(), 0, c.Da, c.Db};
+                for (; o < c.outs.size(); ++o) {
+                    int fresh = 0;
+                    for (auto& t : c.outs[o].terms) fresh += !local.count(t.base);
+                    TNH_REQUIRE(fresh <= kW12MaxIn, TNH_ERR_SHAPE,
+                                "heff_plan: one output of the MPO step needs %d inputs (maximum %d)", fresh, kW12MaxIn);
+                    if ((int)local.size() + fresh > kW12MaxIn) break;
+                    std::map<int, double> acc;
+                    for (auto& t : c.outs[o].terms) {
+                        auto it = local.find(t.base);
+                        int li;
+                        if (it == local.end()) {
+                            li = (int)local.size();
+                            local[t.base] = li;
+                            J.ins.push_back({t.base, t.ld});
+                        } else {
+                            li = it->second;
+                        }
+                        acc[li] += t.coef;
+                    }
+                    W12Out out{c.outs[o].task, (int)c.outs[o].row0, (int)c.outs[o].col0, (int)J.terms.size(), 0};
+                    for (auto& a : acc) J.terms.push_back({a.second, (float)a.second, a.first});
+                    out.t1 = (int)J.terms.size();
+                    J.outs.push_back(out);
+                }
+                cell.nin = (int)local.size();
+                cell.nout = (int)J.outs.size() - cell.out0;
+                J.max_in = std::max(J.max_in, cell.nin);
+                const int ci = (int)J.cells.size();
+                J.cells.push_back(cell);
+                for (int e0 = 0; e0 < c.Da * c.Db; e0 += kW12Elems) J.ctas.push_back({ci, e0});
+            }
+        }
+        TNH_REQUIRE(J.terms.size() < (size_t)INT32_MAX && J.outs.size() < (size_t)INT32_MAX, TNH_ERR_SHAPE,
+                    "heff_plan: MPO step too large");
+        J.upload_all(s);
+    }
+};
+
+GemmTask gemm_task(int64_t M, int64_t N, int64_t K, const HeffOperand& A, const HeffOperand& B, int t, bool tc,
+                   int tile0) {
+    TNH_REQUIRE(M < (1 << 30) && N < (1 << 30) && K < (1 << 30), TNH_ERR_SHAPE, "heff_plan: block too large");
+    GemmTask g{};
+    g.M = (int)M;
+    g.N = (int)N;
+    g.K = (int)K;
+    if (tc) {
+        g.mt = (int)cdiv(M, kTcTileM);
+        g.nt = (int)cdiv(N, kTcTileN);
+        g.kt = (int)cdiv(K, kTcTileK);
+        g.a_base = A.gtc[t].base;
+        g.b_base = B.gtc[t].base;
+    } else {
+        g.mt = (int)cdiv(M, kF64TileM);
+        g.nt = (int)cdiv(N, kF64TileN);
+        g.kt = (int)cdiv(K, kF64TileK);
+        g.a_base = A.g64[t].base;
+        g.b_base = B.g64[t].base;
+        g.lda = A.g64[t].ld;
+        g.ldb = B.g64[t].ld;
+    }
+    g.tile0 = tile0;
+    return g;
+}
+
+void finish_gemm(HeffGemm& G, cudaStream_t s) {
+    G.d_f64 = upload(G.f64, s);
+    G.d_tc = upload(G.tc, s);
+}
+
+void upload_operand(HeffOperand& O, cudaStream_t s) {
+    O.d_g64 = upload(O.g64, s);
+    O.d_gtc = upload(O.gtc, s);
 }
 
 }  // namespace
 
+void HeffOperand::add_task(int64_t rows, int64_t K) {
+    // float64: rows padded to the gather tile (128), pitch to 64 columns
+    g64.push_back(OpGeom{elems64, (int)rup(K, kGatherCols)});
+    elems64 += rup(rows, kGatherRows) * rup(K, kGatherCols);
+    gtc.push_back(OpGeom{tiles, (int)cdiv(K, kTcTileK)});
+    tiles += cdiv(rows, kTcTileM) * cdiv(K, kTcTileK);
+}
+
 HeffPlan::~HeffPlan() = default;
 
-std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L0, const Layout& W10, const Layout& W20,
-                                    const Layout& R0, const Layout& psi0, tnh_precision prec, bool copy_inputs) {
-    TNH_REQUIRE(L0.rank() == 3 && R0.rank() == 3 && W10.rank() == 4 && W20.rank() == 4 && psi0.rank() == 4,
+std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
+                                    const Layout& R, const Layout& X, tnh_precision prec) {
+    TNH_REQUIRE(L.rank() == 3 && R.rank() == 3 && W1.rank() == 4 && W2.rank() == 4 && X.rank() == 4,
                 TNH_ERR_ARG, "heff_plan: ranks must be L 3, W 4, R 3, psi 4");
     TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "heff_plan: bad precision");
+    check_pair(L.inds[0], X.inds[0], "L and psi (a)");
+    check_pair(L.inds[1], W1.inds[0], "L and W1 (w)");
+    check_pair(W1.inds[2], X.inds[1], "W1 and psi (s1)");
+    check_pair(W1.inds[1], W2.inds[0], "W1 and W2 (w1)");
+    check_pair(W2.inds[2], X.inds[2], "W2 and psi (s2)");
+    check_pair(R.inds[0], X.inds[3], "R and psi (b)");
+    check_pair(R.inds[1], W2.inds[1], "R and W2 (w2)");
+    const Index* Yi[4] = {&L.inds[2], &W1.inds[3], &W2.inds[3], &R.inds[2]};
+    for (int i = 0; i < 4; ++i)
+        TNH_REQUIRE(Yi[i]->same_space(X.inds[i]) && Yi[i]->arrow == X.inds[i].arrow, TNH_ERR_SHAPE,
+                    "heff_plan: output index %d does not match psi's (sectors or arrow)", i);
+    if (L.nblocks() && W1.nblocks() && W2.nblocks() && R.nblocks() && X.nblocks())
+        TNH_REQUIRE(add_flux(add_flux(L.flux, W1.flux), add_flux(W2.flux, R.flux)) == std::vector<int>(X.nq(), 0),
+                    TNH_ERR_FLUX, "heff_plan: L, W1, W2, R do not conserve psi's flux");
+    TNH_REQUIRE(X.packed_total() <= X.size || X.nblocks() == 0, TNH_ERR_SHAPE, "heff_plan: psi too small");
+
     cudaStream_t s = ctx->stream;
     auto P = std::make_unique<HeffPlan>();
     P->ctx = ctx;
-    P->stream = ctx->stream;
+    P->stream = s;
     P->prec = prec;
-    Layout L = with_labels(L0, {La, Lw, Lap});
-    Layout W1 = with_labels(W10, {Lw, Lw1, Ls1, Ls1p});
-    Layout W2 = with_labels(W20, {Lw1, Lw2, Ls2, Ls2p});
-    Layout R = with_labels(R0, {Lb, Lw2, Lbp});
-    Layout X = with_labels(psi0, {La, Ls1, Ls2, Lb});
-    // output layout: psi's blocks on the product's indices
-    Layout Y = X;
-    Y.inds = {L.inds[2], W1.inds[3], W2.inds[3], R.inds[2]};
-    for (int i = 0; i < 4; ++i)
-        TNH_REQUIRE(Y.inds[i].same_space(X.inds[i]) && Y.inds[i].arrow == X.inds[i].arrow, TNH_ERR_SHAPE,
-                    "heff_plan: output index %d does not match psi's (sectors or arrow)", i);
+    P->planes = prec == TNH_FP64 ? 0 : planes_of(prec);
     P->n = X.size;
     P->psi = X;
-    // intermediates
-    Layout T1 = make_layout({L.inds[1], L.inds[2], X.inds[1], X.inds[2], X.inds[3]}, add_flux(L.flux, X.flux));
-    Layout T2 = make_layout({T1.inds[1], T1.inds[3], T1.inds[4], W1.inds[1], W1.inds[3]},
-                            add_flux(T1.flux, W1.flux));
-    Layout T3 = make_layout({T2.inds[0], T2.inds[2], T2.inds[4], W2.inds[1], W2.inds[3]},
-                            add_flux(T2.flux, W2.flux));
-    P->c1 = plan_contract(L, X, T1, s);
-    P->c2 = plan_contract(T1, W1, T2, s);
-    P->c3 = plan_contract(T2, W2, T3, s);
-    P->c4 = plan_contract(T3, R, Y, s);
-    P->t1.alloc((size_t)std::max<int64_t>(T1.size, 1) * 8);
-    P->t2.alloc((size_t)std::max<int64_t>(T2.size, 1) * 8);
-    P->t3.alloc((size_t)std::max<int64_t>(T3.size, 1) * 8);
-    if (copy_inputs) {
-        P->Ld = copy_data(L, s);
-        P->Rd = copy_data(R, s);
-        P->W1d = copy_data(W1, s);
-        P->W2d = copy_data(W2, s);
-        P->Lp = P->Ld.as<double>();
-        P->Rp = P->Rd.as<double>();
-        P->W1p = P->W1d.as<double>();
-        P->W2p = P->W2d.as<double>();
-    } else {
-        P->Lp = L.data;
-        P->Rp = R.data;
-        P->W1p = W1.data;
-        P->W2p = W2.data;
+    const Index &ia = X.inds[0], &is1 = X.inds[1], &is2 = X.inds[2], &ib = X.inds[3];
+    const Index &iw = L.inds[1], &iz = R.inds[1];
+
+    // method flops: S1..S4 over the allowed blocks of the labelled chain
+    {
+        Layout Ll = with_labels(L, {La, Lw, Lap});
+        Layout W1l = with_labels(W1, {Lw, Lw1, Ls1, Ls1p});
+        Layout W2l = with_labels(W2, {Lw1, Lw2, Ls2, Ls2p});
+        Layout Rl = with_labels(R, {Lb, Lw2, Lbp});
+        Layout Xl = with_labels(X, {La, Ls1, Ls2, Lb});
+        Layout T1 = make_layout({Ll.inds[1], Ll.inds[2], Xl.inds[1], Xl.inds[2], Xl.inds[3]}, add_flux(L.flux, X.flux));
+        Layout T2 = make_layout({T1.inds[1], T1.inds[3], T1.inds[4], W1l.inds[1], W1l.inds[3]},
+                                add_flux(T1.flux, W1.flux));
+        Layout T3 = make_layout({T2.inds[0], T2.inds[2], T2.inds[4], W2l.inds[1], W2l.inds[3]},
+                                add_flux(T2.flux, W2.flux));
+        P->flops = contract_flops(Ll, Xl) + contract_flops(T1, W1l) + contract_flops(T2, W2l) + contract_flops(T3, Rl);
     }
-    P->flops = P->c1->flops + P->c2->flops + P->c3->flops + P->c4->flops;
+
+    // ---------------- S1: one task per a-sector A with L and psi blocks
+    struct RowRef { int task; int64_t row; };
+    std::map<std::pair<int, int>, std::vector<RowRef>> t1_rows;   // (w element, a'-sector) -> rows
+    std::map<std::array<int, 4>, std::pair<int, int64_t>> t1_cols; // psi block sectors -> (task, first col)
+    std::vector<int64_t> t1_base, t1_ld;
+    std::vector<int> t1_sector;   // a-sector of every S1 task
+    JobBuilder bL, bX;
+    int tf = 0, tt = 0;
+    for (int A = 0; A < ia.nsect; ++A) {
+        std::vector<int> lb, xb;
+        for (int b = 0; b < L.nblocks(); ++b)
+            if (L.sect[(size_t)b * 3] == A) lb.push_back(b);
+        for (int b = 0; b < X.nblocks(); ++b)
+            if (X.sect[(size_t)b * 4] == A) xb.push_back(b);
+        if (lb.empty() || xb.empty()) continue;
+        const int t = (int)t1_base.size();
+        const int64_t K = ia.dim[A];
+        int64_t M = 0, N = 0;
+        for (int b : lb) M += (int64_t)L.bdim(b, 1) * L.bdim(b, 2);
+        for (int b : xb) N += X.belems(b) / K;
+        P->oL.add_task(M, K);
+        P->oX.add_task(N, K);
+        bL.task(M, K);
+        bX.task(N, K);
+        // rows (w, a'): operand A = L^T, element (r = a', c = a)
+        int64_t row = 0;
+        for (int b : lb) {
+            const int Sx = L.sect[(size_t)b * 3 + 1], Ap = L.sect[(size_t)b * 3 + 2];
+            const int Dx = L.bdim(b, 1), Dap = L.bdim(b, 2);
+            for (int xl = 0; xl < Dx; ++xl) {
+                bL.rect(t, row, 0, Dap, K, {GatherTerm{1.0, L.off[b] + (int64_t)xl * Dap, 1, (int64_t)Dx * Dap, 1.0f}});
+                t1_rows[{(int)(iw.off[Sx] + xl), Ap}].push_back({t, row});
+                row += Dap;
+            }
+        }
+        // columns (s1, s2, b): operand B = psi^T, element (r = (s1,s2,b), c = a)
+        int64_t col = 0;
+        for (int b : xb) {
+            const int64_t nb = X.belems(b) / K;
+            bX.rect(t, col, 0, nb, K, {GatherTerm{1.0, X.off[b], 1, nb, 1.0f}});
+            t1_cols[{A, X.sect[(size_t)b * 4 + 1], X.sect[(size_t)b * 4 + 2], X.sect[(size_t)b * 4 + 3]}] = {t, col};
+            col += nb;
+        }
+        t1_base.push_back(P->t1_elems);
+        t1_ld.push_back(N);
+        t1_sector.push_back(A);
+        GemmTask g = gemm_task(M, N, K, P->oL, P->oX, t, false, tf);
+        g.c_base = P->t1_elems;
+        g.ldc = (int)N;
+        GemmTask h = gemm_task(M, N, K, P->oL, P->oX, t, true, tt);
+        h.c_base = P->t1_elems;
+        h.ldc = (int)N;
+        h.c_f32 = 1;
+        tf += g.mt * g.nt;
+        tt += h.mt * h.nt;
+        P->g1.f64.push_back(g);
+        P->g1.tc.push_back(h);
+        P->t1_elems += rup(M * N, 4);
+    }
+    P->g1.tiles64 = tf;
+    P->g1.tilestc = tt;
+
+    // ---------------- two-site MPO product W12[(w,s1,s2) -> (w2,s1',s2')]
+    struct W12Term { int x, s1, s2; double v; };
+    std::map<std::array<int, 3>, std::vector<W12Term>> w12;   // (w2, s1', s2') -> terms
+    {
+        auto e1 = mpo_entries(W1, s), e2 = mpo_entries(W2, s);
+        std::map<int, std::vector<MpoEntry>> by_w1;
+        for (auto& e : e2) by_w1[e.l].push_back(e);
+        std::map<std::array<int, 6>, double> acc;
+        for (auto& a : e1) {
+            auto it = by_w1.find(a.r);
+            if (it == by_w1.end()) continue;
+            for (auto& b : it->second) acc[{b.r, a.sp, b.sp, a.l, a.s, b.s}] += a.v * b.v;
+        }
+        for (auto& kv : acc)
+            if (kv.second != 0.0)
+                w12[{kv.first[0], kv.first[1], kv.first[2]}].push_back({kv.first[3], kv.first[4], kv.first[5], kv.second});
+    }
+
+    // ---------------- S4: one task per b'-sector; fused S2+S3 fills operand A
+    JobBuilder bR;
+    CellBuilder bW;
+    std::vector<int64_t> roff;
+    std::vector<char> covered(X.nblocks(), 0);
+    tf = tt = 0;
+    const Index& ibp = R.inds[2];
+    for (int Bp = 0; Bp < ibp.nsect; ++Bp) {
+        std::vector<int> yb, rb;
+        for (int b = 0; b < X.nblocks(); ++b)
+            if (X.sect[(size_t)b * 4 + 3] == Bp) yb.push_back(b);
+        for (int b = 0; b < R.nblocks(); ++b)
+            if (R.sect[(size_t)b * 3 + 2] == Bp) rb.push_back(b);
+        if (yb.empty() || rb.empty()) continue;
+        const int t = (int)P->g4.f64.size();
+        const int64_t N = ibp.dim[Bp];
+        int64_t M = 0, K = 0;
+        for (int b : yb) M += X.belems(b) / N;
+        for (int b : rb) K += (int64_t)R.bdim(b, 0) * R.bdim(b, 1);
+        P->oT.add_task(M, K);
+        P->oR.add_task(N, K);
+        bR.task(N, K);
+        // K pieces (w2 element z, b-sector B): operand B = R^T, element (r = b', c = b)
+        struct KPiece { int z, B; int64_t col; int Db; };
+        std::vector<KPiece> kp;
+        int64_t col = 0;
+        for (int b : rb) {
+            const int B = R.sect[(size_t)b * 3], Sz = R.sect[(size_t)b * 3 + 1];
+            const int Db = R.bdim(b, 0), Dz = R.bdim(b, 1);
+            for (int zl = 0; zl < Dz; ++zl) {
+                bR.rect(t, 0, col, N, Db, {GatherTerm{1.0, R.off[b] + (int64_t)zl * N, 1, (int64_t)Dz * N, 1.0f}});
+                kp.push_back({(int)(iz.off[Sz] + zl), B, col, Db});
+                col += Db;
+            }
+        }
+        // row pieces (s1', s2', a'): every row of every psi block of this b'-sector
+        int64_t row = 0;
+        const int64_t roff0 = (int64_t)roff.size();
+        for (int b : yb) {
+            covered[b] = 1;
+            const int Ap = X.sect[(size_t)b * 4], S1p = X.sect[(size_t)b * 4 + 1], S2p = X.sect[(size_t)b * 4 + 2];
+            const int Dap = X.bdim(b, 0), d1 = X.bdim(b, 1), d2 = X.bdim(b, 2);
+            for (int u1 = 0; u1 < d1; ++u1)
+                for (int u2 = 0; u2 < d2; ++u2) {
+                    const int s1p = (int)(is1.off[S1p] + u1), s2p = (int)(is2.off[S2p] + u2);
+                    for (int al = 0; al < Dap; ++al)
+                        roff.push_back(X.off[b] + (((int64_t)al * d1 + u1) * d2 + u2) * N);
+                    for (const KPiece& k : kp) {
+                        auto it = w12.find({k.z, s1p, s2p});
+                        if (it == w12.end()) continue;
+                        std::vector<CellBuilder::Term> tm;
+                        for (const W12Term& e : it->second) {
+                            auto rr = t1_rows.find({e.x, Ap});
+                            if (rr == t1_rows.end()) continue;
+                            const auto ps1 = locate(is1, e.s1), ps2 = locate(is2, e.s2);
+                            for (const RowRef& ref : rr->second) {
+                                // T1 columns of the psi block (A of the row's task, S1, S2, B)
+                                auto ci = t1_cols.find({t1_sector[ref.task], ps1.first, ps2.first, k.B});
+                                if (ci == t1_cols.end()) continue;
+                                const int ds2 = is2.dim[ps2.first];
+                                const int64_t c0 = ci->second.second + ((int64_t)ps1.second * ds2 + ps2.second) * k.Db;
+                                const int64_t ld = t1_ld[ref.task];
+                                tm.push_back({t1_base[ref.task] + ref.row * ld + c0, ld, e.v});
+                            }
+                        }
+                        bW.add(Ap, k.B, Dap, k.Db, t, row, k.col, std::move(tm));
+                    }
+                    row += Dap;
+                }
+        }
+        GemmTask g = gemm_task(M, N, K, P->oT, P->oR, t, false, tf);
+        GemmTask h = gemm_task(M, N, K, P->oT, P->oR, t, true, tt);
+        g.use_roff = h.use_roff = 1;
+        g.roff = h.roff = roff0;
+        tf += g.mt * g.nt;
+        tt += h.mt * h.nt;
+        P->g4.f64.push_back(g);
+        P->g4.tc.push_back(h);
+    }
+    P->g4.tiles64 = tf;
+    P->g4.tilestc = tt;
+    for (int b = 0; b < X.nblocks(); ++b) P->zero_y |= !covered[b];
+    if (X.packed_total() < X.size) P->zero_y = true;
+
+    // ---------------- device side
+    bX.finish(P->jX, s);
+    bW.finish(P->jW, s);
+    GatherJob jL, jR;
+    bL.finish(jL, s);
+    bR.finish(jR, s);
+    for (HeffOperand* o : {&P->oL, &P->oX, &P->oT, &P->oR}) upload_operand(*o, s);
+    finish_gemm(P->g1, s);
+    finish_gemm(P->g4, s);
+    P->row_off = upload(roff, s);
+    P->t1.alloc((size_t)std::max<int64_t>(P->t1_elems, 1) * sizeof(double));
+    const int pl = P->planes;
+    auto tc_bytes = [&](const HeffOperand& o) { return (size_t)o.tiles * pl * kTcTileElems * 2; };
+    auto f64_bytes = [](const HeffOperand& o) { return (size_t)o.elems64 * sizeof(double); };
+    P->opX.alloc(std::max<size_t>({f64_bytes(P->oX), tc_bytes(P->oX), 16}));
+    // operand A of S4: the MPO step writes only the covered sub-blocks, the
+    // rest (padding, sub-blocks without a W12 entry) stays zero from here on
+    P->opT64.alloc(std::max<size_t>(f64_bytes(P->oT), 16));
+    CUDA_CHECK(cudaMemsetAsync(P->opT64.p, 0, P->opT64.bytes, s));
+    if (pl > 0) {
+        P->opTtc.alloc(std::max<size_t>(tc_bytes(P->oT), 16));
+        CUDA_CHECK(cudaMemsetAsync(P->opTtc.p, 0, P->opTtc.bytes, s));
+    }
+    P->L64.alloc(std::max<size_t>(f64_bytes(P->oL), 16));
+    P->R64.alloc(std::max<size_t>(f64_bytes(P->oR), 16));
+    launch_gather(jL, P->oL.d_g64.as<OpGeom>(), L.data, P->L64.p, 0, s, "heff_pack_env");
+    launch_gather(jR, P->oR.d_g64.as<OpGeom>(), R.data, P->R64.p, 0, s, "heff_pack_env");
+    if (pl > 0) {
+        P->Ltc.alloc(std::max<size_t>(tc_bytes(P->oL), 16));
+        P->Rtc.alloc(std::max<size_t>(tc_bytes(P->oR), 16));
+        launch_gather(jL, P->oL.d_gtc.as<OpGeom>(), L.data, P->Ltc.p, pl, s, "heff_pack_env");
+        launch_gather(jR, P->oR.d_gtc.as<OpGeom>(), R.data, P->Rtc.p, pl, s, "heff_pack_env");
+    }
+    CUDA_CHECK(cudaGetLastError());
+    if (std::getenv("TNH_DEBUG"))
+        std::fprintf(stderr,
+                     "heff_plan: n %lld, S1 %zu tasks %d tiles, T1 %lld, S4 %zu tasks %d tiles, T3 %lld, "
+                     "MPO step %zu cells %zu ctas %zu inputs %zu outputs %zu terms (max %d inputs)\n",
+                     (long long)P->n, P->g1.tc.size(), P->g1.tilestc, (long long)P->t1_elems, P->g4.tc.size(),
+                     P->g4.tilestc, (long long)P->oT.elems64, P->jW.cells.size(), P->jW.ctas.size(),
+                     P->jW.ins.size(), P->jW.outs.size(), P->jW.terms.size(), P->jW.max_in);
+    // the host tables and the caller's L, R must stay alive until these ran
     CUDA_CHECK(cudaStreamSynchronize(s));
     return P;
 }
@@ -99,10 +539,31 @@ void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
     Ctx* ctx = P.ctx;
     TNH_REQUIRE(prec == TNH_FP64 || prec == P.prec, TNH_ERR_ARG,
                 "heff_apply: precision %d not prepared by this plan", (int)prec);
-    run_contract(ctx, *P.c1, P.Lp, x, P.t1.as<double>(), prec, P.ws);
-    run_contract(ctx, *P.c2, P.t1.as<double>(), P.W1p, P.t2.as<double>(), prec, P.ws);
-    run_contract(ctx, *P.c3, P.t2.as<double>(), P.W2p, P.t3.as<double>(), prec, P.ws);
-    run_contract(ctx, *P.c4, P.t3.as<double>(), P.Rp, y, prec, P.ws);
+    cudaStream_t s = P.stream;
+    if (P.zero_y && P.n > 0) CUDA_CHECK(cudaMemsetAsync(y, 0, (size_t)P.n * sizeof(double), s));
+    if (P.g1.f64.empty() || P.g4.f64.empty()) {
+        if (!P.zero_y && P.n > 0) CUDA_CHECK(cudaMemsetAsync(y, 0, (size_t)P.n * sizeof(double), s));
+        return;
+    }
+    const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
+    if (prec == TNH_FP64) {
+        launch_gather(P.jX, P.oX.d_g64.as<OpGeom>(), x, P.opX.p, 0, s, "heff_pack_x");
+        launch_gemm_f64(P.g1.d_f64.as<GemmTask>(), n1, P.g1.tiles64, P.L64.as<double>(), P.opX.as<double>(),
+                        P.t1.as<double>(), s);
+        launch_w12(P.jW, P.oT.d_g64.as<OpGeom>(), P.t1.as<double>(), P.opT64.p, 0, s);
+        launch_gemm_f64(P.g4.d_f64.as<GemmTask>(), n4, P.g4.tiles64, P.opT64.as<double>(), P.R64.as<double>(), y, s,
+                        P.row_off.as<int64_t>());
+    } else {
+        const int pl = P.planes;
+        int* err = ctx->d_flag.as<int>();
+        launch_gather(P.jX, P.oX.d_gtc.as<OpGeom>(), x, P.opX.p, pl, s, "heff_pack_x");
+        launch_gemm_tc(P.g1.d_tc.as<GemmTask>(), n1, P.g1.tilestc, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(),
+                       P.t1.as<double>(), pl, ctx->num_sms, err, s);
+        launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, pl, s);
+        launch_gemm_tc(P.g4.d_tc.as<GemmTask>(), n4, P.g4.tilestc, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y, pl,
+                       ctx->num_sms, err, s, P.row_off.as<int64_t>());
+    }
+    CUDA_CHECK(cudaGetLastError());
 }
 
 }  // namespace tnh

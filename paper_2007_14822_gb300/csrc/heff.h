@@ -1,29 +1,51 @@
 // Effective-Hamiltonian plan and the device Lanczos eigensolver.
 #pragma once
 
+#include "gather.h"
 #include "tnh_internal.h"
 
 namespace tnh {
+
+// One GEMM operand of the plan in both formats (float64 rows for the FP64
+// GEMM, split-bfloat16 tiles for the tcgen05 GEMM), per task.
+struct HeffOperand {
+    std::vector<OpGeom> g64, gtc;
+    int64_t elems64 = 0, tiles = 0;
+    DevBuf d_g64, d_gtc;
+    void add_task(int64_t rows, int64_t K);
+};
+struct HeffGemm {
+    std::vector<GemmTask> f64, tc;
+    int tiles64 = 0, tilestc = 0;
+    DevBuf d_f64, d_tc;
+};
 
 struct HeffPlan {
     Ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;   // copy: freeing a plan never touches ctx
     tnh_precision prec = TNH_FP64;
+    int planes = 0;         // split-bfloat16 planes of prec (0 for FP64)
     int64_t n = 0;          // elements of the two-site state
     Layout psi;             // its layout
-    double flops = 0.0;
-    std::unique_ptr<ContractPlan> c1, c2, c3, c4;
-    DevBuf t1, t2, t3, Ld, Rd, W1d, W2d;     // owned copies (public entry point)
-    const double *Lp = nullptr, *Rp = nullptr, *W1p = nullptr, *W2p = nullptr;
-    Workspace ws;
+    double flops = 0.0;     // method flops of one application (S1..S4)
+    // operands: S1 = L (A) x psi (B), S4 = T3 (A) x R (B)
+    HeffOperand oL, oX, oT, oR;
+    GatherJob jX;           // per application: pack psi
+    W12Job jW;              // per application: fused S2+S3
+    HeffGemm g1, g4;
+    DevBuf L64, Ltc, R64, Rtc;   // L and R packed once
+    DevBuf opX;             // operand B of S1 (either format)
+    DevBuf opT64, opTtc;    // operand A of S4, one per format
+    DevBuf t1;              // S1 result (float32 in the split modes)
+    DevBuf row_off;         // S4 output row -> element offset in psi's layout
+    int64_t t1_elems = 0;
+    bool zero_y = false;    // some output rows are written by no S4 task
     ~HeffPlan();
 };
 
-// copy_inputs: keep private copies of L, W1, W2, R (else reference the
-// caller's device data, which must outlive the plan)
+// L, W1, W2, R are read while the plan is made and not referenced after.
 std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
-                                    const Layout& R, const Layout& psi, tnh_precision prec,
-                                    bool copy_inputs = true);
+                                    const Layout& R, const Layout& psi, tnh_precision prec);
 void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y);
 
 struct EigResult {

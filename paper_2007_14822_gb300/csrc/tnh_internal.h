@@ -179,13 +179,16 @@ struct GemmTask {
     int64_t c_base;
     int ldc;
     int tile0;               // prefix sum of mt * nt
+    int use_roff;            // 1: row m of C starts at row_off[roff + m] (scatter epilogue)
+    int c_f32;               // tcgen05 GEMM only: C is float32 (else float64)
+    int64_t roff;
 };
 void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, int total_tiles, const double* A,
-                     const double* B, double* C, cudaStream_t s);
+                     const double* B, double* C, cudaStream_t s, const int64_t* row_off = nullptr);
 // tcgen05 split-bf16 GEMM; planes in {1,2,3}; err is a device int flag.
 void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A,
                     const uint16_t* B, double* C, int planes, int num_sms, int* err,
-                    cudaStream_t s);
+                    cudaStream_t s, const int64_t* row_off = nullptr);
 constexpr int kF64TileM = 64, kF64TileN = 64, kF64TileK = 16;
 constexpr int kTcTileM = 128, kTcTileN = 128, kTcTileK = 64;
 constexpr int kTcTileElems = kTcTileM * kTcTileK;   // 8192 bf16 per plane tile
@@ -213,6 +216,8 @@ struct ContractPlan {
 // Label-matched plan for C = A * B (validates labels and arrows).
 std::unique_ptr<ContractPlan> plan_contract(const Layout& A, const Layout& B, const Layout& C,
                                             cudaStream_t s);
+// Flops (2 M N K summed over block pairs) of the contraction A * B.
+double contract_flops(const Layout& A, const Layout& B);
 // Workspace big enough for one execution of the plan in a precision.
 struct Workspace {
     DevBuf a, b, c;

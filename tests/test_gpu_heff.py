@@ -119,6 +119,40 @@ def test_heff_config2_full_size(ctx):
         assert err < TOL[p], (p, err)
 
 
+def _hub_link(rng, arrow):
+    from paper_2007_14822_gb300.tnh import Index
+    # (N, 2Sz) charges with N - 2Sz even, as on a Hubbard link
+    secs = [((n, sz), int(rng.integers(1, 6))) for n in range(-2, 3) for sz in range(-2, 3) if (n - sz) % 2 == 0]
+    return Index(secs, arrow)
+
+
+@pytest.mark.parametrize("model,j", [("j1j2", 0), ("j1j2", 3), ("j1j2", 6), ("hubbard", 2)])
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_heff_distinct_mpo_tensors(ctx, model, j, p):
+    # W1 != W2 (long-range J1-J2 MPO incl. the boundary sites; Hubbard with
+    # U(1) x U(1) charges and d = 4), random environments on a QN link
+    import torch
+    from paper_2007_14822_gb300 import models as pm
+    rng = np.random.default_rng(17 + j)
+    if model == "j1j2":
+        mpo = pm.to_device(pm.j1j2_chain(8, 1.0, 0.5), qn=True)
+        a = H.link_index(36, 7, 9, +1)
+    else:
+        mpo = pm.to_device(pm.hubbard(6, 1.0, 4.0), qn=True)
+        a = _hub_link(rng, +1)
+    W1, W2 = mpo[j], mpo[j + 1]
+    L, Lo = H.random_pair([a.dag(), W1.inds[0].dag(), a], None, 21 + j, "L")
+    R, Ro = H.random_pair([a, W2.inds[1].dag(), a.dag()], None, 22 + j, "R")
+    psi, psio = H.random_pair([a, W1.inds[3], W2.inds[3], a.dag()], None, 23 + j, "psi")
+    plan = ctx.heff_plan(L, W1, W2, R, psi, prec(p))
+    y = torch.zeros_like(psi.data)
+    plan.apply(psi.data, y)
+    yt = psi.with_inds(psi.inds)
+    yt.data = y
+    want = D.heff_apply(Lo, H.to_oracle(W1), H.to_oracle(W2), Ro, psio)
+    assert H.rel_err(H.to_oracle(yt), want) < TOL[p]
+
+
 @pytest.mark.parametrize("p,tol", [("bf16x3", 1e-3), ("bf16", 2e-2)])
 def test_heff_low_precision_modes_error_bounded(ctx, p, tol):
     err, _ = _heff_case(ctx, 64, 1, p)
