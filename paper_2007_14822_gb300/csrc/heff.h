@@ -40,6 +40,18 @@ struct HeffPlan {
     DevBuf row_off;         // S4 output row -> element offset in psi's layout
     int64_t t1_elems = 0;
     bool zero_y = false;    // some output rows are written by no S4 task
+    // one CUDA graph per format (float64, split): the four launches of an
+    // application, replayed with the x and y arguments patched in
+    struct Graph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t nx = nullptr, ny = nullptr;   // the kernel nodes reading x / writing y
+        std::vector<void*> ax, ay;                    // their argument pointer arrays
+        int ix = 0, iy = 0;                           // index of x / y among the arguments
+        const double* x = nullptr;
+        double* y = nullptr;
+        int calls = 0;
+    } graphs[2];
     ~HeffPlan();
 };
 

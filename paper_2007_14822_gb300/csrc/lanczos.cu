@@ -236,6 +236,20 @@ __global__ void tridiag_lowest(const double* __restrict__ alpha, double* __restr
     }
 }
 
+// Fixed-length runs (tol <= 0) need the tridiagonal eigenpair only at the
+// end: intermediate steps only record beta_j = |w| (and alpha_j as a scale
+// for the breakdown test).
+__global__ void set_beta(const double* __restrict__ alpha_j, const double* __restrict__ beta2_last,
+                         double* __restrict__ beta_j, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double bk = sqrt(fmax(*beta2_last, 0.0));
+        *beta_j = bk;
+        out[0] = *alpha_j;
+        out[1] = bk;
+        out[2] = bk;
+    }
+}
+
 int grid_for(int64_t n, int nsms) {
     int64_t g = (n + 255) / 256;
     int64_t cap = (int64_t)nsms * 8;
@@ -322,8 +336,12 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
             }
         }
         vdot(ctx, vw, w, w, n, misc + 1);
-        { KScope ks_("tridiag_lowest", s);
-        tridiag_lowest<<<1, 256, 0, s>>>(alpha, beta, j + 1, misc + 1, out, sv);
+        if (tol > 0.0 || j + 1 == kmax) {
+            KScope ks_("tridiag_lowest", s);
+            tridiag_lowest<<<1, 256, 0, s>>>(alpha, beta, j + 1, misc + 1, out, sv);
+        } else {
+            KScope ks_("set_beta", s);
+            set_beta<<<1, 32, 0, s>>>(alpha + j, misc + 1, beta + j, out);
         }
         CUDA_CHECK(cudaMemcpyAsync(host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CUDA_CHECK(cudaStreamSynchronize(s));
@@ -331,7 +349,14 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
         TNH_REQUIRE(std::isfinite(host[0]) && std::isfinite(host[1]), TNH_ERR_NUMERIC,
                     "eigsolve: non-finite Ritz value at step %d", j);
         const double scale = std::max(1.0, std::fabs(host[0]));
-        if (host[1] <= tol * scale || host[2] <= 1e-14 * scale || j + 1 == kmax) break;
+        if (host[2] <= 1e-14 * scale || j + 1 == kmax) {
+            if (!(tol > 0.0 || j + 1 == kmax)) {   // breakdown in a fixed-length run: T_k was not solved yet
+                KScope ks_("tridiag_lowest", s);
+                tridiag_lowest<<<1, 256, 0, s>>>(alpha, beta, j + 1, misc + 1, out, sv);
+            }
+            break;
+        }
+        if (tol > 0.0 && host[1] <= tol * scale) break;
         { KScope ks_("scale_copy", s);
         scale_copy<<<g, 256, 0, s>>>(w, q + (int64_t)(j + 1) * n, n, nullptr, beta + j, 2);
         }

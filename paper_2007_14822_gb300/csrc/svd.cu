@@ -15,7 +15,7 @@
 //    b. The candidate columns (the largest float32 singular values: maxdim
 //       plus a margin, and all within 1e-4 of the largest) are
 //       re-orthonormalised and re-formed in float64, Y = X V32[:, cand], and
-//       polished by float64 one-sided Jacobi (a warp per column pair), which
+//       polished by float64 one-sided Jacobi (a CTA per column pair), which
 //       converges in one or two sweeps because Y is already nearly
 //       orthogonal.
 //    c. The float64 singular values sigma_j = |Y_j| are pooled, ranked
@@ -88,6 +88,28 @@ __device__ __forceinline__ T warp_sum(T v) {
 // round-robin (circle) schedule: slot j of round k among R+1 slots
 __device__ __forceinline__ int rr_pos(int j, int k, int R) { return j == 0 ? 0 : 1 + (j - 1 + k) % R; }
 
+// ------------------------------------------------ convergence per group
+// A group (matrix) stops after a sweep in which no column pair had a
+// relative off-diagonal |x_p.x_q| / (|x_p||x_q|) above thr: every pair was
+// rotated to zero in that sweep, so what is left is second order in thr.
+// smax[3 g + s % 3] holds the float bits of the largest value seen in
+// sweep s; slot (s + 1) % 3 is cleared at the start of sweep s, when no CTA
+// can still read it, and a finished sweep's slot is read only after the
+// grid barrier that ends it. Every CTA therefore takes the same decision.
+__device__ __forceinline__ bool group_done(const int* smax, int g, int R, int rounds_done, float thr) {
+    const int sw = rounds_done / R;
+    if (sw < 1) return false;
+    return __int_as_float(*(volatile const int*)&smax[3 * g + (sw - 1) % 3]) < thr;
+}
+
+template <class GroupT>
+__device__ bool all_done(const GroupT* groups, int ngroups, const int* smax, int rounds_done, float thr) {
+    int mine = 1;
+    for (int g = threadIdx.x; g < ngroups; g += blockDim.x)
+        mine &= group_done(smax, g, groups[g].rounds, rounds_done, thr);
+    return __syncthreads_and(mine) != 0;
+}
+
 // ------------------------------------------------ stage a: float32 blocks
 struct BGroup {
     int64_t x_off;   // column-major X32: n columns of length len
@@ -99,15 +121,27 @@ struct BGroup {
     int pair0;       // first global block-pair index
 };
 
-// state[0] = last round with a rotation anywhere, state[1] = rounds done
-// fro2[g] = |X_g|_F^2; columns whose squared norm is below 1e-12 fro2 are
-// float32 rounding noise and are not rotated (they would mix forever).
-__global__ void block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups, int total_pairs, int max_rounds,
-                                 int rmax, float* __restrict__ X, float* __restrict__ V, int* __restrict__ last_rot,
-                                 int* state, GridBar* bar, int* err, int stride, const double* __restrict__ fro2) {
+constexpr int kBJThreads = 256;
+constexpr int kBJWarpsPerPair = 1;
+constexpr float kTol32 = 1e-5f;    // float32 rotation threshold
+constexpr float kDone32 = 2e-3f;   // float32 stop (the float64 polish finishes)
+
+// state[1] = rounds done. fro2[g] = |X_g|_F^2; columns whose squared norm
+// is below 1e-12 fro2 are float32 rounding noise and are not rotated (they
+// would mix forever). Each column pair of the inner sweep is handled by
+// kBJWarpsPerPair warps (interleaved rows; more warps per pair did not pay
+// for the extra barrier on GB300).
+__global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups,
+                                                               int total_pairs, int max_rounds, float* __restrict__ X,
+                                                               float* __restrict__ V, int* smax, int* state,
+                                                               GridBar* bar, int* err, int stride,
+                                                               const double* __restrict__ fro2) {
     extern __shared__ float sm[];            // [2b][stride]: X part (len) then V part (n)
-    __shared__ int rotated, skip;
+    __shared__ float red[kBJThreads / 32 / kBJWarpsPerPair][kBJWarpsPerPair][3];   // one slot per pair (<= 8)
+    __shared__ int skip;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int ngrp = nwarp / kBJWarpsPerPair, gw = warp / kBJWarpsPerPair, part = warp % kBJWarpsPerPair;
+    const int rstep = 32 * kBJWarpsPerPair, r0 = part * 32 + lane;
     unsigned epoch = 0;
     int t = 0;
     for (; t < max_rounds; ++t) {
@@ -119,14 +153,16 @@ __global__ void block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups,
             }
             const BGroup G = groups[lo];
             const int R = G.rounds;
-            // one thread decides whether the group has converged, so the
-            // whole CTA takes the same branch around its barriers
-            if (threadIdx.x == 0) skip = (t - *(volatile int*)&last_rot[lo] > R);
+            const int i = item - G.pair0, k = t % R;
+            // one thread decides, so the whole CTA takes the same branch
+            if (threadIdx.x == 0) {
+                skip = group_done(smax, lo, R, t, kDone32);
+                if (k == 0 && i == 0) smax[3 * lo + (t / R + 1) % 3] = 0;
+            }
             __syncthreads();
             const int sk = skip;
             __syncthreads();   // every thread has read skip before thread 0 rewrites it
             if (sk) continue;
-            const int i = item - G.pair0, k = t % R;
             const int bp = rr_pos(i, k, R), bq = rr_pos(G.nblk - 1 - i, k, R);
             // local column list: block bp then block bq (clipped to n)
             const int p0 = bp * G.b, p1 = min(G.n, p0 + G.b);
@@ -144,53 +180,65 @@ __global__ void block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups,
 #pragma unroll 4
                 for (int r = lane; r < Nn; r += 32) d[L + r] = vs[r];
             }
-            if (threadIdx.x == 0) rotated = 0;
             __syncthreads();
             const int ne = nc + (nc & 1), Ri = ne - 1;
-            // float32 only has to find the dominant subspace; float64 finishes
-            const float tol = 2e-6f;
             const float null2 = (float)(1e-12 * fro2[lo]);
-            {
-                for (int ir = 0; ir < Ri; ++ir) {
-                    for (int pr = warp; pr < ne / 2; pr += nwarp) {
-                        const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
-                        if (a >= nc || bb >= nc) continue;
-                        float* xa = sm + (size_t)a * stride;
-                        float* xb = sm + (size_t)bb * stride;
-                        float al = 0.f, be = 0.f, ga = 0.f, al2 = 0.f, be2 = 0.f, ga2 = 0.f;
-                        int r = lane;
-                        for (; r + 32 < L; r += 64) {          // two independent chains
-                            float u = xa[r], v = xb[r], u2 = xa[r + 32], v2 = xb[r + 32];
-                            al = fmaf(u, u, al);
-                            be = fmaf(v, v, be);
-                            ga = fmaf(u, v, ga);
-                            al2 = fmaf(u2, u2, al2);
-                            be2 = fmaf(v2, v2, be2);
-                            ga2 = fmaf(u2, v2, ga2);
-                        }
-                        if (r < L) {
-                            float u = xa[r], v = xb[r];
+            float wmax = 0.f;
+            for (int ir = 0; ir < Ri; ++ir) {
+                for (int pr = gw; pr < ne / 2; pr += ngrp) {
+                    const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
+                    float al = 0.f, be = 0.f, ga = 0.f;
+                    if (a < nc && bb < nc) {
+                        const float* xa = sm + (size_t)a * stride;
+                        const float* xb = sm + (size_t)bb * stride;
+                        for (int r = r0; r < L; r += rstep) {
+                            const float u = xa[r], v = xb[r];
                             al = fmaf(u, u, al);
                             be = fmaf(v, v, be);
                             ga = fmaf(u, v, ga);
                         }
-                        al = warp_sum(al + al2);
-                        be = warp_sum(be + be2);
-                        ga = warp_sum(ga + ga2);
-                        if (!(fabsf(ga) > tol * sqrtf(al * be)) || al <= null2 || be <= null2) continue;
-                        const float zeta = (be - al) / (2.0f * ga);
-                        const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                        const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
-#pragma unroll 4
-                        for (int rr = lane; rr < L + Nn; rr += 32) {
-                            float u = xa[rr], v = xb[rr];
-                            xa[rr] = c * u - sn * v;
-                            xb[rr] = sn * u + c * v;
-                        }
-                        if (lane == 0) rotated = 1;
                     }
-                    __syncthreads();
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {   // three interleaved butterflies
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    }
+                    if (lane == 0) {
+                        red[pr][part][0] = al;
+                        red[pr][part][1] = be;
+                        red[pr][part][2] = ga;
+                    }
                 }
+                __syncthreads();
+                for (int pr = gw; pr < ne / 2; pr += ngrp) {
+                    const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
+                    if (a >= nc || bb >= nc) continue;
+                    // the same sums in the same order in every warp of the pair
+                    float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kBJWarpsPerPair; ++w) {
+                        al += red[pr][w][0];
+                        be += red[pr][w][1];
+                        ga += red[pr][w][2];
+                    }
+                    if (al <= null2 || be <= null2) continue;
+                    const float rel = fabsf(ga) / sqrtf(al * be);
+                    wmax = fmaxf(wmax, rel);
+                    if (!(rel > kTol32)) continue;
+                    const float zeta = (be - al) / (2.0f * ga);
+                    const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
+                    float* xa = sm + (size_t)a * stride;
+                    float* xb = sm + (size_t)bb * stride;
+#pragma unroll 4
+                    for (int rr = r0; rr < L + Nn; rr += rstep) {
+                        const float u = xa[rr], v = xb[rr];
+                        xa[rr] = c * u - sn * v;
+                        xb[rr] = sn * u + c * v;
+                    }
+                }
+                __syncthreads();
             }
             for (int c = warp; c < nc; c += nwarp) {
                 const int col = c < np ? p0 + c : q0 + (c - np);
@@ -202,14 +250,11 @@ __global__ void block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups,
 #pragma unroll 4
                 for (int r = lane; r < Nn; r += 32) vs[r] = d[L + r];
             }
-            if (threadIdx.x == 0 && rotated) {
-                atomicMax(&last_rot[lo], t);
-                atomicMax(&state[0], t);
-            }
+            if (lane == 0 && part == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
             __syncthreads();
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
-        if (t - *(volatile int*)&state[0] > rmax) { ++t; break; }
+        if (all_done(groups, ngroups, smax, t + 1, kDone32)) { ++t; break; }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
@@ -223,18 +268,28 @@ struct JGroup {
     int grp;         // group (index into fro2)
 };
 
-// columns whose squared norm is below 1e-28 |M_g|_F^2 are float64 rounding
-// noise and are not rotated
-__global__ void jacobi_f64(const JGroup* __restrict__ groups, int ngroups, int total_pairs, int max_rounds, int rmax,
-                           double* __restrict__ X, int* __restrict__ last_rot, int* state, GridBar* bar, int* err,
-                           const double* __restrict__ fro2) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
+constexpr int kJ64Threads = 128;
+constexpr int kJ64Regs = 8;   // rows per thread kept in registers (len <= 1024)
+
+// One CTA per column pair and round: the two columns are read once into
+// registers (every thread a few rows), the three dot products are reduced
+// across the CTA, one thread computes the rotation. Columns whose squared
+// norm is below 1e-28 |M_g|_F^2 are float64 rounding noise and are not
+// rotated.
+constexpr float kDone64 = 1e-9f;   // float64 stop
+
+__global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restrict__ groups, int ngroups,
+                                                          int total_pairs, int max_rounds, double* __restrict__ X,
+                                                          int* smax, int* state, GridBar* bar, int* err,
+                                                          const double* __restrict__ fro2) {
+    __shared__ double red[3][kJ64Threads / 32];
+    __shared__ double rot[2];
+    __shared__ int act, skip;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned epoch = 0;
     int t = 0;
     for (; t < max_rounds; ++t) {
-        for (int pi = gw; pi < total_pairs; pi += nw) {
+        for (int pi = blockIdx.x; pi < total_pairs; pi += gridDim.x) {
             int lo = 0, hi = ngroups - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
@@ -242,63 +297,97 @@ __global__ void jacobi_f64(const JGroup* __restrict__ groups, int ngroups, int t
             }
             const JGroup G = groups[lo];
             const int R = G.rounds;
-            if (t - *(volatile int*)&last_rot[lo] > R) continue;
             const int i = pi - G.pair0, ne = R + 1, k = t % R;
+            if (tid == 0) {
+                skip = group_done(smax, lo, R, t, kDone64);
+                if (k == 0 && i == 0) smax[3 * lo + (t / R + 1) % 3] = 0;
+            }
+            __syncthreads();
+            const int sk = skip;
+            __syncthreads();
+            if (sk) continue;
             const int p = rr_pos(i, k, R), q = rr_pos(ne - 1 - i, k, R);
             if (p >= G.n || q >= G.n) continue;
             double* xp = X + G.x_off + (int64_t)p * G.len;
             double* xq = X + G.x_off + (int64_t)q * G.len;
             const int L = G.len;
+            const bool in_regs = L <= kJ64Regs * kJ64Threads;
+            double u[kJ64Regs], v[kJ64Regs];
             double a = 0, b = 0, g = 0;
-            // chunks of 8 elements per lane: the loads of a chunk are independent
-            for (int r0 = 0; r0 < L; r0 += 256) {
-                double u[8], v[8];
+            if (in_regs) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int r = r0 + e * 32 + lane;
+                for (int e = 0; e < kJ64Regs; ++e) {
+                    const int r = tid + e * kJ64Threads;
                     u[e] = r < L ? xp[r] : 0.0;
                     v[e] = r < L ? xq[r] : 0.0;
                 }
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
+                for (int e = 0; e < kJ64Regs; ++e) {
                     a = fma(u[e], u[e], a);
                     b = fma(v[e], v[e], b);
                     g = fma(u[e], v[e], g);
+                }
+            } else {
+                for (int r = tid; r < L; r += kJ64Threads) {
+                    const double x = xp[r], y = xq[r];
+                    a = fma(x, x, a);
+                    b = fma(y, y, b);
+                    g = fma(x, y, g);
                 }
             }
             a = warp_sum(a);
             b = warp_sum(b);
             g = warp_sum(g);
-            const double tol = fmax(1e-15, 2.0 * sqrt((double)L) * 1.1102230246251565e-16);
-            const double null2 = 1e-28 * fro2[G.grp];
-            if (!(fabs(g) > tol * sqrt(a * b)) || a <= null2 || b <= null2) continue;
-            const double zeta = (b - a) / (2.0 * g);
-            const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
-            for (int r0 = 0; r0 < L; r0 += 256) {
-                double u[8], v[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int r = r0 + e * 32 + lane;
-                    u[e] = r < L ? xp[r] : 0.0;
-                    v[e] = r < L ? xq[r] : 0.0;
+            if (lane == 0) {
+                red[0][warp] = a;
+                red[1][warp] = b;
+                red[2][warp] = g;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double A = 0, B = 0, Gg = 0;
+                for (int w = 0; w < kJ64Threads / 32; ++w) {
+                    A += red[0][w];
+                    B += red[1][w];
+                    Gg += red[2][w];
                 }
+                const double tol = 4.0 * sqrt((double)L) * 1.1102230246251565e-16;
+                const double null2 = 1e-28 * fro2[G.grp];
+                act = (fabs(Gg) > tol * sqrt(A * B)) && A > null2 && B > null2;
+                if (A > null2 && B > null2)
+                    atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int((float)(fabs(Gg) / sqrt(A * B))));
+                if (act) {
+                    const double zeta = (B - A) / (2.0 * Gg);
+                    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + tt * tt);
+                    rot[0] = c;
+                    rot[1] = c * tt;
+                }
+            }
+            __syncthreads();
+            if (act) {
+                const double c = rot[0], sn = rot[1];
+                if (in_regs) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int r = r0 + e * 32 + lane;
-                    if (r < L) {
-                        xp[r] = c * u[e] - sn * v[e];
-                        xq[r] = sn * u[e] + c * v[e];
+                    for (int e = 0; e < kJ64Regs; ++e) {
+                        const int r = tid + e * kJ64Threads;
+                        if (r < L) {
+                            xp[r] = c * u[e] - sn * v[e];
+                            xq[r] = sn * u[e] + c * v[e];
+                        }
+                    }
+                } else {
+                    for (int r = tid; r < L; r += kJ64Threads) {
+                        const double x = xp[r], y = xq[r];
+                        xp[r] = c * x - sn * y;
+                        xq[r] = sn * x + c * y;
                     }
                 }
             }
-            if (lane == 0) {
-                atomicMax(&last_rot[lo], t);
-                atomicMax(&state[0], t);
-            }
+            __syncthreads();   // red, rot and act are reused by the next pair
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
-        if (t - *(volatile int*)&state[0] > rmax) { ++t; break; }
+        if (all_done(groups, ngroups, smax, t + 1, kDone64)) { ++t; break; }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
@@ -594,13 +683,10 @@ inline unsigned blocks_for(int64_t n, int cap = 1024) {
 }
 
 // reset the convergence bookkeeping of a cooperative Jacobi launch
-void reset_state(DevBuf& last, DevBuf& state, DevBuf& bar, int n, cudaStream_t s) {
-    std::vector<int> minus1(n, -1);
-    CUDA_CHECK(cudaMemcpyAsync(last.p, minus1.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    static const int st0[4] = {-1, 0, 0, 0};
-    CUDA_CHECK(cudaMemcpyAsync(state.p, st0, 16, cudaMemcpyHostToDevice, s));
+void reset_state(DevBuf& smax, DevBuf& state, DevBuf& bar, int n, cudaStream_t s) {
+    CUDA_CHECK(cudaMemsetAsync(smax.p, 0, (size_t)3 * n * 4, s));
+    CUDA_CHECK(cudaMemsetAsync(state.p, 0, 16, s));
     CUDA_CHECK(cudaMemsetAsync(bar.p, 0, 16, s));
-    // minus1 is pageable: the copy above is staged before returning
 }
 
 }  // namespace
@@ -726,8 +812,10 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     if (ng == 0) return R;
     // one block width for all groups: up to 8 columns while a block pair
     // (X and V columns) fits in shared memory
+    // (at most 8 column pairs per inner step: one per group of warps)
     bmax = 8;
     while (bmax > 1 && (size_t)2 * bmax * stride * 4 > 200 * 1024) bmax >>= 1;
+    static_assert(kBJThreads / 32 / kBJWarpsPerPair >= 8, "one warp group per column pair of a block pair");
     for (auto& G : bg) {
         G.b = bmax;
         int nb = (G.n + bmax - 1) / bmax;
@@ -769,9 +857,9 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     }
     // ---- stage a: float32 block Jacobi
     {
-        DevBuf d_last((size_t)ng * 4), d_state(16), d_bar(16);
-        reset_state(d_last, d_state, d_bar, ng, s);
-        const int threads = 256;
+        DevBuf d_smax((size_t)3 * ng * 4), d_state(16), d_bar(16);
+        reset_state(d_smax, d_state, d_bar, ng, s);
+        const int threads = kBJThreads;
         size_t smem = (size_t)2 * bmax * stride * 4;
         CUDA_CHECK(cudaFuncSetAttribute(block_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int bpsm = 0;
@@ -782,12 +870,11 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         const BGroup* gp = d_bg.as<BGroup>();
         float* Xp = X32.as<float>();
         float* Vp = V32.as<float>();
-        int* lastp = d_last.as<int>();
+        int* smaxp = d_smax.as<int>();
         int* statep = d_state.as<int>();
         GridBar* barp = d_bar.as<GridBar>();
-        void* args[] = {(void*)&gp,    (void*)&ng,     (void*)&bpairs, (void*)&max_rounds, (void*)&rmax,
-                        (void*)&Xp,    (void*)&Vp,     (void*)&lastp,  (void*)&statep,     (void*)&barp,
-                        (void*)&errp,  (void*)&stride, (void*)&frop};
+        void* args[] = {(void*)&gp,   (void*)&ng,    (void*)&bpairs, (void*)&max_rounds, (void*)&Xp,   (void*)&Vp,
+                        (void*)&smaxp, (void*)&statep, (void*)&barp,  (void*)&errp,       (void*)&stride, (void*)&frop};
         {
             KScope ks("svd_jacobi_f32", s);
             CUDA_CHECK(cudaLaunchCooperativeKernel((void*)block_jacobi_f32, dim3(grid), dim3(threads), args, smem, s));
@@ -955,9 +1042,9 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     {
         const int njg = (int)jg.size();
         DevBuf d_jg = upload(jg, s);
-        DevBuf d_last((size_t)njg * 4), d_state(16), d_bar(16);
-        reset_state(d_last, d_state, d_bar, njg, s);
-        const int threads = 32;   // one column pair per CTA spreads float64 work over the SMs
+        DevBuf d_smax((size_t)3 * njg * 4), d_state(16), d_bar(16);
+        reset_state(d_smax, d_state, d_bar, njg, s);
+        const int threads = kJ64Threads;   // one column pair per CTA spreads float64 work over the SMs
         int bpsm = 0;
         CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, jacobi_f64, threads, 0));
         int want = jpairs;
@@ -965,12 +1052,11 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         int max_rounds = 20 * jrmax + 8;
         const JGroup* gp = d_jg.as<JGroup>();
         double* Yp = R->Y.as<double>();
-        int* lastp = d_last.as<int>();
+        int* smaxp = d_smax.as<int>();
         int* statep = d_state.as<int>();
         GridBar* barp = d_bar.as<GridBar>();
-        void* args[] = {(void*)&gp,    (void*)&njg,    (void*)&jpairs, (void*)&max_rounds, (void*)&jrmax,
-                        (void*)&Yp,    (void*)&lastp,  (void*)&statep, (void*)&barp,       (void*)&errp,
-                        (void*)&frop};
+        void* args[] = {(void*)&gp,    (void*)&njg,   (void*)&jpairs, (void*)&max_rounds, (void*)&Yp,
+                        (void*)&smaxp, (void*)&statep, (void*)&barp,  (void*)&errp,       (void*)&frop};
         {
             KScope ks("svd_jacobi_f64", s);
             CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_f64, dim3(grid), dim3(threads), args, 0, s));

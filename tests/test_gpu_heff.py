@@ -112,6 +112,29 @@ def test_heff_qn(ctx, m, nsect, maxd, p):
     assert err < TOL[p], err
 
 
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_heff_graph_replay_with_new_buffers(ctx, p):
+    # the first application launches directly, the second captures a CUDA
+    # graph, later ones replay it with the x / y arguments patched: every
+    # call must give the oracle's result for its own input
+    import torch
+    d = H.heff_inputs(40, None, 5, nsect=7, maxd=12)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    from oracle.blocksparse import BlockTensor
+    xs = [d["psi"].data.clone() * (1.0 + 0.5 * i) for i in range(3)]
+    xs[2] = torch.flip(xs[2], [0])
+    ys = [torch.full_like(d["psi"].data, float("nan")) for _ in range(2)]
+    for call, (xi, yi) in enumerate([(0, 0), (0, 1), (1, 1), (2, 0), (1, 0), (2, 1)]):
+        x, y = xs[xi], ys[yi]
+        plan.apply(x, y)
+        xt = d["psi"].with_inds(d["psi"].inds)
+        xt.data = x
+        yt = d["psi"].with_inds(d["psi"].inds)
+        yt.data = y
+        want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], H.to_oracle(xt))
+        assert H.rel_err(H.to_oracle(yt), want) < TOL[p], (call, xi, yi)
+
+
 def test_heff_config2_full_size(ctx):
     # dense m=256, w=5, d=2: L/R (256,5,256), psi (256,2,2,256), Gaussian, seeded
     for p in ("fp64", "bf16x6"):
@@ -201,3 +224,17 @@ def test_eigsolve_dense(ctx, p):
     x = psi.cpu().numpy()
     ov = abs(float(x @ v[:, 0]))
     assert ov > 1 - (1e-10 if p == "fp64" else 1e-7)
+
+
+@pytest.mark.parametrize("m,k", [(20, 6), (1, 8)])
+def test_eigsolve_fixed_length_matches_oracle_lanczos(ctx, m, k):
+    # tol = 0: exactly k steps (the tridiagonal problem is solved only at the
+    # end) unless the Krylov space is exhausted first (m = 1: dim 4 < k)
+    d = H.heff_inputs(m, None, 13, nsect=1, symmetric=True)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec("fp64"))
+    psi = d["psi"].data.clone()
+    E, r, nmv = plan.eigsolve(psi, krylov_dim=k, tol=0.0)
+    apply = lambda x: D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], x)
+    Eo, xo, res, nmo = D.lanczos(apply, d["psio"], k, 0.0)
+    assert nmv == nmo
+    assert abs(E - Eo) < 1e-10 * abs(Eo)
