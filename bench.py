@@ -18,6 +18,14 @@ One step is one full two-site bond update, every row of the hot path:
 The reported metric counts the algorithmic flops of the step's contractions
 (theta + (K_LANCZOS + 1) H_eff products + environment update; the extra
 products of the bf16 split are not counted) divided by the step time.
+
+Two more measurements go on the same JSON line (skip with --no-extra):
+  heff_qn  H_eff TFLOP/s, BF16x6 and FP64, on three block-sparse workloads
+           (U(1) m=1024, U(1) J1-J2 cylinder m=2048, U(1)xU(1) Hubbard
+           m=4096); flops are the plan's block-pair sum
+  sweep    DMRG sweep time, BF16x6 vs FP64, U(1) Heisenberg chain N=100 at
+           steady m=256 (maxdim-limited), and the relative energy difference
+           of the two runs
 """
 from __future__ import annotations
 
@@ -114,6 +122,122 @@ class GpuBond:
             self.d2h_bytes = 8 + h.numel() * 8
             out["U"] = h
         return out
+
+
+# ---------------------------------------------- block-sparse H_eff workloads
+# (name, model, m, sector recipe, seed): U(1) Heisenberg m=1024 with 40
+# Gaussian sectors of 1..128; the J1-J2 6x24 cylinder (snake order, FSA MPO,
+# bulk sites 62/63, w=26) at m=2048 with 41 sectors of 1..256; U(1)xU(1)
+# Hubbard (U/t=4) at m=4096 with a 15x15 grid of (N, 2Sz) sectors of 1..128.
+QN_CONFIGS = [
+    ("U(1) Heisenberg, m=1024, w=5, 40 sectors of 1..128", "heis", 1024, (40, 128), 5),
+    ("U(1) J1-J2 cylinder 6x24, m=2048, w=26, 41 sectors of 1..256", "cyl", 2048, (41, 256), 6),
+    ("U(1)xU(1) Hubbard U/t=4, m=4096, w=6, d=4, 15x15 sectors of 1..128", "hub", 4096, (15, 128), 7),
+]
+
+
+def qn_link(kind, m, recipe):
+    from paper_2007_14822_gb300 import synth
+    from paper_2007_14822_gb300.tnh import Index
+    if kind == "hub":
+        n, maxd = recipe
+        dims = synth.gaussian_sectors_2d(m, (n, n), maxd)
+        secs = []
+        for u in range(n):          # up / down electrons relative to half filling
+            for v in range(n):
+                du, dv = u - (n - 1) // 2, v - (n - 1) // 2
+                secs.append(((du + dv, du - dv), int(dims[u, v])))
+        return Index(secs, +1)
+    nsect, maxd = recipe
+    dims = synth.gaussian_sectors(m, nsect, maxd)
+    return Index([((2 * (k - (nsect - 1) // 2),), d) for k, d in enumerate(dims)], +1)
+
+
+def qn_heff_inputs(kind, m, recipe, seed):
+    from paper_2007_14822_gb300 import models as pm, synth
+    from paper_2007_14822_gb300.tnh import Tensor
+    if kind == "heis":
+        mpo, j = pm.heisenberg(8), 3
+    elif kind == "cyl":
+        mpo, j = pm.spin_pairs(144, pm.cylinder_pairs(24, 6, 1.0, 0.5)), 62
+    else:
+        mpo, j = pm.hubbard(16, 1.0, 4.0), 7
+    W = pm.to_device(mpo, qn=True)
+    W1, W2 = W[j], W[j + 1]
+    a = qn_link(kind, m, recipe)
+    L = Tensor([a.dag(), W1.inds[0].dag(), a])
+    R = Tensor([a, W2.inds[1].dag(), a.dag()])
+    psi = Tensor([a, W1.inds[3], W2.inds[3], a.dag()])
+    for T, tag in ((L, "L"), (R, "R"), (psi, "psi")):
+        T.fill(lambda k, shp, tag=tag: synth.block_gaussian(seed, tag, k, shp))
+    return L, W1, W2, R, psi
+
+
+def time_apply(torch, plan, x, y, prec, reps):
+    for _ in range(2):
+        plan.apply(x, y, prec)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        plan.apply(x, y, prec)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def bench_qn_heff(ctx, torch, tnh):
+    out = []
+    for name, kind, m, recipe, seed in QN_CONFIGS:
+        L, W1, W2, R, psi = qn_heff_inputs(kind, m, recipe, seed)
+        t0 = time.perf_counter()
+        plan = ctx.heff_plan(L, W1, W2, R, psi, tnh.BF16x6)
+        t_plan = time.perf_counter() - t0
+        y = torch.empty_like(psi.data)
+        t_mix = time_apply(torch, plan, psi.data, y, None, 20)
+        t_64 = time_apply(torch, plan, psi.data, y, tnh.FP64, 3)
+        ctx.profile_begin()
+        plan.apply(psi.data, y)
+        prof = ctx.profile_end()
+        f = plan.flops
+        out.append({"workload": name, "psi_elems": plan.size, "flops_per_matvec": f,
+                    "bf16x6": {"ms": t_mix * 1e3, "tflops": f / t_mix / 1e12},
+                    "fp64": {"ms": t_64 * 1e3, "tflops": f / t_64 / 1e12},
+                    "plan_ms": t_plan * 1e3,
+                    "kernels_bf16x6": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}})
+        plan.free()
+        del L, R, psi, W1, W2, y
+        torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------- sweep time
+# U(1) Heisenberg chain N=100 from the Neel state, bond dimension schedule
+# 32, 64, 128, 256, 256 (cutoff 1e-14, so maxdim binds), 16 Lanczos steps at
+# most: the sweep time is the last sweep's (steady m = 256), both precisions.
+SWEEP_N = 100
+SWEEP_SCHEDULE = [(32, 1e-14), (64, 1e-14), (128, 1e-14), (256, 1e-14), (256, 1e-14)]
+
+
+def bench_sweeps(ctx, tnh):
+    from paper_2007_14822_gb300 import models as pm
+    mpo = pm.heisenberg(SWEEP_N)
+    res = {}
+    for name, prec, tol in (("bf16x6", tnh.BF16x6, 1e-7), ("fp64", tnh.FP64, 1e-9)):
+        W = pm.to_device(mpo, qn=True)
+        A = pm.product_state(W[0].inds[3], [0, 1] * (SWEEP_N // 2))
+        E, st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in SWEEP_SCHEDULE],
+                         [c for _, c in SWEEP_SCHEDULE], krylov_dim=16, tol=tol, prec=prec)
+        last = st[-1]
+        res[name] = {"energy": E, "last_sweep_s": last["seconds"], "maxlink": last["maxlink"],
+                     "matvecs_last_sweep": last["matvecs"], "truncerr": last["truncerr"],
+                     "sweep_s": [x["seconds"] for x in st]}
+    e64 = res["fp64"]["energy"]
+    res["dE_rel_mixed_vs_fp64"] = abs(res["bf16x6"]["energy"] - e64) / abs(e64)
+    res["energy_per_bond_fp64"] = e64 / (SWEEP_N - 1)
+    res["model"] = (f"U(1) Heisenberg chain N={SWEEP_N}, Neel start, maxdim "
+                    f"{[m for m, _ in SWEEP_SCHEDULE]}, cutoff 1e-14, Lanczos <= 16 steps")
+    return res
 
 
 def oracle_bond(host, k=K_LANCZOS):
@@ -226,6 +350,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the block-sparse H_eff and sweep measurements")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -339,6 +464,9 @@ def main():
                     "h2d_bytes_per_step": bond.h2d_bytes, "d2h_bytes_per_step": bond.d2h_bytes},
             "gpu_launches": launches * args.steps, "clocks": clk.summary(), "roofline": roof,
             "heff_tflops": hs, "kernels_per_step": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+    if rank == 0 and not args.no_extra:
+        line["heff_qn"] = bench_qn_heff(ctx, torch, tnh)
+        line["sweep"] = bench_sweeps(ctx, tnh)
     if rank == 0 and not args.no_cpu_baseline:
         cores = blas_threads()
         t0 = time.perf_counter()

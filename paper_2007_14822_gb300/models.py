@@ -225,3 +225,39 @@ def to_device(mpo, qn=True):
         T.fill(block)
         out.append(T)
     return out
+
+
+def product_state(site, states):
+    """MPS (list of tnh.Tensor [left, s, right]) of a product of basis states.
+
+    ``states[j]`` is the sector number of site j's state; every link has one
+    sector (dim 1) carrying the total charge to its left.
+    """
+    from .tnh import Index, Tensor
+    nq = site.nq
+    q = (0,) * nq
+    left = Index([(q, 1)], +1)
+    out = []
+    for st in states:
+        q = tuple(a + b for a, b in zip(q, site.sectors[st][0]))
+        right = Index([(q, 1)], +1)
+        T = Tensor([left, site, right.dag()], None)
+        T.fill(lambda k, shp: np.ones(shp))
+        out.append(T)
+        left = right
+    return out
+
+
+def product_vectors(site, vecs):
+    """MPS of a product state with one (normalised) vector per site; one
+    trivial link sector (site must be a dense index)."""
+    from .tnh import Index, Tensor
+    link = Index([((0,) * site.nq, 1)], +1)
+    out = []
+    for v in vecs:
+        v = np.asarray(v, dtype=np.float64)
+        v = v / np.linalg.norm(v)
+        T = Tensor([link, site, link.dag()], None)
+        T.fill(lambda k, shp, v=v: v.reshape(shp))
+        out.append(T)
+    return out

@@ -21,33 +21,11 @@ def ctx():
 
 
 def device_product_vectors(site, vecs):
-    from paper_2007_14822_gb300.tnh import Index, Tensor
-    out = []
-    link = Index([((0,) * site.nq, 1)], +1)
-    for v in vecs:
-        v = np.asarray(v, dtype=np.float64)
-        v = v / np.linalg.norm(v)
-        T = Tensor([link, site, link.dag()], None)
-        T.fill(lambda k, shp, v=v: v.reshape(shp))
-        out.append(T)
-    return out
+    return pm.product_vectors(site, vecs)
 
 
 def device_product_basis(site, states):
-    from paper_2007_14822_gb300.tnh import Index, Tensor
-    out = []
-    nq = site.nq
-    q = (0,) * nq
-    left = Index([(q, 1)], +1)
-    for st in states:
-        qs = site.sectors[st][0]
-        q = tuple(a + b for a, b in zip(q, qs))
-        right = Index([(q, 1)], +1)
-        T = Tensor([left, site, right.dag()], None)
-        T.fill(lambda k, shp: np.ones(shp))
-        out.append(T)
-        left = right
-    return out
+    return pm.product_state(site, states)
 
 
 def run_both(ctx, host_mpo, oracle_mpo, qn, init, sweeps, prec="fp64", krylov=64, tol=1e-10):
