@@ -121,27 +121,24 @@ struct BGroup {
     int pair0;       // first global block-pair index
 };
 
-constexpr int kBJThreads = 256;
-constexpr int kBJWarpsPerPair = 1;
+constexpr int kBJMaxB = 16;            // columns per block (a block pair has <= 32)
+constexpr int kBJThreads = 32 * kBJMaxB;   // one warp per column pair of an inner step
 constexpr float kTol32 = 1e-5f;    // float32 rotation threshold
 constexpr float kDone32 = 2e-3f;   // float32 stop (the float64 polish finishes)
 
 // state[1] = rounds done. fro2[g] = |X_g|_F^2; columns whose squared norm
 // is below 1e-12 fro2 are float32 rounding noise and are not rotated (they
-// would mix forever). Each column pair of the inner sweep is handled by
-// kBJWarpsPerPair warps (interleaved rows; more warps per pair did not pay
-// for the extra barrier on GB300).
+// would mix forever). A column lives in shared memory as [X part, zero pad
+// to lp (a multiple of 4), V part]: the inner sweep reads and writes it four
+// floats at a time.
 __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups,
                                                                int total_pairs, int max_rounds, float* __restrict__ X,
                                                                float* __restrict__ V, int* smax, int* state,
                                                                GridBar* bar, int* err, int stride,
                                                                const double* __restrict__ fro2) {
-    extern __shared__ float sm[];            // [2b][stride]: X part (len) then V part (n)
-    __shared__ float red[kBJThreads / 32 / kBJWarpsPerPair][kBJWarpsPerPair][3];   // one slot per pair (<= 8)
+    extern __shared__ __align__(16) float sm[];   // [2b][stride]
     __shared__ int skip;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int ngrp = nwarp / kBJWarpsPerPair, gw = warp / kBJWarpsPerPair, part = warp % kBJWarpsPerPair;
-    const int rstep = 32 * kBJWarpsPerPair, r0 = part * 32 + lane;
     unsigned epoch = 0;
     int t = 0;
     for (; t < max_rounds; ++t) {
@@ -169,58 +166,37 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
             const int q0 = bq * G.b, q1 = min(G.n, q0 + G.b);
             const int np = max(0, p1 - p0), nq = max(0, q1 - q0), nc = np + nq;
             if (nc < 2) continue;
-            const int L = G.len, Nn = G.n;
+            const int L = G.len, Nn = G.n, lp = (L + 3) & ~3, tot4 = (lp + Nn + 3) >> 2;
             for (int c = warp; c < nc; c += nwarp) {
                 const int col = c < np ? p0 + c : q0 + (c - np);
                 const float* xs = X + G.x_off + (int64_t)col * L;
                 const float* vs = V + G.v_off + (int64_t)col * Nn;
                 float* d = sm + (size_t)c * stride;
-#pragma unroll 4
-                for (int r = lane; r < L; r += 32) d[r] = xs[r];
-#pragma unroll 4
-                for (int r = lane; r < Nn; r += 32) d[L + r] = vs[r];
+                for (int r = lane; r < lp; r += 32) d[r] = r < L ? xs[r] : 0.f;
+                for (int r = lane; r < 4 * tot4 - lp; r += 32) d[lp + r] = r < Nn ? vs[r] : 0.f;
             }
             __syncthreads();
-            const int ne = nc + (nc & 1), Ri = ne - 1;
+            const int ne = nc + (nc & 1), Ri = ne - 1, l4 = lp >> 2;
             const float null2 = (float)(1e-12 * fro2[lo]);
             float wmax = 0.f;
             for (int ir = 0; ir < Ri; ++ir) {
-                for (int pr = gw; pr < ne / 2; pr += ngrp) {
+                for (int pr = warp; pr < ne / 2; pr += nwarp) {
                     const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
+                    if (a >= nc || bb >= nc) continue;
+                    float4* xa = reinterpret_cast<float4*>(sm + (size_t)a * stride);
+                    float4* xb = reinterpret_cast<float4*>(sm + (size_t)bb * stride);
                     float al = 0.f, be = 0.f, ga = 0.f;
-                    if (a < nc && bb < nc) {
-                        const float* xa = sm + (size_t)a * stride;
-                        const float* xb = sm + (size_t)bb * stride;
-                        for (int r = r0; r < L; r += rstep) {
-                            const float u = xa[r], v = xb[r];
-                            al = fmaf(u, u, al);
-                            be = fmaf(v, v, be);
-                            ga = fmaf(u, v, ga);
-                        }
+                    for (int r = lane; r < l4; r += 32) {
+                        const float4 u = xa[r], v = xb[r];
+                        al = fmaf(u.x, u.x, fmaf(u.y, u.y, fmaf(u.z, u.z, fmaf(u.w, u.w, al))));
+                        be = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, be))));
+                        ga = fmaf(u.x, v.x, fmaf(u.y, v.y, fmaf(u.z, v.z, fmaf(u.w, v.w, ga))));
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {   // three interleaved butterflies
                         al += __shfl_xor_sync(0xffffffffu, al, o);
                         be += __shfl_xor_sync(0xffffffffu, be, o);
                         ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                    }
-                    if (lane == 0) {
-                        red[pr][part][0] = al;
-                        red[pr][part][1] = be;
-                        red[pr][part][2] = ga;
-                    }
-                }
-                __syncthreads();
-                for (int pr = gw; pr < ne / 2; pr += ngrp) {
-                    const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
-                    if (a >= nc || bb >= nc) continue;
-                    // the same sums in the same order in every warp of the pair
-                    float al = 0.f, be = 0.f, ga = 0.f;
-#pragma unroll
-                    for (int w = 0; w < kBJWarpsPerPair; ++w) {
-                        al += red[pr][w][0];
-                        be += red[pr][w][1];
-                        ga += red[pr][w][2];
                     }
                     if (al <= null2 || be <= null2) continue;
                     const float rel = fabsf(ga) / sqrtf(al * be);
@@ -229,13 +205,11 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
                     const float zeta = (be - al) / (2.0f * ga);
                     const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
                     const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
-                    float* xa = sm + (size_t)a * stride;
-                    float* xb = sm + (size_t)bb * stride;
-#pragma unroll 4
-                    for (int rr = r0; rr < L + Nn; rr += rstep) {
-                        const float u = xa[rr], v = xb[rr];
-                        xa[rr] = c * u - sn * v;
-                        xb[rr] = sn * u + c * v;
+#pragma unroll 2
+                    for (int r = lane; r < tot4; r += 32) {
+                        const float4 u = xa[r], v = xb[r];
+                        xa[r] = make_float4(c * u.x - sn * v.x, c * u.y - sn * v.y, c * u.z - sn * v.z, c * u.w - sn * v.w);
+                        xb[r] = make_float4(sn * u.x + c * v.x, sn * u.y + c * v.y, sn * u.z + c * v.z, sn * u.w + c * v.w);
                     }
                 }
                 __syncthreads();
@@ -245,12 +219,10 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
                 float* xs = X + G.x_off + (int64_t)col * L;
                 float* vs = V + G.v_off + (int64_t)col * Nn;
                 const float* d = sm + (size_t)c * stride;
-#pragma unroll 4
                 for (int r = lane; r < L; r += 32) xs[r] = d[r];
-#pragma unroll 4
-                for (int r = lane; r < Nn; r += 32) vs[r] = d[L + r];
+                for (int r = lane; r < Nn; r += 32) vs[r] = d[lp + r];
             }
-            if (lane == 0 && part == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
+            if (lane == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
             __syncthreads();
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
@@ -776,7 +748,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         G.v_off = vo;
         G.len = L;
         G.n = Nn;
-        stride = std::max(stride, L + Nn);
+        stride = std::max(stride, (((L + 3) & ~3) + Nn + 3) & ~3);
         for (int bl : kv.second) {
             auto key = T.key(bl);
             SvdPack p{};
@@ -810,12 +782,10 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     }
     const int ng = (int)bg.size();
     if (ng == 0) return R;
-    // one block width for all groups: up to 8 columns while a block pair
+    // one block width for all groups: up to 16 columns while a block pair
     // (X and V columns) fits in shared memory
-    // (at most 8 column pairs per inner step: one per group of warps)
-    bmax = 8;
+    bmax = kBJMaxB;
     while (bmax > 1 && (size_t)2 * bmax * stride * 4 > 200 * 1024) bmax >>= 1;
-    static_assert(kBJThreads / 32 / kBJWarpsPerPair >= 8, "one warp group per column pair of a block pair");
     for (auto& G : bg) {
         G.b = bmax;
         int nb = (G.n + bmax - 1) / bmax;
