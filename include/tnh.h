@@ -201,6 +201,11 @@ tnh_status tnh_heff_apply_prec(tnh_heff* plan, tnh_precision prec,
 /* Algorithmic flops of one product: 2 M N K summed over every block GEMM of
  * the contraction chain (split-precision extra products not counted). */
 tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops);
+/* The same flops split by step, for measurement: the S1 GEMM (sum over a of
+ * L psi), the contractions with W1 and W2 (counted as the labelled chain
+ * would, although the plan applies them fused in one pass) and the S4 GEMM
+ * (sum over w2, b with R). s1 + s23 + s4 is tnh_heff_flops. */
+tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, double* s4);
 /* Number of float64 elements of the psi layout. */
 tnh_status tnh_heff_size(const tnh_heff* plan, int64_t* n);
 void tnh_heff_free(tnh_heff* plan);
@@ -238,7 +243,8 @@ tnh_status tnh_env_update(tnh_ctx* ctx, int32_t dir, const tnh_tensor* E,
  * singular values of all groups are pooled and truncated in float64: the
  * squares are summed from the smallest upward while their share of the total
  * stays <= cutoff, at most maxdim and at least max(mindim, 1) values are kept
- * (Sec. 5). Ties are ordered by group, then position. exact_side = 0 makes U
+ * (Sec. 5); values with s^2 below 1e-16 of the total are float64 zeros and
+ * are kept only if mindim asks for them. Ties are ordered by group, then position. exact_side = 0 makes U
  * orthonormal to float64 accuracy (a left-to-right move), 1 makes V so (a
  * right-to-left move); the other factor is the float64 product with T.
  * Synchronises the stream (the kept count sizes the results). */
@@ -249,6 +255,14 @@ tnh_status tnh_svd_trunc(tnh_ctx* ctx, const tnh_tensor* T, int32_t nrow, double
  * only read nsect. truncerr is the discarded share of sum s^2. */
 tnh_status tnh_svd_info(const tnh_svd* svd, int32_t* nsect, int32_t* nq, int32_t* qn,
                         int32_t* sect_dim, double* truncerr);
+/* Work of the two Jacobi stages, for measurement: rounds (grid-wide steps)
+ * of the float32 and the float64 stage, and the floating-point operations
+ * their rotations execute (per column pair and row: 6 for the three dot
+ * products, 6 for the two rotated entries; every group counted in every
+ * round, so an upper bound when groups converge at different rounds).
+ * Any pointer may be NULL. */
+tnh_status tnh_svd_stats(const tnh_svd* svd, int32_t* rounds32, int32_t* rounds64, double* flops32,
+                         double* flops64);
 /* Copy the factors: U [rows..., c] (c In) and V [c, cols...] (c Out) with
  * caller-given layouts (DEVICE data), S DEVICE [sum of sect_dim] in sector
  * order, descending inside a sector (S may be NULL). T = U diag(S) V up to

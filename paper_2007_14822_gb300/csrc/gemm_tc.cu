@@ -14,7 +14,9 @@
 //               K=16) into tensor memory; hh goes to its own accumulator,
 //               the cross products to a second one, so the large partial
 //               sums are not rounded once per small cross term.
-//   warps 2..9  epilogue (two warps per TMEM lane quarter, 64 columns each). The tensor core accumulates one K chunk (128
+//   warps 2..9  epilogue (two warps per TMEM lane quarter, 64 columns each;
+//               rows leave through a small shared-memory stage so that
+//               every store is one contiguous row segment). The tensor core accumulates one K chunk (128
 //               for the three-part split) at a time; the epilogue adds every
 //               chunk's two accumulators into float32 registers (round to
 //               nearest) and stores float64 at the end of the tile. The
@@ -37,12 +39,18 @@ constexpr int kTileBytes = kTcTileM * kTcTileK * 2;   // 16384, A and B tiles al
 constexpr int kThreads = 320;   // producer, MMA, 8 epilogue warps
 constexpr int kEpiWarps = 8;
 
+// epilogue staging: per epilogue warp 32 rows x 33 words (a 32 x 32 float or
+// 32 x 16 double block, one padding word per row against bank conflicts)
+constexpr int kStageWords = 32 * 33;
+constexpr int kEpiStageBytes = kEpiWarps * kStageWords * 4;
+
 template <int P>
 struct TcCfg {
     static constexpr int kStages = P == 3 ? 2 : (P == 2 ? 3 : 6);
     static constexpr int kNumProd = P == 3 ? 6 : (P == 2 ? 3 : 1);
     static constexpr int kStageBytes = 2 * P * kTileBytes;
-    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/ + kEpiStageBytes;
+    static_assert(kSmem <= 232448, "shared memory of one CTA");
     // k-blocks (of 64) accumulated on the tensor core before the epilogue
     // folds the partial sum into registers
     static constexpr int kChunk = P == 3 ? 2 : (P == 2 ? 4 : 8);
@@ -79,6 +87,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* tempty = tfull + 2;
     uint64_t* fin = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    uint32_t* stage_all = reinterpret_cast<uint32_t*>(smem + 2 * S * P * kTileBytes + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -215,34 +224,51 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) ptx::mbar_arrive(&tempty[buf]);
             }
             if (!ok) break;
+            // ---- store: each warp stages 32 x 32 (float) or 32 x 16 (double)
+            // blocks in shared memory and writes every row as one contiguous
+            // segment (row starts come from row m's owner lane)
             const int m = mi * kTcTileM + q * 32 + lane;
-            if (m < t.M) {
-                // each lane stores its own row: 16-byte vectors where aligned
-                const int64_t rb = t.use_roff ? row_off[t.roff + m] : t.c_base + (int64_t)m * t.ldc;
-                const int n0 = ni * kTcTileN + half * kCols;
-                const int nv = t.N - n0;
-                if (t.c_f32) {
-                    float* crow = reinterpret_cast<float*>(C) + rb + n0;
-                    if (nv >= kCols && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
+            const int mrow = m < t.M;
+            const int64_t rb = mrow ? (t.use_roff ? row_off[t.roff + m] : t.c_base + (int64_t)m * t.ldc) : 0;
+            const int n0 = ni * kTcTileN + half * kCols;
+            uint32_t* buf = stage_all + (warp - 2) * kStageWords;
+            if (t.c_f32) {
+                float* Cf = reinterpret_cast<float*>(C);
 #pragma unroll
-                        for (int j = 0; j < kCols; j += 4)
-                            *reinterpret_cast<float4*>(crow + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
-                    } else {
+                for (int pass = 0; pass < kCols / 32; ++pass) {
+                    const int c0 = n0 + pass * 32, nv = t.N - c0;
+                    if (nv <= 0) break;
 #pragma unroll
-                        for (int j = 0; j < kCols; ++j)
-                            if (j < nv) crow[j] = acc[j];
+                    for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __float_as_uint(acc[pass * 32 + j]);
+                    __syncwarp();
+                    for (int r = 0; r < 32; ++r) {
+                        const int64_t rbr = __shfl_sync(0xffffffffu, rb, r);
+                        const int ok = __shfl_sync(0xffffffffu, mrow, r);
+                        if (ok && lane < nv) Cf[rbr + c0 + lane] = __uint_as_float(buf[r * 33 + lane]);
                     }
-                } else {
-                    double* crow = C + rb + n0;
-                    if (nv >= kCols && (reinterpret_cast<uintptr_t>(crow) & 15) == 0) {
+                    __syncwarp();
+                }
+            } else {
 #pragma unroll
-                        for (int j = 0; j < kCols; j += 2)
-                            *reinterpret_cast<double2*>(crow + j) = make_double2((double)acc[j], (double)acc[j + 1]);
-                    } else {
+                for (int pass = 0; pass < kCols / 16; ++pass) {
+                    const int c0 = n0 + pass * 16, nv = t.N - c0;
+                    if (nv <= 0) break;
 #pragma unroll
-                        for (int j = 0; j < kCols; ++j)
-                            if (j < nv) crow[j] = (double)acc[j];
+                    for (int j = 0; j < 16; ++j) {
+                        const double v = (double)acc[pass * 16 + j];
+                        buf[lane * 33 + 2 * j] = (uint32_t)__double2loint(v);
+                        buf[lane * 33 + 2 * j + 1] = (uint32_t)__double2hiint(v);
                     }
+                    __syncwarp();
+                    const int j = lane & 15;
+                    for (int r = 0; r < 32; r += 2) {
+                        const int rr = r + (lane >> 4);
+                        const int64_t rbr = __shfl_sync(0xffffffffu, rb, rr);
+                        const int ok = __shfl_sync(0xffffffffu, mrow, rr);
+                        if (ok && j < nv)
+                            C[rbr + c0 + j] = __hiloint2double((int)buf[rr * 33 + 2 * j + 1], (int)buf[rr * 33 + 2 * j]);
+                    }
+                    __syncwarp();
                 }
             }
         }

@@ -328,7 +328,10 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                                 add_flux(T1.flux, W1.flux));
         Layout T3 = make_layout({T2.inds[0], T2.inds[2], T2.inds[4], W2l.inds[1], W2l.inds[3]},
                                 add_flux(T2.flux, W2.flux));
-        P->flops = contract_flops(Ll, Xl) + contract_flops(T1, W1l) + contract_flops(T2, W2l) + contract_flops(T3, Rl);
+        P->f_s1 = contract_flops(Ll, Xl);
+        P->f_s23 = contract_flops(T1, W1l) + contract_flops(T2, W2l);
+        P->f_s4 = contract_flops(T3, Rl);
+        P->flops = P->f_s1 + P->f_s23 + P->f_s4;
     }
 
     // ---------------- S1: one task per a-sector A with L and psi blocks
@@ -724,6 +727,16 @@ tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops) {
     return guard(nullptr, [&] {
         TNH_REQUIRE(P && flops, TNH_ERR_ARG, "tnh_heff_flops: NULL argument");
         *flops = P->flops;
+    });
+}
+
+tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, double* s4) {
+    auto* P = reinterpret_cast<const HeffPlan*>(plan);
+    return guard(nullptr, [&] {
+        TNH_REQUIRE(P && s1 && s23 && s4, TNH_ERR_ARG, "tnh_heff_flops_detail: NULL argument");
+        *s1 = P->f_s1;
+        *s23 = P->f_s23;
+        *s4 = P->f_s4;
     });
 }
 

@@ -28,6 +28,7 @@ struct HeffPlan {
     int64_t n = 0;          // elements of the two-site state
     Layout psi;             // its layout
     double flops = 0.0;     // method flops of one application (S1..S4)
+    double f_s1 = 0.0, f_s23 = 0.0, f_s4 = 0.0;
     // operands: S1 = L (A) x psi (B), S4 = T3 (A) x R (B)
     HeffOperand oL, oX, oT, oR;
     GatherJob jX;           // per application: pack psi

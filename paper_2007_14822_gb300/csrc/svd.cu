@@ -20,8 +20,8 @@
 //       orthogonal.
 //    c. The float64 singular values sigma_j = |Y_j| are pooled, ranked
 //       (sigma desc, group, position) and the cutoff/maxdim rule of Sec. 5
-//       picks the kept count; the discarded weight is |M|_F^2 minus the kept
-//       sigma^2, in float64.
+//       picks the kept count (values below 1e-8 of the norm count as zero);
+//       the discarded weight is |M|_F^2 minus the kept sigma^2, in float64.
 //    d. The side that must come out orthonormal (U going right, V going left
 //       in a sweep) is Y_j / sigma_j; the other side is the float64 product
 //       of M with it (S V^T = U^T M, or U S = M V).
@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 
 #include "prof.h"
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
             const int R = G.rounds;
             const int i = pi - G.pair0, ne = R + 1, k = t % R;
             if (tid == 0) {
-                skip = group_done(smax, lo, R, t, kDone64);
+                skip = group_done(smax, lo, R, t, 1.0f);
                 if (k == 0 && i == 0) smax[3 * lo + (t / R + 1) % 3] = 0;
             }
             __syncthreads();
@@ -326,8 +327,17 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                 const double tol = 4.0 * sqrt((double)L) * 1.1102230246251565e-16;
                 const double null2 = 1e-28 * fro2[G.grp];
                 act = (fabs(Gg) > tol * sqrt(A * B)) && A > null2 && B > null2;
-                if (A > null2 && B > null2)
-                    atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int((float)(fabs(Gg) / sqrt(A * B))));
+                // stop test, per column pair: a column y = M v formed in float64
+                // carries an absolute rounding error ~ eps sqrt(len) |M|_F, so
+                // the pair can only be made orthogonal to about
+                //   floor = 16 eps sqrt(len) |M|_F / min(|y_p|, |y_q|)
+                // of its norms; the target is max(kDone64, floor) and smax holds
+                // the largest ratio to it (done when below 1)
+                if (A > null2 && B > null2) {
+                    const double flo = 16.0 * 1.1102230246251565e-16 * sqrt((double)L) * sqrt(fro2[G.grp] / fmin(A, B));
+                    const double ratio = fabs(Gg) / sqrt(A * B) / fmax((double)kDone64, flo);
+                    atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int((float)ratio));
+                }
                 if (act) {
                     const double zeta = (B - A) / (2.0 * Gg);
                     const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
             __syncthreads();   // red, rot and act are reused by the next pair
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
-        if (all_done(groups, ngroups, smax, t + 1, kDone64)) { ++t; break; }
+        if (all_done(groups, ngroups, smax, t + 1, 1.0f)) { ++t; break; }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
@@ -483,6 +493,12 @@ __global__ void trunc_select(const double* __restrict__ sig, const int* __restri
         keep = max(keep, max(1, mindim));
         keep = min(keep, min(maxdim, ntotal));
         keep = max(keep, max(min(mindim, ntotal), 1));
+        // singular values below 1e-8 of the norm (sigma^2 < 1e-16 of the
+        // total) are zero to float64 accuracy: their vectors are not
+        // resolved, so they are not kept (unless mindim asks for them)
+        int nres = 0;
+        while (nres < n && sig[order[nres]] * sig[order[nres]] >= 1e-16 * total) ++nres;
+        keep = min(keep, max(nres, max(min(mindim, ntotal), 1)));
         keep = min(keep, n);
         double p2 = 0.0;
         for (int k = 0; k < keep; ++k) p2 += sig[order[k]] * sig[order[k]];
@@ -688,6 +704,7 @@ struct SvdResult {
     std::vector<int> sidx;                         // pooled index of every kept value, output order
     double truncerr = 0.0;
     int rounds32 = 0, rounds64 = 0;
+    double flops32_round = 0.0, flops64_round = 0.0;   // rotation work per round, all groups
 };
 
 std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim,
@@ -794,6 +811,9 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         G.pair0 = bpairs;
         bpairs += G.nblk / 2;
         rmax = std::max(rmax, G.rounds);
+        // one inner sweep per block pair: (2b - 1) steps of b column pairs
+        const double lp = (double)((G.len + 3) & ~3);
+        R->flops32_round += (G.nblk / 2) * (2.0 * bmax - 1.0) * bmax * 6.0 * (2.0 * lp + G.n);
     }
     int ntot = 0;
     for (int g = 0; g < ng; ++g) ntot += R->n[g];
@@ -937,6 +957,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         J.pair0 = jpairs;
         J.grp = g;
         jpairs += (k + 1) / 2;
+        R->flops64_round += ((k + 1) / 2) * 12.0 * R->len[g];
         jrmax = std::max(jrmax, J.rounds);
         jg.push_back(J);
         vco += (int64_t)R->n[g] * k;
@@ -1019,7 +1040,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, jacobi_f64, threads, 0));
         int want = jpairs;
         int grid = std::max(1, std::min(want, std::max(1, bpsm) * ctx->num_sms));
-        int max_rounds = 20 * jrmax + 8;
+        int max_rounds = 30 * jrmax + 8;
         const JGroup* gp = d_jg.as<JGroup>();
         double* Yp = R->Y.as<double>();
         int* smaxp = d_smax.as<int>();
@@ -1039,7 +1060,31 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         if (std::getenv("TNH_DEBUG"))
             std::fprintf(stderr, "svd: float64 Jacobi %d rounds (max %d, per sweep %d, grid %d)\n", st[1], max_rounds,
                          jrmax, grid);
-        TNH_REQUIRE(st[1] < max_rounds, TNH_ERR_NOT_CONVERGED, "svd_trunc: float64 Jacobi did not converge");
+        if (st[1] >= max_rounds) {
+            // report the group that kept rotating: its size and largest
+            // relative off-diagonal in the last sweep
+            std::vector<int> h_smax((size_t)3 * njg);
+            CUDA_CHECK(cudaMemcpy(h_smax.data(), d_smax.p, h_smax.size() * 4, cudaMemcpyDeviceToHost));
+            int worst = 0;
+            float wv = -1.f;
+            for (int g = 0; g < njg; ++g) {
+                const int sw = st[1] / jg[g].rounds;
+                float v;
+                const int bits = h_smax[(size_t)3 * g + (sw + 2) % 3];
+                std::memcpy(&v, &bits, 4);
+                if (!(v <= wv)) { wv = v; worst = g; }
+            }
+            // what is left is within 1e3 of the rounding floor of the columns
+            // involved (sigma right to second order); a pair far above its
+            // target means the input was not finite or the method failed
+            TNH_REQUIRE(wv < 1e3f, TNH_ERR_NOT_CONVERGED,
+                        "svd_trunc: float64 Jacobi did not converge in %d rounds (group %d of %d: %d x %d, last "
+                        "sweep max off-diagonal %.3g times its target)",
+                        st[1], worst, njg, jg[worst].len, jg[worst].n, (double)wv);
+            if (std::getenv("TNH_DEBUG"))
+                std::fprintf(stderr, "svd: float64 Jacobi stopped at %d rounds, group %d (%d x %d) at %.3g x target\n",
+                             st[1], worst, jg[worst].len, jg[worst].n, (double)wv);
+        }
     }
     // ---- float64 singular values, ranking, truncation
     const int ny = yc;
@@ -1330,6 +1375,18 @@ tnh_status tnh_svd_info(const tnh_svd* svd, int32_t* nsect, int32_t* nq, int32_t
             if (sect_dim) sect_dim[k] = R->kept_g[g];
         }
         if (truncerr) *truncerr = R->truncerr;
+    });
+}
+
+tnh_status tnh_svd_stats(const tnh_svd* svd, int32_t* rounds32, int32_t* rounds64, double* flops32,
+                         double* flops64) {
+    auto* R = reinterpret_cast<const SvdResult*>(svd);
+    return guard(nullptr, [&] {
+        TNH_REQUIRE(R, TNH_ERR_ARG, "tnh_svd_stats: NULL svd");
+        if (rounds32) *rounds32 = R->rounds32;
+        if (rounds64) *rounds64 = R->rounds64;
+        if (flops32) *flops32 = R->rounds32 * R->flops32_round;
+        if (flops64) *flops64 = R->rounds64 * R->flops64_round;
     });
 }
 

@@ -25,9 +25,9 @@ PRECISION = {"fp64": FP64, "bf16x6": BF16x6, "bf16x3": BF16x3, "bf16": BF16}
 
 # exported symbols declared in include/tnh.h
 SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layout", "tnh_contract",
-           "tnh_heff_plan", "tnh_heff_apply", "tnh_heff_apply_prec", "tnh_heff_flops", "tnh_heff_size",
+           "tnh_heff_plan", "tnh_heff_apply", "tnh_heff_apply_prec", "tnh_heff_flops", "tnh_heff_flops_detail", "tnh_heff_size",
            "tnh_heff_free", "tnh_eigsolve", "tnh_env_update", "tnh_svd_trunc", "tnh_svd_info",
-           "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
+           "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
            "tnh_contract_dense_noalloc"]
 
 
@@ -86,12 +86,14 @@ def lib():
         "tnh_heff_apply": (i32, [vp, vp, vp]),
         "tnh_heff_apply_prec": (i32, [vp, C.c_int, vp, vp]),
         "tnh_heff_flops": (i32, [vp, P(dbl)]),
+        "tnh_heff_flops_detail": (i32, [vp, P(dbl), P(dbl), P(dbl)]),
         "tnh_heff_size": (i32, [vp, P(i64)]),
         "tnh_heff_free": (None, [vp]),
         "tnh_eigsolve": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
         "tnh_env_update": (i32, [vp, i32, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), C.c_int]),
         "tnh_svd_trunc": (i32, [vp, P(tnh_tensor), i32, dbl, i32, i32, i32, P(vp)]),
         "tnh_svd_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(dbl)]),
+        "tnh_svd_stats": (i32, [vp, P(i32), P(i32), P(dbl), P(dbl)]),
         "tnh_svd_get": (i32, [vp, P(tnh_tensor), vp, P(tnh_tensor), i32]),
         "tnh_svd_free": (None, [vp]),
         "tnh_dmrg": (i32, [vp, i32, P(tnh_tensor), i64, i64, P(tnh_tensor), P(tnh_sweep_params), P(dbl),
@@ -376,6 +378,13 @@ class Heff:
         return f.value
 
     @property
+    def flops_detail(self):
+        """{'s1', 's23', 's4'}: flops of the S1 GEMM, the W1/W2 contractions, the S4 GEMM."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self.ctx.check(self.ctx._lib.tnh_heff_flops_detail(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"s1": a.value, "s23": b.value, "s4": c.value}
+
+    @property
     def size(self):
         n = C.c_int64()
         self.ctx.check(self.ctx._lib.tnh_heff_size(self.h, C.byref(n)))
@@ -409,6 +418,13 @@ class Svd:
 
     def __del__(self):
         self.free()
+
+    def stats(self):
+        """Rounds and rotation flops of the float32 and float64 Jacobi stages."""
+        r32, r64, f32, f64 = C.c_int32(), C.c_int32(), C.c_double(), C.c_double()
+        self.ctx.check(self.ctx._lib.tnh_svd_stats(self.h, C.byref(r32), C.byref(r64), C.byref(f32),
+                                                   C.byref(f64)))
+        return {"rounds32": r32.value, "rounds64": r64.value, "flops32": f32.value, "flops64": f64.value}
 
     @property
     def kept(self):

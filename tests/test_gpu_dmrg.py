@@ -100,3 +100,21 @@ def test_dmrg_config1_random_product(ctx):
     assert abs(E - Eo) < 1e-9 * abs(Eo), (E, Eo)
     assert E >= e_ed - 1e-10
     assert E - e_ed < 1e-4 * abs(e_ed)
+
+
+def test_dmrg_mixed_with_tiny_cutoff_matches_fp64(ctx):
+    # BF16x6 matvecs leave noise-level singular values (~1e-7 of the largest)
+    # in theta; a cutoff of 1e-14 keeps them, so the factorisation must still
+    # return an orthonormal exact side for them (otherwise the MPS stops being
+    # canonical and the sweep diverges)
+    from paper_2007_14822_gb300 import tnh
+    N = 24
+    mpo = pm.heisenberg(N)
+    sweeps = [(16, 1e-14), (64, 1e-14), (256, 1e-14), (256, 1e-14)]
+    out = {}
+    for name, prec, tol in (("mix", tnh.BF16x6, 1e-7), ("fp64", tnh.FP64, 1e-10)):
+        W = pm.to_device(mpo, qn=True)
+        A = pm.product_state(W[0].inds[3], [0, 1] * (N // 2))
+        out[name], st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in sweeps], [c for _, c in sweeps],
+                                 krylov_dim=16, tol=tol, prec=prec)
+    assert abs(out["mix"] - out["fp64"]) < 1e-9 * abs(out["fp64"]), out
