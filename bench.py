@@ -360,6 +360,44 @@ def time_steps(torch, bond, steps, flush, e2e=False):
     return total
 
 
+def max_over_ranks(x, dist, device):
+    """The job's time is the slowest rank's (all ranks call this)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_probe(which, torch, build, tnh):
+    """A short run of one workload, for ncu: the kernels launch in a fixed
+    order (plan-time packing of L and R first, then the applications)."""
+    build.build()
+    ctx = tnh.Context(0)
+    if which == "svd-bond":
+        bond = GpuBond(ctx, host_inputs())
+        ctx.contract(bond.A1, bond.A2, bond.theta, tnh.FP64)
+        plan = ctx.heff_plan(bond.L, bond.W, bond.W, bond.R, bond.theta, tnh.BF16x6)
+        E, res, k = plan.eigsolve(bond.theta.data, krylov_dim=K_LANCZOS, tol=0.0)
+        plan.free()
+        svd = ctx.svd_trunc(bond.theta, 2, CUTOFF, MAXDIM)
+        print("probe svd-bond: E", E, "kept", svd.kept, svd.stats())
+        svd.free()
+    else:
+        i = {"heff-u1": 0, "heff-cyl": 1, "heff-hub": 2}[which]
+        name, kind, m, recipe, seed = QN_CONFIGS[i]
+        L, W1, W2, R, psi = qn_heff_inputs(kind, m, recipe, seed)
+        plan = ctx.heff_plan(L, W1, W2, R, psi, tnh.BF16x6)
+        y = torch.empty_like(psi.data)
+        for _ in range(3):
+            plan.apply(psi.data, y)
+        torch.cuda.synchronize()
+        print("probe", which, name, "flops", plan.flops, "n", plan.size)
+        plan.free()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +406,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the block-sparse H_eff and sweep measurements")
+    ap.add_argument("--probe", choices=["heff-u1", "heff-cyl", "heff-hub", "svd-bond"],
+                    help="run one workload briefly for a profiler (no JSON line): a block-sparse H_eff plan "
+                         "and three BF16x6 applications, or the bench bond up to its SVD")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -401,6 +442,9 @@ def main():
 
     import torch
     from paper_2007_14822_gb300 import build, tnh
+    if args.probe:
+        run_probe(args.probe, torch, build, tnh)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -420,10 +464,7 @@ def main():
     with ClockSampler(local) as clk:
         t_dev = time_steps(torch, bond, args.steps, flush)
     torch.cuda.synchronize()
-    if dist:
-        t = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = t.item()
+    t_dev = max_over_ranks(t_dev, dist, "cuda")
     # end to end: host buffers in, result out, every step
     t_e2e = time_steps(torch, bond, max(1, args.steps // 2), flush, e2e=True) / max(1, args.steps // 2)
     # per-kernel breakdown of one step (profiled separately)
