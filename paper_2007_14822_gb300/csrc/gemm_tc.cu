@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
                 const int local = tile - t.tile0;
                 const int mi = local / t.nt, ni = local - mi * t.nt;
-                const uint16_t* a = A + (t.a_base + (int64_t)mi * t.kt) * P * kTcTileElems;
-                const uint16_t* b = B + (t.b_base + (int64_t)ni * t.kt) * P * kTcTileElems;
+                const int ks = t.kstride ? t.kstride : t.kt;
+                const uint16_t* a = A + (t.a_base + (int64_t)mi * ks) * P * kTcTileElems;
+                const uint16_t* b = B + (t.b_base + (int64_t)ni * ks) * P * kTcTileElems;
                 for (int kb = 0; kb < t.kt; ++kb) {
                     if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, err, 1)) { ok = false; break; }
                     ptx::mbar_expect_tx(&full[stage], 2 * P * kTileBytes);
@@ -294,6 +295,26 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
     gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err, row_off);
 }
 
+__global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds, int nred, int64_t total,
+                                                     const float* __restrict__ part, void* __restrict__ out,
+                                                     const int64_t* __restrict__ row_off) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nred - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (reds[mid].e0 <= e) lo = mid; else hi = mid - 1;
+        }
+        const SplitRed R = reds[lo];
+        const int64_t loc = e - R.e0, mn = (int64_t)R.M * R.N;
+        const int m = (int)(loc / R.N), n = (int)(loc - (int64_t)m * R.N);
+        double acc = 0.0;
+        for (int j = 0; j < R.S; ++j) acc += (double)part[R.part + j * mn + loc];
+        if (R.use_roff) static_cast<double*>(out)[row_off[R.roff + m] + n] = acc;
+        else if (R.out_f32) static_cast<float*>(out)[R.c_base + (int64_t)m * R.ldc + n] = (float)acc;
+        else static_cast<double*>(out)[R.c_base + (int64_t)m * R.ldc + n] = acc;
+    }
+}
+
 }  // namespace
 
 void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A, const uint16_t* B,
@@ -305,6 +326,19 @@ void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const 
         launch_p<2>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
     else
         launch_p<1>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
+}
+
+}  // namespace tnh
+
+namespace tnh {
+
+void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const float* part, void* out,
+                          const int64_t* row_off, int num_sms, cudaStream_t s) {
+    if (total == 0 || nred == 0) return;
+    KScope ks("splitk_reduce", s);
+    const int64_t want = (total + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(num_sms > 0 ? num_sms : 148) * 8));
+    splitk_reduce<<<grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
 }
 
 }  // namespace tnh

@@ -28,6 +28,7 @@
 // final energy and residual), so it keeps the float64 operands of L and R too.
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -259,7 +260,82 @@ GemmTask gemm_task(int64_t M, int64_t N, int64_t K, const HeffOperand& A, const 
 
 void finish_gemm(HeffGemm& G, cudaStream_t s) {
     G.d_f64 = upload(G.f64, s);
+    G.tc_base = G.tc;
     G.d_tc = upload(G.tc, s);
+}
+
+// Rebuild the launched tcgen05 tasks of G for a K-split factor (1: the block
+// tasks themselves). With split > 1 every block task goes through the
+// partial slabs (also those too short to split), so that the reduction is
+// the one launch that writes the output.
+void set_split(HeffGemm& G, int split, cudaStream_t s) {
+    G.split = split;
+    G.tc.clear();
+    G.reds.clear();
+    G.red_total = G.part_elems = 0;
+    int tile0 = 0;
+    if (split <= 1) {
+        for (GemmTask t : G.tc_base) {
+            t.tile0 = tile0;
+            tile0 += t.mt * t.nt;
+            G.tc.push_back(t);
+        }
+    } else {
+        for (const GemmTask& b : G.tc_base) {
+            const int S = std::max(1, std::min(split, b.kt));
+            const int64_t mn = (int64_t)b.M * b.N;
+            SplitRed r{};
+            r.M = b.M;
+            r.N = b.N;
+            r.S = S;
+            r.use_roff = b.use_roff;
+            r.out_f32 = b.c_f32;
+            r.ldc = b.ldc;
+            r.part = G.part_elems;
+            r.roff = b.roff;
+            r.c_base = b.c_base;
+            r.e0 = G.red_total;
+            for (int j = 0; j < S; ++j) {
+                const int k0 = (int)((int64_t)j * b.kt / S), k1 = (int)((int64_t)(j + 1) * b.kt / S);
+                GemmTask t = b;
+                t.kstride = b.kt;
+                t.a_base = b.a_base + k0;
+                t.b_base = b.b_base + k0;
+                t.kt = k1 - k0;
+                t.K = std::min(b.K - k0 * kTcTileK, (k1 - k0) * kTcTileK);
+                t.c_f32 = 1;
+                t.use_roff = 0;
+                t.c_base = G.part_elems + j * mn;
+                t.ldc = b.N;
+                t.tile0 = tile0;
+                tile0 += t.mt * t.nt;
+                G.tc.push_back(t);
+            }
+            G.part_elems += S * mn;
+            G.red_total += mn;
+            G.reds.push_back(r);
+        }
+    }
+    G.tilestc = tile0;
+    G.d_tc = upload(G.tc, s);
+    G.d_reds = upload(G.reds, s);
+    CUDA_CHECK(cudaStreamSynchronize(s));   // the host vectors may change right after
+}
+
+// One tcgen05 GEMM of the plan, and its reduction when K is split.
+void launch_stage(const HeffGemm& G, const HeffPlan& P, const uint16_t* A, const uint16_t* B, void* out,
+                  const int64_t* row_off, cudaStream_t s) {
+    Ctx* ctx = P.ctx;
+    int* err = ctx->d_flag.as<int>();
+    if (G.split <= 1) {
+        launch_gemm_tc(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, A, B, static_cast<double*>(out), P.planes,
+                       ctx->num_sms, err, s, row_off);
+    } else {
+        launch_gemm_tc(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, A, B, P.part.as<double>(), P.planes,
+                       ctx->num_sms, err, s, nullptr);
+        launch_splitk_reduce(G.d_reds.as<SplitRed>(), (int)G.reds.size(), G.red_total, P.part.as<float>(), out,
+                             row_off, ctx->num_sms, s);
+    }
 }
 
 void upload_operand(HeffOperand& O, cudaStream_t s) {
@@ -276,6 +352,101 @@ void HeffOperand::add_task(int64_t rows, int64_t K) {
     gtc.push_back(OpGeom{tiles, (int)cdiv(K, kTcTileK)});
     tiles += cdiv(rows, kTcTileM) * cdiv(K, kTcTileK);
 }
+
+namespace {
+
+void ensure_part(HeffPlan& P, int64_t elems) {
+    const size_t need = (size_t)std::max<int64_t>(elems, 4) * sizeof(float);
+    if (P.part.bytes < need) P.part.alloc(need);
+}
+
+int64_t base_tiles(const HeffGemm& G) {
+    int64_t n = 0;
+    for (const GemmTask& t : G.tc_base) n += (int64_t)t.mt * t.nt;
+    return n;
+}
+
+// Autotuner of the K-split factor of the two tcgen05 GEMMs. Each candidate
+// (1, 2, 4, 8; only splits that can fill the GPU better) is timed with CUDA
+// events on the plan's own operands, one warm-up and three timed runs of
+// the GEMM and its reduction; the fastest wins. Choices are kept in the
+// context by a coarse shape signature (tasks, tiles and mean K blocks per
+// task, in half octaves), so the bonds of a sweep at similar sizes reuse
+// them. TNH_HEFF_SPLIT="s1,s4" forces a choice.
+void tune_splits(HeffPlan& P) {
+    Ctx* ctx = P.ctx;
+    cudaStream_t s = P.stream;
+    auto bucket = [](double x) { return (int)std::lround(2.0 * std::log2(std::max(1.0, x))); };
+    std::vector<int> key{P.planes};
+    for (const HeffGemm* G : {&P.g1, &P.g4}) {
+        int64_t kt = 0;
+        for (const GemmTask& t : G->tc_base) kt += t.kt;
+        key.push_back(bucket((double)G->tc_base.size()));
+        key.push_back(bucket((double)base_tiles(*G)));
+        key.push_back(bucket((double)kt / std::max<size_t>(1, G->tc_base.size())));
+    }
+    std::pair<int, int> choice{1, 1};
+    bool measured = false;
+    if (const char* f = std::getenv("TNH_HEFF_SPLIT")) {
+        int a = 1, b = 1;
+        if (std::sscanf(f, "%d,%d", &a, &b) == 2) choice = {std::max(1, a), std::max(1, b)};
+    } else if (ctx->heff_tune.count(key)) {
+        choice = ctx->heff_tune[key];
+    } else {
+        DevBuf ytmp((size_t)std::max<int64_t>(P.n, 1) * sizeof(double));
+        cudaEvent_t e0, e1;
+        CUDA_CHECK(cudaEventCreate(&e0));
+        CUDA_CHECK(cudaEventCreate(&e1));
+        auto time_split = [&](HeffGemm& G, bool s1, int split) {
+            set_split(G, split, s);
+            ensure_part(P, G.part_elems);
+            auto run = [&] {
+                if (s1) launch_stage(G, P, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(), P.t1.p, nullptr, s);
+                else launch_stage(G, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), ytmp.p, P.row_off.as<int64_t>(), s);
+            };
+            run();
+            CUDA_CHECK(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) run();
+            CUDA_CHECK(cudaEventRecord(e1, s));
+            CUDA_CHECK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+            return ms;
+        };
+        int best[2] = {1, 1};
+        HeffGemm* Gs[2] = {&P.g1, &P.g4};
+        for (int g = 0; g < 2; ++g) {
+            HeffGemm& G = *Gs[g];
+            int maxkt = 1;
+            for (const GemmTask& t : G.tc_base) maxkt = std::max(maxkt, t.kt);
+            const int64_t tiles = base_tiles(G);
+            float tbest = time_split(G, g == 0, 1);
+            for (int split : {2, 4, 8}) {
+                if (split > maxkt || tiles * (split / 2) >= 2 * (int64_t)ctx->num_sms) break;
+                const float tm = time_split(G, g == 0, split);
+                if (tm < 0.97f * tbest) {
+                    tbest = tm;
+                    best[g] = split;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        check_device_flag(ctx);
+        choice = {best[0], best[1]};
+        ctx->heff_tune[key] = choice;
+        measured = true;
+    }
+    set_split(P.g1, choice.first, s);
+    set_split(P.g4, choice.second, s);
+    ensure_part(P, std::max(P.g1.part_elems, P.g4.part_elems));
+    if (std::getenv("TNH_DEBUG"))
+        std::fprintf(stderr, "heff_plan: K split S1 %d, S4 %d (%s; S1 %lld tiles, S4 %lld tiles)\n", choice.first,
+                     choice.second, measured ? "measured" : "cached or forced", (long long)base_tiles(P.g1),
+                     (long long)base_tiles(P.g4));
+}
+
+}  // namespace
 
 HeffPlan::~HeffPlan() {
     for (auto& g : graphs) {
@@ -513,6 +684,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     auto tc_bytes = [&](const HeffOperand& o) { return (size_t)o.tiles * pl * kTcTileElems * 2; };
     auto f64_bytes = [](const HeffOperand& o) { return (size_t)o.elems64 * sizeof(double); };
     P->opX.alloc(std::max<size_t>({f64_bytes(P->oX), tc_bytes(P->oX), 16}));
+    CUDA_CHECK(cudaMemsetAsync(P->opX.p, 0, P->opX.bytes, s));
     // operand A of S4: the MPO step writes only the covered sub-blocks, the
     // rest (padding, sub-blocks without a W12 entry) stays zero from here on
     P->opT64.alloc(std::max<size_t>(f64_bytes(P->oT), 16));
@@ -532,6 +704,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         launch_gather(jR, P->oR.d_gtc.as<OpGeom>(), R.data, P->Rtc.p, pl, s, "heff_pack_env");
     }
     CUDA_CHECK(cudaGetLastError());
+    if (pl > 0 && !P->g1.tc_base.empty() && !P->g4.tc_base.empty()) tune_splits(*P);
     if (std::getenv("TNH_DEBUG"))
         std::fprintf(stderr,
                      "heff_plan: n %lld, S1 %zu tasks %d tiles, T1 %lld, S4 %zu tasks %d tiles, T3 %lld, "
@@ -546,30 +719,6 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
 
 namespace {
 
-// The four launches of one application (x -> y).
-void launch_chain(HeffPlan& P, bool f64, const double* x, double* y) {
-    Ctx* ctx = P.ctx;
-    cudaStream_t s = P.stream;
-    const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
-    if (f64) {
-        launch_gather(P.jX, P.oX.d_g64.as<OpGeom>(), x, P.opX.p, 0, s, "heff_pack_x");
-        launch_gemm_f64(P.g1.d_f64.as<GemmTask>(), n1, P.g1.tiles64, P.L64.as<double>(), P.opX.as<double>(),
-                        P.t1.as<double>(), s);
-        launch_w12(P.jW, P.oT.d_g64.as<OpGeom>(), P.t1.as<double>(), P.opT64.p, 0, s);
-        launch_gemm_f64(P.g4.d_f64.as<GemmTask>(), n4, P.g4.tiles64, P.opT64.as<double>(), P.R64.as<double>(), y, s,
-                        P.row_off.as<int64_t>());
-    } else {
-        const int pl = P.planes;
-        int* err = ctx->d_flag.as<int>();
-        launch_gather(P.jX, P.oX.d_gtc.as<OpGeom>(), x, P.opX.p, pl, s, "heff_pack_x");
-        launch_gemm_tc(P.g1.d_tc.as<GemmTask>(), n1, P.g1.tilestc, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(),
-                       P.t1.as<double>(), pl, ctx->num_sms, err, s);
-        launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, pl, s);
-        launch_gemm_tc(P.g4.d_tc.as<GemmTask>(), n4, P.g4.tilestc, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y, pl,
-                       ctx->num_sms, err, s, P.row_off.as<int64_t>());
-    }
-}
-
 cudaGraphNode_t last_node(cudaStream_t s) {
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t* deps = nullptr;
@@ -577,6 +726,43 @@ cudaGraphNode_t last_node(cudaStream_t s) {
     CUDA_CHECK(cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd));
     TNH_REQUIRE(st == cudaStreamCaptureStatusActive && nd == 1, TNH_ERR_CUDA, "heff: unexpected capture state");
     return deps[0];
+}
+
+// The launches of one application (x -> y) on stream s. While capturing
+// (G != nullptr) the node that reads x and the node that writes y are
+// recorded with the position of that pointer among their arguments:
+// gather_kernel(tiles, segs, terms, geom, src, dst) reads x as argument 4;
+// y is written by gemm_f64_kernel(tasks, ntasks, A, B, C, row_off) as
+// argument 4, gemm_tc_kernel(tasks, ntasks, tiles, A, B, C, err, row_off) as
+// argument 5, or splitk_reduce(reds, nred, total, part, out, row_off) as
+// argument 4.
+void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_t s, HeffPlan::Graph* G) {
+    const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
+    if (f64) {
+        launch_gather(P.jX, P.oX.d_g64.as<OpGeom>(), x, P.opX.p, 0, s, "heff_pack_x");
+        if (G) G->nx = last_node(s);
+        launch_gemm_f64(P.g1.d_f64.as<GemmTask>(), n1, P.g1.tiles64, P.L64.as<double>(), P.opX.as<double>(),
+                        P.t1.as<double>(), s);
+        launch_w12(P.jW, P.oT.d_g64.as<OpGeom>(), P.t1.as<double>(), P.opT64.p, 0, s);
+        launch_gemm_f64(P.g4.d_f64.as<GemmTask>(), n4, P.g4.tiles64, P.opT64.as<double>(), P.R64.as<double>(), y, s,
+                        P.row_off.as<int64_t>());
+        if (G) {
+            G->ny = last_node(s);
+            G->iy = 4;
+            G->ny_args = 6;
+        }
+    } else {
+        launch_gather(P.jX, P.oX.d_gtc.as<OpGeom>(), x, P.opX.p, P.planes, s, "heff_pack_x");
+        if (G) G->nx = last_node(s);
+        launch_stage(P.g1, P, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(), P.t1.p, nullptr, s);
+        launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, P.planes, s);
+        launch_stage(P.g4, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y, P.row_off.as<int64_t>(), s);
+        if (G) {
+            G->ny = last_node(s);
+            G->iy = P.g4.split > 1 ? 4 : 5;
+            G->ny_args = P.g4.split > 1 ? 6 : 8;
+        }
+    }
 }
 
 std::vector<void*> node_args(cudaGraphNode_t n, int count) {
@@ -595,14 +781,10 @@ void patch(cudaGraphExec_t ex, cudaGraphNode_t n, std::vector<void*>& args, int 
     CUDA_CHECK(cudaGraphExecKernelNodeSetParams(ex, n, &p));
 }
 
-// Capture the chain once (x and y of this call); later calls patch the two
-// pointer arguments. Argument positions: gather_kernel(tiles, segs, terms,
-// geom, src, dst) reads x as argument 4; gemm_tc_kernel(tasks, ntasks,
-// tiles, A, B, C, err, row_off) and gemm_f64_kernel(tasks, ntasks, A, B, C,
-// row_off) write y as argument 5 / 4.
-// The capture runs on a stream of its own (the plan's stream may be the
-// legacy default stream, which cannot be captured); the graph is replayed on
-// the plan's stream.
+// Capture the chain once (x and y of this call) on a stream of its own (the
+// plan's stream may be the legacy default stream, which cannot be
+// captured); the graph is replayed on the plan's stream, and later calls
+// patch the two pointer arguments.
 void capture(HeffPlan& P, HeffPlan::Graph& G, bool f64, const double* x, double* y) {
     cudaStream_t s = nullptr;
     CUDA_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -612,28 +794,7 @@ void capture(HeffPlan& P, HeffPlan::Graph& G, bool f64, const double* x, double*
     } sg{s};
     CUDA_CHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     try {
-        const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
-        // the same launches as launch_chain, with the two nodes remembered
-        Ctx* ctx = P.ctx;
-        const int pl = P.planes;
-        int* err = ctx->d_flag.as<int>();
-        if (f64) launch_gather(P.jX, P.oX.d_g64.as<OpGeom>(), x, P.opX.p, 0, s, "heff_pack_x");
-        else launch_gather(P.jX, P.oX.d_gtc.as<OpGeom>(), x, P.opX.p, pl, s, "heff_pack_x");
-        G.nx = last_node(s);
-        if (f64) {
-            launch_gemm_f64(P.g1.d_f64.as<GemmTask>(), n1, P.g1.tiles64, P.L64.as<double>(), P.opX.as<double>(),
-                            P.t1.as<double>(), s);
-            launch_w12(P.jW, P.oT.d_g64.as<OpGeom>(), P.t1.as<double>(), P.opT64.p, 0, s);
-            launch_gemm_f64(P.g4.d_f64.as<GemmTask>(), n4, P.g4.tiles64, P.opT64.as<double>(), P.R64.as<double>(), y,
-                            s, P.row_off.as<int64_t>());
-        } else {
-            launch_gemm_tc(P.g1.d_tc.as<GemmTask>(), n1, P.g1.tilestc, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(),
-                           P.t1.as<double>(), pl, ctx->num_sms, err, s);
-            launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, pl, s);
-            launch_gemm_tc(P.g4.d_tc.as<GemmTask>(), n4, P.g4.tilestc, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y,
-                           pl, ctx->num_sms, err, s, P.row_off.as<int64_t>());
-        }
-        G.ny = last_node(s);
+        launch_chain(P, f64, x, y, s, &G);
     } catch (...) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(s, &g);
@@ -643,9 +804,8 @@ void capture(HeffPlan& P, HeffPlan::Graph& G, bool f64, const double* x, double*
     CUDA_CHECK(cudaStreamEndCapture(s, &G.graph));
     CUDA_CHECK(cudaGraphInstantiate(&G.exec, G.graph, 0));
     G.ix = 4;
-    G.iy = f64 ? 4 : 5;
     G.ax = node_args(G.nx, 6);
-    G.ay = node_args(G.ny, f64 ? 6 : 8);
+    G.ay = node_args(G.ny, G.ny_args);
     G.x = x;
     G.y = y;
 }
@@ -667,7 +827,7 @@ void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
     // direct launches while profiling (per-kernel events) and on the first
     // call (kernel attributes are set outside any capture)
     if ((prof && prof->on) || G.calls++ == 0) {
-        launch_chain(P, f64, x, y);
+        launch_chain(P, f64, x, y, s, nullptr);
         CUDA_CHECK(cudaGetLastError());
         return;
     }

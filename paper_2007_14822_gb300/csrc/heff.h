@@ -14,10 +14,17 @@ struct HeffOperand {
     DevBuf d_g64, d_gtc;
     void add_task(int64_t rows, int64_t K);
 };
+// One GEMM of the plan. The tcgen05 tasks are launched as given in tc: the
+// block tasks of tc_base, or, with split > 1, every block task cut into up
+// to split K ranges that write float32 partials, summed by one reduction
+// launch (reds) into the real output.
 struct HeffGemm {
-    std::vector<GemmTask> f64, tc;
+    std::vector<GemmTask> f64, tc, tc_base;
     int tiles64 = 0, tilestc = 0;
-    DevBuf d_f64, d_tc;
+    int split = 1;
+    std::vector<SplitRed> reds;
+    int64_t red_total = 0, part_elems = 0;
+    DevBuf d_f64, d_tc, d_reds;
 };
 
 struct HeffPlan {
@@ -39,6 +46,7 @@ struct HeffPlan {
     DevBuf opT64, opTtc;    // operand A of S4, one per format
     DevBuf t1;              // S1 result (float32 in the split modes)
     DevBuf row_off;         // S4 output row -> element offset in psi's layout
+    DevBuf part;            // float32 partial slabs of K-split GEMMs
     int64_t t1_elems = 0;
     bool zero_y = false;    // some output rows are written by no S4 task
     // one CUDA graph per format (float64, split): the four launches of an
@@ -49,6 +57,7 @@ struct HeffPlan {
         cudaGraphNode_t nx = nullptr, ny = nullptr;   // the kernel nodes reading x / writing y
         std::vector<void*> ax, ay;                    // their argument pointer arrays
         int ix = 0, iy = 0;                           // index of x / y among the arguments
+        int ny_args = 0;                              // argument count of the y node's kernel
         const double* x = nullptr;
         double* y = nullptr;
         int calls = 0;

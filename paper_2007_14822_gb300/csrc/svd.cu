@@ -324,26 +324,40 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                     B += red[1][w];
                     Gg += red[2][w];
                 }
-                const double tol = 4.0 * sqrt((double)L) * 1.1102230246251565e-16;
-                const double null2 = 1e-28 * fro2[G.grp];
-                act = (fabs(Gg) > tol * sqrt(A * B)) && A > null2 && B > null2;
+                // The decisions and the rotation angle are computed in float32
+                // (float64 division and square root are slow on this GPU); the
+                // angle only needs to reduce x_p.x_q, and the rotation is made
+                // orthogonal to float64 accuracy by rescaling (c, s) with a
+                // series for 1/sqrt(c^2 + s^2) (|c^2 + s^2 - 1| ~ 1e-7).
+                const double inv = 1.0 / fro2[G.grp];
+                const float a = (float)(A * inv), b = (float)(B * inv), gg = (float)(Gg * inv);
+                const float d = (float)((B - A) * inv);
+                const float null2 = 1e-28f;
+                const float tol = 4.0f * sqrtf((float)L) * 1.1102230246251565e-16f;
+                const bool live = a > null2 && b > null2;
+                const float rel = live ? fabsf(gg) / sqrtf(a * b) : 0.f;
+                act = live && rel > tol;
                 // stop test, per column pair: a column y = M v formed in float64
                 // carries an absolute rounding error ~ eps sqrt(len) |M|_F, so
                 // the pair can only be made orthogonal to about
                 //   floor = 16 eps sqrt(len) |M|_F / min(|y_p|, |y_q|)
                 // of its norms; the target is max(kDone64, floor) and smax holds
                 // the largest ratio to it (done when below 1)
-                if (A > null2 && B > null2) {
-                    const double flo = 16.0 * 1.1102230246251565e-16 * sqrt((double)L) * sqrt(fro2[G.grp] / fmin(A, B));
-                    const double ratio = fabs(Gg) / sqrt(A * B) / fmax((double)kDone64, flo);
-                    atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int((float)ratio));
+                if (live) {
+                    const float flo = 16.0f * 1.1102230246251565e-16f * sqrtf((float)L) * rsqrtf(fminf(a, b));
+                    atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(rel / fmaxf(kDone64, flo)));
                 }
                 if (act) {
-                    const double zeta = (B - A) / (2.0 * Gg);
-                    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double c = 1.0 / sqrt(1.0 + tt * tt);
-                    rot[0] = c;
-                    rot[1] = c * tt;
+                    const float zeta = d / (2.0f * gg);
+                    const float az = fabsf(zeta);
+                    const float tt = az > 1e8f ? 0.5f / zeta
+                                               : (zeta >= 0.f ? 1.f : -1.f) / (az + sqrtf(1.f + zeta * zeta));
+                    const float c32 = rsqrtf(1.f + tt * tt);
+                    double c = (double)c32, sn = (double)(c32 * tt);
+                    const double dl = fma(c, c, sn * sn) - 1.0;
+                    const double f = 1.0 + dl * (-0.5 + 0.375 * dl);
+                    rot[0] = c * f;
+                    rot[1] = sn * f;
                 }
             }
             __syncthreads();

@@ -124,6 +124,8 @@ struct Ctx {
     std::string err;
     DevBuf d_flag;    // int[4]: [0] device error code written by bounded waits
     std::unique_ptr<Profiler> prof;
+    // H_eff K-split choices measured by the plan autotuner, by shape signature
+    std::map<std::vector<int>, std::pair<int, int>> heff_tune;
     ~Ctx();
 };
 
@@ -182,6 +184,8 @@ struct GemmTask {
     int use_roff;            // 1: row m of C starts at row_off[roff + m] (scatter epilogue)
     int c_f32;               // tcgen05 GEMM only: C is float32 (else float64)
     int64_t roff;
+    int kstride;             // tcgen05 GEMM: operand tiles per tile row (0: kt); a K-split sub-task
+                             // covers kt k-blocks starting at its a_base / b_base
 };
 void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, int total_tiles, const double* A,
                      const double* B, double* C, cudaStream_t s, const int64_t* row_off = nullptr);
@@ -189,6 +193,19 @@ void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, int total_tiles, const
 void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A,
                     const uint16_t* B, double* C, int planes, int num_sms, int* err,
                     cudaStream_t s, const int64_t* row_off = nullptr);
+// K-split reduction: out = sum over S float32 partial slabs [S][M][N]
+// (summed in float64, fixed order), written to float32 or float64 rows.
+struct SplitRed {
+    int M, N, S;
+    int use_roff, out_f32;
+    int ldc;
+    int64_t part;    // first element of the partial slabs
+    int64_t roff;    // use_roff: row m starts at row_off[roff + m]
+    int64_t c_base;  // else: row m starts at c_base + m * ldc
+    int64_t e0;      // prefix of M * N over the reductions of one launch
+};
+void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const float* part, void* out,
+                          const int64_t* row_off, int num_sms, cudaStream_t s);
 constexpr int kF64TileM = 64, kF64TileN = 64, kF64TileK = 16;
 constexpr int kTcTileM = 128, kTcTileN = 128, kTcTileK = 64;
 constexpr int kTcTileElems = kTcTileM * kTcTileK;   // 8192 bf16 per plane tile

@@ -135,6 +135,16 @@ def test_heff_graph_replay_with_new_buffers(ctx, p):
         assert H.rel_err(H.to_oracle(yt), want) < TOL[p], (call, xi, yi)
 
 
+@pytest.mark.parametrize("split", ["2,8", "4,3", "1,2"])
+@pytest.mark.parametrize("m,nsect,maxd", [(130, 1, 130), (300, 15, 60)])
+def test_heff_k_split_matches_oracle(ctx, split, m, nsect, maxd, monkeypatch):
+    # the plan autotuner may cut the S1 / S4 GEMMs into K ranges with float32
+    # partials and a reduction; force each shape of it and check the result
+    monkeypatch.setenv("TNH_HEFF_SPLIT", split)
+    err, plan = _heff_case(ctx, m, nsect, "bf16x6", maxd=maxd)
+    assert err < TOL["bf16x6"], err
+
+
 def test_heff_config2_full_size(ctx):
     # dense m=256, w=5, d=2: L/R (256,5,256), psi (256,2,2,256), Gaussian, seeded
     for p in ("fp64", "bf16x6"):
