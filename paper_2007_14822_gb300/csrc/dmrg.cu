@@ -136,8 +136,12 @@ extern "C" tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, i
         for (int j = N - 1; j >= 2; --j) update_R(j);
 
         double E = 0.0;
+        const bool dbg = std::getenv("TNH_DEBUG") != nullptr;
+        using clk = std::chrono::steady_clock;
+        auto since = [](clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); };
         for (int sw = 0; sw < p->nsweep; ++sw) {
             auto t0 = std::chrono::steady_clock::now();
+            double ph[6] = {0, 0, 0, 0, 0, 0};   // theta, plan, eigsolve, svd, factors, environment (s)
             double maxerr = 0.0, resid = 0.0;
             int64_t nmv = 0;
             for (int pass = 0; pass < 2; ++pass) {
@@ -150,22 +154,31 @@ extern "C" tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, i
                     DTensor th = new_tensor({a1.inds[0], a1.inds[1], a2.inds[1], a2.inds[2]},
                                             fsum(a1.flux, a2.flux), s);
                     th.L = relabel(th.L, {1, 2, 4, 5});
+                    auto tp = clk::now();
                     {
                         auto cp = plan_contract(a1, a2, th.L, s);
                         Workspace ws;
                         run_contract(c, *cp, a1.data, a2.data, th.L.data, eprec, ws);
                         CUDA_CHECK(cudaStreamSynchronize(s));
                     }
+                    ph[0] += since(tp);
                     // eigensolver
                     {
+                        tp = clk::now();
                         auto P = make_heff(c, Ls[j].L, W[j], W[j + 1], Rs[j + 2].L, th.L, prec);
+                        ph[1] += since(tp);
+                        tp = clk::now();
                         EigResult r = eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
+                        ph[2] += since(tp);
                         E = r.energy;
                         resid = r.resid;
                         nmv += r.matvecs;
                     }
                     // truncated SVD
+                    tp = clk::now();
                     SvdResult* sv = svd_run(c, th.L, 2, p->cutoff[sw], p->maxdim[sw], p->mindim, dir > 0 ? 0 : 1);
+                    ph[3] += since(tp);
+                    tp = clk::now();
                     try {
                         SvdShape sh = svd_shape(sv);
                         maxerr = std::max(maxerr, sh.truncerr);
@@ -192,13 +205,21 @@ extern "C" tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, i
                         throw;
                     }
                     svd_delete(sv);
+                    ph[4] += since(tp);
+                    tp = clk::now();
                     if (dir > 0) update_L(j);
                     else update_R(j + 1);
+                    ph[5] += since(tp);
                 }
             }
             CUDA_CHECK(cudaStreamSynchronize(s));
             check_device_flag(c);
             double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (dbg)
+                std::fprintf(stderr,
+                             "dmrg: sweep %d %.3f s: theta %.3f, H_eff plan %.3f, eigensolver %.3f, SVD %.3f, "
+                             "factors %.3f, environment %.3f\n",
+                             sw, secs, ph[0], ph[1], ph[2], ph[3], ph[4], ph[5]);
             if (stats) {
                 tnh_sweep_stat& st = stats[sw];
                 st.sweep = sw;

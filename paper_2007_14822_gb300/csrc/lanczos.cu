@@ -8,10 +8,10 @@
 //   twice: h = Q^T w, w -= Q h      (classical Gram-Schmidt, applied twice)
 //   beta_j = |w|;  q_{j+1} = w / beta_j.
 // After every step the lowest eigenvalue of the tridiagonal matrix T_j is
-// found by multisection on its Sturm sequence and its eigenvector by two
-// steps of inverse iteration (tridiagonal Gaussian elimination with partial
-// pivoting); the Ritz residual estimate is beta_j |s_j|. Every vector
-// operation is float64 with a fixed-order (deterministic) reduction.
+// found by multisection on its Sturm sequence (division-free minors) and its
+// eigenvector by one twisted factorization of T_j - theta, refined by the
+// Rayleigh quotient; the Ritz residual estimate is beta_j |s_j|. Every
+// vector operation is float64 with a fixed-order (deterministic) reduction.
 #include <cmath>
 
 #include "heff.h"
@@ -98,58 +98,30 @@ __global__ void axpy_dev(double* __restrict__ y, const double* __restrict__ x, c
         y[i] -= a * x[i];
 }
 
-// Number of eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm count).
+// Number of eigenvalues of the symmetric tridiagonal (a, b) below x: the
+// number of negative pivots d_i = p_{i+1} / p_i of T - x = L D L^T
+// (Sylvester's inertia), read off the signs of the leading minors
+//   p_0 = 1, p_1 = a_0 - x, p_{i+1} = (a_i - x) p_i - b_{i-1}^2 p_{i-1}
+// without a division (float64 division is slow on this GPU). An exactly
+// zero pivot is taken as a tiny positive one (p_{i+1} = 2^-200 p_i), and the
+// pair (p_{i-1}, p_i) is rescaled by an exact power of two when it leaves
+// [2^-500, 2^500].
 __device__ int sturm_count(const double* a, const double* b2, int k, double x) {
     int c = 0;
-    double d = a[0] - x;
-    if (d < 0) ++c;
+    double pm = 1.0, p = a[0] - x;
+    if (p == 0.0) p = 0x1p-200;
+    if (p < 0.0) ++c;
     for (int i = 1; i < k; ++i) {
-        if (d == 0.0) d = 1e-300;
-        d = (a[i] - x) - b2[i - 1] / d;
-        if (d < 0) ++c;
+        double pn = (a[i] - x) * p - b2[i - 1] * pm;
+        if (pn == 0.0) pn = p * 0x1p-200;
+        if ((pn < 0.0) != (p < 0.0)) ++c;
+        pm = p;
+        p = pn;
+        const double ap = fabs(p);
+        if (ap > 0x1p500) { p *= 0x1p-500; pm *= 0x1p-500; }
+        else if (ap < 0x1p-500 && fabs(pm) < 0x1p-500) { p *= 0x1p500; pm *= 0x1p500; }
     }
     return c;
-}
-
-// Solve (T - theta) s = rhs in place (tridiagonal Gaussian elimination with
-// partial pivoting); dd/dl/du/du2 are scratch of length k.
-__device__ void tri_solve(const double* a, const double* b, int k, double theta, double* rhs, double* dd,
-                          double* dl, double* du, double* du2) {
-    double tnorm = 1e-300;
-    for (int i = 0; i < k; ++i) {
-        dd[i] = a[i] - theta;
-        tnorm = fmax(tnorm, fabs(a[i]) + (i + 1 < k ? fabs(b[i]) : 0.0) + (i > 0 ? fabs(b[i - 1]) : 0.0));
-    }
-    for (int i = 0; i + 1 < k; ++i) { dl[i] = b[i]; du[i] = b[i]; du2[i] = 0.0; }
-    // a zero pivot (theta is an eigenvalue) is replaced by eps * |T|, which
-    // keeps the solution finite and pointing along the eigenvector
-    const double tiny = fmax(1e-15 * tnorm, 1e-200);
-    for (int i = 0; i + 1 < k; ++i) {
-        if (fabs(dd[i]) >= fabs(dl[i])) {
-            if (dd[i] == 0.0) dd[i] = tiny;
-            double f = dl[i] / dd[i];
-            dd[i + 1] -= f * du[i];
-            rhs[i + 1] -= f * rhs[i];
-            if (i + 2 < k) du2[i] = 0.0;
-        } else {
-            double f = dd[i] / dl[i];
-            dd[i] = dl[i];
-            double t = dd[i + 1];
-            dd[i + 1] = du[i] - f * t;
-            if (i + 2 < k) {
-                du2[i] = du[i + 1];
-                du[i + 1] = -f * du2[i];
-            }
-            du[i] = t;
-            double r = rhs[i];
-            rhs[i] = rhs[i + 1];
-            rhs[i + 1] = r - f * rhs[i + 1];
-        }
-    }
-    if (dd[k - 1] == 0.0) dd[k - 1] = tiny;
-    rhs[k - 1] /= dd[k - 1];
-    if (k > 1) rhs[k - 2] = (rhs[k - 2] - du[k - 2] * rhs[k - 1]) / dd[k - 2];
-    for (int i = k - 3; i >= 0; --i) rhs[i] = (rhs[i] - du[i] * rhs[i + 1] - du2[i] * rhs[i + 2]) / dd[i];
 }
 
 constexpr int kMaxKrylov = 256;
@@ -161,9 +133,9 @@ __global__ void tridiag_lowest(const double* __restrict__ alpha, double* __restr
                                const double* __restrict__ beta2_last, double* __restrict__ out,
                                double* __restrict__ s) {
     __shared__ double a[kMaxKrylov], b[kMaxKrylov], b2[kMaxKrylov];
-    __shared__ double lo_s, hi_s;
+    __shared__ double lo_s, hi_s, tiny_s;
     __shared__ int first_s;
-    __shared__ double dd[kMaxKrylov], dl[kMaxKrylov], du[kMaxKrylov], du2[kMaxKrylov], v[kMaxKrylov];
+    __shared__ double dd[kMaxKrylov], dl[kMaxKrylov], v[kMaxKrylov];
     const int t = threadIdx.x, nt = blockDim.x;
     for (int i = t; i < k; i += nt) a[i] = alpha[i];
     for (int i = t; i + 1 < k; i += nt) { b[i] = beta[i]; b2[i] = beta[i] * beta[i]; }
@@ -180,59 +152,111 @@ __global__ void tridiag_lowest(const double* __restrict__ alpha, double* __restr
         hi_s = hi + pad;
     }
     __syncthreads();
-    // multisection: nt probes per round
-    for (int round = 0; round < 12; ++round) {
+    // multisection: 32 probes per round, by the first warp only (float64
+    // throughput of one SM bounds many probes; 5 bits per round suffice)
+    if (t < 32) {
         double lo = lo_s, hi = hi_s;
-        if (hi - lo <= 2e-16 * fmax(fabs(lo), fabs(hi))) break;
-        if (t == 0) first_s = nt;
+        for (int round = 0; round < 24; ++round) {
+            if (hi - lo <= 2e-16 * fmax(fabs(lo), fabs(hi))) break;
+            const double x = lo + (hi - lo) * (double)(t + 1) / 33.0;
+            const unsigned below = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x) >= 1);
+            const int f = below ? __ffs(below) - 1 : 32;   // first probe with an eigenvalue below it
+            const double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / 33.0;
+            const double nhi = f == 32 ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+            lo = nlo;
+            hi = nhi;
+        }
+        if (t == 0) {
+            lo_s = lo;
+            hi_s = hi;
+        }
+    }
+    __syncthreads();
+    if (k == 1) {   // uniform branch: the other one has barriers
+        if (t == 0) {
+            double bk = sqrt(fmax(*beta2_last, 0.0));
+            beta[0] = bk;
+            out[0] = a[0];
+            out[1] = bk;
+            out[2] = bk;
+            s[0] = 1.0;
+        }
+    } else {
+        // eigenvector for theta by one twisted factorization of T - theta:
+        // D+ from the top (thread 0) and D- from the bottom (thread 1) run
+        // concurrently; the twist r minimises |gamma_r|, v_r = 1, and v is
+        // recurred outwards (threads 0 and 1 again)
+        const double theta = 0.5 * (lo_s + hi_s);
+        if (t == 0) {
+            double tn = 1e-300;
+            for (int i = 0; i < k; ++i)
+                tn = fmax(tn, fabs(a[i]) + (i + 1 < k ? fabs(b[i]) : 0.0) + (i > 0 ? fabs(b[i - 1]) : 0.0));
+            tiny_s = fmax(1e-15 * tn, 1e-200);
+        }
         __syncthreads();
-        double x = lo + (hi - lo) * (double)(t + 1) / (double)(nt + 1);
-        int c = sturm_count(a, b2, k, x);
-        if (c >= 1) atomicMin(&first_s, t);
+        const double tiny = tiny_s;
+        if (t == 0) {
+            double d = a[0] - theta;
+            for (int i = 0; i < k; ++i) {
+                if (i > 0) d = (a[i] - theta) - b2[i - 1] / d;
+                if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
+                dd[i] = d;   // D+
+            }
+        } else if (t == 1) {
+            double d = a[k - 1] - theta;
+            for (int i = k - 1; i >= 0; --i) {
+                if (i < k - 1) d = (a[i] - theta) - b2[i] / d;
+                if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
+                dl[i] = d;   // D-
+            }
+        }
         __syncthreads();
         if (t == 0) {
-            int f = first_s;
-            double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / (double)(nt + 1);
-            double nhi = f == nt ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(nt + 1);
-            lo_s = nlo;
-            hi_s = nhi;
+            int r = 0;
+            double gbest = INFINITY;
+            for (int i = 0; i < k; ++i) {
+                const double g = fabs(dd[i] + dl[i] - (a[i] - theta));
+                if (g < gbest) { gbest = g; r = i; }
+            }
+            first_s = r;
         }
         __syncthreads();
-    }
-    if (t == 0 && k == 1) {
-        double bk = sqrt(fmax(*beta2_last, 0.0));
-        beta[0] = bk;
-        out[0] = a[0];
-        out[1] = bk;
-        out[2] = bk;
-        s[0] = 1.0;
-    } else if (t == 0) {
-        double theta = 0.5 * (lo_s + hi_s);
-        for (int i = 0; i < k; ++i) v[i] = 1.0;
-        for (int rep = 0; rep < 3; ++rep) {
-            tri_solve(a, b, k, theta, v, dd, dl, du, du2);
-            double mx = 0.0;
-            for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(v[i]));
-            if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
+        const int r = first_s;
+        if (t == 0) {   // v_r = 1 and the part above the twist
+            double vi = 1.0;
+            v[r] = 1.0;
+            for (int i = r - 1; i >= 0; --i) {
+                vi = -(b[i] / dd[i]) * vi;
+                v[i] = vi;
+            }
+        } else if (t == 1) {   // the part below the twist (starts from v_r = 1 itself)
+            double vi = 1.0;
+            for (int i = r + 1; i < k; ++i) {
+                vi = -(b[i - 1] / dl[i]) * vi;
+                v[i] = vi;
+            }
+        }
+        __syncthreads();
+        if (t == 0) {
             double nrm = 0.0;
-            for (int i = 0; i < k; ++i) { v[i] /= mx; nrm += v[i] * v[i]; }
-            nrm = sqrt(nrm);
-            for (int i = 0; i < k; ++i) v[i] /= nrm;
+            for (int i = 0; i < k; ++i) nrm = fma(v[i], v[i], nrm);
+            const double inv = 1.0 / sqrt(nrm);
+            for (int i = 0; i < k; ++i) v[i] *= inv;
+            // Rayleigh quotient refines theta to machine precision
+            double rq = 0.0;
+            for (int i = 0; i < k; ++i) {
+                double tv = a[i] * v[i];
+                if (i > 0) tv += b[i - 1] * v[i - 1];
+                if (i + 1 < k) tv += b[i] * v[i + 1];
+                rq += v[i] * tv;
+            }
+            double bk = sqrt(fmax(*beta2_last, 0.0));
+            beta[k - 1] = bk;
+            out[0] = rq;
+            out[1] = bk * fabs(v[k - 1]);
+            out[2] = bk;
+            for (int i = 0; i < k; ++i) s[i] = v[i];
         }
-        // Rayleigh quotient refines theta to machine precision
-        double rq = 0.0;
-        for (int i = 0; i < k; ++i) {
-            double tv = a[i] * v[i];
-            if (i > 0) tv += b[i - 1] * v[i - 1];
-            if (i + 1 < k) tv += b[i] * v[i + 1];
-            rq += v[i] * tv;
-        }
-        double bk = sqrt(fmax(*beta2_last, 0.0));
-        beta[k - 1] = bk;
-        out[0] = rq;
-        out[1] = bk * fabs(v[k - 1]);
-        out[2] = bk;
-        for (int i = 0; i < k; ++i) s[i] = v[i];
     }
 }
 

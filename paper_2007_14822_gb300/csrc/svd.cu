@@ -15,7 +15,7 @@
 //    b. The candidate columns (the largest float32 singular values: maxdim
 //       plus a margin, and all within 1e-4 of the largest) are
 //       re-orthonormalised and re-formed in float64, Y = X V32[:, cand], and
-//       polished by float64 one-sided Jacobi (a CTA per column pair), which
+//       polished by float64 one-sided block Jacobi (blocks of 4 columns), which
 //       converges in one or two sweeps because Y is already nearly
 //       orthogonal.
 //    c. The float64 singular values sigma_j = |Y_j| are pooled, ranked
@@ -236,42 +236,47 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
 struct JGroup {
     int64_t x_off;   // column-major Y: n columns of length len
     int len, n;
-    int rounds;
-    int pair0;
+    int b;           // columns per block
+    int nblk;        // blocks, rounded up to even
+    int rounds;      // nblk - 1
+    int pair0;       // first global block-pair index
     int grp;         // group (index into fro2)
 };
 
-constexpr int kJ64Threads = 128;
-constexpr int kJ64Regs = 8;   // rows per thread kept in registers (len <= 1024)
+constexpr int kJ64MaxB = 4;                // columns per block (a block pair has <= 8)
+constexpr int kJ64Threads = 32 * kJ64MaxB;   // one warp per column pair of an inner step
+constexpr float kDone64 = 1e-9f;           // float64 stop
 
-// One CTA per column pair and round: the two columns are read once into
-// registers (every thread a few rows), the three dot products are reduced
-// across the CTA, one thread computes the rotation. Columns whose squared
-// norm is below 1e-28 |M_g|_F^2 are float64 rounding noise and are not
-// rotated.
-constexpr float kDone64 = 1e-9f;   // float64 stop
-
+// Float64 one-sided block Jacobi: blocks of b columns paired round-robin;
+// one CTA per block pair and round loads its 2b columns into shared memory
+// and runs one inner sweep (one warp per column pair), so every grid barrier
+// is shared by (2b - 1) b rotations. The decisions and the rotation angle
+// are computed in float32 (float64 division and square root are slow on
+// this GPU); the angle only needs to reduce x_p.x_q, and the rotation is
+// made orthogonal to float64 accuracy by rescaling (c, s) with a series for
+// 1/sqrt(c^2 + s^2) (|c^2 + s^2 - 1| ~ 1e-7). Columns whose squared norm is
+// below 1e-28 |M_g|_F^2 are float64 rounding noise and are not rotated.
+// hist (debug, may be null): largest relative off-diagonal per (group, sweep).
 __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restrict__ groups, int ngroups,
                                                           int total_pairs, int max_rounds, double* __restrict__ X,
                                                           int* smax, int* state, GridBar* bar, int* err,
-                                                          const double* __restrict__ fro2) {
-    __shared__ double red[3][kJ64Threads / 32];
-    __shared__ double rot[2];
-    __shared__ int act, skip;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                                                          const double* __restrict__ fro2, int* hist, int stride) {
+    extern __shared__ double smd[];   // [2b][stride]
+    __shared__ int skip;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned epoch = 0;
     int t = 0;
     for (; t < max_rounds; ++t) {
-        for (int pi = blockIdx.x; pi < total_pairs; pi += gridDim.x) {
+        for (int item = blockIdx.x; item < total_pairs; item += gridDim.x) {
             int lo = 0, hi = ngroups - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (groups[mid].pair0 <= pi) lo = mid; else hi = mid - 1;
+                if (groups[mid].pair0 <= item) lo = mid; else hi = mid - 1;
             }
             const JGroup G = groups[lo];
             const int R = G.rounds;
-            const int i = pi - G.pair0, ne = R + 1, k = t % R;
-            if (tid == 0) {
+            const int i = item - G.pair0, k = t % R;
+            if (threadIdx.x == 0) {
                 skip = group_done(smax, lo, R, t, 1.0f);
                 if (k == 0 && i == 0) smax[3 * lo + (t / R + 1) % 3] = 0;
             }
@@ -279,108 +284,86 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
             const int sk = skip;
             __syncthreads();
             if (sk) continue;
-            const int p = rr_pos(i, k, R), q = rr_pos(ne - 1 - i, k, R);
-            if (p >= G.n || q >= G.n) continue;
-            double* xp = X + G.x_off + (int64_t)p * G.len;
-            double* xq = X + G.x_off + (int64_t)q * G.len;
+            const int bp = rr_pos(i, k, R), bq = rr_pos(G.nblk - 1 - i, k, R);
+            const int p0 = bp * G.b, p1 = min(G.n, p0 + G.b);
+            const int q0 = bq * G.b, q1 = min(G.n, q0 + G.b);
+            const int np = max(0, p1 - p0), nq = max(0, q1 - q0), nc = np + nq;
+            if (nc < 2) continue;
             const int L = G.len;
-            const bool in_regs = L <= kJ64Regs * kJ64Threads;
-            double u[kJ64Regs], v[kJ64Regs];
-            double a = 0, b = 0, g = 0;
-            if (in_regs) {
-#pragma unroll
-                for (int e = 0; e < kJ64Regs; ++e) {
-                    const int r = tid + e * kJ64Threads;
-                    u[e] = r < L ? xp[r] : 0.0;
-                    v[e] = r < L ? xq[r] : 0.0;
-                }
-#pragma unroll
-                for (int e = 0; e < kJ64Regs; ++e) {
-                    a = fma(u[e], u[e], a);
-                    b = fma(v[e], v[e], b);
-                    g = fma(u[e], v[e], g);
-                }
-            } else {
-                for (int r = tid; r < L; r += kJ64Threads) {
-                    const double x = xp[r], y = xq[r];
-                    a = fma(x, x, a);
-                    b = fma(y, y, b);
-                    g = fma(x, y, g);
-                }
-            }
-            a = warp_sum(a);
-            b = warp_sum(b);
-            g = warp_sum(g);
-            if (lane == 0) {
-                red[0][warp] = a;
-                red[1][warp] = b;
-                red[2][warp] = g;
+            double* Xg = X + G.x_off;
+            for (int c = warp; c < nc; c += nwarp) {
+                const int col = c < np ? p0 + c : q0 + (c - np);
+                const double* xs = Xg + (int64_t)col * L;
+                double* d = smd + (size_t)c * stride;
+                for (int r = lane; r < L; r += 32) d[r] = xs[r];
             }
             __syncthreads();
-            if (tid == 0) {
-                double A = 0, B = 0, Gg = 0;
-                for (int w = 0; w < kJ64Threads / 32; ++w) {
-                    A += red[0][w];
-                    B += red[1][w];
-                    Gg += red[2][w];
-                }
-                // The decisions and the rotation angle are computed in float32
-                // (float64 division and square root are slow on this GPU); the
-                // angle only needs to reduce x_p.x_q, and the rotation is made
-                // orthogonal to float64 accuracy by rescaling (c, s) with a
-                // series for 1/sqrt(c^2 + s^2) (|c^2 + s^2 - 1| ~ 1e-7).
-                const double inv = 1.0 / fro2[G.grp];
-                const float a = (float)(A * inv), b = (float)(B * inv), gg = (float)(Gg * inv);
-                const float d = (float)((B - A) * inv);
-                const float null2 = 1e-28f;
-                const float tol = 4.0f * sqrtf((float)L) * 1.1102230246251565e-16f;
-                const bool live = a > null2 && b > null2;
-                const float rel = live ? fabsf(gg) / sqrtf(a * b) : 0.f;
-                act = live && rel > tol;
-                // stop test, per column pair: a column y = M v formed in float64
-                // carries an absolute rounding error ~ eps sqrt(len) |M|_F, so
-                // the pair can only be made orthogonal to about
-                //   floor = 16 eps sqrt(len) |M|_F / min(|y_p|, |y_q|)
-                // of its norms; the target is max(kDone64, floor) and smax holds
-                // the largest ratio to it (done when below 1)
-                if (live) {
-                    const float flo = 16.0f * 1.1102230246251565e-16f * sqrtf((float)L) * rsqrtf(fminf(a, b));
-                    atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(rel / fmaxf(kDone64, flo)));
-                }
-                if (act) {
-                    const float zeta = d / (2.0f * gg);
+            const int ne = nc + (nc & 1), Ri = ne - 1;
+            const double inv = 1.0 / fro2[G.grp];
+            const float tol = 4.0f * sqrtf((float)L) * 1.1102230246251565e-16f;
+            const float flo0 = 16.0f * 1.1102230246251565e-16f * sqrtf((float)L);
+            float wmax = 0.f, hmax = 0.f;
+            for (int ir = 0; ir < Ri; ++ir) {
+                for (int pr = warp; pr < ne / 2; pr += nwarp) {
+                    const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
+                    if (a >= nc || bb >= nc) continue;
+                    double* xa = smd + (size_t)a * stride;
+                    double* xb = smd + (size_t)bb * stride;
+                    double A = 0, B = 0, Gg = 0;
+                    for (int r = lane; r < L; r += 32) {
+                        const double u = xa[r], v = xb[r];
+                        A = fma(u, u, A);
+                        B = fma(v, v, B);
+                        Gg = fma(u, v, Gg);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        A += __shfl_xor_sync(0xffffffffu, A, o);
+                        B += __shfl_xor_sync(0xffffffffu, B, o);
+                        Gg += __shfl_xor_sync(0xffffffffu, Gg, o);
+                    }
+                    // every lane has the same sums: the decision is uniform
+                    const float af = (float)(A * inv), bf = (float)(B * inv), gf = (float)(Gg * inv);
+                    const bool live = af > 1e-28f && bf > 1e-28f;
+                    const float rel = live ? fabsf(gf) / (sqrtf(af) * sqrtf(bf)) : 0.f;
+                    if (live) {
+                        // stop test, per column pair: a column y = M v formed in float64
+                        // carries an absolute rounding error ~ eps sqrt(len) |M|_F, so the
+                        // pair can only be made orthogonal to about
+                        //   floor = 16 eps sqrt(len) |M|_F / min(|y_p|, |y_q|)
+                        // of its norms; the target is max(kDone64, floor), smax holds the
+                        // largest ratio to it (done when below 1)
+                        const float flo = flo0 * rsqrtf(fminf(af, bf));
+                        wmax = fmaxf(wmax, rel / fmaxf(kDone64, flo));
+                        hmax = fmaxf(hmax, rel);
+                    }
+                    if (!(live && rel > tol)) continue;
+                    const float df = (float)((B - A) * inv);
+                    const float zeta = df / (2.0f * gf);
                     const float az = fabsf(zeta);
-                    const float tt = az > 1e8f ? 0.5f / zeta
-                                               : (zeta >= 0.f ? 1.f : -1.f) / (az + sqrtf(1.f + zeta * zeta));
+                    const float tt = az > 1e8f ? 0.5f / zeta : (zeta >= 0.f ? 1.f : -1.f) / (az + sqrtf(1.f + zeta * zeta));
                     const float c32 = rsqrtf(1.f + tt * tt);
-                    double c = (double)c32, sn = (double)(c32 * tt);
-                    const double dl = fma(c, c, sn * sn) - 1.0;
+                    const double c0 = (double)c32, s0 = (double)(c32 * tt);
+                    const double dl = fma(c0, c0, s0 * s0) - 1.0;
                     const double f = 1.0 + dl * (-0.5 + 0.375 * dl);
-                    rot[0] = c * f;
-                    rot[1] = sn * f;
+                    const double c = c0 * f, sn = s0 * f;
+                    for (int r = lane; r < L; r += 32) {
+                        const double u = xa[r], v = xb[r];
+                        xa[r] = c * u - sn * v;
+                        xb[r] = sn * u + c * v;
+                    }
                 }
+                __syncthreads();
             }
+            for (int c = warp; c < nc; c += nwarp) {
+                const int col = c < np ? p0 + c : q0 + (c - np);
+                double* xs = Xg + (int64_t)col * L;
+                const double* d = smd + (size_t)c * stride;
+                for (int r = lane; r < L; r += 32) xs[r] = d[r];
+            }
+            if (lane == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
+            if (hist && lane == 0 && hmax > 0.f && t / R < 48) atomicMax(&hist[lo * 48 + t / R], __float_as_int(hmax));
             __syncthreads();
-            if (act) {
-                const double c = rot[0], sn = rot[1];
-                if (in_regs) {
-#pragma unroll
-                    for (int e = 0; e < kJ64Regs; ++e) {
-                        const int r = tid + e * kJ64Threads;
-                        if (r < L) {
-                            xp[r] = c * u[e] - sn * v[e];
-                            xq[r] = sn * u[e] + c * v[e];
-                        }
-                    }
-                } else {
-                    for (int r = tid; r < L; r += kJ64Threads) {
-                        const double x = xp[r], y = xq[r];
-                        xp[r] = c * x - sn * y;
-                        xq[r] = sn * x + c * y;
-                    }
-                }
-            }
-            __syncthreads();   // red, rot and act are reused by the next pair
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
         if (all_done(groups, ngroups, smax, t + 1, 1.0f)) { ++t; break; }
@@ -721,6 +704,47 @@ struct SvdResult {
     double flops32_round = 0.0, flops64_round = 0.0;   // rotation work per round, all groups
 };
 
+// One cooperative launch of the float32 block Jacobi over the groups bg
+// (device copy d_bg); returns the rounds it took.
+int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg, float* X, float* V,
+                     const double* fro2, int bmax, int stride, const char* what) {
+    cudaStream_t s = ctx->stream;
+    int ng = (int)bg.size(), bpairs = 0, rmax = 1;
+    for (const BGroup& G : bg) {
+        bpairs = std::max(bpairs, G.pair0 + G.nblk / 2);
+        rmax = std::max(rmax, G.rounds);
+    }
+    if (ng == 0 || bpairs == 0) return 0;
+    int* errp = ctx->d_flag.as<int>();
+    DevBuf d_smax((size_t)3 * ng * 4), d_state(16), d_bar(16);
+    reset_state(d_smax, d_state, d_bar, ng, s);
+    const int threads = kBJThreads;
+    size_t smem = (size_t)2 * bmax * stride * 4;
+    CUDA_CHECK(cudaFuncSetAttribute(block_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int bpsm = 0;
+    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, block_jacobi_f32, threads, smem));
+    TNH_REQUIRE(bpsm >= 1, TNH_ERR_CUDA, "svd: block Jacobi does not fit on an SM");
+    int grid = std::max(1, std::min(bpairs, bpsm * ctx->num_sms));
+    int max_rounds = 30 * rmax + 4;
+    const BGroup* gp = d_bg.as<BGroup>();
+    int* smaxp = d_smax.as<int>();
+    int* statep = d_state.as<int>();
+    GridBar* barp = d_bar.as<GridBar>();
+    void* args[] = {(void*)&gp,    (void*)&ng,     (void*)&bpairs, (void*)&max_rounds, (void*)&X,      (void*)&V,
+                    (void*)&smaxp, (void*)&statep, (void*)&barp,   (void*)&errp,       (void*)&stride, (void*)&fro2};
+    {
+        KScope ks("svd_jacobi_f32", s);
+        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)block_jacobi_f32, dim3(grid), dim3(threads), args, smem, s));
+    }
+    int st[2];
+    CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));   // bookkeeping buffers are freed on return
+    if (std::getenv("TNH_DEBUG"))
+        std::fprintf(stderr, "svd: float32 block Jacobi%s %d rounds (max %d, per sweep %d, grid %d, b %d)\n", what,
+                     st[1], max_rounds, rmax, grid, bmax);
+    return st[1];
+}
+
 std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim,
                                    int exact_side) {
     cudaStream_t s = ctx->stream;
@@ -860,37 +884,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         set_identity_f32<<<dim3(16, ng), 256, 0, s>>>(d_bg.as<BGroup>(), V32.as<float>());
     }
     // ---- stage a: float32 block Jacobi
-    {
-        DevBuf d_smax((size_t)3 * ng * 4), d_state(16), d_bar(16);
-        reset_state(d_smax, d_state, d_bar, ng, s);
-        const int threads = kBJThreads;
-        size_t smem = (size_t)2 * bmax * stride * 4;
-        CUDA_CHECK(cudaFuncSetAttribute(block_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int bpsm = 0;
-        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, block_jacobi_f32, threads, smem));
-        TNH_REQUIRE(bpsm >= 1, TNH_ERR_CUDA, "svd: block Jacobi does not fit on an SM");
-        int grid = std::max(1, std::min(bpairs, bpsm * ctx->num_sms));
-        int max_rounds = 30 * rmax + 4;
-        const BGroup* gp = d_bg.as<BGroup>();
-        float* Xp = X32.as<float>();
-        float* Vp = V32.as<float>();
-        int* smaxp = d_smax.as<int>();
-        int* statep = d_state.as<int>();
-        GridBar* barp = d_bar.as<GridBar>();
-        void* args[] = {(void*)&gp,   (void*)&ng,    (void*)&bpairs, (void*)&max_rounds, (void*)&Xp,   (void*)&Vp,
-                        (void*)&smaxp, (void*)&statep, (void*)&barp,  (void*)&errp,       (void*)&stride, (void*)&frop};
-        {
-            KScope ks("svd_jacobi_f32", s);
-            CUDA_CHECK(cudaLaunchCooperativeKernel((void*)block_jacobi_f32, dim3(grid), dim3(threads), args, smem, s));
-        }
-        int st[2];
-        CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
-        CUDA_CHECK(cudaStreamSynchronize(s));   // bookkeeping buffers are freed on scope exit
-        R->rounds32 = st[1];
-        if (std::getenv("TNH_DEBUG"))
-            std::fprintf(stderr, "svd: float32 block Jacobi %d rounds (max %d, per sweep %d, grid %d, b %d)\n", st[1],
-                         max_rounds, rmax, grid, bmax);
-    }
+    R->rounds32 = run_block_jacobi(ctx, bg, d_bg, X32.as<float>(), V32.as<float>(), frop, bmax, stride, "");
     // ---- rank the float32 singular values, pick the candidates
     std::vector<ColSet> cs32(ng);
     for (int g = 0, c0 = 0; g < ng; ++g) {
@@ -915,16 +909,31 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     CUDA_CHECK(cudaMemcpyAsync(h_pos.data(), pos.p, (size_t)ntot * 4, cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));
     check_device_flag(ctx);
-    // candidates: at least max(maxdim, mindim) + 32, and every column whose
-    // float32 singular value is within 1e-4 of the largest. Restricting the
-    // float64 polish to a subspace biases sigma_i^2 by at most
+    // candidates: the kept count that the float32 singular values predict
+    // (cutoff and maxdim rule with the exact float64 total) plus a margin of
+    // 16 + 1/8, and every column whose float32 singular value is within 1e-4
+    // of the largest. The float64 truncation below needs the candidates only:
+    // its discarded weight is the exact total minus the kept sum. Restricting
+    // the float64 polish to a subspace biases sigma_i^2 by at most
     // sigma_excluded^2 sin^2(angle) (angle ~ float32 accuracy), so excluded
     // columns below 1e-4 sigma_max shift no sigma^2 by more than ~1e-20
     // sigma_max^2.
-    std::vector<double> h_sig32(ntot);
+    std::vector<double> h_sig32(ntot), h_fro2(ng);
     CUDA_CHECK(cudaMemcpy(h_sig32.data(), sig32.p, (size_t)ntot * 8, cudaMemcpyDeviceToHost));
+    CUDA_CHECK(cudaMemcpy(h_fro2.data(), d_fro2.p, (size_t)ng * 8, cudaMemcpyDeviceToHost));
     const double smax = ntot ? h_sig32[h_order[0]] : 0.0;
-    int ncand = std::min(ntot, std::max(maxdim, mindim) + 32);
+    double fro_total = 0.0;
+    for (double f : h_fro2) fro_total += f;
+    int k32 = ntot;
+    if (fro_total > 0.0) {
+        double pre = 0.0;
+        for (int k = 0; k <= ntot; ++k) {
+            if ((fro_total - pre) / fro_total <= cutoff) { k32 = k; break; }
+            if (k < ntot) pre += h_sig32[h_order[k]] * h_sig32[h_order[k]];
+        }
+    }
+    k32 = std::min(std::max(k32, std::max(mindim, 1)), maxdim);
+    int ncand = std::min(ntot, k32 + 16 + k32 / 8);
     while (ncand < ntot && h_sig32[h_order[ncand]] >= 1e-4 * smax) ++ncand;
     std::vector<std::vector<int>> cand(ng);
     for (int k = 0; k < ncand; ++k) cand[h_gid[h_order[k]]].push_back(h_pos[h_order[k]]);
@@ -967,12 +976,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         J.x_off = yo;
         J.len = R->len[g];
         J.n = k;
-        J.rounds = std::max(1, k + (k & 1) - 1);
-        J.pair0 = jpairs;
         J.grp = g;
-        jpairs += (k + 1) / 2;
-        R->flops64_round += ((k + 1) / 2) * 12.0 * R->len[g];
-        jrmax = std::max(jrmax, J.rounds);
         jg.push_back(J);
         vco += (int64_t)R->n[g] * k;
         yo += (int64_t)R->len[g] * k;
@@ -991,34 +995,34 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         // of X V32 differ from those of X at first order in that error:
         // re-orthonormalise the candidate columns in float64 by two
         // Newton-Schulz steps Vc <- Vc (3 I - Vc^T Vc) / 2 (quadratic).
-        {
-            std::vector<SGemm> g1, g2;
-            std::vector<NsSet> ns;
-            int64_t go = 0;
-            int t1 = 0, t2 = 0;
-            for (const CandSet& c : csets) {
-                SGemm a{};   // G = Vc^T Vc (k x k, row-major)
-                a.M = c.k; a.N = c.k; a.K = c.n;
-                a.a = c.c_off; a.ars = c.n; a.acs = 1;
-                a.b = c.c_off; a.brs = 1; a.bcs = c.n;
-                a.c = go; a.crs = c.k; a.ccs = 1;
-                a.nt = (c.k + 63) / 64; a.tile0 = t1;
-                t1 += ((c.k + 63) / 64) * a.nt;
-                g1.push_back(a);
-                SGemm b{};   // Vc' = Vc T (n x k, column-major)
-                b.M = c.n; b.N = c.k; b.K = c.k;
-                b.a = c.c_off; b.ars = 1; b.acs = c.n;
-                b.b = go; b.brs = c.k; b.bcs = 1;
-                b.c = c.c_off; b.crs = 1; b.ccs = c.n;
-                b.nt = (c.k + 63) / 64; b.tile0 = t2;
-                t2 += ((c.n + 63) / 64) * b.nt;
-                g2.push_back(b);
-                ns.push_back(NsSet{go, c.k});
-                go += (int64_t)c.k * c.k;
-            }
-            DevBuf Gb((size_t)std::max<int64_t>(go, 1) * 8), Vc2((size_t)std::max<int64_t>(vco, 1) * 8);
-            DevBuf d_g1 = upload(g1, s), d_g2 = upload(g2, s), d_ns = upload(ns, s);
-            for (int it = 0; it < 2; ++it) {
+        std::vector<SGemm> g1, g2;
+        std::vector<NsSet> ns;
+        int64_t go = 0;
+        int t1 = 0, t2 = 0;
+        for (const CandSet& c : csets) {
+            SGemm a{};   // G = Vc^T Vc (k x k, row-major)
+            a.M = c.k; a.N = c.k; a.K = c.n;
+            a.a = c.c_off; a.ars = c.n; a.acs = 1;
+            a.b = c.c_off; a.brs = 1; a.bcs = c.n;
+            a.c = go; a.crs = c.k; a.ccs = 1;
+            a.nt = (c.k + 63) / 64; a.tile0 = t1;
+            t1 += ((c.k + 63) / 64) * a.nt;
+            g1.push_back(a);
+            SGemm b{};   // Vc' = Vc T (n x k, column-major)
+            b.M = c.n; b.N = c.k; b.K = c.k;
+            b.a = c.c_off; b.ars = 1; b.acs = c.n;
+            b.b = go; b.brs = c.k; b.bcs = 1;
+            b.c = c.c_off; b.crs = 1; b.ccs = c.n;
+            b.nt = (c.k + 63) / 64; b.tile0 = t2;
+            t2 += ((c.n + 63) / 64) * b.nt;
+            g2.push_back(b);
+            ns.push_back(NsSet{go, c.k});
+            go += (int64_t)c.k * c.k;
+        }
+        DevBuf Gb((size_t)std::max<int64_t>(go, 1) * 8), Vc2((size_t)std::max<int64_t>(vco, 1) * 8);
+        DevBuf d_g1 = upload(g1, s), d_g2 = upload(g2, s), d_ns = upload(ns, s);
+        auto newton_schulz = [&](int iters) {
+            for (int it = 0; it < iters; ++it) {
                 {
                     KScope ks("svd_sgemm_f64", s);
                     sgemm_f64<<<t1, 256, 0, s>>>(d_g1.as<SGemm>(), (int)g1.size(), Vc.as<double>(), Vc.as<double>(),
@@ -1035,23 +1039,45 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
                 }
                 std::swap(Vc, Vc2);
             }
-            {
-                KScope ks("svd_sgemm_f64", s);
-                sgemm_f64<<<tiles, 256, 0, s>>>(d_gm.as<SGemm>(), (int)gemms.size(), R->X64.as<double>(),
-                                                 Vc.as<double>(), R->Y.as<double>());
-            }
-            CUDA_CHECK(cudaStreamSynchronize(s));   // temporaries are freed on scope exit
-        }
+        };
+        auto form_y = [&] {
+            KScope ks("svd_sgemm_f64", s);
+            sgemm_f64<<<tiles, 256, 0, s>>>(d_gm.as<SGemm>(), (int)gemms.size(), R->X64.as<double>(), Vc.as<double>(),
+                                             R->Y.as<double>());
+        };
+        newton_schulz(2);
+        form_y();
+        CUDA_CHECK(cudaStreamSynchronize(s));   // temporaries are freed on scope exit
     }
     // ---- stage b: float64 polish
     {
+        // blocks of kJ64MaxB columns when the columns are short (a round then
+        // carries 28 rotations for one grid barrier), single column pairs when
+        // they are long (the float64 work of a round would dominate)
+        int lmax = 1;
+        for (const JGroup& J : jg) lmax = std::max(lmax, J.len);
+        int b64 = lmax <= 256 ? kJ64MaxB : 1;
+        while (b64 > 1 && (size_t)2 * b64 * lmax * 8 > 200 * 1024) b64 >>= 1;
+        for (JGroup& J : jg) {
+            J.b = b64;
+            const int nb = (J.n + b64 - 1) / b64;
+            J.nblk = std::max(2, nb + (nb & 1));
+            J.rounds = J.nblk - 1;
+            J.pair0 = jpairs;
+            jpairs += J.nblk / 2;
+            R->flops64_round += (J.nblk / 2) * (2.0 * b64 - 1.0) * b64 * 12.0 * J.len;
+            jrmax = std::max(jrmax, J.rounds);
+        }
         const int njg = (int)jg.size();
         DevBuf d_jg = upload(jg, s);
         DevBuf d_smax((size_t)3 * njg * 4), d_state(16), d_bar(16);
         reset_state(d_smax, d_state, d_bar, njg, s);
-        const int threads = kJ64Threads;   // one column pair per CTA spreads float64 work over the SMs
+        const int threads = 32 * b64;
+        const size_t smem64 = (size_t)2 * b64 * lmax * 8;
+        CUDA_CHECK(cudaFuncSetAttribute(jacobi_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
         int bpsm = 0;
-        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, jacobi_f64, threads, 0));
+        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, jacobi_f64, threads, smem64));
+        TNH_REQUIRE(bpsm >= 1, TNH_ERR_CUDA, "svd: float64 block Jacobi does not fit on an SM");
         int want = jpairs;
         int grid = std::max(1, std::min(want, std::max(1, bpsm) * ctx->num_sms));
         int max_rounds = 30 * jrmax + 8;
@@ -1060,20 +1086,38 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         int* smaxp = d_smax.as<int>();
         int* statep = d_state.as<int>();
         GridBar* barp = d_bar.as<GridBar>();
+        const bool dbg = std::getenv("TNH_DEBUG") != nullptr;
+        DevBuf d_hist(dbg ? (size_t)njg * 48 * 4 : 16);
+        if (dbg) CUDA_CHECK(cudaMemsetAsync(d_hist.p, 0, (size_t)njg * 48 * 4, s));
+        int* histp = dbg ? d_hist.as<int>() : nullptr;
+        int stride64 = lmax;
         void* args[] = {(void*)&gp,    (void*)&njg,   (void*)&jpairs, (void*)&max_rounds, (void*)&Yp,
-                        (void*)&smaxp, (void*)&statep, (void*)&barp,  (void*)&errp,       (void*)&frop};
+                        (void*)&smaxp, (void*)&statep, (void*)&barp,  (void*)&errp,       (void*)&frop,
+                        (void*)&histp, (void*)&stride64};
         {
             KScope ks("svd_jacobi_f64", s);
-            CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_f64, dim3(grid), dim3(threads), args, 0, s));
+            CUDA_CHECK(cudaLaunchCooperativeKernel((void*)jacobi_f64, dim3(grid), dim3(threads), args, smem64, s));
         }
         int st[2];
         CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
         CUDA_CHECK(cudaStreamSynchronize(s));
         check_device_flag(ctx);
         R->rounds64 = st[1];
-        if (std::getenv("TNH_DEBUG"))
+        if (dbg) {
             std::fprintf(stderr, "svd: float64 Jacobi %d rounds (max %d, per sweep %d, grid %d)\n", st[1], max_rounds,
                          jrmax, grid);
+            std::vector<int> h((size_t)njg * 48);
+            CUDA_CHECK(cudaMemcpy(h.data(), d_hist.p, h.size() * 4, cudaMemcpyDeviceToHost));
+            int big = 0;
+            for (int g = 0; g < njg; ++g) if (jg[g].n > jg[big].n) big = g;
+            std::fprintf(stderr, "svd: float64 history, group %d (%d x %d):", big, jg[big].len, jg[big].n);
+            for (int w = 0; w < 48 && w * jg[big].rounds < st[1]; ++w) {
+                float v;
+                std::memcpy(&v, &h[(size_t)big * 48 + w], 4);
+                std::fprintf(stderr, " %.1e", (double)v);
+            }
+            std::fprintf(stderr, "\n");
+        }
         if (st[1] >= max_rounds) {
             // report the group that kept rotating: its size and largest
             // relative off-diagonal in the last sweep
