@@ -12,12 +12,14 @@
 //       inner Jacobi sweep over its 2b columns. One cooperative launch
 //       works on all groups, with a bounded grid barrier between rounds.
 //       This gives V32 with columns orthogonal to float32 accuracy.
-//    b. The candidate columns (the largest float32 singular values: maxdim
-//       plus a margin, and all within 1e-4 of the largest) are
-//       re-orthonormalised and re-formed in float64, Y = X V32[:, cand], and
-//       polished by float64 one-sided block Jacobi (blocks of 4 columns), which
-//       converges in one or two sweeps because Y is already nearly
-//       orthogonal.
+//    b. The candidate columns (the largest float32 singular values: the kept
+//       count that they predict plus a margin, and all within 1e-4 of the
+//       largest) are re-orthonormalised and re-formed in float64,
+//       Y = X V32[:, cand], and polished by float64 one-sided block Jacobi
+//       (blocks of 4 columns when the columns are at most 256 long, column
+//       pairs otherwise). Y is already nearly orthogonal in its leading
+//       columns; the sweeps left are spent on the small singular values that
+//       float32 could not resolve.
 //    c. The float64 singular values sigma_j = |Y_j| are pooled, ranked
 //       (sigma desc, group, position) and the cutoff/maxdim rule of Sec. 5
 //       picks the kept count (values below 1e-8 of the norm count as zero);
