@@ -360,7 +360,57 @@ def product_mps_vectors(site_index, vecs):
     return A
 
 
-def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None):
+# ------------------------------------- sums of MPOs and excited states
+def overlap_left(LO, P, A):
+    """LO'[pb, b] = sum LO[pa, a] P[pa, s, pb] A[a, s, b].
+
+    The overlap of a previous state P with the current MPS A over the sites
+    left of a bond (Sec. 7.2, excited states). Real data: the bra is P with
+    its arrows reversed.
+    """
+    LO = LO.relabel(["pa", "a"])
+    Pb = dag(P).relabel(["pa", "s", "pb"])
+    Ak = A.relabel(["a", "s", "b"])
+    return contract(contract(LO, Pb), Ak, out_labels=["pb", "b"])
+
+
+def overlap_right(RO, P, A):
+    """RO'[pa, a] = sum P[pa, s, pb] A[a, s, b] RO[pb, b]."""
+    RO = RO.relabel(["pb", "b"])
+    Pb = dag(P).relabel(["pa", "s", "pb"])
+    Ak = A.relabel(["a", "s", "b"])
+    return contract(contract(Pb, RO), Ak, out_labels=["pa", "a"])
+
+
+def overlap_boundaries(P, A):
+    """LO_0 and RO_N: 1 on the boundary links (both of dimension 1), or no
+    block at all when the two states carry different total charge."""
+    N = len(A)
+    LO = BlockTensor.zeros([P[0].inds[0], A[0].inds[0].dag()])
+    RO = BlockTensor.zeros([P[N - 1].inds[2], A[N - 1].inds[2].dag()])
+    for T in (LO, RO):
+        for v in T.blocks.values():
+            v[0, 0] = 1.0
+    return LO, RO
+
+
+def projected_state(LO, P1, P2, RO):
+    """phi[a, s1, s2, b] = sum LO[pa, a] P1[pa, s1, pc] P2[pc, s2, pb] RO[pb, b].
+
+    The previous state P written in the two-site basis of the current MPS
+    (left-orthogonal left of the bond, right-orthogonal right of it): the
+    vector whose projector, times the weight, is added to H_eff. The
+    contraction gives the bra; with real data its arrow-reversed copy is the
+    ket in theta's layout.
+    """
+    t = contract(LO.relabel(["pa", "a"]), dag(P1).relabel(["pa", "s1", "pc"]))
+    t = contract(t, dag(P2).relabel(["pc", "s2", "pb"]))
+    t = contract(t, RO.relabel(["pb", "b"]), out_labels=["a", "s1", "s2", "b"])
+    return dag(t)
+
+
+def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None,
+         ortho=(), weight=1.0):
     """Two-site DMRG (Sec. 7.2) with the schedule ``sweeps``.
 
     ``sweeps`` is a list of (maxdim, cutoff), one entry per sweep. The MPS
@@ -372,27 +422,50 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None):
     A_{j+1} going right, U S -> A_j and V -> A_{j+1} going left) and updates
     one environment. No noise or subspace expansion. The returned energy is
     the eigenvalue at the last bond of the last sweep.
+
+    ``mpo`` may be a list of MPOs: H is their sum (Sec. 7.2), kept as
+    separate terms, each with its own environments, and H_eff . x is the
+    sum of the terms' products. ``ortho`` lists previous states (MPS): the
+    projector onto each, times ``weight``, is added to H (Sec. 7.2, excited
+    states), so H_eff . x gains weight * phi <phi, x> per previous state,
+    phi being that state in the current two-site basis.
     """
-    W = mpo.W
-    N = len(W)
+    mpos = list(mpo) if isinstance(mpo, (list, tuple)) else [mpo]
+    N = len(mpos[0].W)
     A = [a.copy() for a in mps]
-    Ls = [None] * (N + 1)
-    Rs = [None] * (N + 1)
-    Ls[0] = left_boundary(A[0], W[0], mpo.start)
-    Rs[N] = right_boundary(A[N - 1], W[N - 1], mpo.done)
-    for j in range(N - 1, 1, -1):
-        Rs[j] = env_right(Rs[j + 1], A[j], W[j])
+    T = len(mpos)
+    Ls = [[None] * (N + 1) for _ in range(T)]
+    Rs = [[None] * (N + 1) for _ in range(T)]
+    for t, m in enumerate(mpos):
+        Ls[t][0] = left_boundary(A[0], m.W[0], m.start)
+        Rs[t][N] = right_boundary(A[N - 1], m.W[N - 1], m.done)
+        for j in range(N - 1, 1, -1):
+            Rs[t][j] = env_right(Rs[t][j + 1], A[j], m.W[j])
+    P = [list(p) for p in ortho]
+    LO = [[None] * (N + 1) for _ in P]
+    RO = [[None] * (N + 1) for _ in P]
+    for i, p in enumerate(P):
+        LO[i][0], RO[i][N] = overlap_boundaries(p, A)
+        for j in range(N - 1, 1, -1):
+            RO[i][j] = overlap_right(RO[i][j + 1], p[j], A[j])
     energy = None
     stats = []
     for sw, (maxdim, cutoff) in enumerate(sweeps):
         maxerr, nmv = 0.0, 0
         for j, direction in [(j, +1) for j in range(N - 1)] + \
                             [(j, -1) for j in range(N - 2, -1, -1)]:
-            L, R = Ls[j], Rs[j + 2]
             th = theta(A[j], A[j + 1])
+            phis = [projected_state(LO[i][j], p[j], p[j + 1], RO[i][j + 2])
+                    for i, p in enumerate(P)]
 
-            def apply(x, L=L, R=R, j=j):
-                return heff_apply(L, W[j], W[j + 1], R, x)
+            def apply(x, j=j, phis=phis):
+                y = None
+                for t, m in enumerate(mpos):
+                    yt = heff_apply(Ls[t][j], m.W[j], m.W[j + 1], Rs[t][j + 2], x)
+                    y = yt if y is None else y.axpy(1.0, yt)
+                for phi in phis:
+                    y = y.axpy(weight * phi.vdot(x), phi)
+                return y
 
             energy, th, res, k = lanczos(apply, th, krylov_dim, tol)
             nmv += k
@@ -401,11 +474,17 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None):
             if direction > 0:
                 A[j] = U
                 A[j + 1] = scale_link(V, S, 0)
-                Ls[j + 1] = env_left(Ls[j], A[j], W[j])
+                for t, m in enumerate(mpos):
+                    Ls[t][j + 1] = env_left(Ls[t][j], A[j], m.W[j])
+                for i, p in enumerate(P):
+                    LO[i][j + 1] = overlap_left(LO[i][j], p[j], A[j])
             else:
                 A[j] = scale_link(U, S, 2)
                 A[j + 1] = V
-                Rs[j + 1] = env_right(Rs[j + 2], A[j + 1], W[j + 1])
+                for t, m in enumerate(mpos):
+                    Rs[t][j + 1] = env_right(Rs[t][j + 2], A[j + 1], m.W[j + 1])
+                for i, p in enumerate(P):
+                    RO[i][j + 1] = overlap_right(RO[i][j + 2], p[j + 1], A[j + 1])
         st = dict(sweep=sw, energy=energy, maxdim=max(a.inds[2].dim for a in A),
                   truncerr=maxerr, matvecs=nmv)
         stats.append(st)
@@ -414,15 +493,26 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None):
     return energy, A, stats
 
 
+def mps_overlap(P, A):
+    """<P|A> of two MPS (real data), by a left-to-right overlap sweep."""
+    LO, _ = overlap_boundaries(P, A)
+    for j in range(len(A)):
+        LO = overlap_left(LO, P[j], A[j])
+    return sum(float(np.sum(v)) for v in LO.blocks.values())
+
+
 def mps_expectation(mpo, A):
-    """<psi|H|psi>/<psi|psi> by full left-to-right environment sweeps."""
-    W = mpo.W
-    N = len(W)
-    L = left_boundary(A[0], W[0], mpo.start)
-    for j in range(N):
-        L = env_left(L, A[j], W[j])
-    Rb = right_boundary(A[N - 1], W[N - 1], mpo.done)
-    num = L.vdot(Rb)
+    """<psi|H|psi>/<psi|psi> by full left-to-right environment sweeps
+    (``mpo`` may be a list of MPOs: the sum of their expectations)."""
+    num = 0.0
+    for m in (list(mpo) if isinstance(mpo, (list, tuple)) else [mpo]):
+        W = m.W
+        N = len(W)
+        L = left_boundary(A[0], W[0], m.start)
+        for j in range(N):
+            L = env_left(L, A[j], W[j])
+        Rb = right_boundary(A[N - 1], W[N - 1], m.done)
+        num += L.vdot(Rb)
     a0 = A[0].inds[0]
     E = BlockTensor.zeros([a0.dag(), a0])
     for v in E.blocks.values():

@@ -297,3 +297,111 @@ def test_dmrg_is_variational_and_truncation_bounded():
                             models.SPIN_QN, (0,))
     assert E >= e_ed - 1e-10
     assert E - e_ed <= 1e-4 * abs(e_ed)
+
+
+# ------------------------------------------- sums of MPOs, excited states
+def full_state(A, j=None, th=None):
+    """The d^N vector of an MPS by dense contraction; with ``j`` and ``th``
+    the pair (A[j], A[j+1]) is replaced by the two-site tensor th."""
+    mats = [T.to_dense() for T in A]
+    if j is not None:
+        t = th.to_dense()
+        mats = mats[:j] + [t.reshape(t.shape[0], -1, t.shape[3])] + mats[j + 2:]
+    v = mats[0][0]                              # (s, b)
+    for t in mats[1:]:
+        v = np.einsum("xa,asb->xsb", v, t).reshape(-1, t.shape[2])
+    return v[:, 0]
+
+
+def test_mps_overlap_and_projected_state_match_full_vectors():
+    # random dense MPS P and A; bond (2, 3) of A holds a random theta
+    N, j = 6, 2
+    mpo = dense_site_mpo(models.heisenberg_mpo(N))
+    P = random_mps(mpo, [2, 4, 5, 4, 2], 21)
+    A = random_mps(mpo, [2, 3, 4, 3, 2], 22)
+    ref = float(full_state(P) @ full_state(A))
+    assert abs(D.mps_overlap(P, A) - ref) < 1e-12 * max(1.0, abs(ref))
+    LO, RO = D.overlap_boundaries(P, A)
+    for k in range(j):
+        LO = D.overlap_left(LO, P[k], A[k])
+    for k in range(N - 1, j + 1, -1):
+        RO = D.overlap_right(RO, P[k], A[k])
+    phi = D.projected_state(LO, P[j], P[j + 1], RO)
+    th = D.theta(A[j], A[j + 1])
+    assert abs(phi.vdot(th) - ref) < 1e-12 * max(1.0, abs(ref))
+    # <phi, theta2> = <P|psi(theta2)> for any theta2 in the same space
+    th2 = D.from_vector(synth.gaussian(23, (D.to_vector(th).size,)), th)
+    ref2 = float(full_state(P) @ full_state(A, j, th2))
+    assert abs(phi.vdot(th2) - ref2) < 1e-12 * max(1.0, abs(ref2))
+
+
+def test_dmrg_sum_of_mpos_majumdar_ghosh():
+    # H = H_J1 + H_J2 as two MPOs; J2/J1 = 1/2 has E0 = -3N/8 exactly
+    N = 10
+    h1 = models.heisenberg_like_mpo(N, [(i, i + 1, 1.0) for i in range(N - 1)])
+    h2 = models.heisenberg_like_mpo(N, [(i, i + 2, 0.5) for i in range(N - 2)])
+    A = D.product_mps_basis(h1.site_index, [0, 1] * (N // 2), 1)
+    E, A, st = _dmrg([h1, h2], A, [(8, 1e-12), (32, 1e-12), (64, 1e-13), (64, 1e-13)])
+    assert abs(E + 3 * N / 8) < 1e-10 * 3 * N / 8
+    assert abs(D.mps_expectation([h1, h2], A) - E) < 1e-9
+    # the ground state is the dimer product of singlets, on which every
+    # next-nearest-neighbour S_i . S_(i+2) has zero expectation (the two
+    # spins sit in different singlets)
+    assert abs(D.mps_expectation(h2, A)) < 1e-9
+
+
+def test_dmrg_sum_of_mpos_tfim_free_fermion():
+    from test_oracle_models import tfim_closed_form
+    N, J, h = 10, 1.0, 1.3
+    terms = [models.tfim_mpo(N, J, 0.0), models.tfim_mpo(N, 0.0, h)]
+    A = D.product_mps_vectors(terms[0].site_index, synth.product_spinors(3, N, 2))
+    E, A, st = _dmrg(terms, A, [(8, 1e-12), (24, 1e-13), (32, 1e-13)])
+    assert abs(E - tfim_closed_form(N, J, h)) < 1e-10 * abs(E)
+
+
+def tfim_levels(N, J, h):
+    """Lowest levels of the open TFIM: E0 = -sum eps_k, E0 + 2 eps_k for one
+    excited Jordan-Wigner mode (eps_k = singular values of the bidiagonal)."""
+    M = np.diag([h] * N) + np.diag([J] * (N - 1), 1)
+    eps = np.sort(np.linalg.svd(M, compute_uv=False))
+    E0 = -float(np.sum(eps))
+    return E0, E0 + 2 * eps[0], E0 + 2 * eps[1]
+
+
+def test_tfim_levels_match_ed():
+    N, J, h = 6, 1.0, 1.5
+    e = ed.ground_energy(N, 2, models.tfim_terms(N, J, h), k=3)
+    np.testing.assert_allclose(e, tfim_levels(N, J, h), rtol=0, atol=1e-12)
+
+
+def test_dmrg_excited_states_tfim():
+    N, J, h = 8, 1.0, 1.5
+    E0x, E1x, E2x = tfim_levels(N, J, h)
+    mpo = models.tfim_mpo(N, J, h)
+    sweeps = [(8, 1e-13), (32, 1e-14), (32, 1e-14), (32, 1e-14)]
+    start = lambda seed: D.product_mps_vectors(mpo.site_index, synth.product_spinors(seed, N, 2))
+    E0, A0, _ = _dmrg(mpo, start(4), sweeps)
+    E1, A1, _ = _dmrg(mpo, start(5), sweeps + [(32, 1e-14)] * 2, ortho=[A0], weight=20.0)
+    E2, A2, _ = _dmrg(mpo, start(6), sweeps + [(32, 1e-14)] * 2, ortho=[A0, A1], weight=20.0)
+    assert abs(E0 - E0x) < 1e-10 * abs(E0x)
+    assert abs(E1 - E1x) < 1e-9 * abs(E1x)
+    assert abs(E2 - E2x) < 1e-9 * abs(E2x)
+    assert abs(D.mps_overlap(A0, A1)) < 1e-6
+    assert abs(D.mps_overlap(A0, A2)) < 1e-6 and abs(D.mps_overlap(A1, A2)) < 1e-6
+    # without the projector the same start falls back to the ground state
+    Eg, _, _ = _dmrg(mpo, start(5), sweeps)
+    assert abs(Eg - E0x) < 1e-9 * abs(E0x)
+
+
+def test_dmrg_excited_state_heisenberg_qn_vs_ed():
+    N = 8
+    mpo = models.heisenberg_mpo(N)
+    e_ed = ed.ground_energy(N, 2, models.spin_pair_terms(models.heisenberg_pairs(N)),
+                            models.SPIN_QN, (0,), k=2)
+    sweeps = [(8, 1e-13), (16, 1e-14), (16, 1e-14), (16, 1e-14), (16, 1e-14), (16, 1e-14)]
+    E0, A0, _ = _dmrg(mpo, D.product_mps_basis(mpo.site_index, [0, 1] * (N // 2), 1), sweeps)
+    E1, A1, _ = _dmrg(mpo, D.product_mps_basis(mpo.site_index, [1, 0] * (N // 2), 1), sweeps,
+                      ortho=[A0], weight=5.0)
+    assert abs(E0 - e_ed[0]) < 1e-10 * abs(e_ed[0])
+    assert abs(E1 - e_ed[1]) < 1e-9 * abs(e_ed[1])
+    assert abs(D.mps_overlap(A0, A1)) < 1e-6
