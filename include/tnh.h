@@ -191,6 +191,21 @@ tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor* A, const t
 tnh_status tnh_heff_plan(tnh_ctx* ctx, const tnh_tensor* L, const tnh_tensor* W1,
                          const tnh_tensor* W2, const tnh_tensor* R,
                          const tnh_tensor* psi, tnh_precision prec, tnh_heff** plan);
+/* H_eff of a sum of MPOs, H = sum_t H_t (Sec. 7.2): nterm environments and
+ * MPO tensors L[t], W1[t], W2[t], R[t] as for tnh_heff_plan, every term with
+ * its own w, w1, w2 link indices (the a, s and b indices agree). The plan is
+ * the one of the terms' direct sum: the w links are joined sector by sector,
+ * term after term, so every grouped GEMM covers all terms and S4 sums them
+ * along its K dimension. Same ownership as tnh_heff_plan; TNH_ERR_SHAPE if
+ * the terms' shared indices differ. */
+tnh_status tnh_heff_plan_sum(tnh_ctx* ctx, int32_t nterm, const tnh_tensor* L, const tnh_tensor* W1,
+                             const tnh_tensor* W2, const tnh_tensor* R, const tnh_tensor* psi,
+                             tnh_precision prec, tnh_heff** plan);
+/* Projectors added to the plan's product (excited-state DMRG, Sec. 7.2):
+ * from now on every application also adds weight * phi_i <phi_i, x> for the
+ * k vectors phi (DEVICE float64 [k][n] in the psi layout, copied; k = 0
+ * removes them), in float64 with deterministic reductions. k <= 256. */
+tnh_status tnh_heff_set_projectors(tnh_heff* plan, int32_t k, const double* phi, double weight);
 /* y = H_eff . x; x and y are DEVICE float64 vectors in the psi layout of the
  * plan (they must not alias). Asynchronous on the plan's context stream. */
 tnh_status tnh_heff_apply(tnh_heff* plan, const double* x, double* y);
@@ -304,6 +319,42 @@ typedef struct {
 tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, int64_t start,
                     int64_t done, const tnh_tensor* mps, const tnh_sweep_params* p,
                     double* energy, tnh_sweep_stat* stats);
+
+/* DMRG beyond one MPO (Sec. 7.2):
+ * - H is the sum of nterm MPOs, run as if summed (each term keeps its own
+ *   boundary states; the driver works on their direct sum, see
+ *   tnh_heff_plan_sum);
+ * - northo previous states (MPS of N sites each, e.g. read back with
+ *   tnh_dmrg_mps_get) each add weight * |P_i><P_i| to H, so the run finds
+ *   the lowest state above them (excited states). Their data is read during
+ *   the call only. The reported energy includes the penalty terms. */
+typedef struct {
+    int32_t nterm;              /* MPOs summed, >= 1 */
+    const tnh_tensor* mpo;      /* [nterm * N]: term t, site j at t * N + j */
+    const int64_t* start;       /* [nterm] left boundary link state of each term */
+    const int64_t* done;        /* [nterm] right boundary link state of each term */
+    int32_t northo;             /* previous states, >= 0 */
+    const tnh_tensor* ortho;    /* [northo * N]: state i, site j at i * N + j */
+    double weight;              /* energy penalty of every previous state */
+} tnh_dmrg_problem;
+tnh_status tnh_dmrg_ex(tnh_ctx* ctx, int32_t N, const tnh_dmrg_problem* prob,
+                       const tnh_tensor* mps, const tnh_sweep_params* p, double* energy,
+                       tnh_sweep_stat* stats);
+
+/* The MPS left by the last tnh_dmrg / tnh_dmrg_ex on this context. After a
+ * full sweep it is right-orthogonal from site 1 on, so it can start another
+ * run as it is (checkpoint and resume). N = 0 before any run.
+ * tnh_dmrg_mps_link: link j in 0..N (link j is the left index of site j,
+ * link N the right index of site N-1): sector count, nq, QNs [nsect * nq]
+ * and sector dims [nsect] (nq, qn and sect_dim may be NULL, e.g. to learn
+ * nsect first). tnh_dmrg_mps_get copies site j into A (DEVICE data), whose
+ * indices must be [link j (Out), site (Out), link j+1 (In)] with these
+ * sectors; blocks of A that are not stored are zeroed, a stored block that A
+ * lacks is TNH_ERR_SHAPE. Synchronises the stream. */
+tnh_status tnh_dmrg_mps_size(tnh_ctx* ctx, int32_t* N);
+tnh_status tnh_dmrg_mps_link(tnh_ctx* ctx, int32_t j, int32_t* nsect, int32_t* nq, int32_t* qn,
+                             int32_t* sect_dim);
+tnh_status tnh_dmrg_mps_get(tnh_ctx* ctx, int32_t j, tnh_tensor* A);
 
 #ifdef __cplusplus
 }

@@ -164,6 +164,69 @@ Layout make_layout(const std::vector<Index>& inds, const std::vector<int>& flux)
     return L;
 }
 
+Layout direct_sum(const std::vector<Layout>& T, const std::vector<int>& cat, DevBuf& buf, cudaStream_t s) {
+    TNH_REQUIRE(!T.empty(), TNH_ERR_ARG, "direct sum: no terms");
+    const int r = T[0].rank();
+    std::vector<char> joined(r, 0);
+    for (int i : cat) {
+        TNH_REQUIRE(i >= 0 && i < r, TNH_ERR_ARG, "direct sum: index position %d out of range", i);
+        joined[i] = 1;
+    }
+    Layout S;
+    S.inds = T[0].inds;
+    for (size_t t = 1; t < T.size(); ++t) {
+        TNH_REQUIRE(T[t].rank() == r, TNH_ERR_SHAPE, "direct sum: term %zu has rank %d, not %d", t, T[t].rank(), r);
+        for (int i = 0; i < r; ++i) {
+            const Index& a = T[t].inds[i];
+            Index& d = S.inds[i];
+            TNH_REQUIRE(a.arrow == d.arrow, TNH_ERR_ARROW, "direct sum: term %zu index %d has another arrow", t, i);
+            TNH_REQUIRE(a.nq == d.nq, TNH_ERR_SHAPE, "direct sum: term %zu index %d has another nq", t, i);
+            if (joined[i]) {
+                d.nsect += a.nsect;
+                d.qn.insert(d.qn.end(), a.qn.begin(), a.qn.end());
+                d.dim.insert(d.dim.end(), a.dim.begin(), a.dim.end());
+            } else {
+                TNH_REQUIRE(a.same_space(T[0].inds[i]), TNH_ERR_SHAPE,
+                            "direct sum: term %zu index %d differs from term 0's", t, i);
+            }
+        }
+    }
+    for (auto& ix : S.inds) ix.finish();
+    S.flux = T[0].flux;
+    std::vector<int> shift(r, 0);
+    std::vector<int64_t> base(T.size(), 0);
+    int64_t total = 0;
+    bool have_flux = false;
+    for (size_t t = 0; t < T.size(); ++t) {
+        const Layout& L = T[t];
+        if (L.nblocks()) {
+            if (have_flux)
+                TNH_REQUIRE(L.flux == S.flux, TNH_ERR_FLUX, "direct sum: term %zu has another flux", t);
+            S.flux = L.flux;
+            have_flux = true;
+        }
+        base[t] = total;
+        for (int b = 0; b < L.nblocks(); ++b) {
+            std::vector<int> k = L.key(b);
+            for (int i = 0; i < r; ++i) k[i] += shift[i];
+            S.sect.insert(S.sect.end(), k.begin(), k.end());
+            S.off.push_back(total + L.off[b]);
+        }
+        total += L.size;
+        for (int i = 0; i < r; ++i)
+            if (joined[i]) shift[i] += L.inds[i].nsect;
+    }
+    S.size = total;
+    buf.alloc((size_t)std::max<int64_t>(total, 1) * sizeof(double));
+    for (size_t t = 0; t < T.size(); ++t)
+        if (T[t].size > 0 && T[t].data)
+            CUDA_CHECK(cudaMemcpyAsync(buf.as<double>() + base[t], T[t].data, (size_t)T[t].size * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+    S.data = buf.as<double>();
+    S.build_lookup();
+    return S;
+}
+
 void make_chunks(const std::vector<Piece>& pieces, std::vector<Chunk>& chunks, int per_chunk) {
     chunks.clear();
     for (int p = 0; p < (int)pieces.size(); ++p) {

@@ -10,6 +10,20 @@
 // the right-to-left pass in reverse (the paper does not define the
 // schedule; this is the usual one). The reported energy is the eigenvalue
 // at the last bond of the sweep.
+//
+// Sum of MPOs (Sec. 7.2): H = sum_t H_t is run as the direct sum of the
+// terms' MPOs. Every MPO link index gets the sectors of all terms in turn,
+// the site tensors are block diagonal (a block never joins two terms) and
+// the boundary environments select every term's start / done state. The
+// environments of all terms are then the sectors of one block-sparse
+// environment, one H_eff plan covers every term in each grouped launch, and
+// S4 sums the terms along its K dimension: the loop over terms is part of the
+// grouped GEMMs, with no block of the explicitly summed MPO formed.
+//
+// Excited states (Sec. 7.2): for every previous state P_i the driver keeps
+// overlap environments LO_i (sites left of the bond) and RO_i (right of
+// it); phi_i = LO_i P_i[j] P_i[j+1] RO_i is P_i in the current two-site
+// basis, and weight * phi_i <phi_i, x> is added to every H_eff . x.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -24,10 +38,7 @@ namespace tnh {
 
 namespace {
 
-struct DTensor {
-    Layout L;
-    DevBuf buf;
-};
+using DTensor = OwnedTensor;
 
 DTensor new_tensor(const std::vector<Index>& inds, const std::vector<int>& flux, cudaStream_t s) {
     DTensor t;
@@ -69,10 +80,297 @@ Layout relabel(Layout T, std::initializer_list<int64_t> labels) {
     return T;
 }
 
+Layout dagger(Layout T) {
+    for (auto& ix : T.inds) ix.arrow = -ix.arrow;
+    for (auto& f : T.flux) f = -f;
+    return T;
+}
+
 std::vector<int> fsum(const std::vector<int>& a, const std::vector<int>& b) {
     std::vector<int> r(a.size());
     for (size_t k = 0; k < a.size(); ++k) r[k] = a[k] + b[k];
     return r;
+}
+
+// out = A * B in float64 (labels of A, B and out decide the contraction)
+void contract64(Ctx* c, const Layout& A, const Layout& B, const Layout& out) {
+    auto P = plan_contract(A, B, out, c->stream);
+    Workspace ws;
+    run_contract(c, *P, A.data, B.data, out.data, TNH_FP64, ws);
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+}
+
+// ---- overlap environments of a previous state P with the MPS A (real data:
+// the bra is P with its arrows reversed). LO [p (Out), a (In)] covers the
+// sites left of a link, RO [p (In), a (Out)] the sites right of it.
+enum : int64_t { Opa = 1, Oa, Os, Opb, Ob, Os2, Opc };
+
+// LO' [pb, b] = sum LO[pa, a] P[pa, s, pb] A[a, s, b]
+DTensor overlap_left(Ctx* c, const Layout& LO, const Layout& P, const Layout& A) {
+    cudaStream_t s = c->stream;
+    Layout lo = relabel(LO, {Opa, Oa});
+    Layout pb = relabel(dagger(P), {Opa, Os, Opb});
+    Layout ak = relabel(A, {Oa, Os, Ob});
+    DTensor X = new_tensor({lo.inds[1], pb.inds[1], pb.inds[2]}, fsum(lo.flux, pb.flux), s);
+    X.L = relabel(X.L, {Oa, Os, Opb});
+    contract64(c, lo, pb, X.L);
+    DTensor out = new_tensor({pb.inds[2], A.inds[2]}, fsum(X.L.flux, A.flux), s);
+    out.L = relabel(out.L, {Opb, Ob});
+    contract64(c, X.L, ak, out.L);
+    return out;
+}
+
+// RO' [pa, a] = sum P[pa, s, pb] A[a, s, b] RO[pb, b]
+DTensor overlap_right(Ctx* c, const Layout& RO, const Layout& P, const Layout& A) {
+    cudaStream_t s = c->stream;
+    Layout ro = relabel(RO, {Opb, Ob});
+    Layout pb = relabel(dagger(P), {Opa, Os, Opb});
+    Layout ak = relabel(A, {Oa, Os, Ob});
+    DTensor Y = new_tensor({pb.inds[0], pb.inds[1], ro.inds[1]}, fsum(pb.flux, ro.flux), s);
+    Y.L = relabel(Y.L, {Opa, Os, Ob});
+    contract64(c, pb, ro, Y.L);
+    DTensor out = new_tensor({pb.inds[0], A.inds[0]}, fsum(Y.L.flux, A.flux), s);
+    out.L = relabel(out.L, {Opa, Oa});
+    contract64(c, Y.L, ak, out.L);
+    return out;
+}
+
+// phi[a, s1, s2, b] = sum LO[pa, a] P1[pa, s1, pc] P2[pc, s2, pb] RO[pb, b],
+// written into `out` (theta's layout). The contraction yields the bra, whose
+// arrow-reversed layout has the same blocks and offsets as theta's.
+void projected_state(Ctx* c, const Layout& LO, const Layout& P1, const Layout& P2, const Layout& RO,
+                     const Layout& theta, double* out) {
+    cudaStream_t s = c->stream;
+    Layout lo = relabel(LO, {Opa, Oa});
+    Layout p1 = relabel(dagger(P1), {Opa, Os, Opc});
+    Layout p2 = relabel(dagger(P2), {Opc, Os2, Opb});
+    Layout ro = relabel(RO, {Opb, Ob});
+    DTensor Y1 = new_tensor({lo.inds[1], p1.inds[1], p1.inds[2]}, fsum(lo.flux, p1.flux), s);
+    Y1.L = relabel(Y1.L, {Oa, Os, Opc});
+    contract64(c, lo, p1, Y1.L);
+    DTensor Y2 = new_tensor({Y1.L.inds[0], Y1.L.inds[1], p2.inds[1], p2.inds[2]}, fsum(Y1.L.flux, p2.flux), s);
+    Y2.L = relabel(Y2.L, {Oa, Os, Os2, Opb});
+    contract64(c, Y1.L, p2, Y2.L);
+    Layout bra = relabel(dagger(theta), {Oa, Os, Os2, Ob});
+    TNH_REQUIRE(bra.inds[0].same_space(Y2.L.inds[0]) && bra.inds[3].same_space(ro.inds[1]), TNH_ERR_SHAPE,
+                "dmrg: previous state and MPS disagree on a link");
+    bra.data = out;
+    CUDA_CHECK(cudaMemsetAsync(out, 0, (size_t)std::max<int64_t>(theta.size, 1) * sizeof(double), s));
+    contract64(c, Y2.L, ro, bra);
+}
+
+struct Problem {
+    std::vector<std::vector<Layout>> W;   // [term][site]
+    std::vector<int64_t> start, done;     // [term]
+    std::vector<std::vector<Layout>> P;   // [previous state][site]
+    double weight = 0.0;
+};
+
+void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh_sweep_params* p, double* energy,
+              tnh_sweep_stat* stats) {
+    TNH_REQUIRE(N >= 2, TNH_ERR_ARG, "tnh_dmrg: N = %d < 2", N);
+    TNH_REQUIRE(p->nsweep >= 1 && p->maxdim && p->cutoff, TNH_ERR_ARG, "tnh_dmrg: empty sweep schedule");
+    const tnh_precision prec = (tnh_precision)p->precision;
+    const tnh_precision eprec = (tnh_precision)p->env_precision;
+    TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad precision");
+    TNH_REQUIRE(eprec == TNH_FP64 || planes_of(eprec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad env precision");
+    CUDA_CHECK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    const int T = (int)pr.W.size();
+    // the MPO: one term as given, several as their direct sum
+    std::vector<Layout> W(N);
+    std::vector<DevBuf> Wbuf(T > 1 ? N : 0);
+    for (int j = 0; j < N; ++j) {
+        for (int t = 0; t < T; ++t)
+            TNH_REQUIRE(pr.W[t][j].rank() == 4, TNH_ERR_ARG, "tnh_dmrg: MPO tensors have rank 4");
+        if (T == 1) {
+            W[j] = pr.W[0][j];
+        } else {
+            std::vector<Layout> terms;
+            for (int t = 0; t < T; ++t) terms.push_back(pr.W[t][j]);
+            W[j] = direct_sum(terms, {0, 1}, Wbuf[j], s);
+        }
+    }
+    std::vector<DTensor> A(N);
+    for (int j = 0; j < N; ++j) {
+        Layout a = parse_tensor(&mps[j], "mps");
+        TNH_REQUIRE(a.rank() == 3, TNH_ERR_ARG, "tnh_dmrg: MPS tensors have rank 3");
+        A[j] = new_tensor(a.inds, a.flux, s);
+        for (int b = 0; b < a.nblocks(); ++b) {
+            int d = A[j].L.find(a.key(b));
+            TNH_REQUIRE(d >= 0, TNH_ERR_FLUX, "tnh_dmrg: MPS site %d block %d has another flux", j, b);
+            CUDA_CHECK(cudaMemcpyAsync(A[j].L.data + A[j].L.off[d], a.data + a.off[b],
+                                       (size_t)a.belems(b) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    const int nq = A[0].L.nq();
+    const std::vector<int> zero(nq, 0);
+    std::vector<DTensor> Ls(N + 1), Rs(N + 1);
+    {
+        const Index& a0 = A[0].L.inds[0];
+        Ls[0] = new_tensor({a0.dag(), W[0].inds[0].dag(), a0}, zero, s);
+        const Index& bN = A[N - 1].L.inds[2];
+        Rs[N] = new_tensor({bN.dag(), W[N - 1].inds[1].dag(), bN}, zero, s);
+        int64_t o0 = 0, oN = 0;
+        for (int t = 0; t < T; ++t) {
+            const int64_t w0 = pr.W[t][0].inds[0].total, wN = pr.W[t][N - 1].inds[1].total;
+            TNH_REQUIRE(pr.start[t] >= 0 && pr.start[t] < w0 && pr.done[t] >= 0 && pr.done[t] < wN, TNH_ERR_ARG,
+                        "tnh_dmrg: term %d boundary state out of range", t);
+            set_one(Ls[0], {0, o0 + pr.start[t], 0}, s);
+            set_one(Rs[N], {0, oN + pr.done[t], 0}, s);
+            o0 += w0;
+            oN += wN;
+        }
+    }
+    auto update_R = [&](int j) {   // R_j from R_{j+1}, A_j, W_j
+        const Layout& a = A[j].L;
+        Rs[j] = new_tensor({a.inds[0], W[j].inds[0], a.inds[0].dag()}, zero, s);
+        auto P = make_env(c, -1, Rs[j + 1].L, a, W[j], Rs[j].L);
+        run_env(c, *P, Rs[j + 1].L.data, a.data, W[j].data, Rs[j].L.data, eprec);
+        CUDA_CHECK(cudaStreamSynchronize(s));
+    };
+    auto update_L = [&](int j) {   // L_{j+1} from L_j, A_j, W_j
+        const Layout& a = A[j].L;
+        Ls[j + 1] = new_tensor({a.inds[2], W[j].inds[1], a.inds[2].dag()}, zero, s);
+        auto P = make_env(c, 1, Ls[j].L, a, W[j], Ls[j + 1].L);
+        run_env(c, *P, Ls[j].L.data, a.data, W[j].data, Ls[j + 1].L.data, eprec);
+        CUDA_CHECK(cudaStreamSynchronize(s));
+    };
+    for (int j = N - 1; j >= 2; --j) update_R(j);
+
+    // overlap environments of the previous states
+    const int K = (int)pr.P.size();
+    std::vector<std::vector<DTensor>> LO(K), RO(K);
+    for (int i = 0; i < K; ++i) {
+        const std::vector<Layout>& P = pr.P[i];
+        for (int j = 0; j < N; ++j)
+            TNH_REQUIRE(P[j].rank() == 3 && P[j].inds[1].same_space(A[j].L.inds[1]) && P[j].nq() == nq,
+                        TNH_ERR_SHAPE, "tnh_dmrg: previous state %d site %d does not match the MPS", i, j);
+        LO[i].resize(N + 1);
+        RO[i].resize(N + 1);
+        LO[i][0] = new_tensor({P[0].inds[0], A[0].L.inds[0].dag()}, zero, s);
+        RO[i][N] = new_tensor({P[N - 1].inds[2], A[N - 1].L.inds[2].dag()}, zero, s);
+        // both boundary links have dimension 1; a missing block means the two
+        // states carry different total charge (zero overlap)
+        if (LO[i][0].L.nblocks()) set_one(LO[i][0], {0, 0}, s);
+        if (RO[i][N].L.nblocks()) set_one(RO[i][N], {0, 0}, s);
+        for (int j = N - 1; j >= 2; --j) RO[i][j] = overlap_right(c, RO[i][j + 1].L, P[j], A[j].L);
+    }
+
+    double E = 0.0;
+    const bool dbg = std::getenv("TNH_DEBUG") != nullptr;
+    using clk = std::chrono::steady_clock;
+    auto since = [](clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); };
+    for (int sw = 0; sw < p->nsweep; ++sw) {
+        auto t0 = std::chrono::steady_clock::now();
+        double ph[6] = {0, 0, 0, 0, 0, 0};   // theta, plan, eigsolve, svd, factors, environment (s)
+        double maxerr = 0.0, resid = 0.0;
+        int64_t nmv = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int step = 0; step < N - 1; ++step) {
+                const int j = pass == 0 ? step : N - 2 - step;
+                const int dir = pass == 0 ? 1 : -1;
+                // theta = A_j * A_{j+1}
+                Layout a1 = relabel(A[j].L, {1, 2, 3});
+                Layout a2 = relabel(A[j + 1].L, {3, 4, 5});
+                DTensor th = new_tensor({a1.inds[0], a1.inds[1], a2.inds[1], a2.inds[2]},
+                                        fsum(a1.flux, a2.flux), s);
+                th.L = relabel(th.L, {1, 2, 4, 5});
+                auto tp = clk::now();
+                {
+                    auto cp = plan_contract(a1, a2, th.L, s);
+                    Workspace ws;
+                    run_contract(c, *cp, a1.data, a2.data, th.L.data, eprec, ws);
+                    CUDA_CHECK(cudaStreamSynchronize(s));
+                }
+                ph[0] += since(tp);
+                // eigensolver
+                {
+                    tp = clk::now();
+                    auto P = make_heff(c, Ls[j].L, W[j], W[j + 1], Rs[j + 2].L, th.L, prec);
+                    if (K) {
+                        DevBuf phi((size_t)K * std::max<int64_t>(th.L.size, 1) * sizeof(double));
+                        for (int i = 0; i < K; ++i)
+                            projected_state(c, LO[i][j].L, pr.P[i][j], pr.P[i][j + 1], RO[i][j + 2].L, th.L,
+                                            phi.as<double>() + (int64_t)i * th.L.size);
+                        set_projectors(*P, K, phi.as<double>(), pr.weight);
+                        CUDA_CHECK(cudaStreamSynchronize(s));
+                    }
+                    ph[1] += since(tp);
+                    tp = clk::now();
+                    EigResult r = eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
+                    ph[2] += since(tp);
+                    E = r.energy;
+                    resid = r.resid;
+                    nmv += r.matvecs;
+                }
+                // truncated SVD
+                tp = clk::now();
+                SvdResult* sv = svd_run(c, th.L, 2, p->cutoff[sw], p->maxdim[sw], p->mindim, dir > 0 ? 0 : 1);
+                ph[3] += since(tp);
+                tp = clk::now();
+                try {
+                    SvdShape sh = svd_shape(sv);
+                    maxerr = std::max(maxerr, sh.truncerr);
+                    if (dbg) {
+                        int kept = 0;
+                        for (int d : sh.dims) kept += d;
+                        std::fprintf(stderr, "dmrg: sweep %d bond %d dir %+d E %.14f kept %d in %zu sectors truncerr %.3e\n",
+                                     sw, j, dir, E, kept, sh.dims.size(), sh.truncerr);
+                    }
+                    Index link;
+                    link.nsect = (int)sh.dims.size();
+                    link.nq = nq;
+                    link.arrow = 1;
+                    for (auto& q : sh.qn) link.qn.insert(link.qn.end(), q.begin(), q.end());
+                    link.dim = sh.dims;
+                    link.finish();
+                    DTensor U = new_tensor({th.L.inds[0], th.L.inds[1], link.dag()}, zero, s);
+                    DTensor V = new_tensor({link, th.L.inds[2], th.L.inds[3]}, th.L.flux, s);
+                    svd_fetch(sv, U.L, nullptr, V.L, dir > 0 ? 2 : 1);
+                    A[j] = std::move(U);
+                    A[j + 1] = std::move(V);
+                } catch (...) {
+                    svd_delete(sv);
+                    throw;
+                }
+                svd_delete(sv);
+                ph[4] += since(tp);
+                tp = clk::now();
+                if (dir > 0) {
+                    update_L(j);
+                    for (int i = 0; i < K; ++i) LO[i][j + 1] = overlap_left(c, LO[i][j].L, pr.P[i][j], A[j].L);
+                } else {
+                    update_R(j + 1);
+                    for (int i = 0; i < K; ++i)
+                        RO[i][j + 1] = overlap_right(c, RO[i][j + 2].L, pr.P[i][j + 1], A[j + 1].L);
+                }
+                ph[5] += since(tp);
+            }
+        }
+        CUDA_CHECK(cudaStreamSynchronize(s));
+        check_device_flag(c);
+        double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dbg)
+            std::fprintf(stderr,
+                         "dmrg: sweep %d %.3f s: theta %.3f, H_eff plan %.3f, eigensolver %.3f, SVD %.3f, "
+                         "factors %.3f, environment %.3f\n",
+                         sw, secs, ph[0], ph[1], ph[2], ph[3], ph[4], ph[5]);
+        if (stats) {
+            tnh_sweep_stat& st = stats[sw];
+            st.sweep = sw;
+            st.energy = E;
+            st.resid = resid;
+            st.truncerr = maxerr;
+            int ml = 0;
+            for (int j = 0; j < N; ++j) ml = std::max<int>(ml, (int)A[j].L.inds[2].total);
+            st.maxlink = ml;
+            st.matvecs = nmv;
+            st.seconds = secs;
+        }
+    }
+    *energy = E;
+    c->mps = std::move(A);
 }
 
 }  // namespace
@@ -81,158 +379,98 @@ std::vector<int> fsum(const std::vector<int>& a, const std::vector<int>& b) {
 
 using namespace tnh;
 
-extern "C" tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, int64_t start, int64_t done,
-                               const tnh_tensor* mps, const tnh_sweep_params* p, double* energy,
-                               tnh_sweep_stat* stats) {
+extern "C" {
+
+tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, int64_t start, int64_t done,
+                    const tnh_tensor* mps, const tnh_sweep_params* p, double* energy, tnh_sweep_stat* stats) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     return guard(c, [&] {
         TNH_REQUIRE(c && mpo && mps && p && energy, TNH_ERR_ARG, "tnh_dmrg: NULL argument");
         TNH_REQUIRE(N >= 2, TNH_ERR_ARG, "tnh_dmrg: N = %d < 2", N);
-        TNH_REQUIRE(p->nsweep >= 1 && p->maxdim && p->cutoff, TNH_ERR_ARG, "tnh_dmrg: empty sweep schedule");
-        const tnh_precision prec = (tnh_precision)p->precision;
-        const tnh_precision eprec = (tnh_precision)p->env_precision;
-        TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad precision");
-        TNH_REQUIRE(eprec == TNH_FP64 || planes_of(eprec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad env precision");
-        CUDA_CHECK(cudaSetDevice(c->device));
-        cudaStream_t s = c->stream;
-        std::vector<Layout> W;
-        std::vector<DTensor> A(N);
-        for (int j = 0; j < N; ++j) {
-            W.push_back(parse_tensor(&mpo[j], "mpo"));
-            Layout a = parse_tensor(&mps[j], "mps");
-            TNH_REQUIRE(a.rank() == 3 && W[j].rank() == 4, TNH_ERR_ARG, "tnh_dmrg: MPS rank 3, MPO rank 4");
-            A[j] = new_tensor(a.inds, a.flux, s);
-            for (int b = 0; b < a.nblocks(); ++b) {
-                int d = A[j].L.find(a.key(b));
-                CUDA_CHECK(cudaMemcpyAsync(A[j].L.data + A[j].L.off[d], a.data + a.off[b],
-                                           (size_t)a.belems(b) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            }
-        }
-        const int nq = A[0].L.nq();
-        const std::vector<int> zero(nq, 0);
-        std::vector<DTensor> Ls(N + 1), Rs(N + 1);
-        {
-            const Index& a0 = A[0].L.inds[0];
-            Ls[0] = new_tensor({a0.dag(), W[0].inds[0].dag(), a0}, zero, s);
-            set_one(Ls[0], {0, start, 0}, s);
-            const Index& bN = A[N - 1].L.inds[2];
-            Rs[N] = new_tensor({bN.dag(), W[N - 1].inds[1].dag(), bN}, zero, s);
-            set_one(Rs[N], {0, done, 0}, s);
-        }
-        auto update_R = [&](int j) {   // R_j from R_{j+1}, A_j, W_j
-            const Layout& a = A[j].L;
-            Rs[j] = new_tensor({a.inds[0], W[j].inds[0], a.inds[0].dag()}, zero, s);
-            auto P = make_env(c, -1, Rs[j + 1].L, a, W[j], Rs[j].L);
-            run_env(c, *P, Rs[j + 1].L.data, a.data, W[j].data, Rs[j].L.data, eprec);
-            CUDA_CHECK(cudaStreamSynchronize(s));
-        };
-        auto update_L = [&](int j) {   // L_{j+1} from L_j, A_j, W_j
-            const Layout& a = A[j].L;
-            Ls[j + 1] = new_tensor({a.inds[2], W[j].inds[1], a.inds[2].dag()}, zero, s);
-            auto P = make_env(c, 1, Ls[j].L, a, W[j], Ls[j + 1].L);
-            run_env(c, *P, Ls[j].L.data, a.data, W[j].data, Ls[j + 1].L.data, eprec);
-            CUDA_CHECK(cudaStreamSynchronize(s));
-        };
-        for (int j = N - 1; j >= 2; --j) update_R(j);
-
-        double E = 0.0;
-        const bool dbg = std::getenv("TNH_DEBUG") != nullptr;
-        using clk = std::chrono::steady_clock;
-        auto since = [](clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); };
-        for (int sw = 0; sw < p->nsweep; ++sw) {
-            auto t0 = std::chrono::steady_clock::now();
-            double ph[6] = {0, 0, 0, 0, 0, 0};   // theta, plan, eigsolve, svd, factors, environment (s)
-            double maxerr = 0.0, resid = 0.0;
-            int64_t nmv = 0;
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int step = 0; step < N - 1; ++step) {
-                    const int j = pass == 0 ? step : N - 2 - step;
-                    const int dir = pass == 0 ? 1 : -1;
-                    // theta = A_j * A_{j+1}
-                    Layout a1 = relabel(A[j].L, {1, 2, 3});
-                    Layout a2 = relabel(A[j + 1].L, {3, 4, 5});
-                    DTensor th = new_tensor({a1.inds[0], a1.inds[1], a2.inds[1], a2.inds[2]},
-                                            fsum(a1.flux, a2.flux), s);
-                    th.L = relabel(th.L, {1, 2, 4, 5});
-                    auto tp = clk::now();
-                    {
-                        auto cp = plan_contract(a1, a2, th.L, s);
-                        Workspace ws;
-                        run_contract(c, *cp, a1.data, a2.data, th.L.data, eprec, ws);
-                        CUDA_CHECK(cudaStreamSynchronize(s));
-                    }
-                    ph[0] += since(tp);
-                    // eigensolver
-                    {
-                        tp = clk::now();
-                        auto P = make_heff(c, Ls[j].L, W[j], W[j + 1], Rs[j + 2].L, th.L, prec);
-                        ph[1] += since(tp);
-                        tp = clk::now();
-                        EigResult r = eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
-                        ph[2] += since(tp);
-                        E = r.energy;
-                        resid = r.resid;
-                        nmv += r.matvecs;
-                    }
-                    // truncated SVD
-                    tp = clk::now();
-                    SvdResult* sv = svd_run(c, th.L, 2, p->cutoff[sw], p->maxdim[sw], p->mindim, dir > 0 ? 0 : 1);
-                    ph[3] += since(tp);
-                    tp = clk::now();
-                    try {
-                        SvdShape sh = svd_shape(sv);
-                        maxerr = std::max(maxerr, sh.truncerr);
-                        if (std::getenv("TNH_DEBUG")) {
-                            int kept = 0;
-                            for (int d : sh.dims) kept += d;
-                            std::fprintf(stderr, "dmrg: sweep %d bond %d dir %+d E %.14f kept %d in %zu sectors truncerr %.3e\n",
-                                         sw, j, dir, E, kept, sh.dims.size(), sh.truncerr);
-                        }
-                        Index link;
-                        link.nsect = (int)sh.dims.size();
-                        link.nq = nq;
-                        link.arrow = 1;
-                        for (auto& q : sh.qn) link.qn.insert(link.qn.end(), q.begin(), q.end());
-                        link.dim = sh.dims;
-                        link.finish();
-                        DTensor U = new_tensor({th.L.inds[0], th.L.inds[1], link.dag()}, zero, s);
-                        DTensor V = new_tensor({link, th.L.inds[2], th.L.inds[3]}, th.L.flux, s);
-                        svd_fetch(sv, U.L, nullptr, V.L, dir > 0 ? 2 : 1);
-                        A[j] = std::move(U);
-                        A[j + 1] = std::move(V);
-                    } catch (...) {
-                        svd_delete(sv);
-                        throw;
-                    }
-                    svd_delete(sv);
-                    ph[4] += since(tp);
-                    tp = clk::now();
-                    if (dir > 0) update_L(j);
-                    else update_R(j + 1);
-                    ph[5] += since(tp);
-                }
-            }
-            CUDA_CHECK(cudaStreamSynchronize(s));
-            check_device_flag(c);
-            double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            if (dbg)
-                std::fprintf(stderr,
-                             "dmrg: sweep %d %.3f s: theta %.3f, H_eff plan %.3f, eigensolver %.3f, SVD %.3f, "
-                             "factors %.3f, environment %.3f\n",
-                             sw, secs, ph[0], ph[1], ph[2], ph[3], ph[4], ph[5]);
-            if (stats) {
-                tnh_sweep_stat& st = stats[sw];
-                st.sweep = sw;
-                st.energy = E;
-                st.resid = resid;
-                st.truncerr = maxerr;
-                int ml = 0;
-                for (int j = 0; j < N; ++j) ml = std::max<int>(ml, (int)A[j].L.inds[2].total);
-                st.maxlink = ml;
-                st.matvecs = nmv;
-                st.seconds = secs;
-            }
-        }
-        *energy = E;
+        Problem pr;
+        pr.W.resize(1);
+        for (int j = 0; j < N; ++j) pr.W[0].push_back(parse_tensor(&mpo[j], "mpo"));
+        pr.start = {start};
+        pr.done = {done};
+        run_dmrg(c, N, pr, mps, p, energy, stats);
     });
 }
+
+tnh_status tnh_dmrg_ex(tnh_ctx* ctx, int32_t N, const tnh_dmrg_problem* prob, const tnh_tensor* mps,
+                       const tnh_sweep_params* p, double* energy, tnh_sweep_stat* stats) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && prob && mps && p && energy, TNH_ERR_ARG, "tnh_dmrg_ex: NULL argument");
+        TNH_REQUIRE(N >= 2, TNH_ERR_ARG, "tnh_dmrg_ex: N = %d < 2", N);
+        TNH_REQUIRE(prob->nterm >= 1 && prob->mpo && prob->start && prob->done, TNH_ERR_ARG,
+                    "tnh_dmrg_ex: need at least one MPO with its boundary states");
+        TNH_REQUIRE(prob->northo >= 0 && (prob->northo == 0 || prob->ortho), TNH_ERR_ARG,
+                    "tnh_dmrg_ex: previous states missing");
+        Problem pr;
+        pr.W.resize(prob->nterm);
+        for (int t = 0; t < prob->nterm; ++t) {
+            for (int j = 0; j < N; ++j) pr.W[t].push_back(parse_tensor(&prob->mpo[(size_t)t * N + j], "mpo"));
+            pr.start.push_back(prob->start[t]);
+            pr.done.push_back(prob->done[t]);
+        }
+        pr.P.resize(prob->northo);
+        for (int i = 0; i < prob->northo; ++i)
+            for (int j = 0; j < N; ++j) pr.P[i].push_back(parse_tensor(&prob->ortho[(size_t)i * N + j], "ortho"));
+        pr.weight = prob->weight;
+        run_dmrg(c, N, pr, mps, p, energy, stats);
+    });
+}
+
+tnh_status tnh_dmrg_mps_size(tnh_ctx* ctx, int32_t* N) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && N, TNH_ERR_ARG, "tnh_dmrg_mps_size: NULL argument");
+        *N = (int32_t)c->mps.size();
+    });
+}
+
+tnh_status tnh_dmrg_mps_link(tnh_ctx* ctx, int32_t j, int32_t* nsect, int32_t* nq, int32_t* qn, int32_t* sect_dim) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && nsect, TNH_ERR_ARG, "tnh_dmrg_mps_link: NULL argument");
+        const int N = (int)c->mps.size();
+        TNH_REQUIRE(N > 0, TNH_ERR_ARG, "tnh_dmrg_mps_link: no DMRG run on this context");
+        TNH_REQUIRE(j >= 0 && j <= N, TNH_ERR_ARG, "tnh_dmrg_mps_link: link %d out of 0..%d", j, N);
+        const Index& ix = j < N ? c->mps[j].L.inds[0] : c->mps[N - 1].L.inds[2];
+        *nsect = ix.nsect;
+        if (nq) *nq = ix.nq;
+        if (qn) std::copy(ix.qn.begin(), ix.qn.end(), qn);
+        if (sect_dim) std::copy(ix.dim.begin(), ix.dim.end(), sect_dim);
+    });
+}
+
+tnh_status tnh_dmrg_mps_get(tnh_ctx* ctx, int32_t j, tnh_tensor* A) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && A, TNH_ERR_ARG, "tnh_dmrg_mps_get: NULL argument");
+        const int N = (int)c->mps.size();
+        TNH_REQUIRE(j >= 0 && j < N, TNH_ERR_ARG, "tnh_dmrg_mps_get: site %d out of 0..%d", j, N - 1);
+        CUDA_CHECK(cudaSetDevice(c->device));
+        const Layout& src = c->mps[j].L;
+        Layout dst = parse_tensor(A, "A");
+        TNH_REQUIRE(dst.rank() == 3, TNH_ERR_SHAPE, "tnh_dmrg_mps_get: A must have rank 3");
+        for (int i = 0; i < 3; ++i)
+            TNH_REQUIRE(dst.inds[i].same_space(src.inds[i]) && dst.inds[i].arrow == src.inds[i].arrow, TNH_ERR_SHAPE,
+                        "tnh_dmrg_mps_get: index %d of A differs from the stored site %d", i, j);
+        cudaStream_t s = c->stream;
+        for (int b = 0; b < src.nblocks(); ++b)
+            TNH_REQUIRE(dst.find(src.key(b)) >= 0, TNH_ERR_SHAPE, "tnh_dmrg_mps_get: A lacks stored block %d", b);
+        for (int b = 0; b < dst.nblocks(); ++b) {
+            const int d = src.find(dst.key(b));
+            const size_t bytes = (size_t)dst.belems(b) * sizeof(double);
+            if (d >= 0)
+                CUDA_CHECK(cudaMemcpyAsync(dst.data + dst.off[b], src.data + src.off[d], bytes,
+                                           cudaMemcpyDeviceToDevice, s));
+            else
+                CUDA_CHECK(cudaMemsetAsync(dst.data + dst.off[b], 0, bytes, s));
+        }
+        CUDA_CHECK(cudaStreamSynchronize(s));
+    });
+}
+
+}  // extern "C"

@@ -810,11 +810,8 @@ void capture(HeffPlan& P, HeffPlan::Graph& G, bool f64, const double* x, double*
     G.y = y;
 }
 
-}  // namespace
-
-void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
-    TNH_REQUIRE(prec == TNH_FP64 || prec == P.prec, TNH_ERR_ARG,
-                "heff_apply: precision %d not prepared by this plan", (int)prec);
+// The MPO part of one application (graph replay after the first call).
+void heff_chain(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
     cudaStream_t s = P.stream;
     if (P.zero_y && P.n > 0) CUDA_CHECK(cudaMemsetAsync(y, 0, (size_t)P.n * sizeof(double), s));
     if (P.g1.f64.empty() || P.g4.f64.empty() || P.jX.ntiles == 0) {
@@ -846,6 +843,15 @@ void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
     CUDA_CHECK(cudaGraphLaunch(G.exec, s));
 }
 
+}  // namespace
+
+void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
+    TNH_REQUIRE(prec == TNH_FP64 || prec == P.prec, TNH_ERR_ARG,
+                "heff_apply: precision %d not prepared by this plan", (int)prec);
+    heff_chain(P, prec, x, y);
+    add_projectors(P, x, y);
+}
+
 }  // namespace tnh
 
 using namespace tnh;
@@ -861,6 +867,42 @@ tnh_status tnh_heff_plan(tnh_ctx* ctx, const tnh_tensor* L, const tnh_tensor* W1
         auto P = make_heff(c, parse_tensor(L, "L"), parse_tensor(W1, "W1"), parse_tensor(W2, "W2"),
                            parse_tensor(R, "R"), parse_tensor(psi, "psi", false), prec);
         *plan = reinterpret_cast<tnh_heff*>(P.release());
+    });
+}
+
+tnh_status tnh_heff_plan_sum(tnh_ctx* ctx, int32_t nterm, const tnh_tensor* L, const tnh_tensor* W1,
+                             const tnh_tensor* W2, const tnh_tensor* R, const tnh_tensor* psi, tnh_precision prec,
+                             tnh_heff** plan) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && plan && L && W1 && W2 && R && psi, TNH_ERR_ARG, "tnh_heff_plan_sum: NULL argument");
+        TNH_REQUIRE(nterm >= 1, TNH_ERR_ARG, "tnh_heff_plan_sum: nterm = %d", nterm);
+        CUDA_CHECK(cudaSetDevice(c->device));
+        std::vector<Layout> l, w1, w2, r;
+        for (int t = 0; t < nterm; ++t) {
+            l.push_back(parse_tensor(&L[t], "L"));
+            w1.push_back(parse_tensor(&W1[t], "W1"));
+            w2.push_back(parse_tensor(&W2[t], "W2"));
+            r.push_back(parse_tensor(&R[t], "R"));
+            TNH_REQUIRE(l[t].rank() == 3 && r[t].rank() == 3 && w1[t].rank() == 4 && w2[t].rank() == 4,
+                        TNH_ERR_ARG, "tnh_heff_plan_sum: ranks must be L 3, W 4, R 3");
+        }
+        // make_heff synchronises the stream before it returns, after which
+        // the staged direct sums are no longer read
+        DevBuf bl, bw1, bw2, br;
+        Layout sl = direct_sum(l, {1}, bl, c->stream), sw1 = direct_sum(w1, {0, 1}, bw1, c->stream),
+               sw2 = direct_sum(w2, {0, 1}, bw2, c->stream), sr = direct_sum(r, {1}, br, c->stream);
+        auto P = make_heff(c, sl, sw1, sw2, sr, parse_tensor(psi, "psi", false), prec);
+        *plan = reinterpret_cast<tnh_heff*>(P.release());
+    });
+}
+
+tnh_status tnh_heff_set_projectors(tnh_heff* plan, int32_t k, const double* phi, double weight) {
+    auto* P = reinterpret_cast<HeffPlan*>(plan);
+    return guard(P ? P->ctx : nullptr, [&] {
+        TNH_REQUIRE(P, TNH_ERR_ARG, "tnh_heff_set_projectors: NULL plan");
+        set_projectors(*P, k, phi, weight);
+        CUDA_CHECK(cudaStreamSynchronize(P->stream));
     });
 }
 

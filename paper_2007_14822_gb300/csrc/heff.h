@@ -27,6 +27,13 @@ struct HeffGemm {
     DevBuf d_f64, d_tc, d_reds;
 };
 
+// ---- device vector helpers (float64, deterministic reductions) -----------
+struct VecWork {
+    DevBuf partial, scal;   // reduction partials, device scalars
+    int blocks = 0;
+    void ensure(int nsms);
+};
+
 struct HeffPlan {
     Ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;   // copy: freeing a plan never touches ctx
@@ -62,13 +69,25 @@ struct HeffPlan {
         double* y = nullptr;
         int calls = 0;
     } graphs[2];
+    // previous-state projectors (excited-state DMRG, Sec. 7.2): every
+    // application adds weight * phi_i <phi_i, x> for the nproj vectors phi_i
+    int nproj = 0;
+    double pweight = 0.0;
+    DevBuf proj;            // [nproj][n]
+    DevBuf pcoef;           // [nproj] device scalars
+    VecWork pvw;
     ~HeffPlan();
 };
 
 // L, W1, W2, R are read while the plan is made and not referenced after.
 std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
                                     const Layout& R, const Layout& psi, tnh_precision prec);
+// H_eff (of the plan's MPO terms) plus the projectors, if any.
 void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y);
+// Replace the projectors: phi is DEVICE [k][P.n] (copied), weight the penalty.
+void set_projectors(HeffPlan& P, int k, const double* phi, double weight);
+// y += P.pweight * sum_i phi_i <phi_i, x> (float64, deterministic).
+void add_projectors(HeffPlan& P, const double* x, double* y);
 
 struct EigResult {
     double energy = 0, resid = 0;
@@ -77,12 +96,6 @@ struct EigResult {
 // Lanczos on the plan; psi (device, length P.n) in/out.
 EigResult eigsolve(HeffPlan& P, double* psi, int krylov_dim, double tol);
 
-// ---- device vector helpers (float64, deterministic reductions) -----------
-struct VecWork {
-    DevBuf partial, scal;   // reduction partials, device scalars
-    int blocks = 0;
-    void ensure(int nsms);
-};
 void vdot(Ctx* ctx, VecWork& w, const double* x, const double* y, int64_t n, double* d_out);
 void vscale_copy(Ctx* ctx, const double* x, double* y, int64_t n, const double* d_num, const double* d_den,
                  int mode);

@@ -306,6 +306,37 @@ void vscale_copy(Ctx* ctx, const double* x, double* y, int64_t n, const double* 
     }
 }
 
+void set_projectors(HeffPlan& P, int k, const double* phi, double weight) {
+    TNH_REQUIRE(k >= 0 && k <= kMaxKrylov, TNH_ERR_ARG, "projectors: %d vectors, at most %d", k, kMaxKrylov);
+    TNH_REQUIRE(k == 0 || phi, TNH_ERR_ARG, "projectors: vectors are NULL");
+    TNH_REQUIRE(std::isfinite(weight), TNH_ERR_ARG, "projectors: weight %g", weight);
+    P.nproj = 0;
+    P.pweight = weight;
+    if (k == 0 || P.n == 0) return;
+    const size_t bytes = (size_t)k * P.n * sizeof(double);
+    if (P.proj.bytes < bytes) P.proj.alloc(bytes);
+    if (P.pcoef.bytes < (size_t)k * sizeof(double)) P.pcoef.alloc((size_t)k * sizeof(double));
+    CUDA_CHECK(cudaMemcpyAsync(P.proj.p, phi, bytes, cudaMemcpyDeviceToDevice, P.stream));
+    P.pvw.ensure(P.ctx->num_sms);
+    P.nproj = k;
+}
+
+void add_projectors(HeffPlan& P, const double* x, double* y) {
+    if (P.nproj == 0 || P.n == 0) return;
+    cudaStream_t s = P.stream;
+    const int64_t n = P.n;
+    const double* phi = P.proj.as<double>();
+    { KScope ks_("multidot_partial", s);
+    multidot_partial<<<dim3(P.pvw.blocks, P.nproj), kRedThreads, 0, s>>>(phi, n, x, n, P.pvw.partial.as<double>());
+    }
+    { KScope ks_("reduce_partials", s);
+    reduce_partials<<<P.nproj, kRedThreads, 0, s>>>(P.pvw.partial.as<double>(), P.pvw.blocks, P.pcoef.as<double>());
+    }
+    { KScope ks_("multi_axpy", s);
+    multi_axpy<<<grid_for(n, P.ctx->num_sms), 256, 0, s>>>(y, phi, n, P.nproj, P.pcoef.as<double>(), P.pweight, 0, n);
+    }
+}
+
 EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
     Ctx* ctx = P.ctx;
     cudaStream_t s = ctx->stream;

@@ -109,11 +109,23 @@ struct Layout {
     }
 };
 
+// A tensor that owns its device data.
+struct OwnedTensor {
+    Layout L;
+    DevBuf buf;
+};
+
 Index parse_index(const tnh_index& in, const char* what);
 Layout parse_tensor(const tnh_tensor* t, const char* what, bool need_data = true);
 // Allowed blocks of the given indices at the given flux, lexicographic, packed.
 Layout make_layout(const std::vector<Index>& inds, const std::vector<int>& flux);
 std::vector<int> block_flux(const std::vector<Index>& inds, const int* key, int nq);
+// Direct sum of tensors along the index positions in cat: those indices
+// get the sectors of every term in turn, the other indices must agree, and
+// the blocks of term t keep their keys with the cat sectors shifted past the
+// earlier terms' (no block mixes two terms). The data of the terms is copied
+// one after the other into buf (stream-ordered on s).
+Layout direct_sum(const std::vector<Layout>& T, const std::vector<int>& cat, DevBuf& buf, cudaStream_t s);
 
 // ------------------------------------------------------------------ context
 struct Profiler;
@@ -126,6 +138,8 @@ struct Ctx {
     std::unique_ptr<Profiler> prof;
     // H_eff K-split choices measured by the plan autotuner, by shape signature
     std::map<std::vector<int>, std::pair<int, int>> heff_tune;
+    // the MPS left by the last DMRG run
+    std::vector<OwnedTensor> mps;
     ~Ctx();
 };
 

@@ -28,7 +28,8 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_heff_plan", "tnh_heff_apply", "tnh_heff_apply_prec", "tnh_heff_flops", "tnh_heff_flops_detail", "tnh_heff_size",
            "tnh_heff_free", "tnh_eigsolve", "tnh_env_update", "tnh_svd_trunc", "tnh_svd_info",
            "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
-           "tnh_contract_dense_noalloc"]
+           "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
+           "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get"]
 
 
 class TnhError(RuntimeError):
@@ -58,6 +59,12 @@ class tnh_sweep_stat(C.Structure):
     _fields_ = [("sweep", C.c_int32), ("energy", C.c_double), ("resid", C.c_double),
                 ("truncerr", C.c_double), ("maxlink", C.c_int32), ("matvecs", C.c_int64),
                 ("seconds", C.c_double)]
+
+
+class tnh_dmrg_problem(C.Structure):
+    _fields_ = [("nterm", C.c_int32), ("mpo", C.POINTER(tnh_tensor)), ("start", C.POINTER(C.c_int64)),
+                ("done", C.POINTER(C.c_int64)), ("northo", C.c_int32), ("ortho", C.POINTER(tnh_tensor)),
+                ("weight", C.c_double)]
 
 
 _lib = None
@@ -99,6 +106,14 @@ def lib():
         "tnh_dmrg": (i32, [vp, i32, P(tnh_tensor), i64, i64, P(tnh_tensor), P(tnh_sweep_params), P(dbl),
                            P(tnh_sweep_stat)]),
         "tnh_contract_dense_noalloc": (i32, [vp, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor)]),
+        "tnh_heff_plan_sum": (i32, [vp, i32, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), P(tnh_tensor),
+                                    P(tnh_tensor), C.c_int, P(vp)]),
+        "tnh_heff_set_projectors": (i32, [vp, i32, vp, dbl]),
+        "tnh_dmrg_ex": (i32, [vp, i32, P(tnh_dmrg_problem), P(tnh_tensor), P(tnh_sweep_params), P(dbl),
+                              P(tnh_sweep_stat)]),
+        "tnh_dmrg_mps_size": (i32, [vp, P(i32)]),
+        "tnh_dmrg_mps_link": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
+        "tnh_dmrg_mps_get": (i32, [vp, i32, P(tnh_tensor)]),
         "tnh_profile_begin": (i32, [vp]),
         "tnh_profile_end": (i32, [vp, i32, P(i32), C.c_char_p, P(i64), P(dbl)]),
     }
@@ -318,6 +333,18 @@ class Context:
         self._children.add(plan)
         return plan
 
+    def heff_plan_sum(self, Ls, W1s, W2s, Rs, psi, prec=FP64):
+        """H_eff of a sum of MPOs: one (L, W1, W2, R) per term."""
+        keep = []
+        n = len(Ls)
+        arrs = [(tnh_tensor * n)(*[t._c(keep) for t in ts]) for ts in (Ls, W1s, W2s, Rs)]
+        p = psi._c(keep)
+        h = C.c_void_p()
+        self.check(self._lib.tnh_heff_plan_sum(self.h, n, *arrs, C.byref(p), int(prec), C.byref(h)))
+        plan = Heff(self, h)
+        self._children.add(plan)
+        return plan
+
     def env_update(self, direction, E, A, W, out, prec=FP64):
         keep = []
         args = [t._c(keep) for t in (E, A, W, out)]
@@ -335,11 +362,13 @@ class Context:
         return res
 
     def dmrg(self, mpo, mps, start, done, maxdim, cutoff, mindim=1, krylov_dim=32, tol=1e-10,
-             prec=FP64, env_prec=FP64):
+             prec=FP64, env_prec=FP64, ortho=(), weight=1.0):
+        """Two-site DMRG sweeps. ``mpo`` is one MPO (list of site tensors) or,
+        with ``start``/``done`` lists, a list of MPOs whose sum is H;
+        ``ortho`` lists previous states (MPS) to stay orthogonal to, with the
+        energy penalty ``weight``. Returns (energy, per-sweep stats); the
+        final MPS is read with ``dmrg_mps``."""
         keep = []
-        N = len(mpo)
-        W = (tnh_tensor * N)(*[w._c(keep) for w in mpo])
-        A = (tnh_tensor * N)(*[a._c(keep) for a in mps])
         ns = len(maxdim)
         md = (C.c_int32 * ns)(*maxdim)
         co = (C.c_double * ns)(*cutoff)
@@ -347,9 +376,48 @@ class Context:
                              int(mindim), int(krylov_dim), float(tol), int(prec), int(env_prec))
         stats = (tnh_sweep_stat * ns)()
         e = C.c_double()
-        self.check(self._lib.tnh_dmrg(self.h, N, W, int(start), int(done), A, C.byref(p), C.byref(e), stats))
+        terms = isinstance(start, (list, tuple))
+        N = len(mpo[0]) if terms else len(mpo)
+        A = (tnh_tensor * N)(*[a._c(keep) for a in mps])
+        if not terms and not ortho:
+            W = (tnh_tensor * N)(*[w._c(keep) for w in mpo])
+            self.check(self._lib.tnh_dmrg(self.h, N, W, int(start), int(done), A, C.byref(p), C.byref(e), stats))
+        else:
+            mpos = list(mpo) if terms else [mpo]
+            starts = list(start) if terms else [start]
+            dones = list(done) if terms else [done]
+            W = (tnh_tensor * (len(mpos) * N))(*[w._c(keep) for m in mpos for w in m])
+            st = (C.c_int64 * len(mpos))(*starts)
+            dn = (C.c_int64 * len(mpos))(*dones)
+            no = len(ortho)
+            O = (tnh_tensor * max(1, no * N))(*[a._c(keep) for m in ortho for a in m])
+            prob = tnh_dmrg_problem(len(mpos), W, st, dn, no, O, float(weight))
+            self.check(self._lib.tnh_dmrg_ex(self.h, N, C.byref(prob), A, C.byref(p), C.byref(e), stats))
         return e.value, [dict(sweep=s.sweep, energy=s.energy, resid=s.resid, truncerr=s.truncerr,
                               maxlink=s.maxlink, matvecs=s.matvecs, seconds=s.seconds) for s in stats]
+
+    def dmrg_link(self, j):
+        """Sectors [(qn, dim)] of link j of the MPS left by the last DMRG run."""
+        ns, nq = C.c_int32(), C.c_int32()
+        self.check(self._lib.tnh_dmrg_mps_link(self.h, int(j), C.byref(ns), C.byref(nq), None, None))
+        qn = (C.c_int32 * max(1, ns.value * nq.value))()
+        sd = (C.c_int32 * max(1, ns.value))()
+        self.check(self._lib.tnh_dmrg_mps_link(self.h, int(j), C.byref(ns), C.byref(nq), qn, sd))
+        return [(tuple(qn[i * nq.value:(i + 1) * nq.value]), int(sd[i])) for i in range(ns.value)]
+
+    def dmrg_mps(self, site):
+        """The MPS left by the last DMRG run, as device tensors [link, site, link]."""
+        n = C.c_int32()
+        self.check(self._lib.tnh_dmrg_mps_size(self.h, C.byref(n)))
+        links = [Index(self.dmrg_link(j), +1) for j in range(n.value + 1)]
+        out = []
+        for j in range(n.value):
+            T = Tensor([links[j], site, links[j + 1].dag()])
+            keep = []
+            t = T._c(keep)
+            self.check(self._lib.tnh_dmrg_mps_get(self.h, j, C.byref(t)))
+            out.append(T)
+        return out
 
 
 class Heff:
@@ -389,6 +457,16 @@ class Heff:
         n = C.c_int64()
         self.ctx.check(self.ctx._lib.tnh_heff_size(self.h, C.byref(n)))
         return n.value
+
+    def set_projectors(self, phi, weight):
+        """Add weight * phi_i <phi_i, x> to every product (phi: CUDA float64
+        [k, n], or None to remove)."""
+        if phi is None:
+            self.ctx.check(self.ctx._lib.tnh_heff_set_projectors(self.h, 0, None, 0.0))
+            return
+        k = phi.shape[0] if phi.dim() == 2 else 1
+        self.ctx.check(self.ctx._lib.tnh_heff_set_projectors(self.h, int(k), _ptr(phi.contiguous()),
+                                                             float(weight)))
 
     def eigsolve(self, psi, krylov_dim=64, tol=1e-10):
         e, r, k = C.c_double(), C.c_double(), C.c_int32()

@@ -118,3 +118,120 @@ def test_dmrg_mixed_with_tiny_cutoff_matches_fp64(ctx):
         out[name], st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in sweeps], [c for _, c in sweeps],
                                  krylov_dim=16, tol=tol, prec=prec)
     assert abs(out["mix"] - out["fp64"]) < 1e-9 * abs(out["fp64"]), out
+
+
+# ------------------------------------------- sums of MPOs, excited states
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_dmrg_sum_of_mpos_j1j2(ctx, prec):
+    # H = H_J1 + H_J2 given as two MPOs, against the oracle's sum of terms and
+    # the Majumdar-Ghosh energy -3N/8
+    from paper_2007_14822_gb300 import tnh
+    N = 12
+    nn = [(i, i + 1, 1.0) for i in range(N - 1)]
+    nnn = [(i, i + 2, 0.5) for i in range(N - 2)]
+    hosts = [pm.spin_pairs(N, nn), pm.spin_pairs(N, nnn)]
+    Ws = [pm.to_device(h, qn=True) for h in hosts]
+    site = Ws[0][0].inds[3]
+    sweeps = [(8, 1e-12), (32, 1e-12), (64, 1e-13), (64, 1e-13)]
+    A = pm.product_state(site, [0, 1] * (N // 2))
+    E, st = ctx.dmrg(Ws, A, [h.start for h in hosts], [h.done for h in hosts], [m for m, _ in sweeps],
+                     [c for _, c in sweeps], krylov_dim=64, tol=1e-10 if prec == "fp64" else 1e-7,
+                     prec=tnh.PRECISION[prec])
+    ao = D.product_mps_basis(om.heisenberg_mpo(N).site_index, [0, 1] * (N // 2), 1)
+    Eo, _, _ = D.dmrg([om.heisenberg_like_mpo(N, nn), om.heisenberg_like_mpo(N, nnn)], ao, sweeps, 64, 1e-10)
+    assert abs(E - Eo) < 1e-9 * abs(Eo), (E, Eo)
+    assert abs(E + 3 * N / 8) < 1e-9 * 3 * N / 8
+
+
+def test_dmrg_sum_of_mpos_tfim_dense(ctx):
+    # dense storage: bond and field parts of the TFIM as two MPOs
+    from test_oracle_models import tfim_closed_form
+    N, J, h = 10, 1.0, 1.3
+    hosts = [pm.tfim(N, J, 0.0), pm.tfim(N, 0.0, h)]
+    Ws = [pm.to_device(x, qn=False) for x in hosts]
+    vecs = synth.product_spinors(3, N, 2)
+    A = pm.product_vectors(Ws[0][0].inds[3], vecs)
+    sweeps = [(8, 1e-12), (24, 1e-13), (32, 1e-13)]
+    E, st = ctx.dmrg(Ws, A, [x.start for x in hosts], [x.done for x in hosts], [m for m, _ in sweeps],
+                     [c for _, c in sweeps], krylov_dim=64, tol=1e-10)
+    terms = [om.tfim_mpo(N, J, 0.0), om.tfim_mpo(N, 0.0, h)]
+    Eo, _, _ = D.dmrg(terms, D.product_mps_vectors(terms[0].site_index, vecs), sweeps, 64, 1e-10)
+    assert abs(E - Eo) < 1e-9 * abs(Eo), (E, Eo)
+    assert abs(E - tfim_closed_form(N, J, h)) < 1e-9 * abs(E)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_dmrg_excited_states_tfim(ctx, prec):
+    # ground state, then the two lowest states above it with the projectors
+    # of the earlier ones; levels of the open TFIM in closed form
+    from paper_2007_14822_gb300 import tnh
+    from test_oracle_dmrg import tfim_levels
+    N, J, h = 8, 1.0, 1.5
+    levels = tfim_levels(N, J, h)
+    host = pm.tfim(N, J, h)
+    W = pm.to_device(host, qn=False)
+    site = W[0].inds[3]
+    sweeps = [(8, 1e-13), (32, 1e-14), (32, 1e-14), (32, 1e-14), (32, 1e-14), (32, 1e-14)]
+    kw = dict(krylov_dim=64, tol=1e-10 if prec == "fp64" else 1e-7, prec=tnh.PRECISION[prec])
+    states, energies = [], []
+    for k in range(3):
+        A = pm.product_vectors(site, synth.product_spinors(4 + k, N, 2))
+        E, st = ctx.dmrg(W, A, host.start, host.done, [m for m, _ in sweeps], [c for _, c in sweeps],
+                         ortho=list(states), weight=20.0, **kw)
+        energies.append(E)
+        states.append(ctx.dmrg_mps(site))
+    for E, ex in zip(energies, levels):
+        assert abs(E - ex) < 1e-9 * abs(ex), (energies, levels)
+    # the oracle's overlap of the device states (read back through the ABI)
+    ost = [[H.to_oracle(T) for T in s] for s in states]
+    for a in range(3):
+        assert abs(D.mps_overlap(ost[a], ost[a]) - 1.0) < 1e-9
+        for b in range(a):
+            assert abs(D.mps_overlap(ost[a], ost[b])) < 1e-6
+
+
+def test_dmrg_excited_state_qn_matches_oracle(ctx):
+    N = 8
+    host = pm.heisenberg(N)
+    W = pm.to_device(host, qn=True)
+    site = W[0].inds[3]
+    sweeps = [(8, 1e-13), (16, 1e-14), (16, 1e-14), (16, 1e-14), (16, 1e-14), (16, 1e-14)]
+    md, co = [m for m, _ in sweeps], [c for _, c in sweeps]
+    E0, _ = ctx.dmrg(W, pm.product_state(site, [0, 1] * (N // 2)), host.start, host.done, md, co, krylov_dim=64)
+    psi0 = ctx.dmrg_mps(site)
+    E1, _ = ctx.dmrg(W, pm.product_state(site, [1, 0] * (N // 2)), host.start, host.done, md, co, krylov_dim=64,
+                     ortho=[psi0], weight=5.0)
+    # the oracle's run from the device ground state
+    omp = om.heisenberg_mpo(N)
+    Eo1, Ao1, _ = D.dmrg(omp, D.product_mps_basis(omp.site_index, [1, 0] * (N // 2), 1), sweeps,
+                         ortho=[[H.to_oracle(T) for T in psi0]], weight=5.0)
+    e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)), om.SPIN_QN, (0,), k=2)
+    assert abs(E0 - e_ed[0]) < 1e-9 * abs(e_ed[0])
+    assert abs(E1 - Eo1) < 1e-9 * abs(Eo1), (E1, Eo1)
+    assert abs(E1 - e_ed[1]) < 1e-9 * abs(e_ed[1])
+
+
+def test_dmrg_checkpoint_resume(ctx):
+    # two sweeps, read the MPS back, two more sweeps from it: the same
+    # energies as four sweeps in one run (same inputs, deterministic kernels)
+    N = 16
+    host = pm.heisenberg(N)
+    W = pm.to_device(host, qn=True)
+    site = W[0].inds[3]
+    sweeps = [(8, 1e-12), (16, 1e-12), (32, 1e-12), (48, 1e-12)]
+    md, co = [m for m, _ in sweeps], [c for _, c in sweeps]
+    start = pm.product_state(site, [0, 1] * (N // 2))
+    E4, st4 = ctx.dmrg(W, start, host.start, host.done, md, co, krylov_dim=32)
+    E2, st2 = ctx.dmrg(W, pm.product_state(site, [0, 1] * (N // 2)), host.start, host.done, md[:2], co[:2],
+                       krylov_dim=32)
+    ck = ctx.dmrg_mps(site)
+    # the checkpoint is the state of sweep 2
+    assert abs(E2 - st4[1]["energy"]) < 1e-12 * abs(E2)
+    ck_host = [T.block_arrays() for T in ck]
+    Er, str_ = ctx.dmrg(W, ck, host.start, host.done, md[2:], co[2:], krylov_dim=32)
+    assert abs(Er - E4) < 1e-12 * abs(E4), (Er, E4)
+    assert [s["maxlink"] for s in str_] == [s["maxlink"] for s in st4[2:]]
+    # the checkpoint tensors were read, not modified
+    for T, h in zip(ck, ck_host):
+        for k, v in T.block_arrays().items():
+            np.testing.assert_array_equal(v, h[k])

@@ -248,3 +248,65 @@ def test_eigsolve_fixed_length_matches_oracle_lanczos(ctx, m, k):
     Eo, xo, res, nmo = D.lanczos(apply, d["psio"], k, 0.0)
     assert nmv == nmo
     assert abs(E - Eo) < 1e-10 * abs(Eo)
+
+
+# ------------------------------------------- sums of MPOs, projectors
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("nsect", [1, 7])
+def test_heff_plan_sum_matches_sum_of_terms(ctx, p, nsect):
+    # H = H_J1J2 + H_Heisenberg (different MPO link dimensions): one plan of
+    # the terms' direct sum against the oracle's sum of the two products
+    import torch
+    from paper_2007_14822_gb300 import models as pm
+    j = 3
+    terms = [pm.to_device(pm.j1j2_chain(8, 1.0, 0.5), qn=True), pm.to_device(pm.heisenberg(8), qn=True)]
+    a = H.link_index(40, nsect, 12 if nsect > 1 else 40, +1)
+    Ls, Rs, Los, Ros, W1s, W2s = [], [], [], [], [], []
+    for t, mpo in enumerate(terms):
+        W1, W2 = mpo[j], mpo[j + 1]
+        L, Lo = H.random_pair([a.dag(), W1.inds[0].dag(), a], None, 31 + t, "L")
+        R, Ro = H.random_pair([a, W2.inds[1].dag(), a.dag()], None, 41 + t, "R")
+        Ls.append(L), Rs.append(R), Los.append(Lo), Ros.append(Ro), W1s.append(W1), W2s.append(W2)
+    psi, psio = H.random_pair([a, W1s[0].inds[3], W2s[0].inds[3], a.dag()], None, 51, "psi")
+    plan = ctx.heff_plan_sum(Ls, W1s, W2s, Rs, psi, prec(p))
+    y = torch.zeros_like(psi.data)
+    plan.apply(psi.data, y)
+    plan.apply(psi.data, y)      # second call: graph capture
+    yt = psi.with_inds(psi.inds)
+    yt.data = y
+    want = None
+    for t in range(2):
+        wt = D.heff_apply(Los[t], H.to_oracle(W1s[t]), H.to_oracle(W2s[t]), Ros[t], psio)
+        want = wt if want is None else want.axpy(1.0, wt)
+    assert H.rel_err(H.to_oracle(yt), want) < TOL[p]
+    # the flops are the two terms' flops
+    f = [ctx.heff_plan(Ls[t], W1s[t], W2s[t], Rs[t], psi, prec(p)).flops for t in range(2)]
+    assert plan.flops == pytest.approx(sum(f))
+
+
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_heff_projectors_added(ctx, p):
+    # y = H_eff x + w sum_i phi_i <phi_i, x> with two random phi
+    import torch
+    d = H.heff_inputs(24, None, 9, nsect=5, maxd=8)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    n = plan.size
+    phis = [H.random_pair(d["psi"].inds, d["psi"].flux, 60 + i, "phi") for i in range(2)]
+    phi = torch.stack([t.data[:n] for t, _ in phis])
+    w = 3.5
+    plan.set_projectors(phi, w)
+    y = torch.zeros_like(d["psi"].data)
+    for _ in range(3):           # direct, captured, replayed
+        plan.apply(d["psi"].data, y)
+    yt = d["psi"].with_inds(d["psi"].inds)
+    yt.data = y
+    want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    for _, po in phis:
+        want = want.axpy(w * po.vdot(d["psio"]), po)
+    assert H.rel_err(H.to_oracle(yt), want) < TOL[p]
+    # removing them gives H_eff alone
+    plan.set_projectors(None, 0.0)
+    plan.apply(d["psi"].data, y)
+    yt.data = y
+    want0 = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    assert H.rel_err(H.to_oracle(yt), want0) < TOL[p]
