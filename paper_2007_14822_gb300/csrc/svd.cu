@@ -91,6 +91,46 @@ __device__ __forceinline__ T warp_sum(T v) {
 // round-robin (circle) schedule: slot j of round k among R+1 slots
 __device__ __forceinline__ int rr_pos(int j, int k, int R) { return j == 0 ? 0 : 1 + (j - 1 + k) % R; }
 
+// Column copies between global memory and the shared-memory stage of a
+// Jacobi round, by the threads t = 0..nt-1 of a warp or CTA: each pass puts
+// kStageBatch loads in flight before it stores any of them. (A plain
+// load-then-store loop waits for every load in turn: the compiler cannot
+// move a load above a store through a pointer that may alias it.)
+constexpr int kStageBatch = 16;
+template <class T>
+__device__ __forceinline__ void stage_in(T* __restrict__ dst, const T* __restrict__ src, int n, int npad, int t,
+                                         int nt) {
+    for (int base = t; base < npad; base += nt * kStageBatch) {
+        T v[kStageBatch];
+#pragma unroll
+        for (int u = 0; u < kStageBatch; ++u) {
+            const int r = base + u * nt;
+            v[u] = r < n ? src[r] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kStageBatch; ++u) {
+            const int r = base + u * nt;
+            if (r < npad) dst[r] = v[u];
+        }
+    }
+}
+template <class T>
+__device__ __forceinline__ void stage_out(T* __restrict__ dst, const T* __restrict__ src, int n, int t, int nt) {
+    for (int base = t; base < n; base += nt * kStageBatch) {
+        T v[kStageBatch];
+#pragma unroll
+        for (int u = 0; u < kStageBatch; ++u) {
+            const int r = base + u * nt;
+            v[u] = r < n ? src[r] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kStageBatch; ++u) {
+            const int r = base + u * nt;
+            if (r < n) dst[r] = v[u];
+        }
+    }
+}
+
 // ------------------------------------------------ convergence per group
 // A group (matrix) stops after a sweep in which no column pair had a
 // relative off-diagonal |x_p.x_q| / (|x_p||x_q|) above thr: every pair was
@@ -156,7 +196,7 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
             const int i = item - G.pair0, k = t % R;
             // one thread decides, so the whole CTA takes the same branch
             if (threadIdx.x == 0) {
-                skip = group_done(smax, lo, R, t, kDone32);
+                skip = group_done(smax, lo, R, t, 1.0f);
                 if (k == 0 && i == 0) smax[3 * lo + (t / R + 1) % 3] = 0;
             }
             __syncthreads();
@@ -175,12 +215,19 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
                 const float* xs = X + G.x_off + (int64_t)col * L;
                 const float* vs = V + G.v_off + (int64_t)col * Nn;
                 float* d = sm + (size_t)c * stride;
-                for (int r = lane; r < lp; r += 32) d[r] = r < L ? xs[r] : 0.f;
-                for (int r = lane; r < 4 * tot4 - lp; r += 32) d[lp + r] = r < Nn ? vs[r] : 0.f;
+                stage_in(d, xs, L, lp, lane, 32);
+                stage_in(d + lp, vs, Nn, 4 * tot4 - lp, lane, 32);
             }
             __syncthreads();
             const int ne = nc + (nc & 1), Ri = ne - 1, l4 = lp >> 2;
             const float null2 = (float)(1e-12 * fro2[lo]);
+            // stop test, per column pair: float32 rotations leave every column
+            // with an absolute error of a few eps32 |M|_F, so a pair can only be
+            // made orthogonal to about floor = 64 eps32 |M|_F / min(|x_p|, |x_q|)
+            // of its norms; the target is max(kDone32, floor) and smax holds the
+            // largest ratio to it (done when below 1). Columns too small for
+            // float32 to resolve are left to the float64 polish.
+            const float flo0 = 64.f * 5.96e-8f * sqrtf((float)fro2[lo]);
             float wmax = 0.f;
             for (int ir = 0; ir < Ri; ++ir) {
                 for (int pr = warp; pr < ne / 2; pr += nwarp) {
@@ -202,8 +249,8 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
                         ga += __shfl_xor_sync(0xffffffffu, ga, o);
                     }
                     if (al <= null2 || be <= null2) continue;
-                    const float rel = fabsf(ga) / sqrtf(al * be);
-                    wmax = fmaxf(wmax, rel);
+                    const float rel = fabsf(ga) / (sqrtf(al) * sqrtf(be));
+                    wmax = fmaxf(wmax, rel / fmaxf(kDone32, flo0 * rsqrtf(fminf(al, be))));
                     if (!(rel > kTol32)) continue;
                     const float zeta = (be - al) / (2.0f * ga);
                     const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -222,14 +269,14 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
                 float* xs = X + G.x_off + (int64_t)col * L;
                 float* vs = V + G.v_off + (int64_t)col * Nn;
                 const float* d = sm + (size_t)c * stride;
-                for (int r = lane; r < L; r += 32) xs[r] = d[r];
-                for (int r = lane; r < Nn; r += 32) vs[r] = d[lp + r];
+                stage_out(xs, d, L, lane, 32);
+                stage_out(vs, d + lp, Nn, lane, 32);
             }
             if (lane == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
             __syncthreads();
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
-        if (all_done(groups, ngroups, smax, t + 1, kDone32)) { ++t; break; }
+        if (all_done(groups, ngroups, smax, t + 1, 1.0f)) { ++t; break; }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
@@ -265,6 +312,7 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                                                           const double* __restrict__ fro2, int* hist, int stride) {
     extern __shared__ double smd[];   // [2b][stride]
     __shared__ int skip;
+    __shared__ double red[3 * (kJ64Threads / 32)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned epoch = 0;
     int t = 0;
@@ -297,7 +345,7 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                 const int col = c < np ? p0 + c : q0 + (c - np);
                 const double* xs = Xg + (int64_t)col * L;
                 double* d = smd + (size_t)c * stride;
-                for (int r = lane; r < L; r += 32) d[r] = xs[r];
+                stage_in(d, xs, L, L, lane, 32);
             }
             __syncthreads();
             const int ne = nc + (nc & 1), Ri = ne - 1;
@@ -305,18 +353,32 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
             const float tol = 4.0f * sqrtf((float)L) * 1.1102230246251565e-16f;
             const float flo0 = 16.0f * 1.1102230246251565e-16f * sqrtf((float)L);
             float wmax = 0.f, hmax = 0.f;
+            // wpp warps share a column pair (their rows split), so that a block
+            // pair with fewer column pairs than warps still uses every warp
+            const int P = ne / 2;
+            int wpp = 1;
+            while (wpp * 2 * P <= nwarp) wpp *= 2;
+            const int sub = warp % wpp, nt = 32 * wpp, tp = sub * 32 + lane;
             for (int ir = 0; ir < Ri; ++ir) {
-                for (int pr = warp; pr < ne / 2; pr += nwarp) {
-                    const int a = rr_pos(pr, ir, Ri), bb = rr_pos(ne - 1 - pr, ir, Ri);
-                    if (a >= nc || bb >= nc) continue;
-                    double* xa = smd + (size_t)a * stride;
-                    double* xb = smd + (size_t)bb * stride;
+                // the same trip count in every warp, so the barriers below are uniform
+                for (int pb = 0; pb < P; pb += nwarp / wpp) {
+                    const int pr = pb + warp / wpp;
+                    int a = 0, bb = 0;
+                    if (pr < P) {
+                        a = rr_pos(pr, ir, Ri);
+                        bb = rr_pos(ne - 1 - pr, ir, Ri);
+                    }
+                    const bool act = pr < P && a < nc && bb < nc;
+                    double* xa = smd + (size_t)(act ? a : 0) * stride;
+                    double* xb = smd + (size_t)(act ? bb : 0) * stride;
                     double A = 0, B = 0, Gg = 0;
-                    for (int r = lane; r < L; r += 32) {
-                        const double u = xa[r], v = xb[r];
-                        A = fma(u, u, A);
-                        B = fma(v, v, B);
-                        Gg = fma(u, v, Gg);
+                    if (act) {
+                        for (int r = tp; r < L; r += nt) {
+                            const double u = xa[r], v = xb[r];
+                            A = fma(u, u, A);
+                            B = fma(v, v, B);
+                            Gg = fma(u, v, Gg);
+                        }
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -324,6 +386,23 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                         B += __shfl_xor_sync(0xffffffffu, B, o);
                         Gg += __shfl_xor_sync(0xffffffffu, Gg, o);
                     }
+                    if (wpp > 1) {
+                        if (lane == 0) {
+                            red[3 * warp] = A;
+                            red[3 * warp + 1] = B;
+                            red[3 * warp + 2] = Gg;
+                        }
+                        __syncthreads();
+                        const int w0 = warp - sub;
+                        A = B = Gg = 0;
+                        for (int k = 0; k < wpp; ++k) {   // fixed order: every warp of the pair gets the same sums
+                            A += red[3 * (w0 + k)];
+                            B += red[3 * (w0 + k) + 1];
+                            Gg += red[3 * (w0 + k) + 2];
+                        }
+                        __syncthreads();
+                    }
+                    if (!act) continue;
                     // every lane has the same sums: the decision is uniform
                     const float af = (float)(A * inv), bf = (float)(B * inv), gf = (float)(Gg * inv);
                     const bool live = af > 1e-28f && bf > 1e-28f;
@@ -349,7 +428,7 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                     const double dl = fma(c0, c0, s0 * s0) - 1.0;
                     const double f = 1.0 + dl * (-0.5 + 0.375 * dl);
                     const double c = c0 * f, sn = s0 * f;
-                    for (int r = lane; r < L; r += 32) {
+                    for (int r = tp; r < L; r += nt) {
                         const double u = xa[r], v = xb[r];
                         xa[r] = c * u - sn * v;
                         xb[r] = sn * u + c * v;
@@ -361,7 +440,7 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
                 const int col = c < np ? p0 + c : q0 + (c - np);
                 double* xs = Xg + (int64_t)col * L;
                 const double* d = smd + (size_t)c * stride;
-                for (int r = lane; r < L; r += 32) xs[r] = d[r];
+                stage_out(xs, d, L, lane, 32);
             }
             if (lane == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
             if (hist && lane == 0 && hmax > 0.f && t / R < 48) atomicMax(&hist[lo * 48 + t / R], __float_as_int(hmax));
@@ -720,7 +799,7 @@ int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg
     int* errp = ctx->d_flag.as<int>();
     DevBuf d_smax((size_t)3 * ng * 4), d_state(16), d_bar(16);
     reset_state(d_smax, d_state, d_bar, ng, s);
-    const int threads = kBJThreads;
+    const int threads = 32 * std::max(bmax, 4);   // one warp per column pair of an inner step
     size_t smem = (size_t)2 * bmax * stride * 4;
     CUDA_CHECK(cudaFuncSetAttribute(block_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int bpsm = 0;
@@ -840,9 +919,25 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     const int ng = (int)bg.size();
     if (ng == 0) return R;
     // one block width for all groups: up to 16 columns while a block pair
-    // (X and V columns) fits in shared memory
+    // (X and V columns) fits in shared memory. An inner step moves about
+    // 20 bytes per row and column pair through shared memory, which bounds a
+    // round on one SM when columns are long, so for columns longer than 256
+    // narrower blocks (more block pairs, more SMs) are taken while the groups
+    // give fewer block pairs than half the SMs; short columns keep wide
+    // blocks (fewer rounds, each with a fixed cost).
     bmax = kBJMaxB;
     while (bmax > 1 && (size_t)2 * bmax * stride * 4 > 200 * 1024) bmax >>= 1;
+    auto block_pairs = [&](int b) {
+        int p = 0;
+        for (const BGroup& G : bg) {
+            const int nb = (G.n + b - 1) / b;
+            p += std::max(2, nb + (nb & 1)) / 2;
+        }
+        return p;
+    };
+    int lmax32 = 0;
+    for (const BGroup& G : bg) lmax32 = std::max(lmax32, G.len);
+    while (bmax > 4 && lmax32 > 256 && block_pairs(bmax) < ctx->num_sms / 2) bmax >>= 1;
     for (auto& G : bg) {
         G.b = bmax;
         int nb = (G.n + bmax - 1) / bmax;
@@ -1074,7 +1169,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         DevBuf d_jg = upload(jg, s);
         DevBuf d_smax((size_t)3 * njg * 4), d_state(16), d_bar(16);
         reset_state(d_smax, d_state, d_bar, njg, s);
-        const int threads = 32 * b64;
+        const int threads = kJ64Threads;   // b64 < 4: several warps share a column pair
         const size_t smem64 = (size_t)2 * b64 * lmax * 8;
         CUDA_CHECK(cudaFuncSetAttribute(jacobi_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64));
         int bpsm = 0;
