@@ -190,7 +190,22 @@ def time_apply(torch, plan, x, y, prec, reps):
 PEAKS = {}
 
 
-def bench_qn_heff(ctx, torch, tnh):
+def oracle_tensor(T):
+    """The FP64 oracle's copy of a device tensor (blocks copied to the host)."""
+    from oracle.blocksparse import BlockTensor, QNIndex
+    return BlockTensor([QNIndex(i.sectors, i.arrow) for i in T.inds], T.flux, T.block_arrays())
+
+
+def oracle_matvec_seconds(L, W1, W2, R, psi):
+    """One H_eff application by the oracle on the host cores (numpy FP64)."""
+    from oracle import dmrg as D_
+    args = [oracle_tensor(T) for T in (L, W1, W2, R, psi)]
+    t0 = time.perf_counter()
+    D_.heff_apply(*args)
+    return time.perf_counter() - t0
+
+
+def bench_qn_heff(ctx, torch, tnh, oracle_kinds=()):
     out = []
     for name, kind, m, recipe, seed in QN_CONFIGS:
         L, W1, W2, R, psi = qn_heff_inputs(kind, m, recipe, seed)
@@ -221,6 +236,10 @@ def bench_qn_heff(ctx, torch, tnh):
                     "fp64": {"ms": t_64 * 1e3, "tflops": f / t_64 / 1e12},
                     "plan_ms": t_plan * 1e3,
                     "kernels_bf16x6": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}})
+        if kind in oracle_kinds:
+            t_or = oracle_matvec_seconds(L, W1, W2, R, psi)
+            out[-1]["oracle_matvec"] = {"s": t_or, "tflops": f / t_or / 1e12, "cores": blas_threads(),
+                                        "kind": "oracle", "sample": "one H_eff application"}
         plan.free()
         del L, R, psi, W1, W2, y
         torch.cuda.empty_cache()
@@ -254,7 +273,35 @@ def bench_sweeps(ctx, tnh):
     res["energy_per_bond_fp64"] = e64 / (SWEEP_N - 1)
     res["model"] = (f"U(1) Heisenberg chain N={SWEEP_N}, Neel start, maxdim "
                     f"{[m for m, _ in SWEEP_SCHEDULE]}, cutoff 1e-12, Lanczos <= 16 steps")
+    res["small"] = bench_small_sweeps(ctx, tnh)
     return res
+
+
+def bench_small_sweeps(ctx, tnh):
+    """Dense Heisenberg N=20, m=32, cutoff 1e-10, 5 sweeps from a seeded random
+    product state: the whole run on the GPU (FP64) and by the oracle."""
+    from paper_2007_14822_gb300 import models as pm, synth
+    from oracle import dmrg as D_, models as om
+    from oracle.blocksparse import BlockTensor, trivial_index
+    N = 20
+    sweeps = [(32, 1e-10)] * 5
+    vecs = synth.product_spinors(1, N, 2)
+    host = pm.heisenberg(N)
+    W = pm.to_device(host, qn=False)
+    A = pm.product_vectors(W[0].inds[3], vecs)
+    t0 = time.perf_counter()
+    E, st = ctx.dmrg(W, A, host.start, host.done, [m for m, _ in sweeps], [c for _, c in sweeps],
+                     krylov_dim=64, tol=1e-10)
+    t_gpu = time.perf_counter() - t0
+    mo = om.heisenberg_mpo(N)
+    Wo = [BlockTensor.from_dense(w.to_dense(), [trivial_index(i.dim, i.arrow, nq=1) for i in w.inds]) for w in mo.W]
+    site = trivial_index(2, +1, nq=1)
+    t0 = time.perf_counter()
+    Eo, _, _ = D_.dmrg(om.MPO(Wo, site, mo.start, mo.done), D_.product_mps_vectors(site, vecs), sweeps, 64, 1e-10)
+    t_or = time.perf_counter() - t0
+    return {"model": "dense Heisenberg N=20, m=32, cutoff 1e-10, 5 sweeps, random product start (seed 1)",
+            "gpu_fp64_s": t_gpu, "oracle_s": t_or, "oracle_cores": blas_threads(), "energy": E,
+            "energy_oracle": Eo, "dE_rel": abs(E - Eo) / abs(Eo)}
 
 
 def oracle_bond(host, k=K_LANCZOS):
@@ -406,6 +453,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the block-sparse H_eff and sweep measurements")
+    ap.add_argument("--oracle-matvec", default="heis,cyl",
+                    help="block-sparse workloads whose H_eff product is also timed on the oracle (comma list of "
+                         "heis, cyl, hub; the Hubbard one takes minutes on the host)")
     ap.add_argument("--probe", choices=["heff-u1", "heff-cyl", "heff-hub", "svd-bond"],
                     help="run one workload briefly for a profiler (no JSON line): a block-sparse H_eff plan "
                          "and three BF16x6 applications, or the bench bond up to its SVD")
@@ -490,6 +540,11 @@ def main():
         torch.cuda.synchronize()
         hs[name] = heff_flops / (a.elapsed_time(b) / 1e3 / reps) / 1e12
     plan.free()
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's product on the same dense inputs
+        t_or = oracle_matvec_seconds(bond.L, bond.W, bond.W, bond.R, bond.theta)
+        hs["oracle"] = heff_flops / t_or / 1e12
+        hs["oracle_cores"] = blas_threads()
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -538,7 +593,7 @@ def main():
             "gpu_launches": launches * args.steps, "clocks": clk.summary(), "roofline": roof,
             "heff_tflops": hs, "kernels_per_step": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
     if rank == 0 and not args.no_extra:
-        line["heff_qn"] = bench_qn_heff(ctx, torch, tnh)
+        line["heff_qn"] = bench_qn_heff(ctx, torch, tnh, tuple(k for k in args.oracle_matvec.split(",") if k))
         line["sweep"] = bench_sweeps(ctx, tnh)
     if rank == 0 and not args.no_cpu_baseline:
         cores = blas_threads()

@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 
 #include "prof.h"
@@ -26,23 +28,84 @@ void set_error(Ctx* ctx, const std::string& m) {
     g_last_error = m;
 }
 
+namespace {
+
+thread_local bool t_pool_on = false;
+thread_local cudaStream_t t_pool_stream = nullptr;
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+// The library's pool on the current device: device memory, kept after
+// release (release threshold: no limit) until trim_pool.
+cudaMemPool_t device_pool() {
+    int dev = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    CUDA_CHECK(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = ~0ull;
+    CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = pool;
+    return pool;
+}
+
+}  // namespace
+
+AllocScope::AllocScope(cudaStream_t s) : prev_on(t_pool_on), prev_s(t_pool_stream) {
+    t_pool_on = true;
+    t_pool_stream = s;
+}
+
+AllocScope::~AllocScope() {
+    t_pool_on = prev_on;
+    t_pool_stream = prev_s;
+}
+
+void trim_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) cudaMemPoolTrimTo(it->second, 0);
+}
+
 void DevBuf::alloc(size_t n) {
     release();
     if (n == 0) n = 16;
-    cudaError_t e = cudaMalloc(&p, n);
+    cudaError_t e;
+    if (t_pool_on) {
+        e = cudaMallocFromPoolAsync(&p, n, device_pool(), t_pool_stream);
+        pooled = e == cudaSuccess;
+        stream = t_pool_stream;
+    } else {
+        e = cudaMalloc(&p, n);
+        pooled = false;
+    }
     if (e != cudaSuccess) {
         p = nullptr;
+        pooled = false;
         cudaGetLastError();
         TNH_FAIL(e == cudaErrorMemoryAllocation ? TNH_ERR_OOM : TNH_ERR_CUDA,
-                 "cudaMalloc(%zu): %s", n, cudaGetErrorString(e));
+                 "device allocation of %zu bytes: %s", n, cudaGetErrorString(e));
     }
     bytes = n;
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        if (pooled) cudaFreeAsync(p, stream);
+        else cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
+    pooled = false;
 }
 
 void Workspace::ensure(DevBuf& buf, size_t bytes) {
@@ -288,7 +351,16 @@ void tnh_destroy(tnh_ctx* ctx) {
     if (!ctx) return;
     auto* c = reinterpret_cast<Ctx*>(ctx);
     cudaStreamSynchronize(c->stream);
+    const int dev = c->device;
+    cudaStream_t s = c->stream;
     delete c;
+    // hand the pool's unused memory back (buffers of live plans stay)
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) {
+        cudaStreamSynchronize(s);
+        trim_pool();
+        cudaSetDevice(cur);
+    }
 }
 
 const char* tnh_last_error(const tnh_ctx* ctx) {

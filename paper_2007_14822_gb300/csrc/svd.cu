@@ -1032,8 +1032,14 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     k32 = std::min(std::max(k32, std::max(mindim, 1)), maxdim);
     int ncand = std::min(ntot, k32 + 16 + k32 / 8);
     while (ncand < ntot && h_sig32[h_order[ncand]] >= 1e-4 * smax) ++ncand;
+    // A group of len rows has rank <= len: candidates beyond that are null
+    // vectors, which float32 only finds to its own accuracy (X v ~ eps32 |X|)
+    // and which the float64 polish would then have to purify sweep after sweep.
     std::vector<std::vector<int>> cand(ng);
-    for (int k = 0; k < ncand; ++k) cand[h_gid[h_order[k]]].push_back(h_pos[h_order[k]]);
+    for (int k = 0; k < ncand; ++k) {
+        const int g = h_gid[h_order[k]];
+        if ((int)cand[g].size() < R->len[g]) cand[g].push_back(h_pos[h_order[k]]);
+    }
     // ---- float64 re-formation Y = X64 V32[:, cand]
     std::vector<CandSet> csets;
     std::vector<int> candflat;

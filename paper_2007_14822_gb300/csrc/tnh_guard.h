@@ -12,7 +12,12 @@ void set_error(Ctx* ctx, const std::string& m);
 template <class F>
 tnh_status guard(Ctx* ctx, F&& f) {
     try {
-        f();
+        if (ctx) {
+            AllocScope scope(ctx->stream);
+            f();
+        } else {
+            f();
+        }
         return TNH_OK;
     } catch (const Error& e) {
         set_error(ctx, e.msg);

@@ -37,17 +37,37 @@ std::string strf(const char* fmt, ...);
     } while (0)
 
 // ---------------------------------------------------------- device memory
-// Owning device buffer (cudaMalloc / cudaFree; freed on destruction).
+// Owning device buffer, freed on destruction. Inside a library call on a
+// context (AllocScope) it comes from a per-device stream-ordered pool that
+// keeps freed memory for reuse: allocation and release are ordered on the
+// context's stream (cudaMallocFromPoolAsync / cudaFreeAsync), so the many
+// short-lived buffers of a DMRG step cost no device-wide synchronisation.
+// Outside a call it is a plain cudaMalloc / cudaFree.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t stream = nullptr;   // stream of a pooled allocation
+    bool pooled = false;
     DevBuf() = default;
     explicit DevBuf(size_t n) { alloc(n); }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), stream(o.stream), pooled(o.pooled) {
+        o.p = nullptr;
+        o.bytes = 0;
+        o.pooled = false;
+    }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            stream = o.stream;
+            pooled = o.pooled;
+            o.p = nullptr;
+            o.bytes = 0;
+            o.pooled = false;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
@@ -55,6 +75,15 @@ struct DevBuf {
     void release();
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
+// Pooled allocations on stream s for the lifetime of the scope (per thread).
+struct AllocScope {
+    bool prev_on;
+    cudaStream_t prev_s;
+    explicit AllocScope(cudaStream_t s);
+    ~AllocScope();
+};
+// Return the pool's cached memory of the current device to the driver.
+void trim_pool();
 
 template <class T>
 DevBuf upload(const std::vector<T>& v, cudaStream_t s) {
