@@ -221,6 +221,11 @@ tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops);
  * would, although the plan applies them fused in one pass) and the S4 GEMM
  * (sum over w2, b with R). s1 + s23 + s4 is tnh_heff_flops. */
 tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, double* s4);
+/* Diagonal of the MPO part of H_eff (the projectors excluded), DEVICE
+ * float64 [n] in the psi layout:
+ *   d[a,s1,s2,b] = sum L[a,w,a] W1[w,w1,s1,s1] W2[w1,w2,s2,s2] R[b,w2,b].
+ * Synchronises the stream. */
+tnh_status tnh_heff_diag(tnh_heff* plan, double* d);
 /* Number of float64 elements of the psi layout. */
 tnh_status tnh_heff_size(const tnh_heff* plan, int64_t* n);
 void tnh_heff_free(tnh_heff* plan);
@@ -235,6 +240,14 @@ void tnh_heff_free(tnh_heff* plan);
  * Synchronises the context's stream once per iteration. */
 tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol,
                         double* energy, double* resid, int32_t* matvecs);
+/* Lowest eigenpair of H_eff by Davidson: the subspace grows by the
+ * correction (theta - D)^-1 r of the Ritz pair (theta, u), r = H u - theta u,
+ * D the diagonal of the MPO part of H_eff, orthogonalised twice against the
+ * subspace. The projected matrix is solved by float64 Jacobi on the device.
+ * Same arguments, stop rule (|r| <= tol * max(1, |E|)) and final float64
+ * energy and residual as tnh_eigsolve; krylov_dim <= 48. */
+tnh_status tnh_eigsolve_davidson(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol,
+                                 double* energy, double* resid, int32_t* matvecs);
 
 /* ---- environment update ------------------------------------------------ */
 
@@ -298,6 +311,7 @@ typedef struct {
     double lanczos_tol;
     int32_t precision;       /* tnh_precision of the Lanczos matvecs */
     int32_t env_precision;   /* tnh_precision of theta and the environments */
+    int32_t eigensolver;     /* 0: Lanczos (tnh_eigsolve), 1: Davidson (tnh_eigsolve_davidson) */
 } tnh_sweep_params;
 
 typedef struct {

@@ -174,6 +174,7 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
     const tnh_precision eprec = (tnh_precision)p->env_precision;
     TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad precision");
     TNH_REQUIRE(eprec == TNH_FP64 || planes_of(eprec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad env precision");
+    TNH_REQUIRE(p->eigensolver == 0 || p->eigensolver == 1, TNH_ERR_ARG, "tnh_dmrg: eigensolver %d", p->eigensolver);
     CUDA_CHECK(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
     const int T = (int)pr.W.size();
@@ -298,7 +299,8 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
                     }
                     ph[1] += since(tp);
                     tp = clk::now();
-                    EigResult r = eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
+                    EigResult r = p->eigensolver == 1 ? davidson(*P, th.L.data, p->krylov_dim, p->lanczos_tol)
+                                                      : eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
                     ph[2] += since(tp);
                     E = r.energy;
                     resid = r.resid;

@@ -106,6 +106,58 @@ std::vector<MpoEntry> mpo_entries(const Layout& W, cudaStream_t s) {
     return out;
 }
 
+// ---- diagonal of H_eff (the preconditioner of the Davidson eigensolver)
+//   diag[a,s1,s2,b] = sum_(w,w2) Ld[a,w] W12[(w,s1,s2) -> (w2,s1,s2)] Rd[b,w2]
+// with Ld[a,w] = L[a,w,a] and Rd[b,w2] = R[b,w2,b].
+struct EnvDiagSeg {
+    int64_t src;     // block (S, w-sector, S) of L or R
+    int D, Dw;       // its sector dimensions
+    int64_t dst;     // element (row a_off, column w_off) of the dense [m][w] diagonal
+    int ld;          // that array's row pitch (w total)
+};
+struct DiagBlock {
+    int64_t off;                   // psi block
+    int Da, d1, d2, Db;
+    int a_off, b_off, s1_off, s2_off;
+};
+struct DiagTerm {
+    int w, z;
+    double c;
+};
+
+__global__ void env_diag_kernel(const EnvDiagSeg* __restrict__ segs, const double* __restrict__ E,
+                                double* __restrict__ out) {
+    const EnvDiagSeg g = segs[blockIdx.x];
+    const int n = g.D * g.Dw;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int i = e / g.Dw, x = e - i * g.Dw;
+        out[g.dst + (int64_t)i * g.ld + x] = E[g.src + ((int64_t)i * g.Dw + x) * g.D + i];
+    }
+}
+
+__global__ void heff_diag_kernel(const DiagBlock* __restrict__ blocks, const int* __restrict__ tstart,
+                                 const DiagTerm* __restrict__ terms, const double* __restrict__ Ld,
+                                 const double* __restrict__ Rd, int wdim, int zdim, int d2tot,
+                                 double* __restrict__ diag) {
+    const DiagBlock B = blocks[blockIdx.y];
+    const int64_t n = (int64_t)B.Da * B.d1 * B.d2 * B.Db;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e;
+        const int k = (int)(r % B.Db);
+        r /= B.Db;
+        const int u2 = (int)(r % B.d2);
+        r /= B.d2;
+        const int u1 = (int)(r % B.d1);
+        const int i = (int)(r / B.d1);
+        const int ss = (B.s1_off + u1) * d2tot + B.s2_off + u2;
+        const double* lrow = Ld + (int64_t)(B.a_off + i) * wdim;
+        const double* rrow = Rd + (int64_t)(B.b_off + k) * zdim;
+        double acc = 0.0;
+        for (int t = tstart[ss]; t < tstart[ss + 1]; ++t) acc = fma(terms[t].c, lrow[terms[t].w] * rrow[terms[t].z], acc);
+        diag[B.off + e] = acc;
+    }
+}
+
 // Collects the segments of one gather job and orders them by tile.
 struct JobBuilder {
     struct Task { int64_t tile0; int mt, kt; };
@@ -585,6 +637,65 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                 w12[{kv.first[0], kv.first[1], kv.first[2]}].push_back({kv.first[3], kv.first[4], kv.first[5], kv.second});
     }
 
+    // ---------------- diagonal of H_eff: environment diagonals and the
+    // diagonal W12 entries (s1' = s1, s2' = s2) per (s1, s2)
+    {
+        const int wdim = (int)iw.total, zdim = (int)iz.total;
+        const int d1tot = (int)is1.total, d2tot = (int)is2.total;
+        std::vector<std::vector<DiagTerm>> per(d1tot * d2tot);
+        for (auto& kv : w12)
+            for (const W12Term& e : kv.second)
+                if (e.s1 == kv.first[1] && e.s2 == kv.first[2])
+                    per[e.s1 * d2tot + e.s2].push_back(DiagTerm{e.x, kv.first[0], e.v});
+        std::vector<int> tstart(1, 0);
+        std::vector<DiagTerm> terms;
+        for (auto& v : per) {
+            terms.insert(terms.end(), v.begin(), v.end());
+            tstart.push_back((int)terms.size());
+        }
+        std::vector<EnvDiagSeg> ls, rs;
+        for (int b = 0; b < L.nblocks(); ++b) {
+            const int A = L.sect[(size_t)b * 3], Sx = L.sect[(size_t)b * 3 + 1], Ap = L.sect[(size_t)b * 3 + 2];
+            if (A != Ap) continue;
+            ls.push_back(EnvDiagSeg{L.off[b], L.bdim(b, 0), L.bdim(b, 1), ia.off[A] * wdim + iw.off[Sx], wdim});
+        }
+        for (int b = 0; b < R.nblocks(); ++b) {
+            const int B = R.sect[(size_t)b * 3], Sz = R.sect[(size_t)b * 3 + 1], Bp = R.sect[(size_t)b * 3 + 2];
+            if (B != Bp) continue;
+            rs.push_back(EnvDiagSeg{R.off[b], R.bdim(b, 0), R.bdim(b, 1), ib.off[B] * zdim + iz.off[Sz], zdim});
+        }
+        std::vector<DiagBlock> db;
+        for (int b = 0; b < X.nblocks(); ++b) {
+            const int* k = &X.sect[(size_t)b * 4];
+            db.push_back(DiagBlock{X.off[b], X.bdim(b, 0), X.bdim(b, 1), X.bdim(b, 2), X.bdim(b, 3),
+                                   (int)ia.off[k[0]], (int)ib.off[k[3]], (int)is1.off[k[1]], (int)is2.off[k[2]]});
+        }
+        P->dg_wdim = wdim;
+        P->dg_zdim = zdim;
+        P->dg_d2 = d2tot;
+        P->dg_nblocks = (int)db.size();
+        P->dg_maxblock = 0;
+        for (const DiagBlock& d : db)
+            P->dg_maxblock = std::max<int64_t>(P->dg_maxblock, (int64_t)d.Da * d.d1 * d.d2 * d.Db);
+        P->Ld.alloc((size_t)std::max<int64_t>(ia.total * wdim, 1) * sizeof(double));
+        P->Rd.alloc((size_t)std::max<int64_t>(ib.total * zdim, 1) * sizeof(double));
+        CUDA_CHECK(cudaMemsetAsync(P->Ld.p, 0, P->Ld.bytes, s));
+        CUDA_CHECK(cudaMemsetAsync(P->Rd.p, 0, P->Rd.bytes, s));
+        DevBuf d_ls = upload(ls, s), d_rs = upload(rs, s);
+        if (!ls.empty()) {
+            KScope ks("heff_env_diag", s);
+            env_diag_kernel<<<(unsigned)ls.size(), 128, 0, s>>>(d_ls.as<EnvDiagSeg>(), L.data, P->Ld.as<double>());
+        }
+        if (!rs.empty()) {
+            KScope ks("heff_env_diag", s);
+            env_diag_kernel<<<(unsigned)rs.size(), 128, 0, s>>>(d_rs.as<EnvDiagSeg>(), R.data, P->Rd.as<double>());
+        }
+        P->d_dblocks = upload(db, s);
+        P->d_dstart = upload(tstart, s);
+        P->d_dterms = upload(terms, s);
+        CUDA_CHECK(cudaStreamSynchronize(s));   // d_ls, d_rs are freed on scope exit
+    }
+
     // ---------------- S4: one task per b'-sector; fused S2+S3 fills operand A
     JobBuilder bR;
     CellBuilder bW;
@@ -852,6 +963,22 @@ void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y) {
     add_projectors(P, x, y);
 }
 
+const double* heff_diag(HeffPlan& P) {
+    if (P.diag.p) return P.diag.as<double>();
+    cudaStream_t s = P.stream;
+    P.diag.alloc((size_t)std::max<int64_t>(P.n, 1) * sizeof(double));
+    CUDA_CHECK(cudaMemsetAsync(P.diag.p, 0, P.diag.bytes, s));
+    if (P.dg_nblocks > 0) {
+        const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (P.dg_maxblock + 255) / 256), 64);
+        KScope ks("heff_diag", s);
+        heff_diag_kernel<<<dim3(gx, (unsigned)P.dg_nblocks), 256, 0, s>>>(
+            P.d_dblocks.as<DiagBlock>(), P.d_dstart.as<int>(), P.d_dterms.as<DiagTerm>(), P.Ld.as<double>(),
+            P.Rd.as<double>(), P.dg_wdim, P.dg_zdim, P.dg_d2, P.diag.as<double>());
+    }
+    CUDA_CHECK(cudaGetLastError());
+    return P.diag.as<double>();
+}
+
 }  // namespace tnh
 
 using namespace tnh;
@@ -921,6 +1048,17 @@ tnh_status tnh_heff_apply_prec(tnh_heff* plan, tnh_precision prec, const double*
         TNH_REQUIRE(P && x && y, TNH_ERR_ARG, "tnh_heff_apply_prec: NULL argument");
         TNH_REQUIRE(x != y, TNH_ERR_ARG, "tnh_heff_apply_prec: x and y alias");
         heff_apply(*P, prec, x, y);
+    });
+}
+
+tnh_status tnh_heff_diag(tnh_heff* plan, double* d) {
+    auto* P = reinterpret_cast<HeffPlan*>(plan);
+    return guard(P ? P->ctx : nullptr, [&] {
+        TNH_REQUIRE(P && d, TNH_ERR_ARG, "tnh_heff_diag: NULL argument");
+        const double* src = heff_diag(*P);
+        if (P->n > 0)
+            CUDA_CHECK(cudaMemcpyAsync(d, src, (size_t)P->n * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+        CUDA_CHECK(cudaStreamSynchronize(P->stream));
     });
 }
 

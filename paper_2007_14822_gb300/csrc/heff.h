@@ -76,6 +76,12 @@ struct HeffPlan {
     DevBuf proj;            // [nproj][n]
     DevBuf pcoef;           // [nproj] device scalars
     VecWork pvw;
+    // diagonal of H_eff (Davidson preconditioner): environment diagonals
+    // Ld [a][w], Rd [b][w2] taken when the plan is made, per-block and
+    // per-(s1, s2) tables; the diagonal itself is formed on first use
+    DevBuf Ld, Rd, d_dblocks, d_dstart, d_dterms, diag;
+    int dg_wdim = 0, dg_zdim = 0, dg_d2 = 0, dg_nblocks = 0;
+    int64_t dg_maxblock = 0;
     ~HeffPlan();
 };
 
@@ -84,6 +90,8 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                                     const Layout& R, const Layout& psi, tnh_precision prec);
 // H_eff (of the plan's MPO terms) plus the projectors, if any.
 void heff_apply(HeffPlan& P, tnh_precision prec, const double* x, double* y);
+// Diagonal of the MPO part of H_eff (device [P.n], float64), formed once.
+const double* heff_diag(HeffPlan& P);
 // Replace the projectors: phi is DEVICE [k][P.n] (copied), weight the penalty.
 void set_projectors(HeffPlan& P, int k, const double* phi, double weight);
 // y += P.pweight * sum_i phi_i <phi_i, x> (float64, deterministic).
@@ -95,6 +103,8 @@ struct EigResult {
 };
 // Lanczos on the plan; psi (device, length P.n) in/out.
 EigResult eigsolve(HeffPlan& P, double* psi, int krylov_dim, double tol);
+// Davidson with the diagonal preconditioner; same contract as eigsolve.
+EigResult davidson(HeffPlan& P, double* psi, int krylov_dim, double tol);
 
 void vdot(Ctx* ctx, VecWork& w, const double* x, const double* y, int64_t n, double* d_out);
 void vscale_copy(Ctx* ctx, const double* x, double* y, int64_t n, const double* d_num, const double* d_den,

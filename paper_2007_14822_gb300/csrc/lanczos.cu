@@ -274,6 +274,129 @@ __global__ void set_beta(const double* __restrict__ alpha_j, const double* __res
     }
 }
 
+// ---- Davidson helpers
+constexpr int kDavMax = 48;   // largest subspace of the Davidson eigensolver
+
+// T[i][j] = T[j][i] = h[i] for i <= j (new column of the projected matrix)
+__global__ void set_column(double* __restrict__ T, int ld, int j, const double* __restrict__ h) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        T[(int64_t)i * ld + j] = h[i];
+        T[(int64_t)j * ld + i] = h[i];
+    }
+}
+
+// Lowest eigenpair of the symmetric k x k matrix T (row pitch ld) by cyclic
+// two-sided Jacobi in float64 (one CTA): the pairs of one step are disjoint,
+// so all their column rotations run together, then all row rotations.
+// out[0] = lowest eigenvalue, s[0..k) its unit eigenvector.
+__global__ void __launch_bounds__(256) small_eigh_lowest(const double* __restrict__ T, int k, int ld,
+                                                         double* __restrict__ out, double* __restrict__ s) {
+    __shared__ double A[kDavMax][kDavMax + 1], V[kDavMax][kDavMax + 1];
+    __shared__ double cs[kDavMax / 2], sn[kDavMax / 2];
+    __shared__ int pp[kDavMax / 2], qq[kDavMax / 2];
+    __shared__ double red[256];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < k * k; e += nt) {
+        const int i = e / k, j = e - i * k;
+        A[i][j] = T[(int64_t)i * ld + j];
+        V[i][j] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int ke = k + (k & 1), R = ke - 1, np = ke / 2;
+    for (int sweep = 0; sweep < 30 && k > 1; ++sweep) {
+        // off-diagonal and total Frobenius weight (fixed-order reduction)
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < k * k; e += nt) {
+            const int i = e / k, j = e - i * k;
+            const double a2 = A[i][j] * A[i][j];
+            tot += a2;
+            if (i != j) off += a2;
+        }
+        red[tid] = off;
+        __syncthreads();
+        for (int o = nt / 2; o > 0; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        const double offs = red[0];
+        __syncthreads();
+        red[tid] = tot;
+        __syncthreads();
+        for (int o = nt / 2; o > 0; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        const double tots = red[0];
+        __syncthreads();
+        if (!(offs > 1e-30 * tots)) break;
+        for (int st = 0; st < R; ++st) {
+            if (tid < np) {
+                const int a = tid == 0 ? 0 : 1 + (tid - 1 + st) % R;
+                const int b = (ke - 1 - tid) == 0 ? 0 : 1 + (ke - 1 - tid - 1 + st) % R;
+                const int p = min(a, b), q = max(a, b);
+                double c = 1.0, sv = 0.0;
+                if (q < k && A[p][q] != 0.0) {
+                    const double tau = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + t * t);
+                    sv = t * c;
+                }
+                pp[tid] = p;
+                qq[tid] = q < k ? q : p;
+                cs[tid] = c;
+                sn[tid] = q < k ? sv : 0.0;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int e = tid; e < np * k; e += nt) {
+                const int r = e / k, i = e - r * k;
+                const int p = pp[r], q = qq[r];
+                if (p == q) continue;
+                const double c = cs[r], sv = sn[r];
+                const double ap = A[i][p], aq = A[i][q];
+                A[i][p] = c * ap - sv * aq;
+                A[i][q] = sv * ap + c * aq;
+                const double vp = V[i][p], vq = V[i][q];
+                V[i][p] = c * vp - sv * vq;
+                V[i][q] = sv * vp + c * vq;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int e = tid; e < np * k; e += nt) {
+                const int r = e / k, j = e - r * k;
+                const int p = pp[r], q = qq[r];
+                if (p == q) continue;
+                const double c = cs[r], sv = sn[r];
+                const double ap = A[p][j], aq = A[q][j];
+                A[p][j] = c * ap - sv * aq;
+                A[q][j] = sv * ap + c * aq;
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        int m = 0;
+        for (int i = 1; i < k; ++i)
+            if (A[i][i] < A[m][m]) m = i;
+        out[0] = A[m][m];
+        red[0] = (double)m;
+    }
+    __syncthreads();
+    const int m = (int)red[0];
+    for (int i = tid; i < k; i += nt) s[i] = V[i][m];
+}
+
+// t = r / (theta - d), the denominator kept away from zero
+__global__ void davidson_precondition(const double* __restrict__ r, const double* __restrict__ d,
+                                      const double* __restrict__ theta, double* __restrict__ t, int64_t n) {
+    const double th = *theta, floor = 1e-8 * fmax(1.0, fabs(th));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double den = th - d[i];
+        if (fabs(den) < floor) den = den < 0.0 ? -floor : floor;
+        t[i] = r[i] / den;
+    }
+}
+
 int grid_for(int64_t n, int nsms) {
     int64_t g = (n + 255) / 256;
     int64_t cap = (int64_t)nsms * 8;
@@ -441,9 +564,133 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
     return res;
 }
 
+EigResult davidson(HeffPlan& P, double* psi, int kmax, double tol) {
+    Ctx* ctx = P.ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P.n;
+    TNH_REQUIRE(kmax >= 1 && kmax <= kDavMax, TNH_ERR_ARG, "davidson: krylov_dim %d out of 1..%d", kmax, kDavMax);
+    EigResult res;
+    if (n == 0) return res;
+    const double* diag = heff_diag(P);
+    VecWork vw;
+    vw.ensure(ctx->num_sms);
+    DevBuf Q((size_t)kmax * n * sizeof(double)), HQ((size_t)kmax * n * sizeof(double));
+    DevBuf rv((size_t)n * sizeof(double)), tv((size_t)n * sizeof(double)), yv((size_t)n * sizeof(double));
+    DevBuf Tm((size_t)kmax * kmax * sizeof(double));
+    // scalars: h[kmax] sv[kmax] theta, |r|^2, |t|^2, misc
+    DevBuf sc((size_t)(2 * kmax + 16) * sizeof(double));
+    double* h = sc.as<double>();
+    double* sv = h + kmax;
+    double* misc = sv + kmax;   // [0] theta [1] |r|^2 [2] |t|^2 [3] |psi|^2 [4] E [5] |res|^2 [6] |t0|^2
+    double* q = Q.as<double>();
+    double* hq = HQ.as<double>();
+    double* r = rv.as<double>();
+    double* t = tv.as<double>();
+    const int g = grid_for(n, ctx->num_sms);
+    auto norm2 = [&](const double* x, double* out) { vdot(ctx, vw, x, x, n, out); };
+    auto dots = [&](const double* basis, int k, const double* x, double* out) {
+        { KScope ks_("multidot_partial", s);
+        multidot_partial<<<dim3(vw.blocks, k), kRedThreads, 0, s>>>(basis, n, x, n, vw.partial.as<double>());
+        }
+        { KScope ks_("reduce_partials", s);
+        reduce_partials<<<k, kRedThreads, 0, s>>>(vw.partial.as<double>(), vw.blocks, out);
+        }
+    };
+    auto combine = [&](double* out, const double* basis, int k, const double* c, double sign, int overwrite) {
+        KScope ks_("multi_axpy", s);
+        multi_axpy<<<g, 256, 0, s>>>(out, basis, n, k, c, sign, overwrite, n);
+    };
+    norm2(psi, misc + 3);
+    double hn2 = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&hn2, misc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    TNH_REQUIRE(std::isfinite(hn2) && hn2 > 0.0, TNH_ERR_NUMERIC, "davidson: start vector has norm^2 %g", hn2);
+    { KScope ks_("scale_copy", s);
+    scale_copy<<<g, 256, 0, s>>>(psi, q, n, nullptr, misc + 3, 1);
+    }
+    int k = 0;
+    for (int j = 0; j < kmax; ++j) {
+        double* qj = q + (int64_t)j * n;
+        heff_apply(P, P.prec, qj, hq + (int64_t)j * n);
+        k = j + 1;
+        // new column of T = Q^T H Q, lowest Ritz pair (theta, s)
+        dots(q, k, hq + (int64_t)j * n, h);
+        { KScope ks_("davidson_set_column", s);
+        set_column<<<1, 64, 0, s>>>(Tm.as<double>(), kmax, j, h);
+        }
+        { KScope ks_("davidson_small_eigh", s);
+        small_eigh_lowest<<<1, 256, 0, s>>>(Tm.as<double>(), k, kmax, misc, sv);
+        }
+        // u = Q s (into psi), r = H Q s - theta u
+        combine(psi, q, k, sv, 1.0, 1);
+        combine(r, hq, k, sv, 1.0, 1);
+        { KScope ks_("axpy_dev", s);
+        axpy_dev<<<g, 256, 0, s>>>(r, psi, misc, n);
+        }
+        norm2(r, misc + 1);
+        double host[2];
+        CUDA_CHECK(cudaMemcpyAsync(host, misc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+        TNH_REQUIRE(std::isfinite(host[0]) && std::isfinite(host[1]), TNH_ERR_NUMERIC,
+                    "davidson: non-finite Ritz value at step %d", j);
+        const double scale = std::max(1.0, std::fabs(host[0]));
+        if (j + 1 == kmax || (tol > 0.0 && std::sqrt(std::max(host[1], 0.0)) <= tol * scale)) break;
+        // correction t = (theta - D)^-1 r, orthogonalised twice against Q
+        { KScope ks_("davidson_precondition", s);
+        davidson_precondition<<<g, 256, 0, s>>>(r, diag, misc, t, n);
+        }
+        norm2(t, misc + 6);
+        for (int rep = 0; rep < 2; ++rep) {
+            dots(q, k, t, h);
+            combine(t, q, k, h, -1.0, 0);
+        }
+        norm2(t, misc + 2);
+        double tn[5];
+        CUDA_CHECK(cudaMemcpyAsync(tn, misc + 2, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+        // no new direction: the correction lies in the subspace to rounding
+        if (!(tn[0] > 1e-24 * tn[4]) || !(tn[0] > 0.0)) break;
+        { KScope ks_("scale_copy", s);
+        scale_copy<<<g, 256, 0, s>>>(t, q + (int64_t)(j + 1) * n, n, nullptr, misc + 2, 1);
+        }
+    }
+    // normalised Ritz vector in psi, float64 energy and residual
+    norm2(psi, misc + 3);
+    { KScope ks_("scale_copy", s);
+    scale_copy<<<g, 256, 0, s>>>(psi, psi, n, nullptr, misc + 3, 1);
+    }
+    double* y = yv.as<double>();
+    heff_apply(P, TNH_FP64, psi, y);
+    vdot(ctx, vw, psi, y, n, misc + 4);
+    { KScope ks_("axpy_dev", s);
+    axpy_dev<<<g, 256, 0, s>>>(y, psi, misc + 4, n);
+    }
+    vdot(ctx, vw, y, y, n, misc + 5);
+    double fin[2];
+    CUDA_CHECK(cudaMemcpyAsync(fin, misc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    check_device_flag(ctx);
+    res.energy = fin[0];
+    res.resid = std::sqrt(std::max(fin[1], 0.0));
+    res.matvecs = k;
+    return res;
+}
+
 }  // namespace tnh
 
 using namespace tnh;
+
+extern "C" tnh_status tnh_eigsolve_davidson(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol,
+                                            double* energy, double* resid, int32_t* matvecs) {
+    auto* P = reinterpret_cast<HeffPlan*>(plan);
+    return guard(P ? P->ctx : nullptr, [&] {
+        TNH_REQUIRE(P && psi, TNH_ERR_ARG, "tnh_eigsolve_davidson: NULL argument");
+        EigResult r = davidson(*P, psi, krylov_dim, tol);
+        if (energy) *energy = r.energy;
+        if (resid) *resid = r.resid;
+        if (matvecs) *matvecs = r.matvecs;
+    });
+}
 
 extern "C" tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol, double* energy,
                                    double* resid, int32_t* matvecs) {

@@ -29,7 +29,7 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_heff_free", "tnh_eigsolve", "tnh_env_update", "tnh_svd_trunc", "tnh_svd_info",
            "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
            "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
-           "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get"]
+           "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag"]
 
 
 class TnhError(RuntimeError):
@@ -52,7 +52,7 @@ class tnh_tensor(C.Structure):
 class tnh_sweep_params(C.Structure):
     _fields_ = [("nsweep", C.c_int32), ("maxdim", C.POINTER(C.c_int32)), ("cutoff", C.POINTER(C.c_double)),
                 ("mindim", C.c_int32), ("krylov_dim", C.c_int32), ("lanczos_tol", C.c_double),
-                ("precision", C.c_int32), ("env_precision", C.c_int32)]
+                ("precision", C.c_int32), ("env_precision", C.c_int32), ("eigensolver", C.c_int32)]
 
 
 class tnh_sweep_stat(C.Structure):
@@ -97,6 +97,8 @@ def lib():
         "tnh_heff_size": (i32, [vp, P(i64)]),
         "tnh_heff_free": (None, [vp]),
         "tnh_eigsolve": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
+        "tnh_eigsolve_davidson": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
+        "tnh_heff_diag": (i32, [vp, vp]),
         "tnh_env_update": (i32, [vp, i32, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), C.c_int]),
         "tnh_svd_trunc": (i32, [vp, P(tnh_tensor), i32, dbl, i32, i32, i32, P(vp)]),
         "tnh_svd_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(dbl)]),
@@ -362,7 +364,7 @@ class Context:
         return res
 
     def dmrg(self, mpo, mps, start, done, maxdim, cutoff, mindim=1, krylov_dim=32, tol=1e-10,
-             prec=FP64, env_prec=FP64, ortho=(), weight=1.0):
+             prec=FP64, env_prec=FP64, ortho=(), weight=1.0, eigensolver="lanczos"):
         """Two-site DMRG sweeps. ``mpo`` is one MPO (list of site tensors) or,
         with ``start``/``done`` lists, a list of MPOs whose sum is H;
         ``ortho`` lists previous states (MPS) to stay orthogonal to, with the
@@ -373,7 +375,8 @@ class Context:
         md = (C.c_int32 * ns)(*maxdim)
         co = (C.c_double * ns)(*cutoff)
         p = tnh_sweep_params(ns, C.cast(md, C.POINTER(C.c_int32)), C.cast(co, C.POINTER(C.c_double)),
-                             int(mindim), int(krylov_dim), float(tol), int(prec), int(env_prec))
+                             int(mindim), int(krylov_dim), float(tol), int(prec), int(env_prec),
+                             {"lanczos": 0, "davidson": 1}[eigensolver])
         stats = (tnh_sweep_stat * ns)()
         e = C.c_double()
         terms = isinstance(start, (list, tuple))
@@ -458,6 +461,11 @@ class Heff:
         self.ctx.check(self.ctx._lib.tnh_heff_size(self.h, C.byref(n)))
         return n.value
 
+    def diag(self, out):
+        """Diagonal of the MPO part of H_eff into ``out`` (CUDA float64 [n])."""
+        self.ctx.check(self.ctx._lib.tnh_heff_diag(self.h, _ptr(out)))
+        return out
+
     def set_projectors(self, phi, weight):
         """Add weight * phi_i <phi_i, x> to every product (phi: CUDA float64
         [k, n], or None to remove)."""
@@ -468,10 +476,10 @@ class Heff:
         self.ctx.check(self.ctx._lib.tnh_heff_set_projectors(self.h, int(k), _ptr(phi.contiguous()),
                                                              float(weight)))
 
-    def eigsolve(self, psi, krylov_dim=64, tol=1e-10):
+    def eigsolve(self, psi, krylov_dim=64, tol=1e-10, method="lanczos"):
         e, r, k = C.c_double(), C.c_double(), C.c_int32()
-        self.ctx.check(self.ctx._lib.tnh_eigsolve(self.h, _ptr(psi), int(krylov_dim), float(tol),
-                                                  C.byref(e), C.byref(r), C.byref(k)))
+        f = {"lanczos": self.ctx._lib.tnh_eigsolve, "davidson": self.ctx._lib.tnh_eigsolve_davidson}[method]
+        self.ctx.check(f(self.h, _ptr(psi), int(krylov_dim), float(tol), C.byref(e), C.byref(r), C.byref(k)))
         return e.value, r.value, k.value
 
 

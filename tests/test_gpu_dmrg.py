@@ -235,3 +235,18 @@ def test_dmrg_checkpoint_resume(ctx):
     for T, h in zip(ck, ck_host):
         for k, v in T.block_arrays().items():
             np.testing.assert_array_equal(v, h[k])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_dmrg_davidson_heisenberg_qn(ctx, prec):
+    # the sweeps with the Davidson eigensolver reach the oracle's / ED energy
+    from paper_2007_14822_gb300 import tnh
+    N = 12
+    host = pm.heisenberg(N)
+    W = pm.to_device(host, qn=True)
+    A = pm.product_state(W[0].inds[3], [0, 1] * (N // 2))
+    sweeps = [(8, 1e-12), (32, 1e-12), (64, 1e-13), (64, 1e-13)]
+    E, st = ctx.dmrg(W, A, host.start, host.done, [m for m, _ in sweeps], [c for _, c in sweeps], krylov_dim=32,
+                     tol=1e-10 if prec == "fp64" else 1e-7, prec=tnh.PRECISION[prec], eigensolver="davidson")
+    e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)), om.SPIN_QN, (0,))
+    assert abs(E - e_ed) < 1e-9 * abs(e_ed), (E, e_ed)

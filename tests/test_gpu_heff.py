@@ -310,3 +310,49 @@ def test_heff_projectors_added(ctx, p):
     yt.data = y
     want0 = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
     assert H.rel_err(H.to_oracle(yt), want0) < TOL[p]
+
+
+# ------------------------------------------------- diagonal and Davidson
+@pytest.mark.parametrize("m,nsect,maxd", [(6, 1, 6), (12, 5, 4)])
+def test_heff_diag_matches_dense_matrix(ctx, m, nsect, maxd):
+    import torch
+    d = H.heff_inputs(m, None, 19, nsect=nsect, maxd=maxd)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec("fp64"))
+    out = torch.zeros(plan.size, dtype=torch.float64, device="cuda")
+    plan.diag(out)
+    Hm = D.heff_dense_matrix(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    np.testing.assert_allclose(out.cpu().numpy(), np.diag(Hm), rtol=0, atol=1e-12 * np.abs(Hm).max())
+
+
+def test_heff_diag_distinct_mpo_qn(ctx):
+    # W1 != W2 on a QN link (J1-J2 long-range MPO, sites 3 and 4)
+    import torch
+    from paper_2007_14822_gb300 import models as pm
+    mpo = pm.to_device(pm.j1j2_chain(8, 1.0, 0.5), qn=True)
+    W1, W2 = mpo[3], mpo[4]
+    a = H.link_index(10, 3, 4, +1)
+    L, Lo = H.random_pair([a.dag(), W1.inds[0].dag(), a], None, 71, "L")
+    R, Ro = H.random_pair([a, W2.inds[1].dag(), a.dag()], None, 72, "R")
+    psi, psio = H.random_pair([a, W1.inds[3], W2.inds[3], a.dag()], None, 73, "psi")
+    plan = ctx.heff_plan(L, W1, W2, R, psi, prec("fp64"))
+    out = torch.zeros(plan.size, dtype=torch.float64, device="cuda")
+    plan.diag(out)
+    Hm = D.heff_dense_matrix(Lo, H.to_oracle(W1), H.to_oracle(W2), Ro, psio)
+    np.testing.assert_allclose(out.cpu().numpy(), np.diag(Hm), rtol=0, atol=1e-12 * np.abs(Hm).max())
+
+
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("nsect", [1, 5])
+def test_davidson_matches_eigh(ctx, p, nsect):
+    m = 20 if nsect == 1 else 24
+    d = H.heff_inputs(m, None, 13, nsect=nsect, maxd=8 if nsect > 1 else None, symmetric=True)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    Hm = D.heff_dense_matrix(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    w, v = np.linalg.eigh(0.5 * (Hm + Hm.T))
+    psi = d["psi"].data.clone()
+    E, r, k = plan.eigsolve(psi, krylov_dim=48, tol=1e-9 if p == "fp64" else 1e-6, method="davidson")
+    scale = abs(w[0])
+    assert abs(E - w[0]) < 1e-9 * scale, (E, w[0], k)
+    x = psi[:plan.size].cpu().numpy()
+    assert abs(float(x @ v[:, 0])) > 1 - (1e-10 if p == "fp64" else 1e-7)
+    assert r < (1e-8 if p == "fp64" else 1e-5) * scale
