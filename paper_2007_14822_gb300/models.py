@@ -227,6 +227,50 @@ def to_device(mpo, qn=True):
     return out
 
 
+def splitblocks(mpo, qn=True):
+    """MPO as device tensors in the sparse form of ``splitblocks`` (Sec. 12.2):
+    every link state is a sector of its own (dimension 1, its charge, or the
+    trivial charge without ``qn``) and only the blocks holding a nonzero
+    entry are stored. The site index keeps the layout of ``to_device``.
+    H_eff applies only nonzero MPO entries either way; the environment
+    update's contraction with W then skips the zero blocks too."""
+    from .tnh import Index, Tensor
+    nq = len(mpo.site_qn[0])
+    s = site_index(mpo.site_qn, qn)
+    zero = (0,) * nq
+    out = []
+    for j, W in enumerate(mpo.W):
+        wl = Index([(q if qn else zero, 1) for q in mpo.link_qn[j]], -1)
+        wr = Index([(q if qn else zero, 1) for q in mpo.link_qn[j + 1]], +1)
+        inds = [wl, wr, s.dag(), s]
+        soff = np.cumsum([0] + [d for _, d in s.sectors])
+        blocks, offs, data = [], [], []
+        pos = 0
+        for a in range(W.shape[0]):
+            for b in range(W.shape[1]):
+                for u in range(s.nsect):
+                    for v in range(s.nsect):
+                        blk = W[a, b, soff[u]:soff[u + 1], soff[v]:soff[v + 1]]
+                        if not np.any(blk != 0.0):
+                            continue
+                        if qn:
+                            # the block must carry the tensor's (zero) flux
+                            f = tuple(-x + y - p + q for x, y, p, q in
+                                      zip(wl.sectors[a][0], wr.sectors[b][0], s.sectors[u][0], s.sectors[v][0]))
+                            if any(f):
+                                raise ValueError(f"MPO site {j} has weight outside its allowed blocks")
+                        blocks.append((a, b, u, v))
+                        offs.append(pos)
+                        data.append(blk.ravel())
+                        pos += blk.size
+        T = Tensor(inds, None, blocks=blocks, offsets=offs)
+        host = np.concatenate(data) if data else np.zeros(1)
+        import torch
+        T.data = torch.from_numpy(np.ascontiguousarray(host)).to(T.data.device)
+        out.append(T)
+    return out
+
+
 def product_state(site, states):
     """MPS (list of tnh.Tensor [left, s, right]) of a product of basis states.
 

@@ -250,3 +250,26 @@ def test_dmrg_davidson_heisenberg_qn(ctx, prec):
                      tol=1e-10 if prec == "fp64" else 1e-7, prec=tnh.PRECISION[prec], eigensolver="davidson")
     e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)), om.SPIN_QN, (0,))
     assert abs(E - e_ed) < 1e-9 * abs(e_ed), (E, e_ed)
+
+
+@pytest.mark.parametrize("qn", [False, True])
+def test_dmrg_splitblocks_mpo(ctx, qn):
+    # the sparse (split) MPO stores only nonzero blocks and gives the same sweeps
+    N = 10
+    host = pm.heisenberg(N)
+    Ws = pm.splitblocks(host, qn=qn)
+    Wd = pm.to_device(host, qn=qn)
+    assert sum(int(w.data.numel()) for w in Ws) < sum(int(w.data.numel()) for w in Wd)
+    site = Ws[0].inds[3]
+    sweeps = [(8, 1e-12), (16, 1e-12), (32, 1e-13), (32, 1e-13)]
+    if qn:
+        mk = lambda: pm.product_state(site, [0, 1] * (N // 2))
+    else:
+        vecs = synth.product_spinors(1, N, 2)
+        mk = lambda: pm.product_vectors(site, vecs)
+    md, co = [m for m, _ in sweeps], [c for _, c in sweeps]
+    Es, _ = ctx.dmrg(Ws, mk(), host.start, host.done, md, co, krylov_dim=64)
+    Ed, _ = ctx.dmrg(Wd, mk(), host.start, host.done, md, co, krylov_dim=64)
+    e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)))
+    assert abs(Es - Ed) < 1e-12 * abs(Ed), (Es, Ed)
+    assert abs(Es - e_ed) < 1e-9 * abs(e_ed)
