@@ -274,6 +274,39 @@ def bench_sweeps(ctx, tnh):
     res["model"] = (f"U(1) Heisenberg chain N={SWEEP_N}, Neel start, maxdim "
                     f"{[m for m, _ in SWEEP_SCHEDULE]}, cutoff 1e-12, Lanczos <= 16 steps")
     res["small"] = bench_small_sweeps(ctx, tnh)
+    res["cylinder_m2048"] = bench_cylinder_sweeps(ctx, tnh)
+    return res
+
+
+# J1-J2 cylinder (Ly=6 periodic, Lx=4 open, snake order, J2/J1=1/2, w=26) up
+# to m=2048: the bond dimension grows about fourfold per sweep from the Neel
+# state, so seven sweeps of maxdim 256, 512, 1024, 2048 x4 (cutoff 1e-10),
+# six Lanczos steps per bond in both precisions; the sweep time is the last
+# sweep's. Length 4 keeps the FP64 run within the bench's time.
+CYL_SCHEDULE = [(256, 1e-10), (512, 1e-10), (1024, 1e-10)] + [(2048, 1e-10)] * 4
+
+
+def bench_cylinder_sweeps(ctx, tnh):
+    from paper_2007_14822_gb300 import models as pm
+    Lx, Ly = 4, 6
+    N = Lx * Ly
+    mpo = pm.spin_pairs(N, pm.cylinder_pairs(Lx, Ly, 1.0, 0.5))
+    res = {}
+    for name, prec in (("bf16x6", tnh.BF16x6), ("fp64", tnh.FP64)):
+        W = pm.to_device(mpo, qn=True)
+        A = pm.product_state(W[0].inds[3], [0, 1] * (N // 2))
+        t0 = time.perf_counter()
+        E, st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in CYL_SCHEDULE], [c for _, c in CYL_SCHEDULE],
+                         krylov_dim=6, tol=0.0, prec=prec)
+        last = st[-1]
+        res[name] = {"energy": E, "last_sweep_s": last["seconds"], "maxlink": last["maxlink"],
+                     "matvecs_last_sweep": last["matvecs"], "truncerr": last["truncerr"],
+                     "run_s": time.perf_counter() - t0, "sweep_s": [x["seconds"] for x in st]}
+    e64 = res["fp64"]["energy"]
+    res["dE_rel_mixed_vs_fp64"] = abs(res["bf16x6"]["energy"] - e64) / abs(e64)
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["last_sweep_s"] / res["bf16x6"]["last_sweep_s"]
+    res["model"] = (f"U(1) J1-J2 cylinder Ly={Ly} x Lx={Lx} (N={N}, J2/J1=0.5, w={mpo.max_bond()}), Neel start, "
+                    f"maxdim {[m for m, _ in CYL_SCHEDULE]}, cutoff 1e-10, 6 Lanczos steps per bond")
     return res
 
 
