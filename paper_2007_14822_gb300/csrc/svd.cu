@@ -29,11 +29,13 @@
 //       of M with it (S V^T = U^T M, or U S = M V).
 // Every wait is bounded and reports through the device error flag.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <string>
 
 #include "prof.h"
 #include "ptx.cuh"
@@ -826,8 +828,29 @@ int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg
     return st[1];
 }
 
+// TNH_DEBUG: host wall time of the phases of one factorisation
+struct PhaseClock {
+    bool on = std::getenv("TNH_DEBUG") != nullptr;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), last = t0;
+    std::string line;
+    void mark(const char* what) {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        char b[64];
+        std::snprintf(b, sizeof b, " %s %.3f", what, std::chrono::duration<double, std::milli>(now - last).count());
+        line += b;
+        last = now;
+    }
+    ~PhaseClock() {
+        if (on)
+            std::fprintf(stderr, "svd: phases (ms)%s, total %.3f\n", line.c_str(),
+                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    }
+};
+
 std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double cutoff, int maxdim, int mindim,
                                    int exact_side) {
+    PhaseClock clk;
     cudaStream_t s = ctx->stream;
     const int r = T.rank();
     TNH_REQUIRE(nrow >= 1 && nrow < r, TNH_ERR_ARG, "svd_trunc: nrow %d of rank %d", nrow, r);
@@ -980,8 +1003,10 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         KScope ks("svd_set_identity", s);
         set_identity_f32<<<dim3(16, ng), 256, 0, s>>>(d_bg.as<BGroup>(), V32.as<float>());
     }
+    clk.mark("setup");
     // ---- stage a: float32 block Jacobi
     R->rounds32 = run_block_jacobi(ctx, bg, d_bg, X32.as<float>(), V32.as<float>(), frop, bmax, stride, "");
+    clk.mark("f32");
     // ---- rank the float32 singular values, pick the candidates
     std::vector<ColSet> cs32(ng);
     for (int g = 0, c0 = 0; g < ng; ++g) {
@@ -1040,6 +1065,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         const int g = h_gid[h_order[k]];
         if ((int)cand[g].size() < R->len[g]) cand[g].push_back(h_pos[h_order[k]]);
     }
+    clk.mark("rank32");
     // ---- float64 re-formation Y = X64 V32[:, cand]
     std::vector<CandSet> csets;
     std::vector<int> candflat;
@@ -1152,6 +1178,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         form_y();
         CUDA_CHECK(cudaStreamSynchronize(s));   // temporaries are freed on scope exit
     }
+    clk.mark("form64");
     // ---- stage b: float64 polish
     {
         // blocks of kJ64MaxB columns when the columns are short (a round then
@@ -1247,6 +1274,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
                              st[1], worst, jg[worst].len, jg[worst].n, (double)wv);
         }
     }
+    clk.mark("f64");
     // ---- float64 singular values, ranking, truncation
     const int ny = yc;
     std::vector<ColSet> cs64;
