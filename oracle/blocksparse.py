@@ -118,13 +118,27 @@ def block_flux(inds, key, nq=None):
 def allowed_blocks(inds, flux):
     """All sector tuples whose block flux equals ``flux`` (Sec. 8.3).
 
-    Plain enumeration of the full product of sectors, in lexicographic order.
+    Enumeration of the product of the sectors of all indices but the last,
+    in lexicographic order; for each such prefix the flux rule fixes the QN
+    the last index must carry, and its sectors with that QN complete the
+    tuple in increasing order. The result is the lexicographic list of the
+    full product filtered by the flux rule.
     """
     flux = tuple(flux)
+    if not inds:
+        return [()] if not any(flux) else []
+    nq = len(flux)
+    last = inds[-1]
+    by_qn = {}
+    for s in range(last.nsect):
+        by_qn.setdefault(tuple(last.qn(s)), []).append(s)
     out = []
-    for key in itertools.product(*[range(ind.nsect) for ind in inds]):
-        if block_flux(inds, key, len(flux)) == flux:
-            out.append(key)
+    for prefix in itertools.product(*[range(ind.nsect) for ind in inds[:-1]]):
+        f = block_flux(inds[:-1], prefix, nq)
+        # arrow * q_last = flux - f  ->  q_last = arrow * (flux - f)
+        need = qn_scale(last.arrow, qn_sub(flux, f))
+        for s in by_qn.get(tuple(need), ()):
+            out.append(prefix + (s,))
     return out
 
 
@@ -285,10 +299,12 @@ def contract(A, B, out_labels=None):
     C = BlockTensor(inds, flux)
     for key in C.allowed():
         C.blocks[key] = np.zeros(C.block_shape(key))
+    # the blocks of B by their contracted sectors, in B's own order
+    by_contracted = {}
+    for kb, vb in B.blocks.items():
+        by_contracted.setdefault(tuple(kb[q] for q in ib), []).append((kb, vb))
     for ka, va in A.blocks.items():
-        for kb, vb in B.blocks.items():
-            if any(ka[p] != kb[q] for p, q in zip(ia, ib)):
-                continue
+        for kb, vb in by_contracted.get(tuple(ka[p] for p in ia), ()):
             kc = tuple(ka[p] for p in fa) + tuple(kb[q] for q in fb)
             prod = np.tensordot(va, vb, axes=(ia, ib))
             if kc not in C.blocks:

@@ -356,3 +356,49 @@ def test_davidson_matches_eigh(ctx, p, nsect):
     x = psi[:plan.size].cpu().numpy()
     assert abs(float(x @ v[:, 0])) > 1 - (1e-10 if p == "fp64" else 1e-7)
     assert r < (1e-8 if p == "fp64" else 1e-5) * scale
+
+
+# ------------------------------------------- block-sparse workloads, full size
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_heff_qn_workloads_full_size(ctx, which):
+    # the bench's block-sparse H_eff workloads at full size, the plan the bench
+    # times (BF16x6, graph replay): the FP64 product against the oracle on an
+    # input restricted to the blocks of a few a-sectors (the oracle's cost
+    # follows the stored input blocks; for the U(1) m=1024 workload, all of
+    # them), and the BF16x6 product against the FP64 one on the full input
+    import torch
+    import bench
+    from oracle.blocksparse import BlockTensor
+    name, kind, m, recipe, seed = bench.QN_CONFIGS[which]
+    L, W1, W2, R, psi = bench.qn_heff_inputs(kind, m, recipe, seed)
+    plan = ctx.heff_plan(L, W1, W2, R, psi, prec("bf16x6"))
+    n = plan.size
+    x = psi.data.clone()
+    y64 = torch.zeros_like(x)
+    ymx = torch.zeros_like(x)
+    for _ in range(3):
+        plan.apply(x, ymx)
+    plan.apply(x, y64, prec("fp64"))
+    err = (torch.linalg.norm(ymx[:n] - y64[:n]) / torch.linalg.norm(y64[:n])).item()
+    assert err < TOL["bf16x6"], err
+    # sparse input: keep the psi blocks of a few a-sectors
+    nsect_a = psi.inds[0].nsect
+    keep_a = set(range(nsect_a)) if which == 0 else ({nsect_a // 2, nsect_a // 2 + 1} if which == 1 else {nsect_a // 2})
+    xs = torch.zeros_like(x)
+    blocks = {}
+    host = psi.block_arrays()
+    for key, off in zip(psi.blocks, psi.offsets):
+        if key[0] in keep_a:
+            sz = psi.block_size(key)
+            xs[off:off + sz] = psi.data[off:off + sz]
+            blocks[key] = host[key]
+    ys = torch.zeros_like(x)
+    plan.apply(xs, ys, prec("fp64"))
+    Xo = BlockTensor([H.or_index(i) for i in psi.inds], psi.flux, blocks)
+    # L blocks of other a-sectors meet only zero input blocks in S1
+    Lo = BlockTensor([H.or_index(i) for i in L.inds], L.flux,
+                     {k: v for k, v in L.block_arrays().items() if k[0] in keep_a})
+    want = D.heff_apply(Lo, H.to_oracle(W1), H.to_oracle(W2), H.to_oracle(R), Xo)
+    yt = psi.with_inds(psi.inds)
+    yt.data = ys
+    assert H.rel_err(H.to_oracle(yt), want) < TOL["fp64"]

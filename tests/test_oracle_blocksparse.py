@@ -156,3 +156,23 @@ def test_contract_rejects_equal_arrows():
     B = BlockTensor.zeros([i])
     with pytest.raises(ValueError):
         contract(A, B)
+
+
+def test_allowed_blocks_equals_filtered_full_product():
+    # the enumeration completes the last sector from the flux rule; it must be
+    # the lexicographic full product filtered by the flux rule
+    import itertools
+    from oracle.blocksparse import QNIndex, allowed_blocks, block_flux
+    rng = np.random.default_rng(3)
+    for trial in range(30):
+        nq = int(rng.integers(1, 3))
+        rank = int(rng.integers(1, 5))
+        inds = []
+        for _ in range(rank):
+            ns = int(rng.integers(1, 5))
+            secs = [(tuple(int(x) for x in rng.integers(-2, 3, size=nq)), int(rng.integers(1, 3))) for _ in range(ns)]
+            inds.append(QNIndex(secs, int(rng.choice([-1, 1]))))
+        flux = tuple(int(x) for x in rng.integers(-2, 3, size=nq))
+        brute = [k for k in itertools.product(*[range(i.nsect) for i in inds])
+                 if block_flux(inds, k, nq) == flux]
+        assert allowed_blocks(inds, flux) == brute
