@@ -486,9 +486,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the block-sparse H_eff and sweep measurements")
-    ap.add_argument("--oracle-matvec", default="heis,cyl",
+    ap.add_argument("--oracle-matvec", default="heis,cyl,hub",
                     help="block-sparse workloads whose H_eff product is also timed on the oracle (comma list of "
-                         "heis, cyl, hub; the Hubbard one takes minutes on the host)")
+                         "heis, cyl, hub; the Hubbard one takes tens of seconds on the host)")
     ap.add_argument("--probe", choices=["heff-u1", "heff-cyl", "heff-hub", "svd-bond"],
                     help="run one workload briefly for a profiler (no JSON line): a block-sparse H_eff plan "
                          "and three BF16x6 applications, or the bench bond up to its SVD")
