@@ -696,6 +696,99 @@ __global__ void __launch_bounds__(256) sgemm_f64(const SGemm* __restrict__ tasks
     }
 }
 
+// C_t = sum over the K slices of the partial products P[slice][M][N] of
+// task t, in slice order (deterministic), written with C_t's strides
+struct SRed {
+    int M, N, S;
+    int64_t part, c, crs, ccs;
+    int64_t e0;   // prefix of M * N over the reductions of one launch
+};
+__global__ void sgemm_reduce(const SRed* __restrict__ reds, int nred, int64_t total, const double* __restrict__ part,
+                             double* __restrict__ C) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nred - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (reds[mid].e0 <= e) lo = mid; else hi = mid - 1;
+        }
+        const SRed r = reds[lo];
+        const int64_t l = e - r.e0, i = l / r.N, j = l - i * r.N;
+        double v = 0.0;
+        for (int k = 0; k < r.S; ++k) v += part[r.part + (int64_t)k * r.M * r.N + l];
+        C[r.c + i * r.crs + j * r.ccs] = v;
+    }
+}
+
+// The strided FP64 GEMMs of the factorisation are small (a few dozen 64 x 64
+// tiles) with long K: with fewer tiles than half the SMs, each task is cut
+// into up to 8 K slices whose products are summed by sgemm_reduce.
+void launch_sgemm(Ctx* ctx, const std::vector<SGemm>& tasks, const double* A, const double* B, double* C,
+                  cudaStream_t s) {
+    if (tasks.empty()) return;
+    int tiles = 0;
+    int64_t kmax = 0;
+    for (const SGemm& t : tasks) {
+        tiles += ((t.M + 63) / 64) * ((t.N + 63) / 64);
+        kmax = std::max<int64_t>(kmax, t.K);
+    }
+    int S = 1;
+    while (S < 8 && tiles * S * 2 < ctx->num_sms && kmax >= 128 * (S * 2)) S *= 2;
+    std::vector<SGemm> run;
+    std::vector<SRed> reds;
+    int64_t part_elems = 0, red_total = 0;
+    int t0 = 0;
+    for (const SGemm& t : tasks) {
+        const int nt = (t.N + 63) / 64, mt = (t.M + 63) / 64;
+        if (S == 1) {
+            SGemm u = t;
+            u.nt = nt;
+            u.tile0 = t0;
+            t0 += mt * nt;
+            run.push_back(u);
+            continue;
+        }
+        const int64_t ks = ((t.K + S - 1) / S + 15) / 16 * 16;
+        int used = 0;
+        for (int sl = 0; sl < S; ++sl) {
+            const int64_t k0 = sl * ks, k1 = std::min<int64_t>(t.K, k0 + ks);
+            if (k0 >= k1) break;
+            SGemm u = t;
+            u.K = (int)(k1 - k0);
+            u.a = t.a + k0 * t.acs;
+            u.b = t.b + k0 * t.brs;
+            u.c = part_elems + (int64_t)sl * t.M * t.N;
+            u.crs = t.N;
+            u.ccs = 1;
+            u.nt = nt;
+            u.tile0 = t0;
+            t0 += mt * nt;
+            run.push_back(u);
+            ++used;
+        }
+        reds.push_back(SRed{t.M, t.N, used, part_elems, t.c, t.crs, t.ccs, red_total});
+        part_elems += (int64_t)S * t.M * t.N;
+        red_total += (int64_t)t.M * t.N;
+    }
+    DevBuf d_run = upload(run, s);
+    if (S == 1) {
+        KScope ks("svd_sgemm_f64", s);
+        sgemm_f64<<<t0, 256, 0, s>>>(d_run.as<SGemm>(), (int)run.size(), A, B, C);
+        return;
+    }
+    DevBuf part((size_t)std::max<int64_t>(part_elems, 1) * sizeof(double));
+    DevBuf d_reds = upload(reds, s);
+    {
+        KScope ks("svd_sgemm_f64", s);
+        sgemm_f64<<<t0, 256, 0, s>>>(d_run.as<SGemm>(), (int)run.size(), A, B, part.as<double>());
+    }
+    {
+        KScope ks("svd_sgemm_reduce", s);
+        const int g = (int)std::min<int64_t>((red_total + 255) / 256, (int64_t)ctx->num_sms * 8);
+        sgemm_reduce<<<std::max(g, 1), 256, 0, s>>>(d_reds.as<SRed>(), (int)reds.size(), red_total,
+                                                     part.as<double>(), C);
+    }
+}
+
 // exact side, normalised: Ex[:, k] = Y[:, perm[k]] / sigma_k
 struct ExSet {
     int64_t y_off, e_off;
@@ -1114,7 +1207,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     R->Y.alloc((size_t)std::max<int64_t>(yo, 1) * 8);
     {
         DevBuf Vc((size_t)std::max<int64_t>(vco, 1) * 8);
-        DevBuf d_cs = upload(csets, s), d_cand = upload(candflat, s), d_gm = upload(gemms, s);
+        DevBuf d_cs = upload(csets, s), d_cand = upload(candflat, s);
         {
             KScope ks("svd_gather_cand", s);
             gather_cand<<<dim3(16, (unsigned)csets.size()), 256, 0, s>>>(d_cs.as<CandSet>(), d_cand.as<int>(),
@@ -1149,31 +1242,19 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
             go += (int64_t)c.k * c.k;
         }
         DevBuf Gb((size_t)std::max<int64_t>(go, 1) * 8), Vc2((size_t)std::max<int64_t>(vco, 1) * 8);
-        DevBuf d_g1 = upload(g1, s), d_g2 = upload(g2, s), d_ns = upload(ns, s);
+        DevBuf d_ns = upload(ns, s);
         auto newton_schulz = [&](int iters) {
             for (int it = 0; it < iters; ++it) {
-                {
-                    KScope ks("svd_sgemm_f64", s);
-                    sgemm_f64<<<t1, 256, 0, s>>>(d_g1.as<SGemm>(), (int)g1.size(), Vc.as<double>(), Vc.as<double>(),
-                                                 Gb.as<double>());
-                }
+                launch_sgemm(ctx, g1, Vc.as<double>(), Vc.as<double>(), Gb.as<double>(), s);
                 {
                     KScope ks("svd_ns_shift", s);
                     ns_shift<<<dim3(8, (unsigned)ns.size()), 256, 0, s>>>(d_ns.as<NsSet>(), Gb.as<double>());
                 }
-                {
-                    KScope ks("svd_sgemm_f64", s);
-                    sgemm_f64<<<t2, 256, 0, s>>>(d_g2.as<SGemm>(), (int)g2.size(), Vc.as<double>(), Gb.as<double>(),
-                                                 Vc2.as<double>());
-                }
+                launch_sgemm(ctx, g2, Vc.as<double>(), Gb.as<double>(), Vc2.as<double>(), s);
                 std::swap(Vc, Vc2);
             }
         };
-        auto form_y = [&] {
-            KScope ks("svd_sgemm_f64", s);
-            sgemm_f64<<<tiles, 256, 0, s>>>(d_gm.as<SGemm>(), (int)gemms.size(), R->X64.as<double>(), Vc.as<double>(),
-                                             R->Y.as<double>());
-        };
+        auto form_y = [&] { launch_sgemm(ctx, gemms, R->X64.as<double>(), Vc.as<double>(), R->Y.as<double>(), s); };
         newton_schulz(2);
         form_y();
         CUDA_CHECK(cudaStreamSynchronize(s));   // temporaries are freed on scope exit
@@ -1421,17 +1502,13 @@ void svd_get(SvdResult& R, const Layout& U, double* S, const Layout& Vl, int abs
         s0 += kk;
     }
     DevBuf Ex((size_t)eo * 8), Pb((size_t)po * 8);
-    DevBuf d_ex = upload(ex, s), d_perm = upload(permflat, s), d_gm = upload(gm, s);
+    DevBuf d_ex = upload(ex, s), d_perm = upload(permflat, s);
     {
         KScope ks("svd_form_exact", s);
         form_exact<<<dim3(16, (unsigned)ex.size()), 256, 0, s>>>(d_ex.as<ExSet>(), d_perm.as<int>(), R.Y.as<double>(),
                                                                  sk.as<double>(), Ex.as<double>());
     }
-    {
-        KScope ks("svd_sgemm_f64", s);
-        sgemm_f64<<<tiles, 256, 0, s>>>(d_gm.as<SGemm>(), (int)gm.size(), Ex.as<double>(), R.X64.as<double>(),
-                                         Pb.as<double>());
-    }
+    launch_sgemm(ctx, gm, Ex.as<double>(), R.X64.as<double>(), Pb.as<double>(), s);
     // scatter into the caller's blocks
     std::vector<OutPiece> uo, vo;
     for (int k = 0; k < ns; ++k) {
