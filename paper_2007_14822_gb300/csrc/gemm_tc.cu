@@ -295,8 +295,9 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
     gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err, row_off);
 }
 
+template <class PartT>
 __global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds, int nred, int64_t total,
-                                                     const float* __restrict__ part, void* __restrict__ out,
+                                                     const PartT* __restrict__ part, void* __restrict__ out,
                                                      const int64_t* __restrict__ row_off) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = nred - 1;
@@ -338,7 +339,16 @@ void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const
     KScope ks("splitk_reduce", s);
     const int64_t want = (total + 255) / 256;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(num_sms > 0 ? num_sms : 148) * 8));
-    splitk_reduce<<<grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
+    splitk_reduce<float><<<grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
+}
+
+void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const double* part, void* out,
+                          const int64_t* row_off, int num_sms, cudaStream_t s) {
+    if (total == 0 || nred == 0) return;
+    KScope ks("splitk_reduce_f64", s);
+    const int64_t want = (total + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(num_sms > 0 ? num_sms : 148) * 8));
+    splitk_reduce<double><<<grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
 }
 
 }  // namespace tnh

@@ -316,6 +316,58 @@ void finish_gemm(HeffGemm& G, cudaStream_t s) {
     G.d_tc = upload(G.tc, s);
 }
 
+// K split of the FP64 GEMM: with fewer 64 x 64 tiles than half the SMs and
+// long K, every task is cut into up to 8 slices of 16-multiples whose float64
+// products are summed in slice order (the output, scatter included, is
+// written by the reduction).
+void set_split64(HeffGemm& G, int num_sms, cudaStream_t s) {
+    int64_t kmax = 0;
+    for (const GemmTask& t : G.f64) kmax = std::max<int64_t>(kmax, t.K);
+    int S = 1;
+    while (S < 8 && G.tiles64 * S * 2 < num_sms && kmax >= (int64_t)256 * S) S *= 2;
+    G.split64 = S;
+    G.f64run.clear();
+    G.reds64.clear();
+    G.red64_total = G.part64_elems = 0;
+    G.tiles64run = 0;
+    if (S == 1) return;
+    for (const GemmTask& b : G.f64) {
+        const int64_t mn = (int64_t)b.M * b.N;
+        const int kt = b.kt, per = (kt + S - 1) / S;
+        int used = 0;
+        for (int k0 = 0; k0 < kt; k0 += per) {
+            GemmTask t = b;
+            t.kt = std::min(per, kt - k0);
+            t.K = (int)std::min<int64_t>(b.K - (int64_t)k0 * kF64TileK, (int64_t)t.kt * kF64TileK);
+            t.a_base = b.a_base + (int64_t)k0 * kF64TileK;
+            t.b_base = b.b_base + (int64_t)k0 * kF64TileK;
+            t.c_base = G.part64_elems + (int64_t)used * mn;
+            t.ldc = b.N;
+            t.use_roff = 0;
+            t.tile0 = G.tiles64run;
+            G.tiles64run += t.mt * t.nt;
+            G.f64run.push_back(t);
+            ++used;
+        }
+        SplitRed r{};
+        r.M = b.M;
+        r.N = b.N;
+        r.S = used;
+        r.use_roff = b.use_roff;
+        r.out_f32 = 0;
+        r.ldc = b.ldc;
+        r.part = G.part64_elems;
+        r.roff = b.roff;
+        r.c_base = b.c_base;
+        r.e0 = G.red64_total;
+        G.reds64.push_back(r);
+        G.part64_elems += (int64_t)used * mn;
+        G.red64_total += mn;
+    }
+    G.d_f64run = upload(G.f64run, s);
+    G.d_reds64 = upload(G.reds64, s);
+}
+
 // Rebuild the launched tcgen05 tasks of G for a K-split factor (1: the block
 // tasks themselves). With split > 1 every block task goes through the
 // partial slabs (also those too short to split), so that the reduction is
@@ -789,6 +841,12 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     for (HeffOperand* o : {&P->oL, &P->oX, &P->oT, &P->oR}) upload_operand(*o, s);
     finish_gemm(P->g1, s);
     finish_gemm(P->g4, s);
+    set_split64(P->g1, ctx->num_sms, s);
+    set_split64(P->g4, ctx->num_sms, s);
+    {
+        const int64_t p64 = std::max(P->g1.part64_elems, P->g4.part64_elems);
+        if (p64 > 0) P->part64.alloc((size_t)p64 * sizeof(double));
+    }
     P->row_off = upload(roff, s);
     P->t1.alloc((size_t)std::max<int64_t>(P->t1_elems, 1) * sizeof(double));
     const int pl = P->planes;
@@ -850,14 +908,26 @@ cudaGraphNode_t last_node(cudaStream_t s) {
 void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_t s, HeffPlan::Graph* G) {
     const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
     if (f64) {
+        // the FP64 GEMM of one stage, K-split or not; the last launch writes out
+        auto f64_stage = [&](const HeffGemm& Gm, int ntasks, const double* A, const double* B, double* out,
+                             const int64_t* roff) {
+            if (Gm.split64 > 1) {
+                launch_gemm_f64(Gm.d_f64run.as<GemmTask>(), (int)Gm.f64run.size(), Gm.tiles64run, A, B,
+                                P.part64.as<double>(), s);
+                launch_splitk_reduce(Gm.d_reds64.as<SplitRed>(), (int)Gm.reds64.size(), Gm.red64_total,
+                                     P.part64.as<double>(), out, roff, P.ctx->num_sms, s);
+            } else {
+                launch_gemm_f64(Gm.d_f64.as<GemmTask>(), ntasks, Gm.tiles64, A, B, out, s, roff);
+            }
+        };
         launch_gather(P.jX, P.oX.d_g64.as<OpGeom>(), x, P.opX.p, 0, s, "heff_pack_x");
         if (G) G->nx = last_node(s);
-        launch_gemm_f64(P.g1.d_f64.as<GemmTask>(), n1, P.g1.tiles64, P.L64.as<double>(), P.opX.as<double>(),
-                        P.t1.as<double>(), s);
+        f64_stage(P.g1, n1, P.L64.as<double>(), P.opX.as<double>(), P.t1.as<double>(), nullptr);
         launch_w12(P.jW, P.oT.d_g64.as<OpGeom>(), P.t1.as<double>(), P.opT64.p, 0, s);
-        launch_gemm_f64(P.g4.d_f64.as<GemmTask>(), n4, P.g4.tiles64, P.opT64.as<double>(), P.R64.as<double>(), y, s,
-                        P.row_off.as<int64_t>());
+        f64_stage(P.g4, n4, P.opT64.as<double>(), P.R64.as<double>(), y, P.row_off.as<int64_t>());
         if (G) {
+            // gemm_f64_kernel(tasks, ntasks, A, B, C, row_off) and
+            // splitk_reduce(reds, nred, total, part, out, row_off) both take y as argument 4
             G->ny = last_node(s);
             G->iy = 4;
             G->ny_args = 6;

@@ -25,6 +25,13 @@ struct HeffGemm {
     std::vector<SplitRed> reds;
     int64_t red_total = 0, part_elems = 0;
     DevBuf d_f64, d_tc, d_reds;
+    // the FP64 GEMM: with split64 > 1 the tasks of f64run write float64
+    // partial slabs (K slices of 16-multiples), summed by reds64 in order
+    int split64 = 1, tiles64run = 0;
+    std::vector<GemmTask> f64run;
+    std::vector<SplitRed> reds64;
+    int64_t red64_total = 0, part64_elems = 0;
+    DevBuf d_f64run, d_reds64;
 };
 
 // ---- device vector helpers (float64, deterministic reductions) -----------
@@ -54,6 +61,7 @@ struct HeffPlan {
     DevBuf t1;              // S1 result (float32 in the split modes)
     DevBuf row_off;         // S4 output row -> element offset in psi's layout
     DevBuf part;            // float32 partial slabs of K-split GEMMs
+    DevBuf part64;          // float64 partial slabs of K-split FP64 GEMMs
     int64_t t1_elems = 0;
     bool zero_y = false;    // some output rows are written by no S4 task
     // one CUDA graph per format (float64, split): the four launches of an

@@ -249,6 +249,9 @@ struct SplitRed {
 };
 void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const float* part, void* out,
                           const int64_t* row_off, int num_sms, cudaStream_t s);
+// The same with float64 partial slabs (K-split FP64 GEMMs).
+void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const double* part, void* out,
+                          const int64_t* row_off, int num_sms, cudaStream_t s);
 constexpr int kF64TileM = 64, kF64TileN = 64, kF64TileK = 16;
 constexpr int kTcTileM = 128, kTcTileN = 128, kTcTileK = 64;
 constexpr int kTcTileElems = kTcTileM * kTcTileK;   // 8192 bf16 per plane tile
