@@ -225,11 +225,11 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
             const float null2 = (float)(1e-12 * fro2[lo]);
             // stop test, per column pair: float32 rotations leave every column
             // with an absolute error of a few eps32 |M|_F, so a pair can only be
-            // made orthogonal to about floor = 64 eps32 |M|_F / min(|x_p|, |x_q|)
+            // made orthogonal to about floor = 256 eps32 |M|_F / min(|x_p|, |x_q|)
             // of its norms; the target is max(kDone32, floor) and smax holds the
             // largest ratio to it (done when below 1). Columns too small for
             // float32 to resolve are left to the float64 polish.
-            const float flo0 = 64.f * 5.96e-8f * sqrtf((float)fro2[lo]);
+            const float flo0 = 256.f * 5.96e-8f * sqrtf((float)fro2[lo]);
             float wmax = 0.f;
             for (int ir = 0; ir < Ri; ++ir) {
                 for (int pr = warp; pr < ne / 2; pr += nwarp) {
