@@ -592,16 +592,21 @@ def main():
     # float32 CUDA-core peak from the unit counts: SMs x 128 FP32 lanes x 2 x max SM clock
     fp32_peak = (peaks.get("sm_count", 152) * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
     st = bond.svd_stats
+    # DRAM bytes (read + write) per launch of the Jacobi kernels on this
+    # workload's bond, from one ncu capture of `bench.py --probe svd-bond`
+    # (profiles/svd_bond_m256_jacobi.md); None for a kernel changed since
+    traffic = {"svd_jacobi_f32": 2212352 + 397824, "svd_jacobi_f64": 2181632 + 555008}
     if name == "svd_jacobi_f32":
         achieved = st["flops32"] / (ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None, "kernel": name,
+                "frac": achieved / fp32_peak, "traffic": traffic.get(name), "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                 "work": f"{st['rounds32']} grid rounds, rotation flops counted per row (6 dot + 6 update)"}
     elif name == "svd_jacobi_f64":
         achieved = st["flops64"] / (ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s", "frac": achieved / 1.25,
-                "traffic": None, "kernel": name, "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                "traffic": traffic.get(name), "kernel": name,
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
                 "work": f"{st['rounds64']} grid rounds, rotation flops counted per row (6 dot + 6 update)"}
     elif name == "gemm_f64":
         achieved = fp64_flops / (ms / 1e3) / 1e12
