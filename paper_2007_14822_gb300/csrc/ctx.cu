@@ -205,20 +205,51 @@ Layout make_layout(const std::vector<Index>& inds, const std::vector<int>& flux)
     Layout L;
     L.inds = inds;
     L.flux = flux;
-    int r = (int)inds.size();
-    int nq = (int)flux.size();
-    std::vector<int> key(r, 0);
+    const int r = (int)inds.size();
+    const int nq = (int)flux.size();
     int64_t off = 0;
-    // odometer over all sector tuples, lexicographic (last index fastest)
-    while (true) {
-        if (block_flux(inds, key.data(), nq) == flux) {
-            L.sect.insert(L.sect.end(), key.begin(), key.end());
-            L.off.push_back(off);
-            int64_t n = 1;
-            for (int i = 0; i < r; ++i) n *= inds[i].dim[key[i]];
-            off += n;
+    if (r == 0) {   // a scalar: one block when the flux is zero
+        bool zero = true;
+        for (int f : flux) zero &= f == 0;
+        if (zero) {
+            L.off.push_back(0);
+            off = 1;
         }
-        int i = r - 1;
+        L.size = off;
+        L.build_lookup();
+        return L;
+    }
+    // Lexicographic tuples (last index fastest): an odometer over the first
+    // r - 1 indices; for each prefix the flux rule fixes the charge the last
+    // index must carry, and its sectors with that charge complete the tuple
+    // in increasing order.
+    const Index& last = inds[r - 1];
+    std::map<std::vector<int>, std::vector<int>> by_q;
+    for (int sct = 0; sct < last.nsect; ++sct) {
+        std::vector<int> q(nq);
+        for (int k = 0; k < nq; ++k) q[k] = last.q(sct, k);
+        by_q[q].push_back(sct);
+    }
+    std::vector<int> key(r, 0), need(nq);
+    while (true) {
+        for (int k = 0; k < nq; ++k) {
+            int f = 0;
+            for (int i = 0; i < r - 1; ++i) f += inds[i].arrow * inds[i].q(key[i], k);
+            need[k] = last.arrow * (flux[k] - f);
+        }
+        auto it = by_q.find(need);
+        if (it != by_q.end()) {
+            int64_t n0 = 1;
+            for (int i = 0; i < r - 1; ++i) n0 *= inds[i].dim[key[i]];
+            for (int sct : it->second) {
+                key[r - 1] = sct;
+                L.sect.insert(L.sect.end(), key.begin(), key.end());
+                L.off.push_back(off);
+                off += n0 * last.dim[sct];
+            }
+            key[r - 1] = 0;
+        }
+        int i = r - 2;
         while (i >= 0 && ++key[i] == inds[i].nsect) { key[i] = 0; --i; }
         if (i < 0) break;
     }

@@ -28,10 +28,12 @@
 // final energy and residual), so it keeps the float64 operands of L and R too.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <string>
 
 #include "heff.h"
 #include "prof.h"
@@ -559,6 +561,26 @@ HeffPlan::~HeffPlan() {
     }
 }
 
+namespace {
+// TNH_DEBUG: host wall time of the phases of one plan
+struct PlanClock {
+    bool on = std::getenv("TNH_DEBUG") != nullptr;
+    std::chrono::steady_clock::time_point last = std::chrono::steady_clock::now();
+    std::string line;
+    void mark(const char* what) {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        char b[64];
+        std::snprintf(b, sizeof b, " %s %.2f", what, std::chrono::duration<double, std::milli>(now - last).count());
+        line += b;
+        last = now;
+    }
+    ~PlanClock() {
+        if (on) std::fprintf(stderr, "heff_plan: phases (ms)%s\n", line.c_str());
+    }
+};
+}  // namespace
+
 std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
                                     const Layout& R, const Layout& X, tnh_precision prec) {
     TNH_REQUIRE(L.rank() == 3 && R.rank() == 3 && W1.rank() == 4 && W2.rank() == 4 && X.rank() == 4,
@@ -591,6 +613,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     const Index &ia = X.inds[0], &is1 = X.inds[1], &is2 = X.inds[2], &ib = X.inds[3];
     const Index &iw = L.inds[1], &iz = R.inds[1];
 
+    PlanClock clk;
     // method flops: S1..S4 over the allowed blocks of the labelled chain
     {
         Layout Ll = with_labels(L, {La, Lw, Lap});
@@ -609,6 +632,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         P->flops = P->f_s1 + P->f_s23 + P->f_s4;
     }
 
+    clk.mark("flops");
     // ---------------- S1: one task per a-sector A with L and psi blocks
     struct RowRef { int task; int64_t row; };
     std::map<std::pair<int, int>, std::vector<RowRef>> t1_rows;   // (w element, a'-sector) -> rows
@@ -671,6 +695,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     P->g1.tiles64 = tf;
     P->g1.tilestc = tt;
 
+    clk.mark("s1");
     // ---------------- two-site MPO product W12[(w,s1,s2) -> (w2,s1',s2')]
     struct W12Term { int x, s1, s2; double v; };
     std::map<std::array<int, 3>, std::vector<W12Term>> w12;   // (w2, s1', s2') -> terms
@@ -689,6 +714,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                 w12[{kv.first[0], kv.first[1], kv.first[2]}].push_back({kv.first[3], kv.first[4], kv.first[5], kv.second});
     }
 
+    clk.mark("w12");
     // ---------------- diagonal of H_eff: environment diagonals and the
     // diagonal W12 entries (s1' = s1, s2' = s2) per (s1, s2)
     {
@@ -745,9 +771,10 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         P->d_dblocks = upload(db, s);
         P->d_dstart = upload(tstart, s);
         P->d_dterms = upload(terms, s);
-        CUDA_CHECK(cudaStreamSynchronize(s));   // d_ls, d_rs are freed on scope exit
+        // d_ls, d_rs are freed on scope exit, in stream order after the gathers
     }
 
+    clk.mark("diag");
     // ---------------- S4: one task per b'-sector; fused S2+S3 fills operand A
     JobBuilder bR;
     CellBuilder bW;
@@ -832,6 +859,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     for (int b = 0; b < X.nblocks(); ++b) P->zero_y |= !covered[b];
     if (X.packed_total() < X.size) P->zero_y = true;
 
+    clk.mark("s4");
     // ---------------- device side
     bX.finish(P->jX, s);
     bW.finish(P->jW, s);
@@ -873,7 +901,9 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         launch_gather(jR, P->oR.d_gtc.as<OpGeom>(), R.data, P->Rtc.p, pl, s, "heff_pack_env");
     }
     CUDA_CHECK(cudaGetLastError());
+    clk.mark("device");
     if (pl > 0 && !P->g1.tc_base.empty() && !P->g4.tc_base.empty()) tune_splits(*P);
+    clk.mark("tune");
     if (std::getenv("TNH_DEBUG"))
         std::fprintf(stderr,
                      "heff_plan: n %lld, S1 %zu tasks %d tiles, T1 %lld, S4 %zu tasks %d tiles, T3 %lld, "

@@ -53,6 +53,26 @@ def test_layout_matches_oracle(lib):
         assert total == sum(sizes)
 
 
+def test_layout_matches_oracle_repeated_charges(lib):
+    # ranks 1..5, sectors with repeated charges (the layout completes the
+    # last index from the flux rule; its sectors must come in increasing order)
+    from oracle.blocksparse import QNIndex, allowed_blocks
+    from paper_2007_14822_gb300 import tnh
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        rank = int(rng.integers(1, 6))
+        inds = []
+        for r in range(rank):
+            ns = int(rng.integers(1, 6))
+            inds.append(tnh.Index([((int(rng.integers(-2, 3)),), int(rng.integers(1, 3))) for _ in range(ns)],
+                                  +1 if rng.random() < 0.5 else -1))
+        flux = (int(rng.integers(-2, 3)),)
+        blocks, offs, total = tnh.layout(inds, flux)
+        assert blocks == allowed_blocks([QNIndex(i.sectors, i.arrow) for i in inds], flux)
+        sizes = [int(np.prod([inds[i].sectors[s][1] for i, s in enumerate(b)])) for b in blocks]
+        assert total == sum(sizes)
+
+
 def test_layout_paper_block_sparse_example(lib):
     # Sec. 9.2 example: blockdims ([2,2],[2,3]), nonzero blocks (1,2),(2,1)
     from paper_2007_14822_gb300 import tnh
