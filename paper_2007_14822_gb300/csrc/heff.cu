@@ -425,7 +425,7 @@ void set_split(HeffGemm& G, int split, cudaStream_t s) {
     G.tilestc = tile0;
     G.d_tc = upload(G.tc, s);
     G.d_reds = upload(G.reds, s);
-    CUDA_CHECK(cudaStreamSynchronize(s));   // the host vectors may change right after
+    // (pageable uploads are staged before they return: the host vectors may change)
 }
 
 // One tcgen05 GEMM of the plan, and its reduction when K is split.

@@ -1085,7 +1085,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         DevBuf d_fs = upload(fs, s);
         KScope ks("svd_group_sumsq", s);
         group_sumsq<<<ng, 256, 0, s>>>(d_fs.as<FroSet>(), R->X64.as<double>(), d_fro2.as<double>());
-        CUDA_CHECK(cudaStreamSynchronize(s));   // d_fs is freed on scope exit
+        // d_fs is freed on scope exit, in stream order after the kernel
     }
     const double* frop = d_fro2.as<double>();
     {
@@ -1257,7 +1257,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         auto form_y = [&] { launch_sgemm(ctx, gemms, R->X64.as<double>(), Vc.as<double>(), R->Y.as<double>(), s); };
         newton_schulz(2);
         form_y();
-        CUDA_CHECK(cudaStreamSynchronize(s));   // temporaries are freed on scope exit
+        // temporaries are freed on scope exit, in stream order after their kernels
     }
     clk.mark("form64");
     // ---- stage b: float64 polish
