@@ -405,3 +405,22 @@ def test_dmrg_excited_state_heisenberg_qn_vs_ed():
     assert abs(E0 - e_ed[0]) < 1e-10 * abs(e_ed[0])
     assert abs(E1 - e_ed[1]) < 1e-9 * abs(e_ed[1])
     assert abs(D.mps_overlap(A0, A1)) < 1e-6
+
+
+def test_heisenberg_bethe_ansatz_energy_density():
+    # bulk energy per bond of the spin-1/2 Heisenberg chain: 1/4 - ln 2 (Bethe
+    # ansatz). On open chains E0(N) = N e + surface + O(1/N), so the slope
+    # between two lengths approaches e: exact diagonalisation at N = 14, 16 and
+    # the oracle's DMRG at N = 24 (beyond exact diagonalisation here)
+    e_bulk = 0.25 - math.log(2)
+    e = {N: ed.ground_energy(N, 2, models.spin_pair_terms(models.heisenberg_pairs(N)), models.SPIN_QN, (0,))
+         for N in (14, 16)}
+    assert abs((e[16] - e[14]) / 2 - e_bulk) < 1e-3
+    N = 24
+    mpo = models.heisenberg_mpo(N)
+    A = D.product_mps_basis(mpo.site_index, [0, 1] * (N // 2), 1)
+    E24, _, _ = _dmrg(mpo, A, [(16, 1e-10), (64, 1e-10), (64, 1e-10)], krylov_dim=16, tol=1e-8)
+    slope = (E24 - e[16]) / 8
+    assert abs(slope - e_bulk) < 6e-4, slope
+    # and a longer chain lies lower per site than a shorter one, toward e
+    assert E24 / N < e[16] / 16
