@@ -595,7 +595,7 @@ def main():
     # DRAM bytes (read + write) per launch of the Jacobi kernels on this
     # workload's bond, from one ncu capture of `bench.py --probe svd-bond`
     # (profiles/svd_bond_m256_jacobi.md); None for a kernel changed since
-    traffic = {"svd_jacobi_f32": 2212352 + 397824, "svd_jacobi_f64": 2181632 + 555008}
+    traffic = {"svd_jacobi_f32": None, "svd_jacobi_f64": 2123520 + 540672}
     if name == "svd_jacobi_f32":
         achieved = st["flops32"] / (ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

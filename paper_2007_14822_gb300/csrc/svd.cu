@@ -173,20 +173,31 @@ constexpr float kDone32 = 2e-3f;   // float32 stop (the float64 polish finishes)
 
 // state[1] = rounds done. fro2[g] = |X_g|_F^2; columns whose squared norm
 // is below 1e-12 fro2 are float32 rounding noise and are not rotated (they
-// would mix forever). A column lives in shared memory as [X part, zero pad
-// to lp (a multiple of 4), V part]: the inner sweep reads and writes it four
-// floats at a time.
-__global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __restrict__ groups, int ngroups,
-                                                               int total_pairs, int max_rounds, float* __restrict__ X,
-                                                               float* __restrict__ V, int* smax, int* state,
-                                                               GridBar* bar, int* err, int stride,
-                                                               const double* __restrict__ fro2) {
-    extern __shared__ __align__(16) float sm[];   // [2b][stride]
+// would mix forever). Only the X columns of a block pair are staged in
+// shared memory ([2B][stride], padded to lp, a multiple of 4: the inner
+// sweep reads and writes them four floats at a time); the inner sweep's
+// rotations are accumulated into Q ([2B][2B], shared memory), and the V
+// columns are updated once per round, V <- V Q, straight from and to global
+// memory. The decisions and the angle use the fast reciprocal and
+// reciprocal square root where the divisor is bounded (the angle only has to
+// reduce x_p.x_q; the float64 polish finishes).
+template <int B>
+__global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const BGroup* __restrict__ groups,
+                                                                       int ngroups, int total_pairs, int max_rounds,
+                                                                       float* __restrict__ X, float* __restrict__ V,
+                                                                       int* smax, int* state, GridBar* bar, int* err,
+                                                                       int stride, const double* __restrict__ fro2,
+                                                                       long long* tdbg) {
+    constexpr int NC = 2 * B;
+    extern __shared__ __align__(16) float sm[];   // [2B][stride] X columns, then Q [2B][2B]
     __shared__ int skip;
+    float* Qs = sm + (size_t)NC * stride;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned epoch = 0;
     int t = 0;
+#define STAMP(j) if (tdbg && blockIdx.x == 0 && threadIdx.x == 0 && t >= 64 && t < 96) tdbg[(t - 64) * 8 + (j)] = clock64();
     for (; t < max_rounds; ++t) {
+        STAMP(0)
         for (int item = blockIdx.x; item < total_pairs; item += gridDim.x) {
             int lo = 0, hi = ngroups - 1;
             while (lo < hi) {
@@ -204,6 +215,7 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
             __syncthreads();
             const int sk = skip;
             __syncthreads();   // every thread has read skip before thread 0 rewrites it
+            STAMP(1)
             if (sk) continue;
             const int bp = rr_pos(i, k, R), bq = rr_pos(G.nblk - 1 - i, k, R);
             // local column list: block bp then block bq (clipped to n)
@@ -211,17 +223,15 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
             const int q0 = bq * G.b, q1 = min(G.n, q0 + G.b);
             const int np = max(0, p1 - p0), nq = max(0, q1 - q0), nc = np + nq;
             if (nc < 2) continue;
-            const int L = G.len, Nn = G.n, lp = (L + 3) & ~3, tot4 = (lp + Nn + 3) >> 2;
+            const int L = G.len, Nn = G.n, lp = (L + 3) & ~3, l4 = lp >> 2;
             for (int c = warp; c < nc; c += nwarp) {
                 const int col = c < np ? p0 + c : q0 + (c - np);
-                const float* xs = X + G.x_off + (int64_t)col * L;
-                const float* vs = V + G.v_off + (int64_t)col * Nn;
-                float* d = sm + (size_t)c * stride;
-                stage_in(d, xs, L, lp, lane, 32);
-                stage_in(d + lp, vs, Nn, 4 * tot4 - lp, lane, 32);
+                stage_in(sm + (size_t)c * stride, X + G.x_off + (int64_t)col * L, L, lp, lane, 32);
             }
+            for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) Qs[e] = e / NC == e % NC ? 1.f : 0.f;
             __syncthreads();
-            const int ne = nc + (nc & 1), Ri = ne - 1, l4 = lp >> 2;
+            STAMP(2)
+            const int ne = nc + (nc & 1), Ri = ne - 1;
             const float null2 = (float)(1e-12 * fro2[lo]);
             // stop test, per column pair: float32 rotations leave every column
             // with an absolute error of a few eps32 |M|_F, so a pair can only be
@@ -251,37 +261,108 @@ __global__ void __launch_bounds__(kBJThreads) block_jacobi_f32(const BGroup* __r
                         ga += __shfl_xor_sync(0xffffffffu, ga, o);
                     }
                     if (al <= null2 || be <= null2) continue;
-                    const float rel = fabsf(ga) / (sqrtf(al) * sqrtf(be));
-                    wmax = fmaxf(wmax, rel / fmaxf(kDone32, flo0 * rsqrtf(fminf(al, be))));
+                    const float ra = rsqrtf(al), rb = rsqrtf(be);
+                    const float rel = fabsf(ga) * ra * rb;
+                    // rsqrt(min(al, be)) = max(ra, rb)
+                    wmax = fmaxf(wmax, __fdividef(rel, fmaxf(kDone32, flo0 * fmaxf(ra, rb))));
                     if (!(rel > kTol32)) continue;
-                    const float zeta = (be - al) / (2.0f * ga);
-                    const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                    const float c = rsqrtf(1.f + tt * tt), sn = c * tt;
+                    const float zeta = (be - al) / (2.0f * ga);   // IEEE: 2 ga is not bounded
+                    const float az = fabsf(zeta), w = fmaf(zeta, zeta, 1.f);
+                    const float tt = az > 1e8f ? __fdividef(0.5f, zeta)
+                                               : copysignf(__fdividef(1.f, az + w * rsqrtf(w)), zeta);
+                    const float c = rsqrtf(fmaf(tt, tt, 1.f)), sn = c * tt;
 #pragma unroll 2
-                    for (int r = lane; r < tot4; r += 32) {
+                    for (int r = lane; r < l4; r += 32) {
                         const float4 u = xa[r], v = xb[r];
                         xa[r] = make_float4(c * u.x - sn * v.x, c * u.y - sn * v.y, c * u.z - sn * v.z, c * u.w - sn * v.w);
                         xb[r] = make_float4(sn * u.x + c * v.x, sn * u.y + c * v.y, sn * u.z + c * v.z, sn * u.w + c * v.w);
                     }
+                    // Q <- Q J: the pairs of an inner step touch disjoint columns of Q
+                    if (lane < nc) {
+                        const float qa = Qs[lane * NC + a], qb = Qs[lane * NC + bb];
+                        Qs[lane * NC + a] = c * qa - sn * qb;
+                        Qs[lane * NC + bb] = sn * qa + c * qb;
+                    }
                 }
                 __syncthreads();
             }
+            STAMP(3)
             for (int c = warp; c < nc; c += nwarp) {
                 const int col = c < np ? p0 + c : q0 + (c - np);
-                float* xs = X + G.x_off + (int64_t)col * L;
-                float* vs = V + G.v_off + (int64_t)col * Nn;
-                const float* d = sm + (size_t)c * stride;
-                stage_out(xs, d, L, lane, 32);
-                stage_out(vs, d + lp, Nn, lane, 32);
+                stage_out(X + G.x_off + (int64_t)col * L, sm + (size_t)c * stride, L, lane, 32);
+            }
+            // V <- V Q on the block pair's columns: each thread takes rows, RB
+            // at a time, all their loads in flight before any store (every row
+            // is read and written by one thread only)
+            if constexpr (NC >= 32) {
+                // wide blocks: one row per thread, Q read from shared memory
+                // (broadcast), so that only the row stays in registers
+                float* Vg = V + G.v_off;
+                for (int r = threadIdx.x; r < Nn; r += blockDim.x) {
+                    float v[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const int col = c < np ? p0 + c : q0 + (c - np);
+                        v[c] = c < nc ? Vg[(int64_t)col * Nn + r] : 0.f;
+                    }
+#pragma unroll 1
+                    for (int j = 0; j < nc; ++j) {
+                        float o = 0.f;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) o = fmaf(v[c], Qs[c * NC + j], o);
+                        const int col = j < np ? p0 + j : q0 + (j - np);
+                        Vg[(int64_t)col * Nn + r] = o;
+                    }
+                }
+            } else {
+                constexpr int RB = 32 / NC;
+                float* Vg = V + G.v_off;
+                for (int r0 = threadIdx.x; r0 < Nn; r0 += blockDim.x * RB) {
+                    float v[RB][NC], o[RB][NC];
+#pragma unroll
+                    for (int u = 0; u < RB; ++u) {
+                        const int r = r0 + u * blockDim.x;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            const int col = c < np ? p0 + c : q0 + (c - np);
+                            v[u][c] = (r < Nn && c < nc) ? Vg[(int64_t)col * Nn + r] : 0.f;
+                            o[u][c] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        if (c >= nc) break;
+                        float q[NC];
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) q[j] = Qs[c * NC + j];
+#pragma unroll
+                        for (int u = 0; u < RB; ++u)
+#pragma unroll
+                            for (int j = 0; j < NC; ++j) o[u][j] = fmaf(v[u][c], q[j], o[u][j]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < RB; ++u) {
+                        const int r = r0 + u * blockDim.x;
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) {
+                            const int col = j < np ? p0 + j : q0 + (j - np);
+                            if (r < Nn && j < nc) Vg[(int64_t)col * Nn + r] = o[u][j];
+                        }
+                    }
+                }
             }
             if (lane == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
             __syncthreads();
+            STAMP(4)
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
+        STAMP(5)
         if (all_done(groups, ngroups, smax, t + 1, 1.0f)) { ++t; break; }
+        STAMP(6)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
+#undef STAMP
 
 // ------------------------------------------------ stage b: float64 pairs
 struct JGroup {
@@ -895,10 +976,20 @@ int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg
     DevBuf d_smax((size_t)3 * ng * 4), d_state(16), d_bar(16);
     reset_state(d_smax, d_state, d_bar, ng, s);
     const int threads = 32 * std::max(bmax, 4);   // one warp per column pair of an inner step
-    size_t smem = (size_t)2 * bmax * stride * 4;
-    CUDA_CHECK(cudaFuncSetAttribute(block_jacobi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // X columns of a block pair, then the accumulated rotation Q
+    size_t smem = ((size_t)2 * bmax * stride + (size_t)4 * bmax * bmax) * 4;
+    const void* kern = nullptr;
+    switch (bmax) {
+        case 1: kern = (const void*)block_jacobi_f32<1>; break;
+        case 2: kern = (const void*)block_jacobi_f32<2>; break;
+        case 4: kern = (const void*)block_jacobi_f32<4>; break;
+        case 8: kern = (const void*)block_jacobi_f32<8>; break;
+        case 16: kern = (const void*)block_jacobi_f32<16>; break;
+        default: TNH_REQUIRE(false, TNH_ERR_ARG, "svd: block width %d", bmax);
+    }
+    CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int bpsm = 0;
-    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, block_jacobi_f32, threads, smem));
+    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kern, threads, smem));
     TNH_REQUIRE(bpsm >= 1, TNH_ERR_CUDA, "svd: block Jacobi does not fit on an SM");
     int grid = std::max(1, std::min(bpairs, bpsm * ctx->num_sms));
     int max_rounds = 30 * rmax + 4;
@@ -906,15 +997,33 @@ int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg
     int* smaxp = d_smax.as<int>();
     int* statep = d_state.as<int>();
     GridBar* barp = d_bar.as<GridBar>();
+    const bool tr = std::getenv("TNH_ROUND_TIMES") != nullptr;
+    DevBuf d_t(tr ? 32 * 8 * 8 : 16);
+    if (tr) CUDA_CHECK(cudaMemsetAsync(d_t.p, 0, 32 * 8 * 8, s));
+    long long* tp = tr ? d_t.as<long long>() : nullptr;
     void* args[] = {(void*)&gp,    (void*)&ng,     (void*)&bpairs, (void*)&max_rounds, (void*)&X,      (void*)&V,
-                    (void*)&smaxp, (void*)&statep, (void*)&barp,   (void*)&errp,       (void*)&stride, (void*)&fro2};
+                    (void*)&smaxp, (void*)&statep, (void*)&barp,   (void*)&errp,       (void*)&stride, (void*)&fro2,
+                    (void*)&tp};
     {
         KScope ks("svd_jacobi_f32", s);
-        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)block_jacobi_f32, dim3(grid), dim3(threads), args, smem, s));
+        CUDA_CHECK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, s));
     }
     int st[2];
     CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));   // bookkeeping buffers are freed on return
+    if (tr && st[1] >= 96) {
+        std::vector<long long> h(32 * 8);
+        CUDA_CHECK(cudaMemcpy(h.data(), d_t.p, h.size() * 8, cudaMemcpyDeviceToHost));
+        double acc[7] = {0};
+        for (int r = 0; r < 32; ++r) {
+            for (int j = 0; j < 6; ++j) acc[j] += (double)(h[r * 8 + j + 1] - h[r * 8 + j]);
+            if (r + 1 < 32) acc[6] += (double)(h[(r + 1) * 8] - h[r * 8 + 6]);
+        }
+        std::fprintf(stderr, "svd f32 round phases (cycles, mean of 32 rounds): skip %.0f stage_in %.0f inner %.0f "
+                     "stage_out %.0f barrier %.0f all_done %.0f loop %.0f, round %.0f\n", acc[0] / 32, acc[1] / 32,
+                     acc[2] / 32, acc[3] / 32, acc[4] / 32, acc[5] / 32, acc[6] / 31,
+                     (double)(h[31 * 8] - h[0]) / 31);
+    }
     if (std::getenv("TNH_DEBUG"))
         std::fprintf(stderr, "svd: float32 block Jacobi%s %d rounds (max %d, per sweep %d, grid %d, b %d)\n", what,
                      st[1], max_rounds, rmax, grid, bmax);
@@ -965,7 +1074,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     std::vector<SvdPack> packs;
     std::vector<BGroup> bg;
     int64_t xo = 0, vo = 0;
-    int bpairs = 0, rmax = 1, stride = 0, bmax = 1;
+    int bpairs = 0, rmax = 1, stride = 0, xstride = 4, bmax = 1;   // stride: X + V column, xstride: X column
     for (auto& kv : byq) {
         std::map<std::vector<int>, int> rk, ck;
         for (int b : kv.second) {
@@ -1001,6 +1110,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
         G.len = L;
         G.n = Nn;
         stride = std::max(stride, (((L + 3) & ~3) + Nn + 3) & ~3);
+        xstride = std::max(xstride, (L + 3) & ~3);
         for (int bl : kv.second) {
             auto key = T.key(bl);
             SvdPack p{};
@@ -1098,7 +1208,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     }
     clk.mark("setup");
     // ---- stage a: float32 block Jacobi
-    R->rounds32 = run_block_jacobi(ctx, bg, d_bg, X32.as<float>(), V32.as<float>(), frop, bmax, stride, "");
+    R->rounds32 = run_block_jacobi(ctx, bg, d_bg, X32.as<float>(), V32.as<float>(), frop, bmax, xstride, "");
     clk.mark("f32");
     // ---- rank the float32 singular values, pick the candidates
     std::vector<ColSet> cs32(ng);
