@@ -167,7 +167,6 @@ struct BGroup {
 };
 
 constexpr int kBJMaxB = 16;            // columns per block (a block pair has <= 32)
-constexpr int kBJThreads = 32 * kBJMaxB;   // one warp per column pair of an inner step
 constexpr float kTol32 = 1e-5f;    // float32 rotation threshold
 constexpr float kDone32 = 2e-3f;   // float32 stop (the float64 polish finishes)
 
@@ -1144,8 +1143,10 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     }
     const int ng = (int)bg.size();
     if (ng == 0) return R;
-    // one block width for all groups: up to 16 columns while a block pair
-    // (X and V columns) fits in shared memory. An inner step moves about
+    // one block width for all groups: up to 16 columns while a block pair's
+    // X and V columns together would fit in 200 KB of shared memory (the
+    // rule the widths were measured with; the kernel stages X only and
+    // keeps V in global memory). An inner step moves about
     // 20 bytes per row and column pair through shared memory, which bounds a
     // round on one SM when columns are long, so for columns longer than 256
     // narrower blocks (more block pairs, more SMs) are taken while the groups
