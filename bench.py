@@ -253,6 +253,14 @@ def bench_qn_heff(ctx, torch, tnh, oracle_kinds=()):
 # last sweep's, both precisions.
 SWEEP_N = 100
 SWEEP_SCHEDULE = [(32, 1e-12), (64, 1e-12), (128, 1e-12), (256, 1e-12), (256, 1e-12)]
+# the oracle's energy for the same run, stored by tests/golden/make_heisenberg_n100.py
+SWEEP_GOLDEN = os.path.join(ROOT, "tests", "golden", "heisenberg_n100_dmrg.json")
+
+
+def sweep_reference():
+    """Stored oracle result of the N=100 sweeps (energy, per-sweep times)."""
+    with open(SWEEP_GOLDEN) as f:
+        return json.load(f)
 
 
 def bench_sweeps(ctx, tnh):
@@ -271,6 +279,11 @@ def bench_sweeps(ctx, tnh):
     e64 = res["fp64"]["energy"]
     res["dE_rel_mixed_vs_fp64"] = abs(res["bf16x6"]["energy"] - e64) / abs(e64)
     res["energy_per_bond_fp64"] = e64 / (SWEEP_N - 1)
+    ref = sweep_reference()
+    res["energy_oracle"] = ref["energy"]
+    res["dE_rel_vs_oracle"] = {k: abs(res[k]["energy"] - ref["energy"]) / abs(ref["energy"]) for k in ("bf16x6", "fp64")}
+    res["oracle_last_sweep_s"] = {"value": ref["sweeps"][-1]["seconds"], "host": ref["host"],
+                                  "kind": "oracle, stored by tests/golden/make_heisenberg_n100.py"}
     res["model"] = (f"U(1) Heisenberg chain N={SWEEP_N}, Neel start, maxdim "
                     f"{[m for m, _ in SWEEP_SCHEDULE]}, cutoff 1e-12, Lanczos <= 16 steps")
     res["small"] = bench_small_sweeps(ctx, tnh)
@@ -371,6 +384,21 @@ def blas_threads():
         if os.environ.get(var):
             return int(os.environ[var])
     return os.cpu_count()
+
+
+def cpu_model():
+    """Host CPU model and logical CPU count (lscpu; the machine type where absent)."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return f"{name or platform.machine()}, {os.cpu_count()} logical CPUs"
 
 
 # --------------------------------------------------------------- clocks
@@ -518,7 +546,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                                 "sample": f"{args.steps} oracle bond updates of the workload"},
+                                 "sample": f"{args.steps} oracle bond updates of the workload",
+                                 "cpu": cpu_model()},
                 "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -639,7 +668,7 @@ def main():
         oracle_bond(host)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                                "sample": "1 oracle bond update of the same workload"}
+                                "sample": "1 oracle bond update of the same workload", "cpu": cpu_model()}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
