@@ -421,7 +421,10 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None,
     two-site state, splits it with the truncated SVD (U -> A_j and S V ->
     A_{j+1} going right, U S -> A_j and V -> A_{j+1} going left) and updates
     one environment. No noise or subspace expansion. The returned energy is
-    the eigenvalue at the last bond of the last sweep.
+    the eigenvalue at the last bond of the last sweep. Each sweep's stats hold
+    its last energy, the largest link dimension, the largest and the summed
+    truncation error of its bonds (svd_trunc's relative discarded weight) and
+    its Lanczos products.
 
     ``mpo`` may be a list of MPOs: H is their sum (Sec. 7.2), kept as
     separate terms, each with its own environments, and H_eff . x is the
@@ -451,7 +454,7 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None,
     energy = None
     stats = []
     for sw, (maxdim, cutoff) in enumerate(sweeps):
-        maxerr, nmv = 0.0, 0
+        maxerr, sumerr, nmv = 0.0, 0.0, 0
         for j, direction in [(j, +1) for j in range(N - 1)] + \
                             [(j, -1) for j in range(N - 2, -1, -1)]:
             th = theta(A[j], A[j + 1])
@@ -471,6 +474,7 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None,
             nmv += k
             U, S, V, err = svd_trunc(th, 2, cutoff, maxdim, mindim)
             maxerr = max(maxerr, err)
+            sumerr += err
             if direction > 0:
                 A[j] = U
                 A[j + 1] = scale_link(V, S, 0)
@@ -486,7 +490,7 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None,
                 for i, p in enumerate(P):
                     RO[i][j + 1] = overlap_right(RO[i][j + 2], p[j + 1], A[j + 1])
         st = dict(sweep=sw, energy=energy, maxdim=max(a.inds[2].dim for a in A),
-                  truncerr=maxerr, matvecs=nmv)
+                  truncerr=maxerr, truncerr_sum=sumerr, matvecs=nmv)
         stats.append(st)
         if observer:
             observer(st)
