@@ -535,8 +535,8 @@ def main():
             return
         host = host_inputs()
         cores = blas_threads()
-        for _ in range(max(0, min(args.warmup, 1))):
-            oracle_bond(host, k=2)
+        for _ in range(args.warmup):
+            oracle_bond(host)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             oracle_bond(host)
