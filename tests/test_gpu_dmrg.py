@@ -102,6 +102,20 @@ def test_dmrg_config1_random_product(ctx):
     assert E - e_ed < 1e-4 * abs(e_ed)
 
 
+def test_dmrg_config1_converged_vs_ed(ctx):
+    # the same chain and start at maxdim 256, cutoff 1e-12: the exact ground
+    # energy (sparse Lanczos over the 184 756 states of Sz=0) to 1e-9
+    from test_oracle_dmrg import dense_site_mpo
+    N = 20
+    sweeps = [(16, 1e-12), (64, 1e-12), (256, 1e-12), (256, 1e-12)]
+    E, st, Eo, sto = run_both(ctx, pm.heisenberg(N), dense_site_mpo(om.heisenberg_mpo(N)), False,
+                              ("vec", synth.product_spinors(1, N, 2)), sweeps)
+    e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)), om.SPIN_QN, (0,))
+    assert abs(E - Eo) < 1e-9 * abs(Eo), (E, Eo)
+    assert abs(E - e_ed) < 1e-9 * abs(e_ed), (E, e_ed)
+    assert E >= e_ed - 1e-12 * abs(e_ed)
+
+
 def test_dmrg_mixed_with_tiny_cutoff_matches_fp64(ctx):
     # BF16x6 matvecs leave noise-level singular values (~1e-7 of the largest)
     # in theta; a cutoff of 1e-14 keeps them, so the factorisation must still

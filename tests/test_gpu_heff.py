@@ -81,6 +81,37 @@ def test_contract_rejects_equal_arrows(ctx):
     assert e.value.code == 3
 
 
+def test_contract_with_nothing_to_contract_gives_zero(ctx):
+    # degenerate block-sparse products; C starts as NaN and must come out 0:
+    # (1) A has no allowed block (odd flux, even charges);
+    # (2) A and B hold blocks, but no pair agrees on the contracted sector
+    #     (each keeps one of its two allowed blocks), as the oracle finds
+    import torch
+    from paper_2007_14822_gb300.tnh import Index, Tensor
+    i = Index([((0,), 3), ((-2,), 2)], +1, 1)
+    k = Index([((0,), 2), ((2,), 4)], +1, 2)
+    l = Index([((0,), 5), ((2,), 3)], +1, 3)
+    A0 = Tensor([i, k], (1,))
+    assert A0.blocks == []
+    B, _ = H.random_pair([k.dag(), l], (0,), 3, "B")
+    A1 = Tensor([i, k], (0,), blocks=[(0, 0)], offsets=[0]).fill(lambda key, shp: synth_block(4, "A", key, shp))
+    B1 = Tensor([k.dag(), l], (0,), blocks=[(1, 1)], offsets=[0]).fill(lambda key, shp: synth_block(4, "B", key, shp))
+    want = ocontract(H.to_oracle(A1).relabel([1, 2]), H.to_oracle(B1).relabel([2, 3]), out_labels=[3, 1])
+    assert all(not np.any(v) for v in want.blocks.values())
+    for p in ("fp64", "bf16x6"):
+        for A_, B_ in ((A0, B), (A1, B1)):
+            Cd = Tensor([l, i], (0,))
+            assert Cd.blocks == [(0, 0), (1, 1)]
+            Cd.data.fill_(float("nan"))
+            ctx.contract(A_, B_, Cd, prec(p))
+            assert torch.all(Cd.data == 0), p
+
+
+def synth_block(seed, tag, key, shp):
+    from paper_2007_14822_gb300 import synth
+    return synth.block_gaussian(seed, tag, key, shp)
+
+
 # ------------------------------------------------------------------ H_eff
 def _heff_case(ctx, m, nsect, p, seed=7, maxd=None):
     d = H.heff_inputs(m, None, seed, nsect=nsect, maxd=maxd)
