@@ -1,5 +1,7 @@
 """The C-ABI library: it builds, loads without a GPU, exports every symbol the
-header declares, and its host-only layout helper agrees with the oracle."""
+header declares, the binding's structs, enum values and argument counts match
+the header as a C compiler reads it, and the host-only layout helper agrees
+with the oracle."""
 import re
 import os
 import subprocess
@@ -87,3 +89,59 @@ def test_layout_rejects_bad_index(lib):
     from paper_2007_14822_gb300 import tnh
     with pytest.raises(tnh.TnhError):
         tnh.layout([tnh.Index([((0,), 0)])], (0,))
+
+
+# ------------------------------------------- struct layouts and enum values
+STRUCTS = ["tnh_index", "tnh_tensor", "tnh_sweep_params", "tnh_sweep_stat", "tnh_dmrg_problem"]
+ENUMS = ["TNH_OK", "TNH_ERR_ARG", "TNH_ERR_LABEL", "TNH_ERR_ARROW", "TNH_ERR_FLUX", "TNH_ERR_SHAPE",
+         "TNH_ERR_OOM", "TNH_ERR_CUDA", "TNH_ERR_TIMEOUT", "TNH_ERR_NUMERIC", "TNH_ERR_NOT_CONVERGED",
+         "TNH_FP64", "TNH_BF16x6", "TNH_BF16x3", "TNH_BF16"]
+
+
+def c_layouts(tmp_path):
+    """sizeof / offsetof of the header's structs and the enum values, as a
+    plain C compiler lays them out from include/tnh.h."""
+    from paper_2007_14822_gb300 import tnh
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tnh.h"', "int main(void) {"]
+    for s in STRUCTS:
+        lines.append(f'    printf("sizeof {s} %zu\\n", sizeof({s}));')
+        for f, _ in getattr(tnh, s)._fields_:
+            lines.append(f'    printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    for e in ENUMS:
+        lines.append(f'    printf("enum {e} %d\\n", (int){e});')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out.splitlines()}
+
+
+def test_binding_structs_and_enums_match_header(tmp_path):
+    import ctypes
+    from paper_2007_14822_gb300 import tnh
+    want = c_layouts(tmp_path)
+    for s in STRUCTS:
+        cls = getattr(tnh, s)
+        assert ctypes.sizeof(cls) == want[("sizeof", s)], s
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == want[(s, f)], (s, f)
+    for e in ENUMS:
+        if e.startswith("TNH_ERR") or e == "TNH_OK":
+            assert tnh.STATUS[want[("enum", e)]] == e
+        else:
+            assert tnh.PRECISION[e[4:].lower()] == want[("enum", e)]
+
+
+def test_binding_argument_counts_match_header(lib):
+    from paper_2007_14822_gb300 import tnh
+    src = open(os.path.join(ROOT, "include", "tnh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = dict(re.findall(r"\b(tnh_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src))
+    assert sorted(protos) == sorted(tnh.SYMBOLS)
+    for name, params in protos.items():
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name
