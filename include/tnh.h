@@ -266,8 +266,10 @@ tnh_status tnh_env_update(tnh_ctx* ctx, int32_t dir, const tnh_tensor* E,
  * their row charge (each group is one dense matrix, as a combiner groups
  * equal-QN sectors, Sec. 4) and every group is factorised by one-sided
  * Jacobi on the device: float32 block sweeps find the dominant subspace,
- * float64 sweeps on the candidate columns (at least maxdim + 32, and every
- * column within 1e-4 of the largest singular value) give the result. The
+ * float64 sweeps on the candidate columns give the result. The candidates
+ * are the kept count k that the float32 values predict under the same
+ * cutoff/maxdim rule, plus 16 + k/8, plus every column within 1e-4 of the
+ * largest singular value, at most a group's row count per group. The
  * singular values of all groups are pooled and truncated in float64: the
  * squares are summed from the smallest upward while their share of the total
  * stays <= cutoff, at most maxdim and at least max(mindim, 1) values are kept
