@@ -236,8 +236,10 @@ void tnh_heff_free(tnh_heff* plan);
  * vectors, dot products, tridiagonal eigensolve and the final energy
  * E = <psi|H psi> and residual |H psi - E psi| run in float64 on the device
  * (the final product is an FP64 H_eff). Stops when the Ritz residual
- * estimate falls below tol * max(1, |E|) or after krylov_dim matvecs.
- * Synchronises the context's stream once per iteration. */
+ * estimate falls below tol * max(1, |E|) or after krylov_dim matvecs
+ * (1 <= krylov_dim <= 255, else TNH_ERR_ARG; a zero or non-finite start
+ * vector is TNH_ERR_NUMERIC). Synchronises the context's stream once per
+ * iteration. */
 tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol,
                         double* energy, double* resid, int32_t* matvecs);
 /* Lowest eigenpair of H_eff by Davidson: the subspace grows by the
