@@ -31,8 +31,20 @@ def hamiltonian_sparse(N, d, terms):
     return H.tocsr()
 
 
+def _require_symmetric(H):
+    """A real Hamiltonian is a symmetric matrix. The eigensolvers below read
+    one triangle only, so a term list that breaks the symmetry (a missing or
+    mis-signed Hermitian conjugate) would pass unnoticed: refuse it."""
+    D = abs(H - H.T)
+    big = abs(H).max() if (H.nnz if sp.issparse(H) else H.size) else 0.0
+    if D.max() > 1e-12 * max(1.0, float(big)):
+        raise ValueError("the Hamiltonian built from these terms is not symmetric")
+
+
 def hamiltonian_dense(N, d, terms):
-    return hamiltonian_sparse(N, d, terms).toarray()
+    H = hamiltonian_sparse(N, d, terms).toarray()
+    _require_symmetric(H)
+    return H
 
 
 def basis_charges(N, site_qn):
@@ -52,6 +64,7 @@ def ground_energy(N, d, terms, site_qn=None, sector=None, k=1):
         ch = basis_charges(N, site_qn)
         sel = np.nonzero(np.all(ch == np.asarray(sector)[None, :], axis=1))[0]
         H = H[sel][:, sel]
+    _require_symmetric(H)
     n = H.shape[0]
     if n <= 4096:
         w = np.linalg.eigh(H.toarray())[0]
