@@ -1,0 +1,137 @@
+"""Planted mistakes in the oracle, on the CPU: each one must fail a pin.
+
+Every case edits one line of an oracle module's source: a wrong coefficient,
+sign or index, a transposed operand, a dropped sum or a wrong boundary rule.
+The edited module is loaded beside the original, every binding of the
+original's functions, classes and arrays (in the oracle and in the pin
+modules) is pointed at the edited ones for the duration of the case, and the
+pin that should catch the mistake is run. Nothing is changed on disk.
+
+Edits that leave every result the same are not listed, because no pin can
+see them:
+- the three-term Lanczos coefficients: the full reorthogonalisation, applied
+  twice, removes the same components again;
+- dropping S from the next site in a left-to-right step: only the Lanczos
+  start vector of the next bond changes, and the MPS stays canonical;
+- the sign of J or h in the transverse-field Ising chain: the spectrum is
+  unchanged under a spin flip on every other site (J) or on every site (h).
+"""
+import importlib
+import inspect
+import math
+import sys
+import types
+
+import numpy as np
+import pytest
+
+import test_oracle_blocksparse as TB
+import test_oracle_dmrg as TD
+import test_oracle_models as TM
+
+# (case id, oracle module, original line(s), planted line(s), pin, pin args)
+CASES = [
+    ("spin operators as Pauli matrices", "oracle.models",
+     "SZ = np.array([[0.5, 0.0], [0.0, -0.5]])", "SZ = np.array([[1.0, 0.0], [0.0, -1.0]])",
+     TM.test_heisenberg_small_closed_forms, (4, -0.75 - math.sqrt(3) / 2)),
+    ("bulk MPO: S-S+ coefficient", "oracle.models",
+     "    W[4, 1] = (0.5 * SM).T", "    W[4, 1] = (1.0 * SM).T",
+     TM.test_heisenberg_bulk_mpo_matches_terms, ()),
+    ("bulk MPO: SzSz sign", "oracle.models",
+     "    W[4, 3] = SZ.T", "    W[4, 3] = -SZ.T",
+     TM.test_heisenberg_bulk_mpo_matches_terms, ()),
+    ("exchange terms: S+S- without its conjugate's coefficient", "oracle.models",
+     "        terms.append((0.5 * J, [(i, SP), (j, SM)]))", "        terms.append((1.0 * J, [(i, SP), (j, SM)]))",
+     TM.test_heisenberg_small_closed_forms, (4, -0.75 - math.sqrt(3) / 2)),
+    ("Hubbard hopping: conjugate with the wrong sign", "oracle.models",
+     "            terms.append((t, [(i, c @ F_SITE), (i + 1, cd)]))",
+     "            terms.append((-t, [(i, c @ F_SITE), (i + 1, cd)]))",
+     TM.test_hubbard_u0_free_fermions, (4,)),
+    ("Hubbard: Jordan-Wigner parity dropped", "oracle.models",
+     "F_SITE = np.diag([1.0, -1.0, -1.0, 1.0])", "F_SITE = np.diag([1.0, 1.0, 1.0, 1.0])",
+     TM.test_hubbard_u0_free_fermions, (4,)),
+    ("Hubbard: interaction on one spin species", "oracle.models",
+     "    terms += [(U, [(i, N_UP @ N_DN)]) for i in range(N)]", "    terms += [(U, [(i, N_UP)]) for i in range(N)]",
+     TM.test_hubbard_dimer_closed_form, (4.0,)),
+    ("J1-J2 chain: next-nearest bonds dropped", "oracle.models",
+     "           [(i, i + 2, J2) for i in range(N - 2)]", "           [(i, i + 2, J2) for i in range(0)]",
+     TM.test_majumdar_ghosh, (6,)),
+    ("H_eff: R transposed", "oracle.dmrg",
+     '    R = R.relabel(["b", "w2", "bp"])\n    psi', '    R = R.relabel(["bp", "w2", "b"])\n    psi',
+     TD.test_heff_equals_projected_hamiltonian, ("heisenberg",)),
+    ("H_eff: W1 applied transposed", "oracle.dmrg",
+     '    W1 = W1.relabel(["w", "w1", "s1", "s1p"])', '    W1 = W1.relabel(["w", "w1", "s1p", "s1"])',
+     TD.test_heff_equals_projected_hamiltonian, ("heisenberg",)),
+    ("H_eff: L transposed", "oracle.dmrg",
+     '    L = L.relabel(["a", "w", "ap"])\n    W1', '    L = L.relabel(["ap", "w", "a"])\n    W1',
+     TD.test_heff_equals_projected_hamiltonian, ("heisenberg",)),
+    ("left environment: W transposed", "oracle.dmrg",
+     '    Wt = W.relabel(["w", "w1", "s", "sp"])\n    Ab = dag(A).relabel(["ap", "sp", "bp"])\n    X = contract(L, Ak)',
+     '    Wt = W.relabel(["w", "w1", "sp", "s"])\n    Ab = dag(A).relabel(["ap", "sp", "bp"])\n    X = contract(L, Ak)',
+     TD.test_heff_hermitian_and_matches_chain_energy, ()),
+    ("Lanczos: Ritz vector with a wrong sign", "oracle.dmrg",
+     "    x = scale(q[0], s[0])", "    x = scale(q[0], -s[0])",
+     TD.test_lanczos_matches_eigh, ()),
+    ("truncation: strict cutoff boundary", "oracle.dmrg",
+     "        if tail[k - 1] <= cutoff:", "        if tail[k - 1] < cutoff:",
+     TD.test_truncation_count_rule, ()),
+    ("truncation: absolute instead of relative error", "oracle.dmrg",
+     "    tail = np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]]) / total",
+     "    tail = np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]])",
+     TD.test_truncation_count_rule, ()),
+    ("truncation: maxdim ignored", "oracle.dmrg",
+     "    keep = min(keep, maxdim, n)", "    keep = min(keep, n)",
+     TD.test_truncation_count_rule, ()),
+    ("SVD: V rows out of order", "oracle.dmrg",
+     "            Vt_.blocks[(ci,) + ck] = Vt[idx, coff[ck]:coff[ck] + cc].reshape((len(idx),) + shp)",
+     "            Vt_.blocks[(ci,) + ck] = Vt[idx[::-1], coff[ck]:coff[ck] + cc].reshape((len(idx),) + shp)",
+     TD.test_svd_trunc_eckart_young_and_predicted_count, ()),
+    ("flux rule: arrows ignored", "oracle.blocksparse",
+     "        f = qn_add(f, qn_scale(ind.arrow, ind.qn(s)))", "        f = qn_add(f, ind.qn(s))",
+     TB.test_allowed_blocks_equals_filtered_full_product, ()),
+    ("contraction: block pairs overwrite instead of sum", "oracle.blocksparse",
+     "            C.blocks[kc] = C.blocks[kc] + prod", "            C.blocks[kc] = prod",
+     TB.test_blocksparse_contract_equals_dense, ()),
+]
+
+
+def plant(monkeypatch, modname, old, new):
+    """Load ``modname`` with ``old`` replaced by ``new`` and rebind, for this
+    test only, every reference to the original module's objects."""
+    mod = importlib.import_module(modname)
+    src = inspect.getsource(mod)
+    assert src.count(old) == 1, f"the line to edit is not unique in {modname}"
+    mutant = types.ModuleType(modname)
+    mutant.__package__ = modname.rsplit(".", 1)[0]
+    mutant.__file__ = mod.__file__
+    exec(compile(src.replace(old, new), mod.__file__, "exec"), mutant.__dict__)
+    repl = {}
+    for name, val in mod.__dict__.items():
+        if name.startswith("__") or name not in mutant.__dict__:
+            continue
+        own = getattr(val, "__module__", None) == modname
+        if ((inspect.isfunction(val) or inspect.isclass(val)) and own) or isinstance(val, np.ndarray):
+            repl[id(val)] = mutant.__dict__[name]
+    for mname, module in list(sys.modules.items()):
+        if module is None or not (mname == "oracle" or mname.startswith("oracle.") or mname.startswith("test_")
+                                  or mname == "helpers"):
+            continue
+        for k, v in list(vars(module).items()):
+            if id(v) in repl:
+                monkeypatch.setattr(module, k, repl[id(v)])
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_pin_passes_on_the_unchanged_oracle(case, monkeypatch):
+    # the loader itself changes nothing: the same source, reloaded, passes
+    _, modname, old, _, pin, args = case
+    plant(monkeypatch, modname, old, old)
+    pin(*args)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_fails_its_pin(case, monkeypatch):
+    _, modname, old, new, pin, args = case
+    plant(monkeypatch, modname, old, new)
+    with pytest.raises((AssertionError, ValueError)):
+        pin(*args)
