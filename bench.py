@@ -563,7 +563,11 @@ def main():
         dist.init_process_group("nccl")
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    build.build()
+    # one rank per node compiles (the ranks share the tree); the others wait
+    if dist is None or local == 0:
+        build.build()
+    if dist:
+        dist.barrier()
     ctx = tnh.Context(local)
     host = host_inputs()
     bond = GpuBond(ctx, host, pinned=True)
@@ -577,8 +581,11 @@ def main():
         t_dev = time_steps(torch, bond, args.steps, flush)
     torch.cuda.synchronize()
     t_dev = max_over_ranks(t_dev, dist, "cuda")
-    # end to end: host buffers in, result out, every step
-    t_e2e = time_steps(torch, bond, max(1, args.steps // 2), flush, e2e=True) / max(1, args.steps // 2)
+    # end to end: host buffers in, result out, every step (slowest rank)
+    if dist:
+        dist.barrier()
+    n_e2e = max(1, args.steps // 2)
+    t_e2e = max_over_ranks(time_steps(torch, bond, n_e2e, flush, e2e=True), dist, "cuda") / n_e2e
     # per-kernel breakdown of one step (profiled separately)
     ctx.profile_begin()
     bond.step()
