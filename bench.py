@@ -609,7 +609,7 @@ def main():
         torch.cuda.synchronize()
         hs[name] = heff_flops / (a.elapsed_time(b) / 1e3 / reps) / 1e12
     plan.free()
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's product on the same dense inputs
         t_or = oracle_matvec_seconds(bond.L, bond.W, bond.W, bond.R, bond.theta)
         hs["oracle"] = heff_flops / t_or / 1e12
@@ -666,10 +666,12 @@ def main():
                     "h2d_bytes_per_step": bond.h2d_bytes, "d2h_bytes_per_step": bond.d2h_bytes},
             "gpu_launches": launches * args.steps, "clocks": clk.summary(), "roofline": roof,
             "heff_tflops": hs, "kernels_per_step": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
-    if rank == 0 and not args.no_extra:
+    # the other workloads and the oracle are reported at N=1 only (at N>1
+    # they would hold every GPU while rank 0 alone works)
+    if rank == 0 and world == 1 and not args.no_extra:
         line["heff_qn"] = bench_qn_heff(ctx, torch, tnh, tuple(k for k in args.oracle_matvec.split(",") if k))
         line["sweep"] = bench_sweeps(ctx, tnh)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = blas_threads()
         t0 = time.perf_counter()
         oracle_bond(host)
