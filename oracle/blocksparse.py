@@ -143,7 +143,9 @@ def allowed_blocks(inds, flux):
 
 
 class BlockTensor:
-    """Block-sparse tensor: indices, flux and a dict sector-tuple -> array."""
+    """Block-sparse tensor: indices, flux and a dict sector-tuple -> array
+    (block-sparse storage, Sec. 6 and Sec. 9.2; the stored blocks obey the
+    flux rule of Sec. 8.3)."""
 
     def __init__(self, inds, flux=None, blocks=None):
         self.inds = list(inds)

@@ -31,13 +31,18 @@ from .blocksparse import BlockTensor, IN, OUT, QNIndex, contract, qn_add
 
 # ------------------------------------------------------------ primitives
 def dag(T):
-    """Reverse every arrow and negate the flux (real data is unchanged)."""
+    """Reverse every arrow and negate the flux (real data is unchanged);
+    the conjugate of Sec. 8.2 and Sec. 8.3 for real tensors."""
     return BlockTensor([i.dag() for i in T.inds], tuple(-x for x in T.flux),
                        T.blocks)
 
 
 def heff_apply(L, W1, W2, R, psi):
-    """H_eff . psi via S1 (sum a), S2 (sum w, s1), S3 (sum w1, s2), S4 (sum w2, b)."""
+    """H_eff . psi via S1 (sum a), S2 (sum w, s1), S3 (sum w1, s2), S4 (sum w2, b).
+
+    The local effective Hamiltonian of two-site DMRG (Sec. 7.2), applied as
+    four pairwise labelled contractions (Sec. 4, Sec. 9.4).
+    """
     L = L.relabel(["a", "w", "ap"])
     W1 = W1.relabel(["w", "w1", "s1", "s1p"])
     W2 = W2.relabel(["w1", "w2", "s2", "s2p"])
@@ -51,7 +56,7 @@ def heff_apply(L, W1, W2, R, psi):
 
 
 def heff_dense_matrix(L, W1, W2, R, psi_like):
-    """H_eff as an explicit matrix on the stored entries of ``psi_like``.
+    """H_eff (Sec. 7.2) as an explicit matrix on the stored entries of ``psi_like``.
 
     Column j is H_eff applied to the j-th unit vector of the block-sparse
     vector space (blocks in sorted order, row-major inside a block).
@@ -86,6 +91,8 @@ def from_vector(v, like):
 def env_left(L, A, W):
     """L_new[b, w', b'] = sum L[a,w,a'] A[a,s,b] W[w,w',s,s'] A[a',s',b'].
 
+    Forming the left environment tensor one site further (Sec. 7.2).
+
     Three pairwise contractions in the order: sum a; sum (w, s); sum (a', s').
     The bra tensor is ``dag(A)`` (real entries, reversed arrows).
     """
@@ -99,7 +106,11 @@ def env_left(L, A, W):
 
 
 def env_right(R, A, W):
-    """R_new[a, w, a'] = sum A[a,s,b] W[w,w',s,s'] A[a',s',b'] R[b,w',b']."""
+    """R_new[a, w, a'] = sum A[a,s,b] W[w,w',s,s'] A[a',s',b'] R[b,w',b'].
+
+    Forming the right environment tensor one site further (Sec. 7.2), in the
+    same three pairwise contractions as ``env_left``.
+    """
     R = R.relabel(["b", "w1", "bp"])
     Ak = A.relabel(["a", "s", "b"])
     Wt = W.relabel(["w", "w1", "s", "sp"])
@@ -110,14 +121,16 @@ def env_right(R, A, W):
 
 
 def theta(A1, A2):
-    """Two-site state theta[a,s1,s2,b] = sum_c A1[a,s1,c] A2[c,s2,b]."""
+    """Two-site state theta[a,s1,s2,b] = sum_c A1[a,s1,c] A2[c,s2,b]: two MPS
+    tensors (Sec. 7.3) contracted over their shared link (Sec. 4)."""
     A1 = A1.relabel(["a", "s1", "c"])
     A2 = A2.relabel(["c", "s2", "b"])
     return contract(A1, A2)
 
 
 def left_boundary(A0, W0, start):
-    """L_0[a, w, a'] = 1 at the MPO link state ``start`` (a, a' have dim 1)."""
+    """L_0[a, w, a'] = 1 at the MPO link state ``start`` (a, a' have dim 1):
+    the left end of the environment recursion of Sec. 7.2."""
     a = A0.inds[0]
     inds = [a.dag(), W0.inds[0].dag(), a]
     T = BlockTensor.zeros(inds)
@@ -129,7 +142,8 @@ def left_boundary(A0, W0, start):
 
 
 def right_boundary(AN, WN, done):
-    """R_N[b, w, b'] = 1 at the MPO link state ``done`` (b, b' have dim 1)."""
+    """R_N[b, w, b'] = 1 at the MPO link state ``done`` (b, b' have dim 1):
+    the right end of the environment recursion of Sec. 7.2."""
     b = AN.inds[2]
     inds = [b.dag(), WN.inds[1].dag(), b]
     T = BlockTensor.zeros(inds)
@@ -192,7 +206,8 @@ def lanczos(apply, x0, krylov_dim=64, tol=1e-10, vdot=None, axpy=None,
 
 
 def energy_residual(apply, x):
-    """E = <x|H x>/<x|x> and r = |H x - E x| (all float64)."""
+    """E = <x|H x>/<x|x> and r = |H x - E x| (all float64), for the local
+    eigenproblem of Sec. 7.2."""
     y = apply(x)
     nx2 = x.vdot(x)
     E = y.vdot(x) / nx2
@@ -316,7 +331,8 @@ def svd_trunc(T, nrow, cutoff, maxdim, mindim=1):
 
 
 def scale_link(T, S, axis):
-    """Multiply T by diag(S) along its link ``axis`` (sector order = sorted Q)."""
+    """Multiply T by diag(S) along its link ``axis`` (sector order = sorted Q):
+    the singular values of Sec. 5 moved into one factor."""
     out = T.copy()
     Qs = sorted(S)
     for key, v in out.blocks.items():
@@ -329,7 +345,8 @@ def scale_link(T, S, axis):
 
 # ----------------------------------------------------------------- MPS
 def product_mps_basis(site_index, states, nq):
-    """Product state with site j in basis state ``states[j]`` (QN MPS)."""
+    """Product state with site j in basis state ``states[j]`` (QN MPS), the
+    initial state of the DMRG example of Sec. 7.2."""
     N = len(states)
     A = []
     q = (0,) * nq
@@ -349,7 +366,8 @@ def product_mps_basis(site_index, states, nq):
 
 
 def product_mps_vectors(site_index, vecs):
-    """Dense product state with site j in the normalised vector ``vecs[j]``."""
+    """Dense product state with site j in the normalised vector ``vecs[j]``
+    (an initial MPS for Sec. 7.2 without conserved charges)."""
     A = []
     left = QNIndex([((0,) * site_index.nq, 1)], OUT)
     for v in vecs:
@@ -375,7 +393,8 @@ def overlap_left(LO, P, A):
 
 
 def overlap_right(RO, P, A):
-    """RO'[pa, a] = sum P[pa, s, pb] A[a, s, b] RO[pb, b]."""
+    """RO'[pa, a] = sum P[pa, s, pb] A[a, s, b] RO[pb, b]: one site of the
+    overlap with a previous state (Sec. 7.2, excited states)."""
     RO = RO.relabel(["pb", "b"])
     Pb = dag(P).relabel(["pa", "s", "pb"])
     Ak = A.relabel(["a", "s", "b"])
@@ -498,7 +517,8 @@ def dmrg(mpo, mps, sweeps, krylov_dim=64, tol=1e-10, mindim=1, observer=None,
 
 
 def mps_overlap(P, A):
-    """<P|A> of two MPS (real data), by a left-to-right overlap sweep."""
+    """<P|A> of two MPS (real data), by a left-to-right overlap sweep
+    (the MPS inner product of Sec. 7.3)."""
     LO, _ = overlap_boundaries(P, A)
     for j in range(len(A)):
         LO = overlap_left(LO, P[j], A[j])

@@ -66,7 +66,8 @@ HUB_QN = [(0, 0), (1, 1), (1, -1), (2, 0)]
 
 
 def op_charge(op, site_qn):
-    """Charge q(s_out) - q(s_in) that a definite-charge operator adds."""
+    """Charge q(s_out) - q(s_in) that a definite-charge operator adds: its
+    flux (Sec. 8.3)."""
     nz = np.argwhere(np.abs(op) > 0)
     if len(nz) == 0:
         return tuple(0 for _ in site_qn[0])
@@ -122,7 +123,8 @@ def j1j2_cylinder_pairs(Lx, Ly, J1=1.0, J2=0.5):
 
 
 def spin_pair_terms(pairs):
-    """S_i . S_j = Sz Sz + (S+ S- + S- S+)/2 for each (i, j, J)."""
+    """S_i . S_j = Sz Sz + (S+ S- + S- S+)/2 for each (i, j, J), the bond
+    term of Eq. (1) in Sec. 7.1."""
     terms = []
     for i, j, J in pairs:
         terms.append((J, [(i, SZ), (j, SZ)]))
@@ -183,6 +185,9 @@ def _link_index(states, qns, arrow):
 
 def fsa_mpo(N, site_ops_qn, onsite, pairs_ops):
     """Finite-state-automaton MPO for on-site terms plus two-site products.
+
+    An exact MPO of a sum of operator products, as OpSum/AutoMPO builds
+    one (Sec. 7.1).
 
     ``onsite[i]``: matrix (or None) added at site i.
     ``pairs_ops``: list of (i, j, [(coef, op_i, op_j), ...]) with i < j; the
@@ -254,7 +259,8 @@ def fsa_mpo(N, site_ops_qn, onsite, pairs_ops):
 
 
 def heisenberg_like_mpo(N, pairs):
-    """MPO of sum_(i,j,J) J S_i . S_j with S=1/2 sites and (2Sz,) QNs."""
+    """MPO of sum_(i,j,J) J S_i . S_j with S=1/2 sites and (2Sz,) QNs (the
+    bond terms of Eq. (1), Sec. 7.1, on any set of pairs)."""
     plist = [(i, j, [(0.5 * J, SP, SM), (0.5 * J, SM, SP), (J, SZ, SZ)])
              for i, j, J in pairs]
     return fsa_mpo(N, SPIN_QN, [None] * N, plist)
@@ -285,7 +291,9 @@ def tfim_mpo(N, J=1.0, h=1.0):
 
 
 def hubbard_mpo(N, t=1.0, U=4.0):
-    """Hubbard chain MPO with (N, 2Sz) QNs; bulk bond dimension 6."""
+    """Hubbard chain MPO with (N, 2Sz) QNs; bulk bond dimension 6. The
+    Hubbard model is one of the benchmark systems of Sec. 12.1 (there on a
+    cylinder); the charges are those of Sec. 8.1."""
     plist = []
     for i in range(N - 1):
         lst = []
