@@ -1,4 +1,7 @@
 // Context, error handling, index/tensor parsing and the layout helper.
+// Indices carry QN sectors and an arrow (Sec. 8.2); a tensor stores only
+// the blocks whose flux matches its own (Sec. 8.3), packed one after the
+// other in block-sparse storage (Sec. 6, Sec. 9.2).
 #include <algorithm>
 #include <cstdarg>
 #include <cstring>

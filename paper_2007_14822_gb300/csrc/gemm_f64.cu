@@ -1,4 +1,5 @@
-// Grouped float64 GEMM on the CUDA cores: the plain FP64 path.
+// Grouped float64 GEMM on the CUDA cores: the plain FP64 path of the
+// matrix-multiply step of a contraction (Sec. 9.4).
 //
 // C_t[M][ldc] = A_t[M][K] * B_t[N][K]^T for every task t, both operands
 // K-major and zero-padded to 64-row / 16-column multiples by the packer

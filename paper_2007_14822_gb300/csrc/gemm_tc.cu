@@ -1,4 +1,6 @@
-// Grouped split-bfloat16 GEMM on the 5th-generation tensor cores (tcgen05).
+// Grouped split-bfloat16 GEMM on the 5th-generation tensor cores (tcgen05):
+// the matrix-multiply step of a permute-then-multiply contraction (Sec. 9.4),
+// one task per output block of a block-sparse product (Sec. 8.3, Sec. 9.2).
 //
 // C_t[M][ldc] (float64, or float32 per task) = sum over products (p, q) of A_t^(p) * B_t^(q)^T,
 // where A^(0..P-1) / B^(0..P-1) are the bfloat16 parts of the float64
