@@ -145,3 +145,55 @@ def test_binding_argument_counts_match_header(lib):
         params = params.strip()
         n = 0 if params in ("", "void") else params.count(",") + 1
         assert len(getattr(lib, name).argtypes) == n, name
+
+
+# ------------------------------------------------------- error statuses
+_NULL_CALLS = r'''
+import ctypes as C, json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2007_14822_gb300 import tnh
+L = tnh.lib()
+out = {}
+for name in tnh.SYMBOLS:
+    f = getattr(L, name)
+    args = [0 if t in (C.c_int32, C.c_int, C.c_int64) else 0.0 if t is C.c_double else None
+            for t in f.argtypes]
+    r = f(*args)
+    msg = L.tnh_last_error(None)
+    out[name] = [r if isinstance(r, int) or r is None else "text", (msg or b"").decode()]
+print(json.dumps(out))
+'''
+
+
+def test_null_handles_give_a_status_not_a_crash(lib):
+    # every entry point called with NULL handles and zero sizes returns
+    # TNH_ERR_ARG with a message (the free functions return nothing), in a
+    # child process so that a crash would fail the test, not the run
+    import json
+    import sys
+    from paper_2007_14822_gb300 import tnh
+    p = subprocess.run([sys.executable, "-c", _NULL_CALLS, ROOT], capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0, p.stderr[-2000:]
+    got = json.loads(p.stdout.strip().splitlines()[-1])
+    assert sorted(got) == sorted(tnh.SYMBOLS)
+    for name, (code, msg) in got.items():
+        if name in ("tnh_destroy", "tnh_heff_free", "tnh_svd_free"):
+            assert code is None, name
+        elif name == "tnh_last_error":
+            assert code in ("text", None), name
+        else:
+            assert code == 1, (name, code, msg)
+            assert msg, name
+
+
+def test_create_without_a_device_fails_with_cuda_status(lib):
+    # nothing falls back to the CPU: with no usable GPU, tnh_create returns
+    # TNH_ERR_CUDA and names the failing CUDA call
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.tnh_create(ctypes.byref(h), 0, None) == 7
+    assert not h.value
+    assert b"cudaGetDeviceCount" in lib.tnh_last_error(None)
