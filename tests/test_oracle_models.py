@@ -121,6 +121,10 @@ def test_cylinder_bond_counts():
     assert nn == Lx * Ly + (Lx - 1) * Ly
     assert nnn == 2 * (Lx - 1) * Ly
     assert max(j - i for i, j, _ in pairs) == 2 * Ly - 1
+    # snake order: consecutive sites are nearest neighbours, so the chain of
+    # sites is a path through the lattice
+    J = {(i, j): c for i, j, c in pairs}
+    assert all(J.get((i, i + 1)) == 1.0 for i in range(Lx * Ly - 1))
 
 
 def test_hubbard_mpo_matches_terms():

@@ -14,7 +14,13 @@ see them:
 - dropping S from the next site in a left-to-right step: only the Lanczos
   start vector of the next bond changes, and the MPS stays canonical;
 - the sign of J or h in the transverse-field Ising chain: the spectrum is
-  unchanged under a spin flip on every other site (J) or on every site (h).
+  unchanged under a spin flip on every other site (J) or on every site (h);
+- the order of the Kronecker factors when ED sums the charges of a basis
+  state: a total charge does not depend on the order of its terms;
+- Lanczos without the reorthogonalisation: in exact arithmetic the
+  three-term recurrence already gives an orthogonal basis, and at the sizes
+  of the pins the lowest Ritz pair still converges; the reorthogonalisation
+  is a safeguard against lost orthogonality, which the outputs do not show.
 """
 import importlib
 import inspect
@@ -92,6 +98,48 @@ CASES = [
     ("contraction: block pairs overwrite instead of sum", "oracle.blocksparse",
      "            C.blocks[kc] = C.blocks[kc] + prod", "            C.blocks[kc] = prod",
      TB.test_blocksparse_contract_equals_dense, ()),
+    ("allowed blocks: arrow of the last index ignored", "oracle.blocksparse",
+     "        need = qn_scale(last.arrow, qn_sub(flux, f))", "        need = qn_sub(flux, f)",
+     TB.test_allowed_blocks_equals_filtered_full_product, ()),
+    ("finite-state MPO: pass-through identity dropped", "oracle.models",
+     "                put(st, st, np.eye(d))", "                pass",
+     TM.test_j1j2_chain_mpo_matches_terms, ()),
+    ("finite-state MPO: on-site term doubled", "oracle.models",
+     '            put("start", "done", onsite[j])', '            put("start", "done", 2 * onsite[j])',
+     TM.test_hubbard_mpo_matches_terms, ()),
+    ("finite-state MPO: link charge with the wrong sign", "oracle.models",
+     "        return tuple(-x for x in op_charge(first_op[st], site_qn))",
+     "        return tuple(x for x in op_charge(first_op[st], site_qn))",
+     TM.test_fsa_heisenberg_mpo_matches_terms, ()),
+    ("Ising MPO: XX bond as XZ", "oracle.models",
+     "        bulk[2, 1] = (-J * PX).T", "        bulk[2, 1] = (-J * PZ).T",
+     TM.test_tfim_mpo_matches_terms, ()),
+    ("Hubbard: down creator built from the up mode", "oracle.models",
+     "CD_UP, CD_DN = C_UP.T.copy(), C_DN.T.copy()", "CD_UP, CD_DN = C_UP.T.copy(), C_UP.T.copy()",
+     TM.test_hubbard_u0_free_fermions, (4,)),
+    ("cylinder: column order instead of snake order", "oracle.models",
+     "    return x * Ly + (y if x % 2 == 0 else Ly - 1 - y)", "    return x * Ly + y",
+     TM.test_cylinder_bond_counts, ()),
+    ("cylinder: one diagonal of J2 dropped", "oracle.models",
+     "                add(s, snake_site(x + 1, (y - 1) % Ly, Ly), J2)", "                pass",
+     TM.test_cylinder_bond_counts, ()),
+    ("H_eff: W2 applied transposed", "oracle.dmrg",
+     '    W2 = W2.relabel(["w1", "w2", "s2", "s2p"])', '    W2 = W2.relabel(["w1", "w2", "s2p", "s2"])',
+     TD.test_heff_equals_projected_hamiltonian, ("heisenberg",)),
+    ("right environment: W transposed", "oracle.dmrg",
+     '    Wt = W.relabel(["w", "w1", "s", "sp"])\n    Ab = dag(A).relabel(["ap", "sp", "bp"])\n    X = contract(Ak, R)',
+     '    Wt = W.relabel(["w", "w1", "sp", "s"])\n    Ab = dag(A).relabel(["ap", "sp", "bp"])\n    X = contract(Ak, R)',
+     TD.test_heff_hermitian_and_matches_chain_energy, ()),
+    ("overlap: output indices swapped", "oracle.dmrg",
+     '    return contract(contract(LO, Pb), Ak, out_labels=["pb", "b"])',
+     '    return contract(contract(LO, Pb), Ak, out_labels=["b", "pb"])',
+     TD.test_mps_overlap_and_projected_state_match_full_vectors, ()),
+    ("truncation: float64 zero threshold too low", "oracle.dmrg",
+     "    nres = int(np.sum(s2 >= 1e-16 * total))", "    nres = int(np.sum(s2 >= 1e-20 * total))",
+     TD.test_truncation_count_rule, ()),
+    ("SVD: pooled values ranked ascending", "oracle.dmrg",
+     "    pool.sort()", "    pool.sort(reverse=True)",
+     TD.test_svd_trunc_eckart_young_and_predicted_count, ()),
 ]
 
 
