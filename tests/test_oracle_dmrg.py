@@ -180,6 +180,37 @@ def test_lanczos_matches_eigh():
     assert np.linalg.norm(M @ x - E * x) < 1e-8
 
 
+def test_energy_residual_rayleigh_quotient():
+    # E = <x|Hx>/<x|x> and r = |Hx - Ex|: zero residual on an eigenvector,
+    # and r^2 = |Hx|^2/|x|^2 - E^2 for a unit vector (Pythagoras, Hx - Ex is
+    # orthogonal to x); vectors are plain numpy arrays with the BlockTensor
+    # operations the function uses
+    class V:
+        def __init__(self, a):
+            self.a = np.asarray(a, dtype=np.float64)
+
+        def vdot(self, o):
+            return float(self.a @ o.a)
+
+        def axpy(self, c, o):
+            return V(self.a + c * o.a)
+
+        def norm(self):
+            return float(np.linalg.norm(self.a))
+    rng = np.random.default_rng(41)
+    M = rng.standard_normal((30, 30))
+    M = M + M.T
+    w, U = np.linalg.eigh(M)
+    apply = lambda v: V(M @ v.a)
+    E, r = D.energy_residual(apply, V(3.0 * U[:, 4]))
+    assert abs(E - w[4]) < 1e-12 * np.abs(w).max() and r < 1e-11 * np.abs(w).max() * 3.0
+    x = rng.standard_normal(30)
+    E, r = D.energy_residual(apply, V(x))
+    u = x / np.linalg.norm(x)
+    assert abs(E - u @ M @ u) < 1e-12 * np.abs(w).max()
+    assert abs(r / np.linalg.norm(x) - np.sqrt(np.sum((M @ u) ** 2) - E ** 2)) < 1e-10 * np.abs(w).max()
+
+
 def test_truncation_count_rule():
     s = np.array([1.0, 0.5, 0.1, 0.01])
     tot = float(np.sum(s ** 2))
