@@ -7,10 +7,12 @@
 //    small fraction of its float32 rate, so the bulk of the rotations is done
 //    in float32 and float64 is kept for the result:
 //    a. float32 block Jacobi on X = M_Q (or M_Q^T): column blocks of b
-//       columns are paired round-robin; each pair of blocks (X and V
-//       columns) is loaded into shared memory by one CTA, which runs one
-//       inner Jacobi sweep over its 2b columns. One cooperative launch
-//       works on all groups, with a bounded grid barrier between rounds.
+//       columns are paired round-robin; the X columns of each pair of
+//       blocks are loaded into shared memory by one CTA, which runs one
+//       inner Jacobi sweep over its 2b columns, accumulates the rotations
+//       into a 2b x 2b matrix Q and updates the V columns once, V <- V Q.
+//       One cooperative launch works on all groups, with a bounded grid
+//       barrier between rounds.
 //       This gives V32 with columns orthogonal to float32 accuracy.
 //    b. The candidate columns (the largest float32 singular values: the kept
 //       count that they predict plus a margin, and all within 1e-4 of the
