@@ -3,7 +3,9 @@
 //   y[a',s1',s2',b'] = sum L[a,w,a'] W1[w,w1,s1,s1'] W2[w1,w2,s2,s2']
 //                          R[b,w2,b'] x[a,s1,s2,b]
 //
-// One application is four launches on the plan's stream:
+// One application is four launches on the plan's stream (plus one ordered
+// reduction of float32 partial tiles after each GEMM that the autotuner
+// splits along K), replayed from a CUDA graph after the first calls:
 //   1. gather  x -> operand B of S1 (split-bfloat16 tiles or float64 rows)
 //   2. S1      T1[(w,a'), (s1,s2,b)] = sum_a L[a,w,a'] x[a,s1,s2,b]: a grouped
 //              GEMM with one task per a-sector (Sec. 9.4: blocks whose
