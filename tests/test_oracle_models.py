@@ -132,3 +132,22 @@ def test_hubbard_mpo_matches_terms():
     mpo = models.hubbard_mpo(N, 1.0, 4.0)
     assert mpo.max_bond() == 6
     _check_mpo(mpo, N, 4, models.hubbard_terms(N, 1.0, 4.0))
+
+
+def test_hubbard_approaches_lieb_wu():
+    # Bethe-ansatz ground-state energy per site of the half-filled Hubbard
+    # chain (Lieb and Wu): e(U) = -4t int_0^inf J0(w) J1(w) / (w (1 + e^(wU/2))) dw,
+    # -0.57373 at U/t = 4. The slopes of the open-chain ED energies E0(N)
+    # approach it from above as N grows (a loose check: the remainder
+    # falls off like 1/N^2)
+    from scipy import integrate, special
+    t, U = 1.0, 4.0
+
+    def f(w):
+        return special.j0(w) * special.j1(w) / (w * (1.0 + math.exp(min(w * U / 2, 700.0))))
+    e_lw = -4.0 * t * integrate.quad(f, 0.0, 200.0, limit=2000)[0]
+    assert abs(e_lw + 0.5737293678984) < 1e-9
+    E = {N: ed.ground_energy(N, 4, models.hubbard_terms(N, t, U), models.HUB_QN, (N, 0)) for N in (6, 8, 10)}
+    s1, s2 = (E[8] - E[6]) / 2, (E[10] - E[8]) / 2
+    assert e_lw < s2 < s1
+    assert s2 - e_lw < 2e-3
