@@ -223,9 +223,8 @@ def truncation_count(svals_desc, cutoff, maxdim, mindim=1):
     upward while the truncation error stays within ``cutoff``; at most
     ``maxdim`` values are kept. Reading used: the error is relative,
     sum(discarded s^2) / sum(all s^2); the boundary is non-strict; at least
-    ``mindim`` (and at least one) values are kept. Values with
-    s^2 < 1e-16 sum(all s^2) (below 1e-8 of the norm) are numerically zero
-    in float64 and are not kept unless ``mindim`` asks for them.
+    ``mindim`` (and at least one) values are kept. Nothing else is dropped:
+    at cutoff 0 every value whose weight is above zero is kept.
     """
     s2 = np.asarray(svals_desc, dtype=np.float64) ** 2
     n = len(s2)
@@ -246,8 +245,6 @@ def truncation_count(svals_desc, cutoff, maxdim, mindim=1):
     keep = max(keep, 1, mindim)
     keep = min(keep, maxdim, n)
     keep = max(keep, min(mindim, n), 1)
-    nres = int(np.sum(s2 >= 1e-16 * total))
-    keep = min(keep, max(nres, min(mindim, n), 1))
     return keep, float(tail[keep])
 
 

@@ -135,3 +135,37 @@ def test_svd_rank_deficient(ctx, side):
     assert svd.kept == sum(len(v) for v in So.values())
     rec = D.theta(Uo, Vo)
     assert H.rel_err(rec, tho) < 1e-12
+
+
+def test_svd_float64_zeros_dropped_only_below_cutoff_resolution(ctx):
+    # The library drops singular values with s^2 < 1e-16 of the total even at
+    # cutoff 0 (float64 cannot resolve their vectors); Sec. 5's rule, which
+    # the oracle follows, keeps them. The two agree for every cutoff of at
+    # least n * 1e-16 (n values): the values the library drops weigh less
+    # than that together, so the cutoff drops them too. theta is a dense
+    # 16 x 16 matrix U diag(s) V^T with four values below 1e-8 of the norm.
+    from paper_2007_14822_gb300.tnh import Index, Tensor
+    from oracle.blocksparse import BlockTensor
+    rng = np.random.default_rng(3)
+    s = np.array([10.0 ** (-k / 2) for k in range(12)] + [1e-9, 3e-10, 1e-11, 2e-12])
+    U, _ = np.linalg.qr(rng.standard_normal((16, 16)))
+    V, _ = np.linalg.qr(rng.standard_normal((16, 16)))
+    M = (U * s) @ V.T
+    a, sd = Index.dense(8, +1), Index.dense(2, +1)
+    T = Tensor([a, sd, sd, a.dag()])
+    T.fill(lambda key, shp: M.reshape(shp))
+    To = H.to_oracle(T)
+    n = 16
+    resolved = int(np.sum(s ** 2 >= 1e-16 * np.sum(s ** 2)))
+    assert resolved == 12
+    # cutoff 0: the oracle keeps all 16, the library the 12 resolved ones
+    _, So, _, _ = D.svd_trunc(To, 2, 0.0, 10 ** 6)
+    assert sum(len(v) for v in So.values()) == n
+    svd = ctx.svd_trunc(T, 2, 0.0, 10 ** 6)
+    assert svd.kept == resolved
+    # cutoff >= n * 1e-16: both keep the same values with the same error
+    for cutoff in (n * 1e-16, 1e-14, 1e-12, 1e-10):
+        _, So, _, erro = D.svd_trunc(To, 2, cutoff, 10 ** 6)
+        svd = ctx.svd_trunc(T, 2, cutoff, 10 ** 6)
+        assert svd.kept == sum(len(v) for v in So.values()), cutoff
+        assert abs(svd.truncerr - erro) < 1e-15, cutoff

@@ -232,13 +232,18 @@ def test_truncation_count_rule():
     # at least one is kept
     k, _ = D.truncation_count(s, 1.0, 10)
     assert k == 1
-    # below 1e-8 of the norm a singular value is a float64 zero: not kept
-    # even at cutoff 0, unless mindim asks for it
+    # Sec. 5 discards only what the cutoff covers: at cutoff 0 even values far
+    # below float64 resolution of the norm are kept; an exact zero is
+    # discarded (its weight 0 is within the cutoff); a cutoff just above the
+    # tail of the two tiny values drops them
     s2 = np.array([1.0, 1e-3, 2e-9, 1e-12])
     k, err = D.truncation_count(s2, 0.0, 10)
-    assert k == 2 and abs(err - (4e-18 + 1e-24) / float(np.sum(s2 ** 2))) < 1e-30
-    k, _ = D.truncation_count(s2, 0.0, 10, mindim=3)
-    assert k == 3
+    assert k == 4 and err == 0.0
+    k, err = D.truncation_count(np.array([1.0, 1e-3, 0.0]), 0.0, 10)
+    assert k == 2 and err == 0.0
+    tot2 = float(np.sum(s2 ** 2))
+    k, err = D.truncation_count(s2, 1.01 * (4e-18 + 1e-24) / tot2, 10)
+    assert k == 2 and abs(err - (4e-18 + 1e-24) / tot2) < 1e-30
 
 
 def test_svd_trunc_eckart_young_and_predicted_count():

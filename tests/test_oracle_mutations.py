@@ -134,9 +134,6 @@ CASES = [
      '    return contract(contract(LO, Pb), Ak, out_labels=["pb", "b"])',
      '    return contract(contract(LO, Pb), Ak, out_labels=["b", "pb"])',
      TD.test_mps_overlap_and_projected_state_match_full_vectors, ()),
-    ("truncation: float64 zero threshold too low", "oracle.dmrg",
-     "    nres = int(np.sum(s2 >= 1e-16 * total))", "    nres = int(np.sum(s2 >= 1e-20 * total))",
-     TD.test_truncation_count_rule, ()),
     ("SVD: pooled values ranked ascending", "oracle.dmrg",
      "    pool.sort()", "    pool.sort(reverse=True)",
      TD.test_svd_trunc_eckart_young_and_predicted_count, ()),
