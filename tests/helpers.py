@@ -91,3 +91,64 @@ def heff_inputs(m, w_qn, seed, nsect=1, maxd=None, symmetric=False):
         from test_oracle_dmrg import dense_site_mpo
         om_W = dense_site_mpo(om.heisenberg_mpo(3)).W[1]
     return dict(L=L, R=R, W=W, psi=psi, Lo=Lo, Ro=Ro, Wo=om_W, psio=psio)
+
+
+# -------------------------------------------------------- per-block parity
+# Element-wise bound: |got - want| <= ELEM_TOL * scale, where scale is the
+# same contraction evaluated by the oracle on the absolute values of every
+# input (the sum of |terms| that bounds the rounding error of each output
+# element). A missed or misplaced K piece, a wrong block or a block written
+# twice changes an element by a sizeable fraction of that sum and fails it.
+ELEM_TOL = {"fp64": 1e-12, "bf16x6": 2e-5}
+# per-block relative error (norm of the block's error over the block's norm)
+BLOCK_TOL = {"fp64": 1e-11, "bf16x6": 1e-5}
+
+
+def abs_tensor(T):
+    """Oracle BlockTensor with every element replaced by its absolute value."""
+    return BlockTensor(T.inds, T.flux, {k: np.abs(v) for k, v in T.blocks.items()})
+
+
+def block_report(got, want, scale):
+    """Worst per-block relative error and worst element error over its scale.
+
+    Blocks of ``got`` that ``want`` does not hold must be zero. A block whose
+    norm is below 1e-2 of its scale's norm (cancellation: a one-element block
+    whose sum happens to be small) is measured against that floor instead of
+    its own norm.
+    """
+    worst_blk, worst_el, where_blk, where_el = 0.0, 0.0, None, None
+    keys = set(want.blocks) | set(got.blocks)
+    for k in keys:
+        w = want.blocks.get(k)
+        g = got.blocks.get(k)
+        s = scale.blocks.get(k)
+        if w is None:
+            w = np.zeros_like(g)
+        if g is None:
+            g = np.zeros_like(w)
+        if s is None:
+            s = np.zeros_like(w)
+        d = np.abs(g - w)
+        if d.size == 0:
+            continue
+        nw, ns = float(np.linalg.norm(w)), float(np.linalg.norm(s))
+        den = max(nw, 1e-2 * ns, 1e-300)
+        rb = float(np.linalg.norm(d)) / den
+        if rb > worst_blk:
+            worst_blk, where_blk = rb, k
+        re = float(np.max(d / np.maximum(s, 1e-300)))
+        if re > worst_el:
+            worst_el, where_el = re, k
+    return dict(block=worst_blk, block_key=where_blk, elem=worst_el, elem_key=where_el)
+
+
+def assert_parity(got, want, scale, p, norm_tol):
+    """Norm-wise error below ``norm_tol``, every block below BLOCK_TOL[p],
+    every element below ELEM_TOL[p] of its absolute-value scale."""
+    err = rel_err(got, want)
+    rep = block_report(got, want, scale)
+    assert err < norm_tol, ("norm-wise", err, rep)
+    assert rep["block"] < BLOCK_TOL[p], ("per block", rep)
+    assert rep["elem"] < ELEM_TOL[p], ("per element", rep)
+    return err, rep

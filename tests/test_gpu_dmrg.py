@@ -69,14 +69,19 @@ def test_dmrg_heisenberg_qn(ctx, prec):
     assert abs(E - e_ed) < 1e-9 * abs(e_ed)
 
 
-def test_dmrg_hubbard_qn(ctx):
-    N = 6
-    sweeps = [(16, 1e-12), (64, 1e-13), (128, 1e-13)]
+@pytest.mark.parametrize("N,prec", [(6, "fp64"), (6, "bf16x6"), (8, "bf16x6")])
+def test_dmrg_hubbard_qn(ctx, N, prec):
+    # U(1) x U(1) (N, 2Sz) Hubbard chain, U/t = 4, half filling, d = 4: the
+    # sweeps in FP64 and with BF16x6 matvecs against the oracle's sweeps at the
+    # same settings and exact diagonalisation (the last maxdim is the exact
+    # bond dimension 4^(N/2), so the sweeps converge to the ground state)
+    sweeps = [(16, 1e-12), (64, 1e-13), (4 ** (N // 2), 1e-13), (4 ** (N // 2), 1e-13)]
     E, st, Eo, sto = run_both(ctx, pm.hubbard(N, 1.0, 4.0), om.hubbard_mpo(N, 1.0, 4.0), True,
-                              ("basis", [1, 2] * (N // 2)), sweeps)
+                              ("basis", [1, 2] * (N // 2)), sweeps, prec=prec,
+                              tol=1e-10 if prec == "fp64" else 1e-7)
     e_ed = ed.ground_energy(N, 4, om.hubbard_terms(N, 1.0, 4.0), om.HUB_QN, (N, 0))
-    assert abs(E - Eo) < 1e-9 * abs(Eo)
-    assert abs(E - e_ed) < 1e-9 * abs(e_ed)
+    assert abs(E - Eo) < 1e-9 * abs(Eo), (E, Eo)
+    assert abs(E - e_ed) < 1e-9 * abs(e_ed), (E, e_ed)
 
 
 def test_dmrg_majumdar_ghosh(ctx):

@@ -51,8 +51,9 @@ def test_contract_block_sparse(ctx, p):
         Cd = Tensor([l, i], (1,))
         ctx.contract(A, B, Cd, prec(p))
         want = ocontract(Ao.relabel([1, 2, 3]), Bo.relabel([3, 4, 2]), out_labels=[4, 1])
-        got = H.to_oracle(Cd)
-        assert H.rel_err(got, want) < TOL[p] * 10
+        scale = ocontract(H.abs_tensor(Ao).relabel([1, 2, 3]), H.abs_tensor(Bo).relabel([3, 4, 2]),
+                          out_labels=[4, 1])
+        H.assert_parity(H.to_oracle(Cd), want, scale, p, TOL[p] * 10)
 
 
 def test_contract_outer_and_full(ctx):
@@ -113,7 +114,16 @@ def synth_block(seed, tag, key, shp):
 
 
 # ------------------------------------------------------------------ H_eff
+def heff_scale(Lo, W1o, W2o, Ro, xo):
+    """The oracle's H_eff on the absolute values of every input: the sum of
+    |terms| of each output element, the scale of its rounding error."""
+    A = H.abs_tensor
+    return D.heff_apply(A(Lo), A(W1o), A(W2o), A(Ro), A(xo))
+
+
 def _heff_case(ctx, m, nsect, p, seed=7, maxd=None):
+    """One product against the oracle; asserts the norm-wise, per-block and
+    per-element bounds and returns the norm-wise error and the plan."""
     d = H.heff_inputs(m, None, seed, nsect=nsect, maxd=maxd)
     plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
     import torch
@@ -123,7 +133,9 @@ def _heff_case(ctx, m, nsect, p, seed=7, maxd=None):
     ytens.data = y
     got = H.to_oracle(ytens)
     want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
-    return H.rel_err(got, want), plan
+    scale = heff_scale(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    err, _ = H.assert_parity(got, want, scale, p, TOL[p])
+    return err, plan
 
 
 @pytest.mark.parametrize("m", [1, 3, 24, 130])
@@ -162,8 +174,10 @@ def test_heff_graph_replay_with_new_buffers(ctx, p):
         xt.data = x
         yt = d["psi"].with_inds(d["psi"].inds)
         yt.data = y
-        want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], H.to_oracle(xt))
-        assert H.rel_err(H.to_oracle(yt), want) < TOL[p], (call, xi, yi)
+        xo = H.to_oracle(xt)
+        want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], xo)
+        scale = heff_scale(d["Lo"], d["Wo"], d["Wo"], d["Ro"], xo)
+        H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
 
 
 @pytest.mark.parametrize("split", ["2,8", "4,3", "1,2"])
@@ -214,12 +228,22 @@ def test_heff_distinct_mpo_tensors(ctx, model, j, p):
     yt = psi.with_inds(psi.inds)
     yt.data = y
     want = D.heff_apply(Lo, H.to_oracle(W1), H.to_oracle(W2), Ro, psio)
-    assert H.rel_err(H.to_oracle(yt), want) < TOL[p]
+    scale = heff_scale(Lo, H.to_oracle(W1), H.to_oracle(W2), Ro, psio)
+    H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
 
 
 @pytest.mark.parametrize("p,tol", [("bf16x3", 1e-3), ("bf16", 2e-2)])
 def test_heff_low_precision_modes_error_bounded(ctx, p, tol):
-    err, _ = _heff_case(ctx, 64, 1, p)
+    # norm-wise only: these modes are not meant to meet the split-mode bounds
+    import torch
+    d = H.heff_inputs(64, None, 7, nsect=1)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    y = torch.zeros_like(d["psi"].data)
+    plan.apply(d["psi"].data, y)
+    yt = d["psi"].with_inds(d["psi"].inds)
+    yt.data = y
+    want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    err = H.rel_err(H.to_oracle(yt), want)
     assert err < tol, err
 
 
@@ -239,14 +263,15 @@ def test_env_update(ctx, direction, p, nsect):
         E, Eo = d["L"], d["Lo"]
         out = Tensor(list(d["L"].inds), (0,))
         ctx.env_update(1, E, A, d["W"], out, prec(p))
-        want = D.env_left(Eo, Ao, d["Wo"])
+        f = D.env_left
     else:
         E, Eo = d["R"], d["Ro"]
         out = Tensor(list(d["R"].inds), (0,))
         ctx.env_update(-1, E, A, d["W"], out, prec(p))
-        want = D.env_right(Eo, Ao, d["Wo"])
-    err = H.rel_err(H.to_oracle(out), want)
-    assert err < TOL[p], err
+        f = D.env_right
+    want = f(Eo, Ao, d["Wo"])
+    scale = f(H.abs_tensor(Eo), H.abs_tensor(Ao), H.abs_tensor(d["Wo"]))
+    H.assert_parity(H.to_oracle(out), want, scale, p, TOL[p])
 
 
 # -------------------------------------------------------------- eigsolve
@@ -305,11 +330,13 @@ def test_heff_plan_sum_matches_sum_of_terms(ctx, p, nsect):
     plan.apply(psi.data, y)      # second call: graph capture
     yt = psi.with_inds(psi.inds)
     yt.data = y
-    want = None
+    want = scale = None
     for t in range(2):
         wt = D.heff_apply(Los[t], H.to_oracle(W1s[t]), H.to_oracle(W2s[t]), Ros[t], psio)
+        st = heff_scale(Los[t], H.to_oracle(W1s[t]), H.to_oracle(W2s[t]), Ros[t], psio)
         want = wt if want is None else want.axpy(1.0, wt)
-    assert H.rel_err(H.to_oracle(yt), want) < TOL[p]
+        scale = st if scale is None else scale.axpy(1.0, st)
+    H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
     # the flops are the two terms' flops
     f = [ctx.heff_plan(Ls[t], W1s[t], W2s[t], Rs[t], psi, prec(p)).flops for t in range(2)]
     assert plan.flops == pytest.approx(sum(f))
@@ -332,15 +359,18 @@ def test_heff_projectors_added(ctx, p):
     yt = d["psi"].with_inds(d["psi"].inds)
     yt.data = y
     want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    scale0 = heff_scale(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    scale = scale0.copy()
     for _, po in phis:
         want = want.axpy(w * po.vdot(d["psio"]), po)
-    assert H.rel_err(H.to_oracle(yt), want) < TOL[p]
+        scale = scale.axpy(w * H.abs_tensor(po).vdot(H.abs_tensor(d["psio"])), H.abs_tensor(po))
+    H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
     # removing them gives H_eff alone
     plan.set_projectors(None, 0.0)
     plan.apply(d["psi"].data, y)
     yt.data = y
     want0 = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
-    assert H.rel_err(H.to_oracle(yt), want0) < TOL[p]
+    H.assert_parity(H.to_oracle(yt), want0, scale0, p, TOL[p])
 
 
 # ------------------------------------------------- diagonal and Davidson
@@ -392,44 +422,29 @@ def test_davidson_matches_eigh(ctx, p, nsect):
 # ------------------------------------------- block-sparse workloads, full size
 @pytest.mark.parametrize("which", [0, 1, 2])
 def test_heff_qn_workloads_full_size(ctx, which):
-    # the bench's block-sparse H_eff workloads at full size, the plan the bench
-    # times (BF16x6, graph replay): the FP64 product against the oracle on an
-    # input restricted to the blocks of a few a-sectors (the oracle's cost
-    # follows the stored input blocks; for the U(1) m=1024 workload, all of
-    # them), and the BF16x6 product against the FP64 one on the full input
+    # the bench's block-sparse H_eff workloads at full size (U(1) m=1024;
+    # J1-J2 cylinder m=2048, w=26; U(1)xU(1) Hubbard m=4096, d=4), the plan
+    # the bench times (BF16x6 after graph capture, and its FP64 product), each
+    # against the oracle on the full input: norm-wise, per block and per
+    # element (the oracle takes up to tens of seconds for the Hubbard one)
     import torch
     import bench
-    from oracle.blocksparse import BlockTensor
     name, kind, m, recipe, seed = bench.QN_CONFIGS[which]
     L, W1, W2, R, psi = bench.qn_heff_inputs(kind, m, recipe, seed)
     plan = ctx.heff_plan(L, W1, W2, R, psi, prec("bf16x6"))
-    n = plan.size
     x = psi.data.clone()
     y64 = torch.zeros_like(x)
     ymx = torch.zeros_like(x)
     for _ in range(3):
         plan.apply(x, ymx)
     plan.apply(x, y64, prec("fp64"))
-    err = (torch.linalg.norm(ymx[:n] - y64[:n]) / torch.linalg.norm(y64[:n])).item()
-    assert err < TOL["bf16x6"], err
-    # sparse input: keep the psi blocks of a few a-sectors
-    nsect_a = psi.inds[0].nsect
-    keep_a = set(range(nsect_a)) if which == 0 else ({nsect_a // 2, nsect_a // 2 + 1} if which == 1 else {nsect_a // 2})
-    xs = torch.zeros_like(x)
-    blocks = {}
-    host = psi.block_arrays()
-    for key, off in zip(psi.blocks, psi.offsets):
-        if key[0] in keep_a:
-            sz = psi.block_size(key)
-            xs[off:off + sz] = psi.data[off:off + sz]
-            blocks[key] = host[key]
-    ys = torch.zeros_like(x)
-    plan.apply(xs, ys, prec("fp64"))
-    Xo = BlockTensor([H.or_index(i) for i in psi.inds], psi.flux, blocks)
-    # L blocks of other a-sectors meet only zero input blocks in S1
-    Lo = BlockTensor([H.or_index(i) for i in L.inds], L.flux,
-                     {k: v for k, v in L.block_arrays().items() if k[0] in keep_a})
-    want = D.heff_apply(Lo, H.to_oracle(W1), H.to_oracle(W2), H.to_oracle(R), Xo)
-    yt = psi.with_inds(psi.inds)
-    yt.data = ys
-    assert H.rel_err(H.to_oracle(yt), want) < TOL["fp64"]
+    args = [H.to_oracle(T) for T in (L, W1, W2, R)]
+    if which != 2:   # the host count of the Hubbard chain enumerates for tens of seconds
+        assert plan.flops == pytest.approx(bench.chain_flops(*args, H.to_oracle(psi)), rel=1e-12)
+    want = D.heff_apply(*args, H.to_oracle(psi))
+    scale = heff_scale(*args, H.to_oracle(psi))
+    for p, y in (("fp64", y64), ("bf16x6", ymx)):
+        yt = psi.with_inds(psi.inds)
+        yt.data = y
+        err, rep = H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
+        print(name, p, "norm-wise", err, "worst block", rep["block"], "worst element", rep["elem"])
