@@ -9,7 +9,9 @@
 // the same labelled contraction for dense tensors, computed by the same
 // kernels (operand packing, FP64 GEMM, result scatter), with every piece of
 // scratch it needs -- the packed operands, the GEMM result and the launch
-// descriptors -- taken from one static device array of fixed size.
+// descriptors -- taken from one static device array of fixed size. The
+// descriptors are written into that array by a small kernel that receives
+// them as launch arguments, so no host buffer is copied either.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds kScratchBytes of it until the process exits. Host code only
@@ -32,6 +34,8 @@ namespace {
 constexpr int kMaxDevices = 64;
 constexpr int kChunk = 8192;                        // elements per pack / unpack block
 constexpr int kMaxChunks = 2048;                    // descriptor room per operand
+
+__device__ __forceinline__ int nchunks_dev(int64_t n) { return (int)((n + kChunk - 1) / kChunk); }
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -79,11 +83,18 @@ Dense view(const tnh_tensor* t, const char* what) {
         d.dim[i] = ix.sect_dim[0];
         d.label[i] = ix.label;
         d.arrow[i] = ix.arrow;
+        // every tensor that fits the scratch has far fewer elements than this
+        TNH_REQUIRE(n <= (int64_t(1) << 40) / d.dim[i], TNH_ERR_ARG, "noalloc: %s has too many elements", what);
         n *= d.dim[i];
     }
-    for (int i = d.rank - 1, s = 1; i >= 0; --i) {
-        d.stride[i] = s;
-        s *= (int)d.dim[i];
+    for (int i = 0; i < d.rank; ++i)
+        for (int j = 0; j < i; ++j)
+            TNH_REQUIRE(d.label[i] != d.label[j], TNH_ERR_LABEL, "noalloc: repeated label %lld in %s",
+                        (long long)d.label[i], what);
+    int64_t st = 1;
+    for (int i = d.rank - 1; i >= 0; --i) {
+        d.stride[i] = st;
+        st *= d.dim[i];
     }
     TNH_REQUIRE(d.off >= 0 && d.off + n <= t->size, TNH_ERR_SHAPE, "noalloc: %s block outside its data", what);
     return d;
@@ -97,11 +108,32 @@ int find_label(const Dense& t, int64_t l) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int fill_chunks(Chunk* out, int piece, int64_t n) {
-    int c = 0;
-    for (int64_t s = 0; s < n; s += kChunk)
-        out[c++] = Chunk{piece, (int)s, (int)std::min<int64_t>(kChunk, n - s)};
-    return c;
+int nchunks(int64_t n) { return (int)((n + kChunk - 1) / kChunk); }
+
+// Launch descriptors of one call: the fixed part travels as a kernel
+// argument, the chunk lists (kChunk elements each) are generated here.
+struct DescHead {
+    Piece p[3];
+    OpGeom ga, gb;
+    GemmTask task;
+    int64_t cbase;
+    int ldc;
+    int64_t n[3];   // elements of packed A, packed B, the result
+};
+struct Desc {
+    DescHead h;
+    Chunk ch[3][kMaxChunks];
+};
+
+__global__ void write_desc_kernel(DescHead h, Desc* __restrict__ d) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) d->h = h;
+    for (int q = 0; q < 3; ++q) {
+        const int nc = nchunks_dev(h.n[q]);
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+            const int64_t s0 = (int64_t)c * kChunk;
+            d->ch[q][c] = Chunk{0, (int)s0, (int)(h.n[q] - s0 < kChunk ? h.n[q] - s0 : (int64_t)kChunk)};
+        }
+    }
 }
 
 }  // namespace
@@ -151,7 +183,10 @@ extern "C" tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor*
         pc.nc = nfb;
         for (int q = 0; q < nfa; ++q) {
             int k = find_label(o, a.label[fa[q]]);
-            TNH_REQUIRE(k >= 0 && o.dim[k] == a.dim[fa[q]], TNH_ERR_LABEL, "noalloc: free label of A not in C");
+            TNH_REQUIRE(k >= 0, TNH_ERR_LABEL, "noalloc: free label %lld of A not in C", (long long)a.label[fa[q]]);
+            TNH_REQUIRE(o.dim[k] == a.dim[fa[q]] && o.arrow[k] == a.arrow[fa[q]], TNH_ERR_SHAPE,
+                        "noalloc: C index for label %lld differs from A's (dimension or arrow)",
+                        (long long)a.label[fa[q]]);
             pa.dims[q] = pc.dims[q] = (int)a.dim[fa[q]];
             pa.strides[q] = a.stride[fa[q]];
             pc.strides[q] = o.stride[k];
@@ -159,7 +194,10 @@ extern "C" tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor*
         }
         for (int q = 0; q < nfb; ++q) {
             int k = find_label(o, b.label[fb[q]]);
-            TNH_REQUIRE(k >= 0 && o.dim[k] == b.dim[fb[q]], TNH_ERR_LABEL, "noalloc: free label of B not in C");
+            TNH_REQUIRE(k >= 0, TNH_ERR_LABEL, "noalloc: free label %lld of B not in C", (long long)b.label[fb[q]]);
+            TNH_REQUIRE(o.dim[k] == b.dim[fb[q]] && o.arrow[k] == b.arrow[fb[q]], TNH_ERR_SHAPE,
+                        "noalloc: C index for label %lld differs from B's (dimension or arrow)",
+                        (long long)b.label[fb[q]]);
             pb.dims[q] = pc.dims[nfa + q] = (int)b.dim[fb[q]];
             pb.strides[q] = b.stride[fb[q]];
             pc.strides[nfa + q] = o.stride[k];
@@ -171,6 +209,12 @@ extern "C" tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor*
             pb.strides[nfb + q] = b.stride[ib[q]];
             K *= a.dim[ia[q]];
         }
+        // the operands and the result must fit the scratch before any size is narrowed to int
+        const int64_t lim = (int64_t)(kScratchBytes / sizeof(double));
+        TNH_REQUIRE(M <= lim / K && N <= lim / K && M <= lim / N, TNH_ERR_ARG,
+                    "noalloc: this contraction (M %lld, N %lld, K %lld) exceeds the static maximum of %zu bytes "
+                    "of scratch (use tnh_contract for larger tensors)", (long long)M, (long long)N, (long long)K,
+                    kScratchBytes);
         pa.rows = pc.rows = (int)M;
         pb.rows = pc.cols = (int)N;
         pa.cols = pb.cols = (int)K;
@@ -186,14 +230,6 @@ extern "C" tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor*
         // scratch layout: descriptors | packed A | packed B | GEMM result
         const size_t a_elems = (size_t)g.mt * kF64TileM * g.lda, b_elems = (size_t)g.nt * kF64TileN * g.ldb;
         const size_t c_elems = (size_t)M * N;
-        struct Desc {
-            Piece p[3];
-            OpGeom ga, gb;
-            GemmTask task;
-            int64_t cbase;
-            int ldc;
-            Chunk ch[3][kMaxChunks];
-        };
         const size_t desc_bytes = align256(sizeof(Desc));
         const size_t off_a = desc_bytes, off_b = off_a + align256(a_elems * 8), off_c = off_b + align256(b_elems * 8);
         const size_t need = off_c + align256(c_elems * 8);
@@ -204,9 +240,7 @@ extern "C" tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor*
         TNH_REQUIRE((na + kChunk - 1) / kChunk <= kMaxChunks && (nb + kChunk - 1) / kChunk <= kMaxChunks &&
                         (ncc + kChunk - 1) / kChunk <= kMaxChunks, TNH_ERR_ARG,
                     "noalloc: operand too large for the static descriptor area");
-        // host staging of the descriptors (fixed size, on the stack)
-        Desc h;
-        std::memset(&h, 0, sizeof h);
+        DescHead h{};
         h.p[0] = pa;
         h.p[1] = pb;
         h.p[2] = pc;
@@ -215,22 +249,23 @@ extern "C" tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor*
         h.task = g;
         h.cbase = 0;
         h.ldc = (int)N;
-        const int nca = fill_chunks(h.ch[0], 0, na), ncb = fill_chunks(h.ch[1], 0, nb), ncu = fill_chunks(h.ch[2], 0, ncc);
+        h.n[0] = na;
+        h.n[1] = nb;
+        h.n[2] = ncc;
+        const int nca = nchunks(na), ncb = nchunks(nb), ncu = nchunks(ncc);
         Desc* d = reinterpret_cast<Desc*>(base);
         cudaStream_t s = c->stream;
-        // the call reuses the array: stage descriptors, zero the padded operand space
-        CUDA_CHECK(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, s));
+        // the call reuses the array: write the descriptors, zero the padded operand space
+        write_desc_kernel<<<8, 256, 0, s>>>(h, d);
         double* pA = reinterpret_cast<double*>(base + off_a);
         double* pB = reinterpret_cast<double*>(base + off_b);
         double* pC = reinterpret_cast<double*>(base + off_c);
         CUDA_CHECK(cudaMemsetAsync(pA, 0, a_elems * 8, s));
         CUDA_CHECK(cudaMemsetAsync(pB, 0, b_elems * 8, s));
-        launch_pack_f64(&d->p[0], d->ch[0], nca, &d->ga, a.data, pA, s);
-        launch_pack_f64(&d->p[1], d->ch[1], ncb, &d->gb, b.data, pB, s);
-        launch_gemm_f64(&d->task, 1, g.mt * g.nt, pA, pB, pC, s);
-        launch_unpack(&d->p[2], d->ch[2], ncu, &d->cbase, &d->ldc, pC, o.data, s);
+        launch_pack_f64(&d->h.p[0], d->ch[0], nca, &d->h.ga, a.data, pA, s);
+        launch_pack_f64(&d->h.p[1], d->ch[1], ncb, &d->h.gb, b.data, pB, s);
+        launch_gemm_f64(&d->h.task, 1, g.mt * g.nt, pA, pB, pC, s);
+        launch_unpack(&d->h.p[2], d->ch[2], ncu, &d->h.cbase, &d->h.ldc, pC, o.data, s);
         CUDA_CHECK(cudaGetLastError());
-        // the staging struct lives on this stack frame: the copy above is
-        // from pageable memory and completes before cudaMemcpyAsync returns
     });
 }
