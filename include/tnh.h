@@ -127,6 +127,31 @@ tnh_status tnh_profile_begin(tnh_ctx* ctx);
 tnh_status tnh_profile_end(tnh_ctx* ctx, int32_t max_kinds, int32_t* nkinds, char* names,
                            int64_t* launches, double* ms);
 
+/* ---- failure injection (test support; no counterpart in the paper) ------
+ * The library turns failures into status codes and keeps the context usable.
+ * These calls make failures happen on purpose, without faulting a device.
+ *
+ * tnh_debug_fail_alloc: the k-th device allocation the library makes from
+ * now on (k = 1: the next one; any context, any thread) fails as if the
+ * device were out of memory, so the call making it returns TNH_ERR_OOM after
+ * releasing everything it had allocated. k = 0 disarms. Process-wide.
+ * TNH_ERR_ARG for k < 0.
+ *
+ * tnh_debug_pool_used: synchronises the context's stream, then writes the
+ * bytes of the library's device memory pool (on the context's device) held
+ * by live allocations: equal before and after a failed call means nothing
+ * leaked.
+ *
+ * tnh_debug_wait_timeout: launches one thread that waits on a barrier
+ * nothing ever completes, with the bounded wait the GEMM pipelines use; it
+ * gives up after limit_ns (1 us .. 1 s), records the site in the context's
+ * device error flag and returns. The call then returns TNH_ERR_TIMEOUT (as
+ * any call that finds the flag set) and clears the flag; the context stays
+ * usable. TNH_ERR_ARG for a limit outside the range. */
+tnh_status tnh_debug_fail_alloc(int64_t k);
+tnh_status tnh_debug_pool_used(tnh_ctx* ctx, uint64_t* bytes);
+tnh_status tnh_debug_wait_timeout(tnh_ctx* ctx, uint64_t limit_ns);
+
 /* ---- layout helper (host only, no device work) ------------------------- */
 
 /* Enumerate the blocks of a tensor with the given indices and flux (Sec. 8.3:
@@ -165,13 +190,18 @@ tnh_status tnh_contract(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
  * scratch (packed operands, GEMM result, launch descriptors) lives in one
  * static device array of 16 MiB that every GPU loading the library holds
  * until the process exits; a contraction needing more than that is refused
- * with TNH_ERR_ARG (use tnh_contract). The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) and caches it: make that
- * first call before any stream capture. Every call reuses the same array,
- * so calls whose work overlaps on the GPU (other streams, other contexts on
- * the same device) race and must be serialised by the caller. Asynchronous
- * on the context's stream, except that staging the launch descriptors from
- * host memory waits for the stream's earlier work. */
+ * with TNH_ERR_ARG (use tnh_contract). The launch descriptors are written
+ * into that array by a kernel that gets them as launch arguments: no host
+ * buffer is copied. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it: make that first call before
+ * any stream capture. Every call reuses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other contexts on the same device)
+ * race and must be serialised by the caller. Asynchronous on the context's
+ * stream. Errors, all raised before anything is launched: TNH_ERR_LABEL for
+ * a label repeated within A, B or C, or a free label missing in C;
+ * TNH_ERR_SHAPE when a C index differs from the A or B index of its label
+ * in dimension or arrow; TNH_ERR_ARROW for a contracted pair with equal
+ * arrows; TNH_ERR_ARG for a tensor that is not dense or too large. */
 tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
                                       tnh_tensor* C);
 

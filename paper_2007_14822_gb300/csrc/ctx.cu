@@ -71,6 +71,12 @@ AllocScope::~AllocScope() {
     t_pool_stream = prev_s;
 }
 
+uint64_t pool_used_bytes() {
+    uint64_t v = 0;
+    CUDA_CHECK(cudaMemPoolGetAttribute(device_pool(), cudaMemPoolAttrUsedMemCurrent, &v));
+    return v;
+}
+
 void trim_pool() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
@@ -82,6 +88,8 @@ void trim_pool() {
 void DevBuf::alloc(size_t n) {
     release();
     if (n == 0) n = 16;
+    if (alloc_fault_injected())
+        TNH_FAIL(TNH_ERR_OOM, "device allocation of %zu bytes: injected failure (tnh_debug_fail_alloc)", n);
     cudaError_t e;
     if (t_pool_on) {
         e = cudaMallocFromPoolAsync(&p, n, device_pool(), t_pool_stream);

@@ -84,6 +84,11 @@ struct AllocScope {
 };
 // Return the pool's cached memory of the current device to the driver.
 void trim_pool();
+// Bytes of the current device's pool held by live allocations.
+uint64_t pool_used_bytes();
+// Test support: true for the allocation that an armed countdown selects
+// (tnh_debug_fail_alloc); that allocation then fails with TNH_ERR_OOM.
+bool alloc_fault_injected();
 
 template <class T>
 DevBuf upload(const std::vector<T>& v, cudaStream_t s) {

@@ -29,7 +29,8 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_heff_free", "tnh_eigsolve", "tnh_env_update", "tnh_svd_trunc", "tnh_svd_info",
            "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
            "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
-           "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag"]
+           "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag",
+           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout"]
 
 
 class TnhError(RuntimeError):
@@ -118,6 +119,9 @@ def lib():
         "tnh_dmrg_mps_get": (i32, [vp, i32, P(tnh_tensor)]),
         "tnh_profile_begin": (i32, [vp]),
         "tnh_profile_end": (i32, [vp, i32, P(i32), C.c_char_p, P(i64), P(dbl)]),
+        "tnh_debug_fail_alloc": (i32, [i64]),
+        "tnh_debug_pool_used": (i32, [vp, P(C.c_uint64)]),
+        "tnh_debug_wait_timeout": (i32, [vp, C.c_uint64]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -295,6 +299,21 @@ class Context:
 
     def sync(self):
         self.check(self._lib.tnh_sync(self.h))
+
+    # ---- failure injection (test support)
+    def debug_fail_alloc(self, k):
+        """The k-th device allocation from now fails with TNH_ERR_OOM (0 disarms)."""
+        _check(self._lib.tnh_debug_fail_alloc(int(k)))
+
+    def debug_pool_used(self):
+        """Bytes of the library's device pool held by live allocations (syncs)."""
+        v = C.c_uint64()
+        self.check(self._lib.tnh_debug_pool_used(self.h, C.byref(v)))
+        return v.value
+
+    def debug_wait_timeout(self, limit_ns):
+        """A bounded device wait that nothing completes: raises TNH_ERR_TIMEOUT."""
+        self.check(self._lib.tnh_debug_wait_timeout(self.h, int(limit_ns)))
 
     def profile_begin(self):
         self.check(self._lib.tnh_profile_begin(self.h))

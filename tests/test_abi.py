@@ -156,8 +156,10 @@ L = tnh.lib()
 out = {}
 for name in tnh.SYMBOLS:
     f = getattr(L, name)
-    args = [0 if t in (C.c_int32, C.c_int, C.c_int64) else 0.0 if t is C.c_double else None
+    args = [0 if t in (C.c_int32, C.c_int, C.c_int64, C.c_uint64) else 0.0 if t is C.c_double else None
             for t in f.argtypes]
+    if name == "tnh_debug_fail_alloc":
+        args = [-1]      # 0 is valid (it disarms the injection)
     r = f(*args)
     msg = L.tnh_last_error(None)
     out[name] = [r if isinstance(r, int) or r is None else "text", (msg or b"").decode()]
