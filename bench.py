@@ -1,31 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the two-site DMRG hot path on one GB300 (replicas on N GPUs).
 
-Workload (dense S=1/2 Heisenberg chain bond, N=100 bulk shapes): bond
-dimension m=256, MPO bond dimension w=5, site dimension d=2. Left/right
-environments L, R are (256, 5, 256), the two MPS tensors A_j, A_{j+1} are
-(256, 2, 256), so the two-site state psi is (256, 2, 2, 256). Entries are
-seeded N(0,1) (L seed 2, R seed 3, A seed 4); L and R get the symmetry that
-environments built from a real MPS have, so H_eff is symmetric.
+Headline workload: the effective-Hamiltonian product H_eff.psi at one bulk
+bond (sites 62/63) of the U(1) J1-J2 cylinder Ly=6 x Lx=24 (J2/J1 = 1/2,
+snake order, finite-state MPO with w = 26) at bond dimension m = 2048: the
+link has 41 Gaussian charge sectors of 1..256 states (2Sz = -40..40), L, R
+and psi hold seeded N(0,1) blocks (seed 6). One step is one application of
+the plan's product y = H_eff x in BF16x6 (split-bfloat16 tcgen05 GEMMs with
+float32 accumulation), replayed from its CUDA graph: pack psi, S1 = L.psi,
+the fused W1.W2 pass, S4 = T3.R. L2 is flushed before every step. The
+metric counts the algorithmic flops of the labelled chain (2MNK summed over
+the allowed block pairs of S1..S4; the extra products of the bf16 split are
+not counted) divided by the step time.
 
-One step is one full two-site bond update, every row of the hot path:
-  theta = A_j A_{j+1}                                  (FP64)
-  H_eff plan; Lanczos, K_LANCZOS matvecs in BF16x6     (split-bf16 tcgen05)
-  energy E = <psi|H psi> and residual                  (FP64 H_eff)
-  truncated SVD, maxdim 256, cutoff 1e-10              (FP64 Jacobi)
-  U -> A_j, S V -> A_{j+1}, L_{j+1} = update(L_j, U, W) (FP64)
-
-The reported metric counts the algorithmic flops of the step's contractions
-(theta + (K_LANCZOS + 1) H_eff products + environment update; the extra
-products of the bf16 split are not counted) divided by the step time.
-
-Two more measurements go on the same JSON line (skip with --no-extra):
-  heff_qn  H_eff TFLOP/s, BF16x6 and FP64, on three block-sparse workloads
-           (U(1) m=1024, U(1) J1-J2 cylinder m=2048, U(1)xU(1) Hubbard
-           m=4096); flops are the plan's block-pair sum
-  sweep    DMRG sweep time, BF16x6 vs FP64, U(1) Heisenberg chain N=100
-           (maxdim 256, cutoff 1e-12), and the relative energy difference of
-           the two runs
+More measurements go on the same JSON line (skip with --no-extra):
+  heff_qn          H_eff TFLOP/s, BF16x6 and FP64, on three block-sparse
+                   workloads (U(1) m=1024, the cylinder m=2048, U(1)xU(1)
+                   Hubbard m=4096); flops are the plan's block-pair sum
+  bond_update_m256 one full bond update of the dense Heisenberg chain at
+                   m=256 (theta, Lanczos in BF16x6, FP64 energy, SVD,
+                   environment update): every step of the hot path
+  sweep            DMRG sweep time, BF16x6 vs FP64, and the relative energy
+                   difference of the two runs and to the oracle
 """
 from __future__ import annotations
 
@@ -154,15 +150,21 @@ def qn_link(kind, m, recipe):
     return Index([((2 * (k - (nsect - 1) // 2),), d) for k, d in enumerate(dims)], +1)
 
 
+def qn_mpo(kind):
+    """Host MPO and the bond (j, j+1) of a block-sparse workload."""
+    from paper_2007_14822_gb300 import models as pm
+    if kind == "heis":
+        return pm.heisenberg(8), 3
+    if kind == "cyl":
+        return pm.spin_pairs(144, pm.cylinder_pairs(24, 6, 1.0, 0.5)), 62
+    return pm.hubbard(16, 1.0, 4.0), 7
+
+
 def qn_heff_inputs(kind, m, recipe, seed):
+    """Device tensors L, W1, W2, R, psi of a block-sparse workload."""
     from paper_2007_14822_gb300 import models as pm, synth
     from paper_2007_14822_gb300.tnh import Tensor
-    if kind == "heis":
-        mpo, j = pm.heisenberg(8), 3
-    elif kind == "cyl":
-        mpo, j = pm.spin_pairs(144, pm.cylinder_pairs(24, 6, 1.0, 0.5)), 62
-    else:
-        mpo, j = pm.hubbard(16, 1.0, 4.0), 7
+    mpo, j = qn_mpo(kind)
     W = pm.to_device(mpo, qn=True)
     W1, W2 = W[j], W[j + 1]
     a = qn_link(kind, m, recipe)
@@ -172,6 +174,80 @@ def qn_heff_inputs(kind, m, recipe, seed):
     for T, tag in ((L, "L"), (R, "R"), (psi, "psi")):
         T.fill(lambda k, shp, tag=tag: synth.block_gaussian(seed, tag, k, shp))
     return L, W1, W2, R, psi
+
+
+def qn_oracle_inputs(kind, m, recipe, seed):
+    """The same workload as oracle BlockTensors, built on the host alone (the
+    same models, sector recipe and keyed block generator; no library call)."""
+    from paper_2007_14822_gb300 import synth
+    from oracle.blocksparse import BlockTensor, QNIndex
+    mpo, j = qn_mpo(kind)
+    a = qn_link(kind, m, recipe)
+    A = QNIndex(a.sectors, +1)
+    site = QNIndex([(q, 1) for q in mpo.site_qn], +1)
+
+    def mpo_tensor(k):
+        wl = QNIndex([(q, 1) for q in mpo.link_qn[k]], -1)
+        wr = QNIndex([(q, 1) for q in mpo.link_qn[k + 1]], +1)
+        return BlockTensor.from_dense(mpo.W[k], [wl, wr, site.dag(), site])
+    W1, W2 = mpo_tensor(j), mpo_tensor(j + 1)
+    fn = lambda tag: (lambda k, shp: synth.block_gaussian(seed, tag, k, shp))
+    L = BlockTensor.from_blocks_fn([A.dag(), W1.inds[0].dag(), A], None, fn("L"))
+    R = BlockTensor.from_blocks_fn([A, W2.inds[1].dag(), A.dag()], None, fn("R"))
+    psi = BlockTensor.from_blocks_fn([A, W1.inds[3], W2.inds[3], A.dag()], None, fn("psi"))
+    return L, W1, W2, R, psi
+
+
+def _pair_flops(A, ca, B, cb):
+    """2MNK summed over the stored block pairs of A and B that agree on the
+    contracted axes (ca of A with cb of B)."""
+    fa = [i for i in range(A.rank) if i not in ca]
+    fb = [i for i in range(B.rank) if i not in cb]
+    byk = {}
+    for kb in B.blocks:
+        byk.setdefault(tuple(kb[i] for i in cb), []).append(kb)
+    flops = 0.0
+    for ka in A.blocks:
+        for kb in byk.get(tuple(ka[i] for i in ca), []):
+            M = np.prod([A.inds[i].sdim(ka[i]) for i in fa]) if fa else 1
+            N = np.prod([B.inds[i].sdim(kb[i]) for i in fb]) if fb else 1
+            K = np.prod([A.inds[i].sdim(ka[i]) for i in ca]) if ca else 1
+            flops += 2.0 * M * N * K
+    return flops
+
+
+class _Keys:
+    """An intermediate of the chain: its indices and every allowed block of
+    its flux (as a labelled contraction stores them), dimensions only."""
+    def __init__(self, inds, flux):
+        from oracle.blocksparse import allowed_blocks
+        self.inds, self.blocks = inds, {k: None for k in allowed_blocks(inds, flux)}
+
+    @property
+    def rank(self):
+        return len(self.inds)
+
+
+def chain_flops(L, W1, W2, R, psi):
+    """Algorithmic flops of one H_eff product on oracle tensors: the labelled
+    chain S1 = L.psi (over a), S2 = .W1 (over w, s1), S3 = .W2 (over w1, s2),
+    S4 = .R (over w2, b), each 2MNK summed over its block pairs, the
+    intermediates holding every allowed block of their flux."""
+    from oracle.blocksparse import qn_add
+    # L[a,w,a'] psi[a,s1,s2,b] -> T1[w,a',s1,s2,b]
+    f1 = _pair_flops(L, [0], psi, [0])
+    fl1 = qn_add(L.flux, psi.flux)
+    T1 = _Keys([L.inds[1], L.inds[2], psi.inds[1], psi.inds[2], psi.inds[3]], fl1)
+    # T1[w,a',s1,s2,b] W1[w,w1,s1,s1'] -> T2[a',s2,b,w1,s1']
+    f2 = _pair_flops(T1, [0, 2], W1, [0, 2])
+    fl2 = qn_add(fl1, W1.flux)
+    T2 = _Keys([T1.inds[1], T1.inds[3], T1.inds[4], W1.inds[1], W1.inds[3]], fl2)
+    # T2[a',s2,b,w1,s1'] W2[w1,w2,s2,s2'] -> T3[a',b,s1',w2,s2']
+    f3 = _pair_flops(T2, [3, 1], W2, [0, 2])
+    T3 = _Keys([T2.inds[0], T2.inds[2], T2.inds[4], W2.inds[1], W2.inds[3]], qn_add(fl2, W2.flux))
+    # T3[a',b,s1',w2,s2'] R[b,w2,b'] -> y[a',s1',s2',b']
+    f4 = _pair_flops(T3, [1, 3], R, [0, 1])
+    return f1 + f2 + f3 + f4
 
 
 def time_apply(torch, plan, x, y, prec, reps):
@@ -478,75 +554,120 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
-def run_probe(which, torch, build, tnh):
-    """A short run of one workload, for ncu: the kernels launch in a fixed
-    order (plan-time packing of L and R first, then the applications)."""
-    build.build()
-    ctx = tnh.Context(0)
-    if which == "svd-bond":
-        bond = GpuBond(ctx, host_inputs())
-        ctx.contract(bond.A1, bond.A2, bond.theta, tnh.FP64)
-        plan = ctx.heff_plan(bond.L, bond.W, bond.W, bond.R, bond.theta, tnh.BF16x6)
-        E, res, k = plan.eigsolve(bond.theta.data, krylov_dim=K_LANCZOS, tol=0.0)
-        plan.free()
-        svd = ctx.svd_trunc(bond.theta, 2, CUTOFF, MAXDIM)
-        print("probe svd-bond: E", E, "kept", svd.kept, svd.stats())
-        svd.free()
-    else:
-        i = {"heff-u1": 0, "heff-cyl": 1, "heff-hub": 2}[which]
-        name, kind, m, recipe, seed = QN_CONFIGS[i]
-        L, W1, W2, R, psi = qn_heff_inputs(kind, m, recipe, seed)
-        plan = ctx.heff_plan(L, W1, W2, R, psi, tnh.BF16x6)
-        y = torch.empty_like(psi.data)
-        for _ in range(3):
-            plan.apply(psi.data, y)
+# DRAM bytes (read + write) per launch of the headline's dominant kernel,
+# from one ncu capture of the headline workload, with the SHA-256 of the
+# kernel's sources at capture time: the figure is reported only while the
+# sources are unchanged.
+TRAFFIC = {}
+
+
+def source_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2007_14822_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+KERNEL_SOURCES = {"gemm_tc": ["gemm_tc.cu", "ptx.cuh", "tnh_internal.h"],
+                  "heff_w12": ["gather.cu", "gather.h"], "heff_pack_x": ["gather.cu", "gather.h"]}
+
+
+def kernel_traffic(name):
+    t = TRAFFIC.get(name)
+    if not t:
+        return None
+    srcs = next((v for k, v in KERNEL_SOURCES.items() if name.startswith(k)), None)
+    if srcs is None or source_sha(srcs) != t["source_sha"]:
+        return None
+    return t["bytes_per_launch"]
+
+
+HEAD = QN_CONFIGS[1]   # the J1-J2 cylinder, m = 2048
+
+
+def time_heff_steps(torch, plan, x, y, steps, flush, host=None):
+    """Device time of `steps` applications, L2 flushed before each; with
+    host = (x_host, y_host) (pinned) every step also copies x in and y out."""
+    s = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(steps):
+        l2_flush(torch, flush)
         torch.cuda.synchronize()
-        print("probe", which, name, "flops", plan.flops, "n", plan.size)
-        plan.free()
-    ctx.close()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        if host:
+            x.copy_(host[0], non_blocking=True)
+        plan.apply(x, y)
+        if host:
+            host[1].copy_(y, non_blocking=True)
+        b.record(s)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b) / 1e3
+    return total
+
+
+def bench_bond_update(ctx, torch, tnh, steps, flush):
+    """The dense m=256 bond update (every step of the hot path), device-timed."""
+    host = host_inputs()
+    bond = GpuBond(ctx, host)
+    for _ in range(3):
+        bond.step()
+    torch.cuda.synchronize()
+    t = time_steps(torch, bond, steps, flush)
+    flops, heff_flops = step_flops()
+    ctx.profile_begin()
+    bond.step()
+    prof = ctx.profile_end()
+    return {"workload": "dense Heisenberg bond, m=256 w=5 d=2 (L/R 256x5x256, psi 256x2x2x256)",
+            "step": f"theta + Lanczos {K_LANCZOS} matvecs BF16x6 + FP64 energy + FP64 Jacobi SVD "
+                    f"(maxdim {MAXDIM}, cutoff {CUTOFF}) + FP64 env update",
+            "flops_per_step": flops, "ms_per_step": t / steps * 1e3, "tflops": flops * steps / t / 1e12,
+            "steps": steps, "kernels_per_step": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the block-sparse H_eff and sweep measurements")
-    ap.add_argument("--oracle-matvec", default="heis,cyl,hub",
-                    help="block-sparse workloads whose H_eff product is also timed on the oracle (comma list of "
-                         "heis, cyl, hub; the Hubbard one takes tens of seconds on the host)")
-    ap.add_argument("--probe", choices=["heff-u1", "heff-cyl", "heff-hub", "svd-bond"],
-                    help="run one workload briefly for a profiler (no JSON line): a block-sparse H_eff plan "
-                         "and three BF16x6 applications, or the bench bond up to its SVD")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads and the sweeps")
+    ap.add_argument("--oracle-matvec", default="heis,hub",
+                    help="extra block-sparse workloads whose H_eff product is also timed on the oracle (comma "
+                         "list of heis, hub; the Hubbard one takes tens of seconds on the host)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
-    flops, heff_flops = step_flops()
-    config = {"workload": "dense Heisenberg bond update, m=256 w=5 d=2 (L/R 256x5x256, psi 256x2x2x256)",
-              "step": f"theta + Lanczos {K_LANCZOS} matvecs BF16x6 + FP64 energy + FP64 Jacobi SVD "
-                      f"(maxdim {MAXDIM}, cutoff {CUTOFF}) + FP64 env update",
-              "flops_per_step": flops, "l2": "flushed between timed steps (256 MB write)",
+    wname, wkind, wm, wrecipe, wseed = HEAD
+    config = {"workload": f"H_eff.psi, {wname} (bulk sites 62/63 of the 6x24 cylinder, seeded N(0,1) blocks, "
+                          f"seed {wseed})",
+              "step": "one BF16x6 application y = H_eff x (graph replay: pack psi, S1, fused W1.W2, S4)",
+              "l2": "flushed before every timed step (256 MB write)",
               "parallelism": f"replicas x{world}"}
 
     if args.impl == "reference":
         if world > 1 and rank != 0:
             return
-        host = host_inputs()
+        args_o = qn_oracle_inputs(wkind, wm, wrecipe, wseed)
+        from oracle import dmrg as D_
+        flops = chain_flops(*args_o)
         cores = blas_threads()
         for _ in range(args.warmup):
-            oracle_bond(host)
+            D_.heff_apply(*args_o)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            oracle_bond(host)
+            D_.heff_apply(*args_o)
         dt = (time.perf_counter() - t0) / args.steps
         val = flops / dt / 1e12
+        config["flops_per_step"] = flops
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": 0,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                                 "sample": f"{args.steps} oracle bond updates of the workload",
+                                 "sample": f"{args.steps} oracle H_eff products of the workload",
                                  "cpu": cpu_model()},
                 "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -554,9 +675,6 @@ def main():
 
     import torch
     from paper_2007_14822_gb300 import build, tnh
-    if args.probe:
-        run_probe(args.probe, torch, build, tnh)
-        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -569,120 +687,112 @@ def main():
     if dist:
         dist.barrier()
     ctx = tnh.Context(local)
-    host = host_inputs()
-    bond = GpuBond(ctx, host, pinned=True)
-    flush = torch.zeros(32 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 256 MB > L2
-    for _ in range(args.warmup):
-        bond.step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    with ClockSampler(local) as clk:
-        t_dev = time_steps(torch, bond, args.steps, flush)
-    torch.cuda.synchronize()
-    t_dev = max_over_ranks(t_dev, dist, "cuda")
-    # end to end: host buffers in, result out, every step (slowest rank)
-    if dist:
-        dist.barrier()
-    n_e2e = max(1, args.steps // 2)
-    t_e2e = max_over_ranks(time_steps(torch, bond, n_e2e, flush, e2e=True), dist, "cuda") / n_e2e
-    # per-kernel breakdown of one step (profiled separately)
-    ctx.profile_begin()
-    bond.step()
-    prof = ctx.profile_end()
-    launches = sum(v[0] for v in prof.values())
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    # H_eff alone, mixed and FP64 (kernel chain of one matvec)
-    plan = ctx.heff_plan(bond.L, bond.W, bond.W, bond.R, bond.theta, tnh.BF16x6)
-    y = torch.empty_like(bond.theta.data)
-    hs = {}
-    for name, p in (("bf16x6", None), ("fp64", tnh.FP64)):
-        for _ in range(3):
-            plan.apply(bond.theta.data, y, p)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20 if p is None else 5
-        a.record()
-        for _ in range(reps):
-            plan.apply(bond.theta.data, y, p)
-        b.record()
-        torch.cuda.synchronize()
-        hs[name] = heff_flops / (a.elapsed_time(b) / 1e3 / reps) / 1e12
-    plan.free()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle's product on the same dense inputs
-        t_or = oracle_matvec_seconds(bond.L, bond.W, bond.W, bond.R, bond.theta)
-        hs["oracle"] = heff_flops / t_or / 1e12
-        hs["oracle_cores"] = blas_threads()
+    props = torch.cuda.get_device_properties(local)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     PEAKS.update(peaks)
-    ms_step = t_dev / args.steps * 1e3
-    value = world * flops * args.steps / t_dev / 1e12
-    # roofline of the dominant kernel
-    name, (nl, ms) = top
-    fp64_flops = 2 * D * D * M ** 3 + heff_flops + (4 * W_DIM * D * M ** 3 + 2 * W_DIM ** 2 * D * D * M * M)
-    # float32 CUDA-core peak from the unit counts: SMs x 128 FP32 lanes x 2 x max SM clock
-    fp32_peak = (peaks.get("sm_count", 152) * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
-    st = bond.svd_stats
-    # DRAM bytes (read + write) per launch of the Jacobi kernels on this
-    # workload's bond, from one ncu capture of `bench.py --probe svd-bond`
-    # (profiles/svd_bond_m256_jacobi.md); None for a kernel changed since
-    traffic = {"svd_jacobi_f32": None, "svd_jacobi_f64": 2123520 + 540672}
-    if name == "svd_jacobi_f32":
-        achieved = st["flops32"] / (ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic.get(name), "kernel": name,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                "work": f"{st['rounds32']} grid rounds, rotation flops counted per row (6 dot + 6 update)"}
-    elif name == "svd_jacobi_f64":
-        achieved = st["flops64"] / (ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s", "frac": achieved / 1.25,
-                "traffic": traffic.get(name), "kernel": name,
-                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
-                "work": f"{st['rounds64']} grid rounds, rotation flops counted per row (6 dot + 6 update)"}
-    elif name == "gemm_f64":
-        achieved = fp64_flops / (ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None, "kernel": name,
-                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}
-    elif name.startswith("gemm_tc"):
-        achieved = K_LANCZOS * heff_flops / (ms / 1e3) / 1e12
-        pk = peaks.get("bf16_tflops", 1900.0)
+    L, W1, W2, R, psi = qn_heff_inputs(wkind, wm, wrecipe, wseed)
+    plan = ctx.heff_plan(L, W1, W2, R, psi, tnh.BF16x6)
+    flops = plan.flops
+    config["flops_per_step"] = flops
+    config["psi_elems"] = plan.size
+    x = psi.data.clone()
+    y = torch.empty_like(x)
+    flush = torch.zeros(32 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 256 MB > L2
+    for _ in range(max(args.warmup, 3)):
+        plan.apply(x, y)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        t_dev = time_heff_steps(torch, plan, x, y, args.steps, flush)
+    torch.cuda.synchronize()
+    t_dev = max_over_ranks(t_dev, dist, "cuda")
+    # end to end: psi from pinned host memory in, the product out, every step
+    if dist:
+        dist.barrier()
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    n_e2e = max(3, args.steps // 2)
+    t_e2e = max_over_ranks(time_heff_steps(torch, plan, x, y, n_e2e, flush, host=(xh, yh)), dist, "cuda") / n_e2e
+    # per-kernel times over the same steps (direct launches, CUDA events on
+    # the launching stream around every kernel)
+    ctx.profile_begin()
+    for _ in range(args.steps):
+        l2_flush(torch, flush)
+        plan.apply(x, y)
+    prof = ctx.profile_end()
+    launches = sum(v[0] for v in prof.values()) // args.steps
+    name, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    fd = plan.flops_detail
+    pk = peaks.get("bf16_tflops")
+    peak_src = "measured bf16 burst (MEASURED_PEAKS.json)"
+    if pk is None:
+        pk, peak_src = 1900.0, "fallback 1.9 PFLOP/s bf16"
+    if name.startswith("gemm_tc"):
+        # algorithmic flops of the launches of this kernel per step: S1 and S4
+        alg = (fd["s1"] + fd["s4"]) * args.steps / nl
+        achieved = alg / (ms / nl / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "traffic": None, "kernel": name, "peak_source": "measured bf16 (burst)"}
+                "traffic": kernel_traffic(name), "kernel": name, "peak_source": peak_src,
+                "achieved_issued": 6 * achieved, "frac_issued": 6 * achieved / pk,
+                "work": "algorithmic flops of S1 and S4 (2MNK per block pair) per launch; BF16x6 issues 6 bf16 "
+                        "products per algorithmic flop (achieved_issued / frac_issued)"}
     else:
-        roof = {"bound": "alu", "achieved": None, "peak": 1.25, "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "kernel": name, "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}
-    roof["kernel_ms_per_step"] = ms
-    roof["launches_per_step"] = nl
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": kernel_traffic(name), "kernel": name, "peak_source": "measured copy (MEASURED_PEAKS.json)"}
+    roof["kernel_ms_per_launch"] = ms / nl
+    roof["launches_per_step"] = nl / args.steps
+    value = world * flops * args.steps / t_dev / 1e12
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+bf16x6", "data": "synthetic", "config": config,
+            "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6 (fp32 accumulate)", "data": "synthetic",
+            "config": config,
             "e2e": {"value": world * flops / t_e2e / 1e12, "unit": "TFLOP/s",
-                    "h2d_bytes_per_step": bond.h2d_bytes, "d2h_bytes_per_step": bond.d2h_bytes},
+                    "h2d_bytes_per_step": int(x.numel()) * 8, "d2h_bytes_per_step": int(y.numel()) * 8},
             "gpu_launches": launches * args.steps, "clocks": clk.summary(), "roofline": roof,
-            "heff_tflops": hs, "kernels_per_step": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
-    # the other workloads and the oracle are reported at N=1 only (at N>1
-    # they would hold every GPU while rank 0 alone works)
+            "sm_count": props.multi_processor_count,
+            "kernels_per_step": {k: {"launches": v[0] / args.steps, "ms": v[1] / args.steps}
+                                 for k, v in prof.items()}}
+    # the FP64 product of the same plan (the plain FP64 GPU path)
+    for _ in range(2):
+        plan.apply(x, y, tnh.FP64)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(3):
+        plan.apply(x, y, tnh.FP64)
+    b.record()
+    torch.cuda.synchronize()
+    t64 = a.elapsed_time(b) / 1e3 / 3
+    line["fp64"] = {"ms": t64 * 1e3, "tflops": flops / t64 / 1e12, "speedup_bf16x6": t64 / (t_dev / args.steps)}
+    plan.free()
+    del L, W1, W2, R, psi, x, y
+    torch.cuda.empty_cache()
+    # the other workloads, the sweeps and the oracle are reported at N=1 only
+    # (at N>1 they would hold every GPU while rank 0 alone works)
     if rank == 0 and world == 1 and not args.no_extra:
+        line["bond_update_m256"] = bench_bond_update(ctx, torch, tnh, 5, flush)
         line["heff_qn"] = bench_qn_heff(ctx, torch, tnh, tuple(k for k in args.oracle_matvec.split(",") if k))
         line["sweep"] = bench_sweeps(ctx, tnh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = blas_threads()
-        # a bounded sample: whole oracle bond updates until about 10 s of CPU time
+        # a bounded sample: whole oracle H_eff products of the workload, about 10 s
+        from oracle import dmrg as D_
+        args_o = qn_oracle_inputs(wkind, wm, wrecipe, wseed)
         n, t0 = 0, time.perf_counter()
         while True:
-            oracle_bond(host)
+            D_.heff_apply(*args_o)
             n += 1
             dt = time.perf_counter() - t0
             if dt >= 10.0 or n >= 30:
                 break
-        line["cpu_baseline"] = {"value": n * flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{n} oracle bond updates of the same workload ({dt:.1f} s)",
+        line["cpu_baseline"] = {"value": n * flops / dt / 1e12, "unit": "TFLOP/s", "cores": blas_threads(),
+                                "kind": "oracle",
+                                "sample": f"{n} oracle H_eff products of the same workload ({dt:.1f} s)",
                                 "cpu": cpu_model()}
     if rank == 0:
         print(json.dumps(line))

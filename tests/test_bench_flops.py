@@ -61,3 +61,13 @@ def test_bench_workload_flops():
     total, heff = bench.step_flops()
     assert heff == 1_394_606_080
     assert total == 13_369_868_288
+
+
+@pytest.mark.parametrize("kind,m,recipe", [("heis", 24, (5, 8)), ("hub", 30, (3, 6)), ("cyl", 20, (5, 6))])
+def test_chain_flops_equal_the_counted_heff_contractions(counted, kind, m, recipe):
+    # the headline's flop count (block pairs of S1..S4 on block-sparse
+    # storage) against the contractions of one oracle H_eff product
+    L, W1, W2, R, psi = bench.qn_oracle_inputs(kind, m, recipe, 3)
+    f = bench.chain_flops(L, W1, W2, R, psi)
+    D.heff_apply(L, W1, W2, R, psi)
+    assert counted[0] == f and f > 0

@@ -79,8 +79,8 @@ def test_reference_arm_line_has_the_contract_keys():
         assert k in line, k
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "TFLOP/s"
     assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
-    assert line["config"]["workload"].startswith("dense Heisenberg bond update, m=256")
-    assert line["config"]["flops_per_step"] == bench.step_flops()[0]
+    assert line["config"]["workload"].startswith("H_eff.psi, U(1) J1-J2 cylinder 6x24, m=2048")
+    assert line["config"]["flops_per_step"] == bench.chain_flops(*bench.qn_oracle_inputs(*bench.HEAD[1:]))
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
