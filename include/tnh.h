@@ -251,6 +251,15 @@ tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops);
  * would, although the plan applies them fused in one pass) and the S4 GEMM
  * (sum over w2, b with R). s1 + s23 + s4 is tnh_heff_flops. */
 tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, double* s4);
+/* The choices the plan's autotuner made for its two tcgen05 GEMMs (the
+ * paper's Sec. 9.4 block-contraction strategies are fixed; this is GPU
+ * tuning): choice[0] / choice[2] the N tile policy of S1 / S4 (0: 128-wide
+ * tiles; 1: widths 128, 64 or 32 per output block, fewest operand bytes;
+ * 2: the same, fewest MMA columns), choice[1] / choice[3] their K-split
+ * factor (1, 2, 4, 8), choice[4] 1 when the plan timed the candidates itself
+ * (0: reused from the context or the TNH_TUNE_CACHE file, or forced by
+ * TNH_HEFF_SPLIT / TNH_HEFF_TILES). An FP64 plan reports 0 1 0 1 0. */
+tnh_status tnh_heff_tuning(const tnh_heff* plan, int32_t* choice);
 /* Diagonal of the MPO part of H_eff (the projectors excluded), DEVICE
  * float64 [n] in the psi layout:
  *   d[a,s1,s2,b] = sum L[a,w,a] W1[w,w1,s1,s1] W2[w1,w2,s2,s2] R[b,w2,b].
@@ -399,6 +408,36 @@ tnh_status tnh_dmrg_ex(tnh_ctx* ctx, int32_t N, const tnh_dmrg_problem* prob,
  * indices must be [link j (Out), site (Out), link j+1 (In)] with these
  * sectors; blocks of A that are not stored are zeroed, a stored block that A
  * lacks is TNH_ERR_SHAPE. Synchronises the stream. */
+/* Checkpoints of the runs on this context (the paper writes MPS to HDF5
+ * files, Sec. 10; here one binary file with a header). With path non-NULL,
+ * later tnh_dmrg / tnh_dmrg_ex / tnh_dmrg_resume runs write to path, after
+ * every `every` bond updates (0: only at sweep ends) and at the end of every
+ * sweep but the last: the MPS, the environments valid before the next bond
+ * (left ones up to it, right ones after it), the position (sweep, pass
+ * 0 = left-to-right / 1 = right-to-left, step within the pass), the energy
+ * and statistics so far. The file is written to path.tmp and renamed, so a
+ * crash never leaves a half-written checkpoint. With stop_after > 0 a run
+ * returns TNH_OK after that many bond updates, right after writing its
+ * checkpoint (e.g. a batch job whose time slot ends); tnh_dmrg_position
+ * tells where it stopped. path NULL, every 0, stop_after 0 turn it off.
+ * Settings stay until changed. TNH_ERR_ARG for negative values. */
+tnh_status tnh_dmrg_checkpoint(tnh_ctx* ctx, const char* path, int32_t every, int64_t stop_after);
+/* Continue the run saved in the checkpoint file `path`: prob must be the
+ * problem of the run that wrote it (same MPO terms and boundary states, same
+ * previous states) and p the same sweep schedule (TNH_ERR_SHAPE when the
+ * stored MPS or environments do not fit the MPO, TNH_ERR_ARG for a file
+ * that is not a checkpoint or a schedule that ended before it). The stored
+ * MPS and environments are loaded, the overlap environments of previous
+ * states recomputed, and the schedule continues at the stored bond; stats
+ * [p->nsweep] gets the completed sweeps' statistics from the file and the
+ * rest from this run. The kernels are deterministic: an FP64 run resumed
+ * this way reproduces the uninterrupted run. Synchronous. */
+tnh_status tnh_dmrg_resume(tnh_ctx* ctx, int32_t N, const tnh_dmrg_problem* prob, const char* path,
+                           const tnh_sweep_params* p, double* energy, tnh_sweep_stat* stats);
+/* Where the last run on this context ended: the next bond (sweep, pass,
+ * step) and finished = 1 when the schedule completed (then sweep = nsweep). */
+tnh_status tnh_dmrg_position(tnh_ctx* ctx, int32_t* sweep, int32_t* pass, int32_t* step, int32_t* finished);
+
 tnh_status tnh_dmrg_mps_size(tnh_ctx* ctx, int32_t* N);
 tnh_status tnh_dmrg_mps_link(tnh_ctx* ctx, int32_t j, int32_t* nsect, int32_t* nq, int32_t* qn,
                              int32_t* sect_dim);

@@ -20,6 +20,14 @@
 // S4 sums the terms along its K dimension: the loop over terms is part of the
 // grouped GEMMs, with no block of the explicitly summed MPO formed.
 //
+// Checkpoint and resume (the paper saves MPS to HDF5 files, Sec. 10; here a
+// binary file): with a checkpoint path set on the context, the driver writes
+// the MPS, the environments valid at that point (L_0..L_j and R_{j+2}..R_N
+// for the next bond j), the position (sweep, pass, step) and the statistics
+// so far after every `every` bonds and at the end of every sweep; a resumed
+// run loads them and continues the schedule at that bond. The kernels are
+// deterministic, so a resumed FP64 run reproduces the uninterrupted one.
+//
 // Excited states (Sec. 7.2): for every previous state P_i the driver keeps
 // overlap environments LO_i (sites left of the bond) and RO_i (right of
 // it); phi_i = LO_i P_i[j] P_i[j+1] RO_i is P_i in the current two-site
@@ -28,6 +36,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
+#include <algorithm>
 
 #include "env.h"
 #include "heff.h"
@@ -159,6 +169,169 @@ void projected_state(Ctx* c, const Layout& LO, const Layout& P1, const Layout& P
     contract64(c, Y2.L, ro, bra);
 }
 
+// ---- checkpoint file
+//   "TNHCKPT1", int32 N, nq, sweep, pass, step, ndone
+//   double energy, resid, maxerr, seconds; int64 matvecs
+//   ndone x tnh_sweep_stat (the completed sweeps)
+//   N tensors (the MPS), then for k = 0..N: int32 flag + tensor if set (L_k),
+//   then the same for R_k
+// tensor: int32 rank; per index int64 label, int32 nsect, nq, arrow, qn
+// [nsect*nq], dim [nsect]; int32 flux [nq]; int64 size; float64 data [size].
+constexpr char kCkptMagic[8] = {'T', 'N', 'H', 'C', 'K', 'P', 'T', '1'};
+
+struct Ckpt {
+    int N = 0, nq = 0, sweep = 0, pass = 0, step = 0;
+    double energy = 0, resid = 0, maxerr = 0, seconds = 0;
+    int64_t matvecs = 0;
+    std::vector<tnh_sweep_stat> done;
+};
+
+struct File {
+    FILE* f = nullptr;
+    std::string path;
+    File(const std::string& p, const char* mode) : path(p) {
+        f = std::fopen(p.c_str(), mode);
+        TNH_REQUIRE(f != nullptr, TNH_ERR_ARG, "dmrg checkpoint: cannot open %s", p.c_str());
+    }
+    ~File() { if (f) std::fclose(f); }
+    void put(const void* p, size_t n) {
+        TNH_REQUIRE(std::fwrite(p, 1, n, f) == n, TNH_ERR_ARG, "dmrg checkpoint: write to %s failed", path.c_str());
+    }
+    void get(void* p, size_t n) {
+        TNH_REQUIRE(std::fread(p, 1, n, f) == n, TNH_ERR_ARG, "dmrg checkpoint: %s is truncated", path.c_str());
+    }
+    template <class T> void put(const T& v) { put(&v, sizeof v); }
+    template <class T> T get() { T v; get(&v, sizeof v); return v; }
+};
+
+void put_tensor(File& F, const Layout& T, cudaStream_t s) {
+    F.put<int32_t>(T.rank());
+    for (const Index& ix : T.inds) {
+        F.put<int64_t>(ix.label);
+        F.put<int32_t>(ix.nsect);
+        F.put<int32_t>(ix.nq);
+        F.put<int32_t>(ix.arrow);
+        F.put(ix.qn.data(), ix.qn.size() * sizeof(int));
+        F.put(ix.dim.data(), ix.dim.size() * sizeof(int));
+    }
+    F.put(T.flux.data(), T.flux.size() * sizeof(int));
+    F.put<int64_t>(T.size);
+    std::vector<double> h((size_t)T.size);
+    if (T.size) {
+        CUDA_CHECK(cudaMemcpyAsync(h.data(), T.data, (size_t)T.size * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+    }
+    F.put(h.data(), h.size() * sizeof(double));
+}
+
+DTensor get_tensor(File& F, int nq, cudaStream_t s) {
+    const int rank = F.get<int32_t>();
+    TNH_REQUIRE(rank >= 1 && rank <= kMaxDims, TNH_ERR_ARG, "dmrg checkpoint: %s: bad tensor rank", F.path.c_str());
+    std::vector<Index> inds(rank);
+    for (Index& ix : inds) {
+        ix.label = F.get<int64_t>();
+        ix.nsect = F.get<int32_t>();
+        ix.nq = F.get<int32_t>();
+        ix.arrow = F.get<int32_t>();
+        TNH_REQUIRE(ix.nsect >= 1 && ix.nsect < (1 << 20) && ix.nq == nq && (ix.arrow == 1 || ix.arrow == -1),
+                    TNH_ERR_ARG, "dmrg checkpoint: %s: bad index", F.path.c_str());
+        ix.qn.resize((size_t)ix.nsect * nq);
+        ix.dim.resize(ix.nsect);
+        F.get(ix.qn.data(), ix.qn.size() * sizeof(int));
+        F.get(ix.dim.data(), ix.dim.size() * sizeof(int));
+        for (int d : ix.dim) TNH_REQUIRE(d >= 1, TNH_ERR_ARG, "dmrg checkpoint: %s: bad sector", F.path.c_str());
+        ix.finish();
+    }
+    std::vector<int> flux(nq);
+    F.get(flux.data(), flux.size() * sizeof(int));
+    DTensor t = new_tensor(inds, flux, s);
+    const int64_t n = F.get<int64_t>();
+    TNH_REQUIRE(n == t.L.size, TNH_ERR_ARG, "dmrg checkpoint: %s: tensor size %lld, layout %lld", F.path.c_str(),
+                (long long)n, (long long)t.L.size);
+    std::vector<double> h((size_t)n);
+    F.get(h.data(), h.size() * sizeof(double));
+    if (n) {
+        CUDA_CHECK(cudaMemcpyAsync(t.L.data, h.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+    }
+    return t;
+}
+
+// Write the state before bond `step` of `pass` in `sweep` (L_0..L_j and
+// R_{j+2}..R_N valid, j that bond); written to path.tmp, then renamed.
+void write_checkpoint(const std::string& path, const Ckpt& st, const std::vector<DTensor>& A,
+                      const std::vector<DTensor>& Ls, const std::vector<DTensor>& Rs, cudaStream_t s) {
+    const int N = st.N;
+    const int j = st.pass == 0 ? st.step : N - 2 - st.step;
+    const std::string tmp = path + ".tmp";
+    {
+        File F(tmp, "wb");
+        F.put(kCkptMagic, sizeof kCkptMagic);
+        for (int v : {st.N, st.nq, st.sweep, st.pass, st.step, (int)st.done.size()}) F.put<int32_t>(v);
+        for (double v : {st.energy, st.resid, st.maxerr, st.seconds}) F.put<double>(v);
+        F.put<int64_t>(st.matvecs);
+        for (const tnh_sweep_stat& d : st.done) F.put(d);
+        for (int k = 0; k < N; ++k) put_tensor(F, A[k].L, s);
+        for (int k = 0; k <= N; ++k) {
+            F.put<int32_t>(k <= j);
+            if (k <= j) put_tensor(F, Ls[k].L, s);
+        }
+        for (int k = 0; k <= N; ++k) {
+            F.put<int32_t>(k >= j + 2);
+            if (k >= j + 2) put_tensor(F, Rs[k].L, s);
+        }
+        TNH_REQUIRE(std::fflush(F.f) == 0, TNH_ERR_ARG, "dmrg checkpoint: write to %s failed", tmp.c_str());
+    }
+    TNH_REQUIRE(std::rename(tmp.c_str(), path.c_str()) == 0, TNH_ERR_ARG, "dmrg checkpoint: cannot rename %s",
+                tmp.c_str());
+}
+
+struct Loaded {
+    Ckpt st;
+    std::vector<DTensor> A, Ls, Rs;
+};
+
+Loaded read_checkpoint(const std::string& path, cudaStream_t s) {
+    File F(path, "rb");
+    char m[8];
+    F.get(m, sizeof m);
+    TNH_REQUIRE(std::equal(m, m + 8, kCkptMagic), TNH_ERR_ARG, "dmrg checkpoint: %s is not a checkpoint",
+                path.c_str());
+    Loaded r;
+    Ckpt& st = r.st;
+    st.N = F.get<int32_t>();
+    st.nq = F.get<int32_t>();
+    st.sweep = F.get<int32_t>();
+    st.pass = F.get<int32_t>();
+    st.step = F.get<int32_t>();
+    const int ndone = F.get<int32_t>();
+    TNH_REQUIRE(st.N >= 2 && st.nq >= 0 && st.nq <= 4 && st.sweep >= 0 && (st.pass == 0 || st.pass == 1) &&
+                    st.step >= 0 && st.step < st.N - 1 && ndone == st.sweep,
+                TNH_ERR_ARG, "dmrg checkpoint: %s: bad header", path.c_str());
+    st.energy = F.get<double>();
+    st.resid = F.get<double>();
+    st.maxerr = F.get<double>();
+    st.seconds = F.get<double>();
+    st.matvecs = F.get<int64_t>();
+    st.done.resize(ndone);
+    for (auto& d : st.done) d = F.get<tnh_sweep_stat>();
+    const int N = st.N, j = st.pass == 0 ? st.step : N - 2 - st.step;
+    for (int k = 0; k < N; ++k) r.A.push_back(get_tensor(F, st.nq, s));
+    r.Ls.resize(N + 1);
+    r.Rs.resize(N + 1);
+    for (int k = 0; k <= N; ++k) {
+        const int has = F.get<int32_t>();
+        TNH_REQUIRE(has == (k <= j), TNH_ERR_ARG, "dmrg checkpoint: %s: environment L%d", path.c_str(), k);
+        if (has) r.Ls[k] = get_tensor(F, st.nq, s);
+    }
+    for (int k = 0; k <= N; ++k) {
+        const int has = F.get<int32_t>();
+        TNH_REQUIRE(has == (k >= j + 2), TNH_ERR_ARG, "dmrg checkpoint: %s: environment R%d", path.c_str(), k);
+        if (has) r.Rs[k] = get_tensor(F, st.nq, s);
+    }
+    return r;
+}
+
 struct Problem {
     std::vector<std::vector<Layout>> W;   // [term][site]
     std::vector<int64_t> start, done;     // [term]
@@ -167,7 +340,7 @@ struct Problem {
 };
 
 void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh_sweep_params* p, double* energy,
-              tnh_sweep_stat* stats) {
+              tnh_sweep_stat* stats, Loaded* resume = nullptr) {
     TNH_REQUIRE(N >= 2, TNH_ERR_ARG, "tnh_dmrg: N = %d < 2", N);
     TNH_REQUIRE(p->nsweep >= 1 && p->maxdim && p->cutoff, TNH_ERR_ARG, "tnh_dmrg: empty sweep schedule");
     const tnh_precision prec = (tnh_precision)p->precision;
@@ -193,7 +366,7 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
         }
     }
     std::vector<DTensor> A(N);
-    for (int j = 0; j < N; ++j) {
+    for (int j = 0; j < N && !resume; ++j) {
         Layout a = parse_tensor(&mps[j], "mps");
         TNH_REQUIRE(a.rank() == 3, TNH_ERR_ARG, "tnh_dmrg: MPS tensors have rank 3");
         A[j] = new_tensor(a.inds, a.flux, s);
@@ -204,10 +377,31 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
                                        (size_t)a.belems(b) * sizeof(double), cudaMemcpyDeviceToDevice, s));
         }
     }
+    std::vector<DTensor> Ls(N + 1), Rs(N + 1);
+    if (resume) {
+        TNH_REQUIRE(resume->st.N == N, TNH_ERR_SHAPE, "tnh_dmrg_resume: checkpoint of %d sites, problem of %d",
+                    resume->st.N, N);
+        TNH_REQUIRE(resume->st.sweep < p->nsweep, TNH_ERR_ARG,
+                    "tnh_dmrg_resume: checkpoint at sweep %d, schedule of %d sweeps", resume->st.sweep, p->nsweep);
+        A = std::move(resume->A);
+        Ls = std::move(resume->Ls);
+        Rs = std::move(resume->Rs);
+        for (int j = 0; j < N; ++j)
+            TNH_REQUIRE(A[j].L.rank() == 3 && A[j].L.inds[1].same_space(W[j].inds[3]) &&
+                            A[j].L.inds[1].arrow == W[j].inds[3].arrow,
+                        TNH_ERR_SHAPE, "tnh_dmrg_resume: site %d of the checkpoint does not match the MPO", j);
+        for (int k = 0; k <= N; ++k) {
+            if (Ls[k].L.rank())
+                TNH_REQUIRE(Ls[k].L.rank() == 3 && Ls[k].L.inds[1].same_space(k < N ? W[k].inds[0] : W[N - 1].inds[1]),
+                            TNH_ERR_SHAPE, "tnh_dmrg_resume: environment L%d does not match the MPO", k);
+            if (Rs[k].L.rank())
+                TNH_REQUIRE(Rs[k].L.rank() == 3 && Rs[k].L.inds[1].same_space(k > 0 ? W[k - 1].inds[1] : W[0].inds[0]),
+                            TNH_ERR_SHAPE, "tnh_dmrg_resume: environment R%d does not match the MPO", k);
+        }
+    }
     const int nq = A[0].L.nq();
     const std::vector<int> zero(nq, 0);
-    std::vector<DTensor> Ls(N + 1), Rs(N + 1);
-    {
+    if (!resume) {
         const Index& a0 = A[0].L.inds[0];
         Ls[0] = new_tensor({a0.dag(), W[0].inds[0].dag(), a0}, zero, s);
         const Index& bN = A[N - 1].L.inds[2];
@@ -237,7 +431,12 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
         run_env(c, *P, Ls[j].L.data, a.data, W[j].data, Ls[j + 1].L.data, eprec);
         CUDA_CHECK(cudaStreamSynchronize(s));
     };
-    for (int j = N - 1; j >= 2; --j) update_R(j);
+    if (!resume)
+        for (int j = N - 1; j >= 2; --j) update_R(j);
+    // where the run starts: the checkpoint's next bond, else the beginning
+    const int sw0 = resume ? resume->st.sweep : 0, pass0 = resume ? resume->st.pass : 0;
+    const int step0 = resume ? resume->st.step : 0;
+    const int jstart = pass0 == 0 ? step0 : N - 2 - step0;
 
     // overlap environments of the previous states
     const int K = (int)pr.P.size();
@@ -255,20 +454,39 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
         // states carry different total charge (zero overlap)
         if (LO[i][0].L.nblocks()) set_one(LO[i][0], {0, 0}, s);
         if (RO[i][N].L.nblocks()) set_one(RO[i][N], {0, 0}, s);
-        for (int j = N - 1; j >= 2; --j) RO[i][j] = overlap_right(c, RO[i][j + 1].L, P[j], A[j].L);
+        for (int j = N - 1; j >= jstart + 2; --j) RO[i][j] = overlap_right(c, RO[i][j + 1].L, P[j], A[j].L);
+        for (int j = 0; j < jstart; ++j) LO[i][j + 1] = overlap_left(c, LO[i][j].L, P[j], A[j].L);
     }
 
-    double E = 0.0;
+    double E = resume ? resume->st.energy : 0.0;
     const bool dbg = std::getenv("TNH_DEBUG") != nullptr;
     using clk = std::chrono::steady_clock;
     auto since = [](clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); };
-    for (int sw = 0; sw < p->nsweep; ++sw) {
+    // checkpoint state: completed sweeps' statistics and the bonds done by this call
+    Ckpt ck;
+    ck.N = N;
+    ck.nq = nq;
+    if (resume) {
+        ck.done = resume->st.done;
+        if (stats)
+            for (size_t k = 0; k < ck.done.size(); ++k) stats[k] = ck.done[k];
+    }
+    const std::string ckpath = c->ckpt_path;
+    int64_t bonds = 0;
+    c->pos_finished = false;
+    for (int sw = sw0; sw < p->nsweep; ++sw) {
         auto t0 = std::chrono::steady_clock::now();
         double ph[6] = {0, 0, 0, 0, 0, 0};   // theta, plan, eigsolve, svd, factors, environment (s)
-        double maxerr = 0.0, resid = 0.0;
+        double maxerr = 0.0, resid = 0.0, prior = 0.0;
         int64_t nmv = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int step = 0; step < N - 1; ++step) {
+        if (resume && sw == sw0) {
+            maxerr = resume->st.maxerr;
+            resid = resume->st.resid;
+            nmv = resume->st.matvecs;
+            prior = resume->st.seconds;
+        }
+        for (int pass = (sw == sw0 ? pass0 : 0); pass < 2; ++pass) {
+            for (int step = (sw == sw0 && pass == pass0 ? step0 : 0); step < N - 1; ++step) {
                 const int j = pass == 0 ? step : N - 2 - step;
                 const int dir = pass == 0 ? 1 : -1;
                 // theta = A_j * A_{j+1}
@@ -348,29 +566,73 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
                         RO[i][j + 1] = overlap_right(c, RO[i][j + 2].L, pr.P[i][j + 1], A[j + 1].L);
                 }
                 ph[5] += since(tp);
+                // checkpoint inside the sweep (the end of a sweep writes below)
+                ++bonds;
+                const bool last = pass == 1 && step == N - 2;
+                const bool stop = c->ckpt_stop > 0 && bonds >= c->ckpt_stop;
+                if (!last && (stop || (!ckpath.empty() && c->ckpt_every > 0 && bonds % c->ckpt_every == 0))) {
+                    CUDA_CHECK(cudaStreamSynchronize(s));
+                    check_device_flag(c);
+                    ck.sweep = sw;
+                    ck.pass = step + 1 < N - 1 ? pass : pass + 1;
+                    ck.step = step + 1 < N - 1 ? step + 1 : 0;
+                    ck.energy = E;
+                    ck.resid = resid;
+                    ck.maxerr = maxerr;
+                    ck.matvecs = nmv;
+                    ck.seconds = prior + std::chrono::duration<double>(clk::now() - t0).count();
+                    if (!ckpath.empty()) write_checkpoint(ckpath, ck, A, Ls, Rs, s);
+                    if (stop) {
+                        c->pos_sweep = ck.sweep;
+                        c->pos_pass = ck.pass;
+                        c->pos_step = ck.step;
+                        *energy = E;
+                        c->mps = std::move(A);
+                        return;
+                    }
+                }
             }
         }
         CUDA_CHECK(cudaStreamSynchronize(s));
         check_device_flag(c);
-        double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        double secs = prior + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (dbg)
             std::fprintf(stderr,
                          "dmrg: sweep %d %.3f s: theta %.3f, H_eff plan %.3f, eigensolver %.3f, SVD %.3f, "
                          "factors %.3f, environment %.3f\n",
                          sw, secs, ph[0], ph[1], ph[2], ph[3], ph[4], ph[5]);
-        if (stats) {
-            tnh_sweep_stat& st = stats[sw];
-            st.sweep = sw;
-            st.energy = E;
-            st.resid = resid;
-            st.truncerr = maxerr;
-            int ml = 0;
-            for (int j = 0; j < N; ++j) ml = std::max<int>(ml, (int)A[j].L.inds[2].total);
-            st.maxlink = ml;
-            st.matvecs = nmv;
-            st.seconds = secs;
+        tnh_sweep_stat st{};
+        st.sweep = sw;
+        st.energy = E;
+        st.resid = resid;
+        st.truncerr = maxerr;
+        int ml = 0;
+        for (int j = 0; j < N; ++j) ml = std::max<int>(ml, (int)A[j].L.inds[2].total);
+        st.maxlink = ml;
+        st.matvecs = nmv;
+        st.seconds = secs;
+        if (stats) stats[sw] = st;
+        ck.done.push_back(st);
+        const bool stop = c->ckpt_stop > 0 && bonds >= c->ckpt_stop;
+        if (sw + 1 < p->nsweep && (!ckpath.empty() || stop)) {
+            ck.sweep = sw + 1;
+            ck.pass = ck.step = 0;
+            ck.energy = E;
+            ck.resid = ck.maxerr = ck.seconds = 0.0;
+            ck.matvecs = 0;
+            if (!ckpath.empty()) write_checkpoint(ckpath, ck, A, Ls, Rs, s);
+            if (stop) {
+                c->pos_sweep = ck.sweep;
+                c->pos_pass = c->pos_step = 0;
+                *energy = E;
+                c->mps = std::move(A);
+                return;
+            }
         }
     }
+    c->pos_sweep = p->nsweep;
+    c->pos_pass = c->pos_step = 0;
+    c->pos_finished = true;
     *energy = E;
     c->mps = std::move(A);
 }
@@ -420,6 +682,56 @@ tnh_status tnh_dmrg_ex(tnh_ctx* ctx, int32_t N, const tnh_dmrg_problem* prob, co
             for (int j = 0; j < N; ++j) pr.P[i].push_back(parse_tensor(&prob->ortho[(size_t)i * N + j], "ortho"));
         pr.weight = prob->weight;
         run_dmrg(c, N, pr, mps, p, energy, stats);
+    });
+}
+
+tnh_status tnh_dmrg_checkpoint(tnh_ctx* ctx, const char* path, int32_t every, int64_t stop_after) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c, TNH_ERR_ARG, "tnh_dmrg_checkpoint: ctx is NULL");
+        TNH_REQUIRE(every >= 0 && stop_after >= 0, TNH_ERR_ARG, "tnh_dmrg_checkpoint: every %d, stop_after %lld",
+                    every, (long long)stop_after);
+        c->ckpt_path = path ? path : "";
+        c->ckpt_every = every;
+        c->ckpt_stop = stop_after;
+    });
+}
+
+tnh_status tnh_dmrg_resume(tnh_ctx* ctx, int32_t N, const tnh_dmrg_problem* prob, const char* path,
+                           const tnh_sweep_params* p, double* energy, tnh_sweep_stat* stats) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && prob && path && p && energy, TNH_ERR_ARG, "tnh_dmrg_resume: NULL argument");
+        TNH_REQUIRE(N >= 2, TNH_ERR_ARG, "tnh_dmrg_resume: N = %d < 2", N);
+        TNH_REQUIRE(prob->nterm >= 1 && prob->mpo && prob->start && prob->done, TNH_ERR_ARG,
+                    "tnh_dmrg_resume: need at least one MPO with its boundary states");
+        TNH_REQUIRE(prob->northo >= 0 && (prob->northo == 0 || prob->ortho), TNH_ERR_ARG,
+                    "tnh_dmrg_resume: previous states missing");
+        CUDA_CHECK(cudaSetDevice(c->device));
+        Problem pr;
+        pr.W.resize(prob->nterm);
+        for (int t = 0; t < prob->nterm; ++t) {
+            for (int j = 0; j < N; ++j) pr.W[t].push_back(parse_tensor(&prob->mpo[(size_t)t * N + j], "mpo"));
+            pr.start.push_back(prob->start[t]);
+            pr.done.push_back(prob->done[t]);
+        }
+        pr.P.resize(prob->northo);
+        for (int i = 0; i < prob->northo; ++i)
+            for (int j = 0; j < N; ++j) pr.P[i].push_back(parse_tensor(&prob->ortho[(size_t)i * N + j], "ortho"));
+        pr.weight = prob->weight;
+        Loaded ld = read_checkpoint(path, c->stream);
+        run_dmrg(c, N, pr, nullptr, p, energy, stats, &ld);
+    });
+}
+
+tnh_status tnh_dmrg_position(tnh_ctx* ctx, int32_t* sweep, int32_t* pass, int32_t* step, int32_t* finished) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && sweep && pass && step && finished, TNH_ERR_ARG, "tnh_dmrg_position: NULL argument");
+        *sweep = c->pos_sweep;
+        *pass = c->pos_pass;
+        *step = c->pos_step;
+        *finished = c->pos_finished ? 1 : 0;
     });
 }
 

@@ -17,10 +17,12 @@
 // three bfloat16 parts, 24 significant bits); the float64 format keeps
 // float64 arithmetic.
 //
-// The fused S2+S3 step (w12_kernel below) works per cell instead: the
-// inputs of one (a'-sector, b-sector) pair are staged once and every output
-// sub-block is a weighted sum of them, weights = nonzero entries of the
-// two-site MPO product W1*W2 (Sec. 7.2).
+// The fused S2+S3 step (w12_kernel below) works per cell instead: every
+// output sub-block of one (a'-sector, b-sector) pair is a weighted sum of
+// the cell's T1 sub-blocks, weights = nonzero entries of the two-site MPO
+// product W1*W2 (Sec. 7.2); a thread forms four consecutive columns of one
+// row for every output, reading its inputs with 16-byte loads (a cell's
+// inputs are reused through L1 across its outputs).
 //
 // Output formats: float64 rows (pitch ld) for the FP64 GEMM, or the split
 // bfloat16 swizzled tiles (x = hi + mid + lo) of the tcgen05 GEMM.
@@ -155,74 +157,91 @@ __device__ __forceinline__ int swz(int row, int k) {
     return row * 64 + ((((k >> 3) ^ (row & 7))) << 3) + (k & 7);
 }
 
+// four consecutive source elements (16-byte aligned for float, 32 for double)
+__device__ __forceinline__ void load4(const float* p, float* v) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* v) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 y = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
+// hi / mid / lo bfloat16 parts (round to nearest each) of two float32
+// values, packed in pairs: plane p holds (part p of a) | (part p of b) << 16
+template <int P>
+__device__ __forceinline__ void split2(float a, float b, uint32_t* w) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    w[0] = *reinterpret_cast<uint32_t*>(&h);
+    if (P > 1) {
+        const float2 hf = __bfloat1622float2(h);
+        const float ra = a - hf.x, rb = b - hf.y;
+        __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+        w[1] = *reinterpret_cast<uint32_t*>(&m);
+        if (P > 2) {
+            const float2 mf = __bfloat1622float2(m);
+            __nv_bfloat162 l = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+            w[2] = *reinterpret_cast<uint32_t*>(&l);
+        }
+    }
+}
+
 template <class SrcT, bool kF64, int P>
-__global__ void __launch_bounds__(kW12Elems) w12_kernel(const W12Cta* __restrict__ ctas,
-                                                        const W12Cell* __restrict__ cells,
-                                                        const W12In* __restrict__ ins,
-                                                        const W12Out* __restrict__ outs,
-                                                        const W12Term* __restrict__ terms,
-                                                        const OpGeom* __restrict__ geom,
-                                                        const SrcT* __restrict__ src, void* __restrict__ dst) {
-    extern __shared__ unsigned char w12_smem[];
-    SrcT* in_s = reinterpret_cast<SrcT*>(w12_smem);   // [nin][kW12Elems], one column per thread
+__global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restrict__ ctas,
+                                                          const W12Cell* __restrict__ cells,
+                                                          const W12In* __restrict__ ins,
+                                                          const W12Out* __restrict__ outs,
+                                                          const W12Term* __restrict__ terms,
+                                                          const OpGeom* __restrict__ geom,
+                                                          const SrcT* __restrict__ src, void* __restrict__ dst) {
+    using AccT = typename Acc<kF64>::T;
     const W12Cta T = ctas[blockIdx.x];
     const W12Cell C = cells[T.cell];
-    const int tid = threadIdx.x;
-    const int e = T.e0 + tid;
-    const bool live = e < C.Da * C.Db;
-    const int r = live ? e / C.Db : 0, c = live ? e - r * C.Db : 0;
-    // stage: every input once (independent loads, four at a time)
-    int i = 0;
-    for (; i + 4 <= C.nin; i += 4) {
-        SrcT v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const W12In in = ins[C.in0 + i + u];
-            v[u] = live ? src[in.base + (int64_t)r * in.ld + c] : SrcT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) in_s[(i + u) * kW12Elems + tid] = v[u];
-    }
-    for (; i < C.nin; ++i) {
-        const W12In in = ins[C.in0 + i];
-        in_s[i * kW12Elems + tid] = live ? src[in.base + (int64_t)r * in.ld + c] : SrcT(0);
-    }
-    if (!live) return;   // each thread reads back only its own column: no barrier
-    using AccT = typename Acc<kF64>::T;
+    const int dbq = (C.Db + 3) >> 2;
+    const int q = T.q0 + (int)threadIdx.x;
+    if (q >= C.Da * dbq) return;
+    const int r = q / dbq, c = (q - r * dbq) * 4;
     for (int o = 0; o < C.nout; ++o) {
         const W12Out O = outs[C.out0 + o];
-        AccT v = AccT(0);
+        AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
         for (int j = O.t0; j < O.t1; ++j) {
             const W12Term t = terms[j];
-            if constexpr (kF64) v += t.coef * (AccT)in_s[t.in * kW12Elems + tid];
-            else v += t.coef32 * (AccT)in_s[t.in * kW12Elems + tid];
+            const W12In in = ins[t.in];
+            // T1 rows are padded to multiples of 4 columns with zeros (S1
+            // multiplies zero rows of its psi operand there): four loads
+            // never leave the row's padded segment
+            SrcT x[4];
+            load4(src + in.base + (int64_t)r * in.ld + c, x);
+            const AccT cf = kF64 ? (AccT)t.coef : (AccT)t.coef32;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = fma(cf, (AccT)x[u], v[u]);
         }
+        // the four columns lie inside one K piece of the S4 operand (padded to
+        // 4 columns): columns past Db are padding and are written as zero
         const OpGeom G = geom[O.task];
         const int row = O.row0 + r, col = O.col0 + c;
         if constexpr (kF64) {
-            static_cast<double*>(dst)[G.base + (int64_t)row * G.ld + col] = v;
+            double* d = static_cast<double*>(dst) + G.base + (int64_t)row * G.ld + col;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) d[u] = v[u];
         } else {
             uint16_t* d = static_cast<uint16_t*>(dst) +
                           (G.base + (int64_t)(row >> 7) * G.ld + (col >> 6)) * (int64_t)(P * kTcTileElems) +
                           swz(row & 127, col & 63);
-            uint16_t part[3];
-            split_bf16<P>(v, part);
+            uint32_t w0[3], w1[3];
+            split2<P>(v[0], v[1], w0);
+            split2<P>(v[2], v[3], w1);
 #pragma unroll
-            for (int p = 0; p < P; ++p) d[p * kTcTileElems] = part[p];
+            for (int pl = 0; pl < P; ++pl)
+                *reinterpret_cast<uint2*>(d + pl * kTcTileElems) = make_uint2(w0[pl], w1[pl]);
         }
     }
 }
 
 template <class SrcT, bool kF64, int P>
 void launch_w12_one(const W12Job& J, const OpGeom* geom, const SrcT* src, void* dst, cudaStream_t s) {
-    const int smem = std::max(J.max_in, 1) * kW12Elems * (int)sizeof(SrcT);
-    static int configured = 0;
-    if (smem > configured) {
-        CUDA_CHECK(cudaFuncSetAttribute(w12_kernel<SrcT, kF64, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        smem));
-        configured = smem;
-    }
-    w12_kernel<SrcT, kF64, P><<<(int)J.ctas.size(), kW12Elems, smem, s>>>(
+    w12_kernel<SrcT, kF64, P><<<(int)J.ctas.size(), kW12Threads, 0, s>>>(
         J.d_ctas.as<W12Cta>(), J.d_cells.as<W12Cell>(), J.d_ins.as<W12In>(), J.d_outs.as<W12Out>(),
         J.d_terms.as<W12Term>(), geom, src, dst);
 }

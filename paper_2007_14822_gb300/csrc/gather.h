@@ -37,22 +37,22 @@ struct GatherJob {
 // Fused two-site MPO step (S2+S3). A cell is one pair (a'-sector, b-sector):
 // all its inputs (T1 sub-blocks) and outputs (T3 sub-blocks, placed in the
 // S4 operand) are Da x Db matrices. Every output is a weighted sum of inputs
-// (the nonzero entries of W12). One CTA handles kW12Elems elements (a', b) of
-// one cell: it stages the inputs once, then forms every output.
-constexpr int kW12Elems = 128;
-constexpr int kW12MaxIn = 192;   // inputs per cell (larger cells are split)
+// (the nonzero entries of W12). One thread owns four consecutive columns of
+// one row of the cell (a "quad"; rows of T1 sub-blocks and columns of T3
+// sub-blocks start at multiples of 4) and forms them for every output of
+// the cell; one CTA owns kW12Threads quads.
+constexpr int kW12Threads = 128;
 struct W12Cell { int in0, nin, out0, nout, Da, Db; };
 struct W12In { int64_t base; int64_t ld; };
 struct W12Out { int task, row0, col0, t0, t1; };
 struct W12Term { double coef; float coef32; int in; };
-struct W12Cta { int cell, e0; };
+struct W12Cta { int cell, q0; };
 struct W12Job {
     std::vector<W12Cell> cells;
     std::vector<W12In> ins;
     std::vector<W12Out> outs;
     std::vector<W12Term> terms;
     std::vector<W12Cta> ctas;
-    int max_in = 0;
     DevBuf d_cells, d_ins, d_outs, d_terms, d_ctas;
     void upload_all(cudaStream_t s);
 };

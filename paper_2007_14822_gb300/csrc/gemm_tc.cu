@@ -124,11 +124,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int local = tile - t.tile0;
                 const int mi = local / t.nt, ni = local - mi * t.nt;
                 const int ks = t.kstride ? t.kstride : t.kt;
+                const int tn = t.tn ? t.tn : kTcTileN;
+                // an N tile of tn rows of B is rows [ni*tn, ni*tn + tn) of the
+                // 128-row packed tiles: a contiguous slice of one of them (the
+                // 128-byte swizzle repeats every 8 rows)
+                const int bt = (ni * tn) >> 7, boff = ((ni * tn) & 127) * 64;
+                const uint32_t bbytes = (uint32_t)tn * 128u;
                 const uint16_t* a = A + (t.a_base + (int64_t)mi * ks) * P * kTcTileElems;
-                const uint16_t* b = B + (t.b_base + (int64_t)ni * ks) * P * kTcTileElems;
+                const uint16_t* b = B + (t.b_base + (int64_t)bt * ks) * P * kTcTileElems + boff;
                 for (int kb = 0; kb < t.kt; ++kb) {
                     if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, err, 1)) { ok = false; break; }
-                    ptx::mbar_expect_tx(&full[stage], 2 * P * kTileBytes);
+                    ptx::mbar_expect_tx(&full[stage], P * (kTileBytes + bbytes));
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         ptx::bulk_g2s(sA + (stage * P + p) * kTileBytes,
@@ -136,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         ptx::bulk_g2s(sB + (stage * P + p) * kTileBytes,
-                                      b + ((int64_t)kb * P + p) * kTcTileElems, kTileBytes, &full[stage]);
+                                      b + ((int64_t)kb * P + p) * kTcTileElems, bbytes, &full[stage]);
                     if (++stage == S) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -145,13 +151,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            constexpr uint32_t idesc = ptx::idesc_bf16_f32(kTcTileM, kTcTileN);
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
             int it = 0;
             for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
                 const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+                const int tn = t.tn ? t.tn : kTcTileN;
+                const uint32_t idesc = tn == 128 ? ptx::idesc_bf16_f32(kTcTileM, 128)
+                                                 : (tn == 64 ? ptx::idesc_bf16_f32(kTcTileM, 64)
+                                                             : ptx::idesc_bf16_f32(kTcTileM, 32));
                 for (int k0 = 0; ok && k0 < t.kt; k0 += Cfg::kChunk, ++it) {
                     const int k1 = min(t.kt, k0 + Cfg::kChunk);
                     const int buf = it & 1;
@@ -200,6 +209,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
             const int local = tile - t.tile0;
             const int mi = local / t.nt, ni = local - mi * t.nt;
+            const int tn = t.tn ? t.tn : kTcTileN;
+            // columns of this warp: 128-wide tiles give each half 64; a 64- or
+            // 32-wide tile is read by the half-0 warps alone
+            const int cbase = tn == 128 ? half * kCols : 0;
+            const int ncols = tn == 128 ? kCols : (half == 0 ? tn : 0);
+            const int nend = min(t.N, ni * tn + tn);   // last column of this tile + 1
             float acc[kCols];
 #pragma unroll
             for (int j = 0; j < kCols; ++j) acc[j] = 0.0f;
@@ -208,9 +223,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t tph = (uint32_t)(it >> 1) & 1u;
                 if (!ptx::mbar_wait(&tfull[buf], tph, err, 5)) { ok = false; break; }
                 ptx::tc_fence_after();
-                const uint32_t row_addr = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + half * kCols;
+                const uint32_t row_addr = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + cbase;
 #pragma unroll
                 for (int c0 = 0; c0 < kCols; c0 += 32) {
+                    if (c0 >= ncols) break;
                     uint32_t rh[32], rx[32];
                     ptx::tmem_ld32(row_addr + c0, rh);
                     if (P > 1) ptx::tmem_ld32(row_addr + 128 + c0, rx);
@@ -233,13 +249,48 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int m = mi * kTcTileM + q * 32 + lane;
             const int mrow = m < t.M;
             const int64_t rb = mrow ? (t.use_roff ? row_off[t.roff + m] : t.c_base + (int64_t)m * t.ldc) : 0;
-            const int n0 = ni * kTcTileN + half * kCols;
+            const int n0 = ni * tn + cbase;
             uint32_t* buf = stage_all + (warp - 2) * kStageWords;
-            if (t.c_f32) {
+            // float32 rows that start on 16-byte boundaries and end on them
+            // (every row of a float32 result without scatter whose base,
+            // pitch and width are multiples of 4) leave by bulk copies
+            const bool bulk = t.c_f32 && !t.use_roff && ((t.c_base | (int64_t)t.ldc | (int64_t)t.N) & 3) == 0;
+            // the previous tile's bulk copies must have read the stage
+            ptx::bulk_wait_read();
+            __syncwarp();
+            if (ncols == 0) {
+                // nothing to store for this warp
+            } else if (bulk) {
+                // 16 rows at a time (lanes 0-15, then 16-31) go to the stage
+                // as 16-byte rows of 36 words; every lane copies its own row
+                float* Cf = reinterpret_cast<float*>(C);
+                float* sb = reinterpret_cast<float*>(buf) + (lane & 15) * 36;
+#pragma unroll
+                for (int pass = 0; pass < kCols / 32; ++pass) {
+                    const int c0 = n0 + pass * 32, nv = nend - c0;
+                    if (nv <= 0) break;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        ptx::bulk_wait_read();
+                        __syncwarp();
+                        if ((lane >> 4) == h) {
+                            float4* row = reinterpret_cast<float4*>(sb);
+#pragma unroll
+                            for (int q4 = 0; q4 < 8; ++q4)
+                                row[q4] = make_float4(acc[pass * 32 + 4 * q4], acc[pass * 32 + 4 * q4 + 1],
+                                                      acc[pass * 32 + 4 * q4 + 2], acc[pass * 32 + 4 * q4 + 3]);
+                            ptx::fence_proxy_async_smem();
+                            if (mrow) ptx::bulk_s2g(Cf + rb + c0, sb, (uint32_t)min(nv, 32) * 4u);
+                            ptx::bulk_commit();
+                        }
+                        __syncwarp();
+                    }
+                }
+            } else if (t.c_f32) {
                 float* Cf = reinterpret_cast<float*>(C);
 #pragma unroll
                 for (int pass = 0; pass < kCols / 32; ++pass) {
-                    const int c0 = n0 + pass * 32, nv = t.N - c0;
+                    const int c0 = n0 + pass * 32, nv = nend - c0;
                     if (nv <= 0) break;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __float_as_uint(acc[pass * 32 + j]);
@@ -254,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
 #pragma unroll
                 for (int pass = 0; pass < kCols / 16; ++pass) {
-                    const int c0 = n0 + pass * 16, nv = t.N - c0;
+                    const int c0 = n0 + pass * 16, nv = nend - c0;
                     if (nv <= 0) break;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -276,6 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     }
+    // the bulk copies of the epilogue have completed before the CTA ends
+    if (warp >= 2) ptx::bulk_wait();
     __syncthreads();
     if (warp == 0) {
         ptx::tc_fence_after();
@@ -297,21 +350,41 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
     gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err, row_off);
 }
 
+// K-split reduction: element e of the concatenated outputs belongs to the
+// reduction R with R.e0 <= e < R.e0 + M*N. Block b owns elements
+// [1024 b, 1024 b + 1024), four per thread with a stride of 256; the block
+// looks up the reduction of its first element once, every thread steps on
+// from there (its elements ascend).
+constexpr int kRedPerBlock = 1024;
+
 template <class PartT>
 __global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds, int nred, int64_t total,
                                                      const PartT* __restrict__ part, void* __restrict__ out,
                                                      const int64_t* __restrict__ row_off) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    __shared__ int lo_s;
+    const int64_t base = (int64_t)blockIdx.x * kRedPerBlock;
+    if (threadIdx.x == 0) {
         int lo = 0, hi = nred - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (reds[mid].e0 <= e) lo = mid; else hi = mid - 1;
+            if (reds[mid].e0 <= base) lo = mid; else hi = mid - 1;
         }
-        const SplitRed R = reds[lo];
-        const int64_t loc = e - R.e0, mn = (int64_t)R.M * R.N;
-        const int m = (int)(loc / R.N), n = (int)(loc - (int64_t)m * R.N);
+        lo_s = lo;
+    }
+    __syncthreads();
+    int lo = lo_s;
+#pragma unroll
+    for (int k = 0; k < kRedPerBlock / 256; ++k) {
+        const int64_t e = base + threadIdx.x + k * 256;
+        if (e >= total) break;
+        while (lo + 1 < nred && reds[lo + 1].e0 <= e) ++lo;
+        const SplitRed& R = reds[lo];
+        const int loc = (int)(e - R.e0);   // < M * N < 2^31
+        const int m = loc / R.N, n = loc - m * R.N;
+        const int64_t mn = (int64_t)R.M * R.N;
+        const PartT* p = part + R.part + loc;
         double acc = 0.0;
-        for (int j = 0; j < R.S; ++j) acc += (double)part[R.part + j * mn + loc];
+        for (int j = 0; j < R.S; ++j) acc += (double)p[j * mn];
         if (R.use_roff) static_cast<double*>(out)[row_off[R.roff + m] + n] = acc;
         else if (R.out_f32) static_cast<float*>(out)[R.c_base + (int64_t)m * R.ldc + n] = (float)acc;
         else static_cast<double*>(out)[R.c_base + (int64_t)m * R.ldc + n] = acc;
@@ -339,18 +412,18 @@ void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const
                           const int64_t* row_off, int num_sms, cudaStream_t s) {
     if (total == 0 || nred == 0) return;
     KScope ks("splitk_reduce", s);
-    const int64_t want = (total + 255) / 256;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(num_sms > 0 ? num_sms : 148) * 8));
-    splitk_reduce<float><<<grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
+    const int64_t grid = (total + kRedPerBlock - 1) / kRedPerBlock;
+    TNH_REQUIRE(grid < INT32_MAX, TNH_ERR_SHAPE, "splitk_reduce: %lld elements", (long long)total);
+    splitk_reduce<float><<<(unsigned)grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
 }
 
 void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const double* part, void* out,
                           const int64_t* row_off, int num_sms, cudaStream_t s) {
     if (total == 0 || nred == 0) return;
     KScope ks("splitk_reduce_f64", s);
-    const int64_t want = (total + 255) / 256;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(num_sms > 0 ? num_sms : 148) * 8));
-    splitk_reduce<double><<<grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
+    const int64_t grid = (total + kRedPerBlock - 1) / kRedPerBlock;
+    TNH_REQUIRE(grid < INT32_MAX, TNH_ERR_SHAPE, "splitk_reduce: %lld elements", (long long)total);
+    splitk_reduce<double><<<(unsigned)grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
 }
 
 }  // namespace tnh

@@ -226,8 +226,8 @@ struct JobBuilder {
     }
 };
 
-// Collects the outputs of the fused S2+S3 step per cell (a'-sector, b-sector)
-// and splits cells whose outputs need more than kW12MaxIn inputs.
+// Collects the outputs of the fused S2+S3 step per cell (a'-sector, b-sector);
+// the terms of one output that read the same T1 sub-block are merged.
 struct CellBuilder {
     struct Term { int64_t base, ld; double coef; };
     struct Out { int task; int64_t row0, col0; std::vector<Term> terms; };
@@ -245,45 +245,39 @@ struct CellBuilder {
         J = W12Job();
         for (auto& kv : cells) {
             Cell& c = kv.second;
-            size_t o = 0;
-            while (o < c.outs.size()) {
-                std::map<int64_t, int> local;   // input base -> index in the group
-                std::vector<int64_t> lds;
-                W12Cell cell{(int)J.ins.size(), 0, (int)J.outs.size(), 0, c.Da, c.Db};
-                for (; o < c.outs.size(); ++o) {
-                    int fresh = 0;
-                    for (auto& t : c.outs[o].terms) fresh += !local.count(t.base);
-                    TNH_REQUIRE(fresh <= kW12MaxIn, TNH_ERR_SHAPE,
-                                "heff_plan: one output of the MPO step needs %d inputs (maximum %d)", fresh, kW12MaxIn);
-                    if ((int)local.size() + fresh > kW12MaxIn) break;
-                    std::map<int, double> acc;
-                    for (auto& t : c.outs[o].terms) {
-                        auto it = local.find(t.base);
-                        int li;
-                        if (it == local.end()) {
-                            li = (int)local.size();
-                            local[t.base] = li;
-                            J.ins.push_back({t.base, t.ld});
-                        } else {
-                            li = it->second;
-                        }
-                        acc[li] += t.coef;
+            std::map<int64_t, int> local;   // input base -> index in J.ins
+            W12Cell cell{(int)J.ins.size(), 0, (int)J.outs.size(), 0, c.Da, c.Db};
+            for (const Out& out : c.outs) {
+                std::map<int, double> acc;
+                for (const Term& t : out.terms) {
+                    auto it = local.find(t.base);
+                    int li;
+                    if (it == local.end()) {
+                        li = (int)J.ins.size();
+                        local[t.base] = li;
+                        J.ins.push_back({t.base, t.ld});
+                    } else {
+                        li = it->second;
                     }
-                    W12Out out{c.outs[o].task, (int)c.outs[o].row0, (int)c.outs[o].col0, (int)J.terms.size(), 0};
-                    for (auto& a : acc) J.terms.push_back({a.second, (float)a.second, a.first});
-                    out.t1 = (int)J.terms.size();
-                    J.outs.push_back(out);
+                    acc[li] += t.coef;
                 }
-                cell.nin = (int)local.size();
-                cell.nout = (int)J.outs.size() - cell.out0;
-                J.max_in = std::max(J.max_in, cell.nin);
-                const int ci = (int)J.cells.size();
-                J.cells.push_back(cell);
-                for (int e0 = 0; e0 < c.Da * c.Db; e0 += kW12Elems) J.ctas.push_back({ci, e0});
+                TNH_REQUIRE(out.row0 < INT32_MAX && out.col0 < INT32_MAX && (out.col0 & 3) == 0, TNH_ERR_SHAPE,
+                            "heff_plan: MPO step output out of range");
+                W12Out o{out.task, (int)out.row0, (int)out.col0, (int)J.terms.size(), 0};
+                for (auto& a : acc) J.terms.push_back({a.second, (float)a.second, a.first});
+                o.t1 = (int)J.terms.size();
+                J.outs.push_back(o);
             }
+            cell.nin = (int)J.ins.size() - cell.in0;
+            cell.nout = (int)J.outs.size() - cell.out0;
+            const int ci = (int)J.cells.size();
+            J.cells.push_back(cell);
+            const int64_t quads = (int64_t)c.Da * ((c.Db + 3) / 4);
+            for (int64_t q0 = 0; q0 < quads; q0 += kW12Threads) J.ctas.push_back({ci, (int)q0});
         }
-        TNH_REQUIRE(J.terms.size() < (size_t)INT32_MAX && J.outs.size() < (size_t)INT32_MAX, TNH_ERR_SHAPE,
-                    "heff_plan: MPO step too large");
+        TNH_REQUIRE(J.terms.size() < (size_t)INT32_MAX && J.outs.size() < (size_t)INT32_MAX &&
+                        J.ins.size() < (size_t)INT32_MAX && J.ctas.size() < (size_t)INT32_MAX,
+                    TNH_ERR_SHAPE, "heff_plan: MPO step too large");
         J.upload_all(s);
     }
 };
@@ -474,16 +468,108 @@ int64_t base_tiles(const HeffGemm& G) {
     return n;
 }
 
-// Autotuner of the K-split factor of the two tcgen05 GEMMs. Each candidate
-// (1, 2, 4, 8; only splits that can fill the GPU better) is timed with CUDA
-// events on the plan's own operands, one warm-up and three timed runs of
-// the GEMM and its reduction; the fastest wins. Choices are kept in the
-// context by a coarse shape signature (tasks, tiles and mean K blocks per
-// task, in half octaves), so the bonds of a sweep at similar sizes reuse
-// them. TNH_HEFF_SPLIT="s1,s4" forces a choice.
-void tune_splits(HeffPlan& P) {
+// N tile width of a task under a tile policy. 0: always 128. 1: the width
+// that moves the fewest operand bytes per K block (48 KB of A per tile plus
+// 384 B of B per column, three planes): operand traffic bound. 2: the width
+// that issues the fewest MMA columns (tiles x (width + 16), 16 standing for
+// the per-tile cost): tensor bound. Ties keep the wider tile.
+int tile_width(int N, int policy) {
+    if (policy == 0) return kTcTileN;
+    int best = kTcTileN;
+    double bc = 1e300;
+    for (int tn : {128, 64, 32}) {
+        const double tiles = (double)cdiv(N, tn);
+        const double c = policy == 1 ? tiles * (48.0 + 0.375 * tn) : tiles * (tn + 16.0);
+        if (c < bc - 1e-9) {
+            bc = c;
+            best = tn;
+        }
+    }
+    return best;
+}
+
+void set_tiles(HeffGemm& G, int policy) {
+    G.tile_policy = policy;
+    for (GemmTask& t : G.tc_base) {
+        t.tn = tile_width(t.N, policy);
+        t.nt = (int)cdiv(t.N, t.tn);
+    }
+}
+
+// ---- tuning cache on disk: one line per shape signature,
+//   "heff <key values...> : <tiles S1> <split S1> <tiles S4> <split S4>"
+// read when a context first tunes, appended to after every measurement.
+// The file is named by TNH_TUNE_CACHE (no file: the choices live as long as
+// the context).
+std::string tune_line(const std::vector<int>& key, const std::array<int, 4>& c) {
+    std::string l = "heff";
+    for (int k : key) l += " " + std::to_string(k);
+    l += " :";
+    for (int v : c) l += " " + std::to_string(v);
+    return l;
+}
+
+void load_tune_file(Ctx* ctx) {
+    if (ctx->tune_loaded) return;
+    ctx->tune_loaded = true;
+    const char* path = std::getenv("TNH_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        std::string l(line);
+        if (l.rfind("heff ", 0) != 0) continue;
+        const size_t colon = l.find(':');
+        if (colon == std::string::npos) continue;
+        std::vector<int> key;
+        std::array<int, 4> c{};
+        int v, pos = 5, n = 0;
+        const std::string a = l.substr(5, colon - 5), b = l.substr(colon + 1);
+        const char* p = a.c_str();
+        while (std::sscanf(p, "%d%n", &v, &n) == 1) {
+            key.push_back(v);
+            p += n;
+        }
+        p = b.c_str();
+        int k = 0;
+        while (k < 4 && std::sscanf(p, "%d%n", &v, &n) == 1) {
+            c[k++] = v;
+            p += n;
+        }
+        (void)pos;
+        const bool valid = k == 4 && c[0] >= 0 && c[0] <= 2 && c[2] >= 0 && c[2] <= 2 && c[1] >= 1 && c[1] <= 8 &&
+                           c[3] >= 1 && c[3] <= 8;
+        if (valid && !key.empty()) ctx->heff_tune[key] = c;
+    }
+    std::fclose(f);
+}
+
+void save_tune_line(const std::vector<int>& key, const std::array<int, 4>& c) {
+    const char* path = std::getenv("TNH_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s\n", tune_line(key, c).c_str());
+        std::fclose(f);
+    }
+}
+
+// Autotuner of the two tcgen05 GEMMs of a plan: first the N tile policy
+// (tile_width; 128-wide tiles against tiles fitted to the output blocks'
+// widths by two cost models), then the K-split factor (1, 2, 4, 8; only
+// splits that can fill the GPU better). Each candidate is timed with CUDA
+// events on the plan's own operands, one warm-up and three timed runs of the
+// GEMM and its reduction; a candidate replaces the incumbent only when it is
+// 3% faster. Choices are kept in the context by a coarse shape signature
+// (tasks, tiles and mean K blocks per task, in half octaves), so the bonds
+// of a sweep at similar sizes reuse them, and in the TNH_TUNE_CACHE file
+// across processes. TNH_HEFF_SPLIT="s1,s4" and TNH_HEFF_TILES="p1,p4"
+// force the choices.
+void tune_plan(HeffPlan& P) {
     Ctx* ctx = P.ctx;
     cudaStream_t s = P.stream;
+    set_tiles(P.g1, 0);
+    set_tiles(P.g4, 0);
     auto bucket = [](double x) { return (int)std::lround(2.0 * std::log2(std::max(1.0, x))); };
     std::vector<int> key{P.planes};
     for (const HeffGemm* G : {&P.g1, &P.g4}) {
@@ -493,11 +579,16 @@ void tune_splits(HeffPlan& P) {
         key.push_back(bucket((double)base_tiles(*G)));
         key.push_back(bucket((double)kt / std::max<size_t>(1, G->tc_base.size())));
     }
-    std::pair<int, int> choice{1, 1};
+    load_tune_file(ctx);
+    std::array<int, 4> choice{0, 1, 0, 1};   // tiles S1, split S1, tiles S4, split S4
     bool measured = false;
-    if (const char* f = std::getenv("TNH_HEFF_SPLIT")) {
-        int a = 1, b = 1;
-        if (std::sscanf(f, "%d,%d", &a, &b) == 2) choice = {std::max(1, a), std::max(1, b)};
+    const char* fs = std::getenv("TNH_HEFF_SPLIT");
+    const char* ft = std::getenv("TNH_HEFF_TILES");
+    if (fs || ft) {
+        int a = 1, b = 1, c = 0, d = 0;
+        if (fs && std::sscanf(fs, "%d,%d", &a, &b) != 2) a = b = 1;
+        if (ft && std::sscanf(ft, "%d,%d", &c, &d) != 2) c = d = 0;
+        choice = {std::min(std::max(c, 0), 2), std::max(1, a), std::min(std::max(d, 0), 2), std::max(1, b)};
     } else if (ctx->heff_tune.count(key)) {
         choice = ctx->heff_tune[key];
     } else {
@@ -505,7 +596,7 @@ void tune_splits(HeffPlan& P) {
         cudaEvent_t e0, e1;
         CUDA_CHECK(cudaEventCreate(&e0));
         CUDA_CHECK(cudaEventCreate(&e1));
-        auto time_split = [&](HeffGemm& G, bool s1, int split) {
+        auto time_run = [&](HeffGemm& G, bool s1, int split) {
             set_split(G, split, s);
             ensure_part(P, G.part_elems);
             auto run = [&] {
@@ -521,37 +612,62 @@ void tune_splits(HeffPlan& P) {
             CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
             return ms;
         };
-        int best[2] = {1, 1};
         HeffGemm* Gs[2] = {&P.g1, &P.g4};
         for (int g = 0; g < 2; ++g) {
             HeffGemm& G = *Gs[g];
+            // tile policy at split 1
+            std::vector<int> widths0;
+            for (const GemmTask& t : G.tc_base) widths0.push_back(t.tn);
+            int bestp = 0;
+            float tbest = time_run(G, g == 0, 1);
+            std::vector<std::vector<int>> seen{widths0};
+            for (int policy : {1, 2}) {
+                set_tiles(G, policy);
+                std::vector<int> w;
+                for (const GemmTask& t : G.tc_base) w.push_back(t.tn);
+                if (std::find(seen.begin(), seen.end(), w) != seen.end()) continue;   // same tiles
+                seen.push_back(w);
+                const float tm = time_run(G, g == 0, 1);
+                if (tm < 0.97f * tbest) {
+                    tbest = tm;
+                    bestp = policy;
+                }
+            }
+            set_tiles(G, bestp);
+            // K split with the chosen tiles
             int maxkt = 1;
             for (const GemmTask& t : G.tc_base) maxkt = std::max(maxkt, t.kt);
             const int64_t tiles = base_tiles(G);
-            float tbest = time_split(G, g == 0, 1);
+            int bests = 1;
             for (int split : {2, 4, 8}) {
                 if (split > maxkt || tiles * (split / 2) >= 2 * (int64_t)ctx->num_sms) break;
-                const float tm = time_split(G, g == 0, split);
+                const float tm = time_run(G, g == 0, split);
                 if (tm < 0.97f * tbest) {
                     tbest = tm;
-                    best[g] = split;
+                    bests = split;
                 }
             }
+            choice[2 * g] = bestp;
+            choice[2 * g + 1] = bests;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         check_device_flag(ctx);
-        choice = {best[0], best[1]};
         ctx->heff_tune[key] = choice;
+        save_tune_line(key, choice);
         measured = true;
     }
-    set_split(P.g1, choice.first, s);
-    set_split(P.g4, choice.second, s);
+    set_tiles(P.g1, choice[0]);
+    set_tiles(P.g4, choice[2]);
+    set_split(P.g1, choice[1], s);
+    set_split(P.g4, choice[3], s);
     ensure_part(P, std::max(P.g1.part_elems, P.g4.part_elems));
+    P.tune = choice;
+    P.tune_measured = measured;
     if (std::getenv("TNH_DEBUG"))
-        std::fprintf(stderr, "heff_plan: K split S1 %d, S4 %d (%s; S1 %lld tiles, S4 %lld tiles)\n", choice.first,
-                     choice.second, measured ? "measured" : "cached or forced", (long long)base_tiles(P.g1),
-                     (long long)base_tiles(P.g4));
+        std::fprintf(stderr, "heff_plan: S1 tiles %d split %d, S4 tiles %d split %d (%s; S1 %lld tiles, S4 %lld tiles)\n",
+                     choice[0], choice[1], choice[2], choice[3], measured ? "measured" : "cached or forced",
+                     (long long)base_tiles(P.g1), (long long)base_tiles(P.g4));
 }
 
 }  // namespace
@@ -654,7 +770,10 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         const int64_t K = ia.dim[A];
         int64_t M = 0, N = 0;
         for (int b : lb) M += (int64_t)L.bdim(b, 1) * L.bdim(b, 2);
-        for (int b : xb) N += X.belems(b) / K;
+        // columns (s1, s2, b): every (s1, s2) group of Db columns starts at a
+        // multiple of 4, so that every T1 row segment the MPO step reads is
+        // 16-byte aligned (the padding columns are zero)
+        for (int b : xb) N += (int64_t)X.bdim(b, 1) * X.bdim(b, 2) * rup(X.bdim(b, 3), 4);
         P->oL.add_task(M, K);
         P->oX.add_task(N, K);
         bL.task(M, K);
@@ -670,13 +789,16 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                 row += Dap;
             }
         }
-        // columns (s1, s2, b): operand B = psi^T, element (r = (s1,s2,b), c = a)
+        // columns (s1, s2, b): operand B = psi^T, element (r = (s1,s2,b), c = a);
+        // group g = (s1, s2) of a block starts at column col + g * Dbp
         int64_t col = 0;
         for (int b : xb) {
             const int64_t nb = X.belems(b) / K;
-            bX.rect(t, col, 0, nb, K, {GatherTerm{1.0, X.off[b], 1, nb, 1.0f}});
+            const int Db = X.bdim(b, 3), Dbp = (int)rup(Db, 4), ng = X.bdim(b, 1) * X.bdim(b, 2);
+            for (int g = 0; g < ng; ++g)
+                bX.rect(t, col + (int64_t)g * Dbp, 0, Db, K, {GatherTerm{1.0, X.off[b] + (int64_t)g * Db, 1, nb, 1.0f}});
             t1_cols[{A, X.sect[(size_t)b * 4 + 1], X.sect[(size_t)b * 4 + 2], X.sect[(size_t)b * 4 + 3]}] = {t, col};
-            col += nb;
+            col += (int64_t)ng * Dbp;
         }
         t1_base.push_back(P->t1_elems);
         t1_ld.push_back(N);
@@ -795,7 +917,9 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         const int64_t N = ibp.dim[Bp];
         int64_t M = 0, K = 0;
         for (int b : yb) M += X.belems(b) / N;
-        for (int b : rb) K += (int64_t)R.bdim(b, 0) * R.bdim(b, 1);
+        // K pieces (w2 element, b-sector) of Db columns each start at a multiple
+        // of 4, so the MPO step writes four columns with one store per plane
+        for (int b : rb) K += rup(R.bdim(b, 0), 4) * R.bdim(b, 1);
         P->oT.add_task(M, K);
         P->oR.add_task(N, K);
         bR.task(N, K);
@@ -809,7 +933,7 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
             for (int zl = 0; zl < Dz; ++zl) {
                 bR.rect(t, 0, col, N, Db, {GatherTerm{1.0, R.off[b] + (int64_t)zl * N, 1, (int64_t)Dz * N, 1.0f}});
                 kp.push_back({(int)(iz.off[Sz] + zl), B, col, Db});
-                col += Db;
+                col += rup(Db, 4);
             }
         }
         // row pieces (s1', s2', a'): every row of every psi block of this b'-sector
@@ -837,7 +961,8 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                                 auto ci = t1_cols.find({t1_sector[ref.task], ps1.first, ps2.first, k.B});
                                 if (ci == t1_cols.end()) continue;
                                 const int ds2 = is2.dim[ps2.first];
-                                const int64_t c0 = ci->second.second + ((int64_t)ps1.second * ds2 + ps2.second) * k.Db;
+                                const int64_t c0 =
+                                    ci->second.second + ((int64_t)ps1.second * ds2 + ps2.second) * rup(k.Db, 4);
                                 const int64_t ld = t1_ld[ref.task];
                                 tm.push_back({t1_base[ref.task] + ref.row * ld + c0, ld, e.v});
                             }
@@ -904,15 +1029,15 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     }
     CUDA_CHECK(cudaGetLastError());
     clk.mark("device");
-    if (pl > 0 && !P->g1.tc_base.empty() && !P->g4.tc_base.empty()) tune_splits(*P);
+    if (pl > 0 && !P->g1.tc_base.empty() && !P->g4.tc_base.empty()) tune_plan(*P);
     clk.mark("tune");
     if (std::getenv("TNH_DEBUG"))
         std::fprintf(stderr,
                      "heff_plan: n %lld, S1 %zu tasks %d tiles, T1 %lld, S4 %zu tasks %d tiles, T3 %lld, "
-                     "MPO step %zu cells %zu ctas %zu inputs %zu outputs %zu terms (max %d inputs)\n",
+                     "MPO step %zu cells %zu ctas %zu inputs %zu outputs %zu terms\n",
                      (long long)P->n, P->g1.tc.size(), P->g1.tilestc, (long long)P->t1_elems, P->g4.tc.size(),
                      P->g4.tilestc, (long long)P->oT.elems64, P->jW.cells.size(), P->jW.ctas.size(),
-                     P->jW.ins.size(), P->jW.outs.size(), P->jW.terms.size(), P->jW.max_in);
+                     P->jW.ins.size(), P->jW.outs.size(), P->jW.terms.size());
     // the host tables and the caller's L, R must stay alive until these ran
     CUDA_CHECK(cudaStreamSynchronize(s));
     return P;
@@ -1179,6 +1304,15 @@ tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, 
         *s1 = P->f_s1;
         *s23 = P->f_s23;
         *s4 = P->f_s4;
+    });
+}
+
+tnh_status tnh_heff_tuning(const tnh_heff* plan, int32_t* choice) {
+    auto* P = reinterpret_cast<const HeffPlan*>(plan);
+    return guard(nullptr, [&] {
+        TNH_REQUIRE(P && choice, TNH_ERR_ARG, "tnh_heff_tuning: NULL argument");
+        for (int k = 0; k < 4; ++k) choice[k] = P->tune[k];
+        choice[4] = P->tune_measured ? 1 : 0;
     });
 }
 

@@ -1,6 +1,8 @@
 // Effective-Hamiltonian plan and the device Lanczos eigensolver.
 #pragma once
 
+#include <array>
+
 #include "gather.h"
 #include "tnh_internal.h"
 
@@ -22,6 +24,7 @@ struct HeffGemm {
     std::vector<GemmTask> f64, tc, tc_base;
     int tiles64 = 0, tilestc = 0;
     int split = 1;
+    int tile_policy = 0;   // N tile widths of the tcgen05 tasks (see tile_width)
     std::vector<SplitRed> reds;
     int64_t red_total = 0, part_elems = 0;
     DevBuf d_f64, d_tc, d_reds;
@@ -64,6 +67,8 @@ struct HeffPlan {
     DevBuf part64;          // float64 partial slabs of K-split FP64 GEMMs
     int64_t t1_elems = 0;
     bool zero_y = false;    // some output rows are written by no S4 task
+    std::array<int, 4> tune{0, 1, 0, 1};   // tile policy / K split of S1, then of S4
+    bool tune_measured = false;            // chosen by timing in this plan (not cached or forced)
     // one CUDA graph per format (float64, split): the four launches of an
     // application, replayed with the x and y arguments patched in
     struct Graph {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <cstdio>
 #include <map>
@@ -170,10 +171,19 @@ struct Ctx {
     std::string err;
     DevBuf d_flag;    // int[4]: [0] device error code written by bounded waits
     std::unique_ptr<Profiler> prof;
-    // H_eff K-split choices measured by the plan autotuner, by shape signature
-    std::map<std::vector<int>, std::pair<int, int>> heff_tune;
+    // H_eff GEMM choices of the plan autotuner (tile policy and K split of S1,
+    // then of S4) by shape signature; loaded from TNH_TUNE_CACHE once
+    std::map<std::vector<int>, std::array<int, 4>> heff_tune;
+    bool tune_loaded = false;
     // the MPS left by the last DMRG run
     std::vector<OwnedTensor> mps;
+    // checkpointing of DMRG runs (tnh_dmrg_checkpoint) and where the last
+    // run ended: next bond (sweep, pass, step) and whether it finished
+    std::string ckpt_path;
+    int ckpt_every = 0;
+    int64_t ckpt_stop = 0;
+    int pos_sweep = 0, pos_pass = 0, pos_step = 0;
+    bool pos_finished = false;
     ~Ctx();
 };
 
@@ -234,6 +244,8 @@ struct GemmTask {
     int64_t roff;
     int kstride;             // tcgen05 GEMM: operand tiles per tile row (0: kt); a K-split sub-task
                              // covers kt k-blocks starting at its a_base / b_base
+    int tn;                  // tcgen05 GEMM: N tile width 128, 64 or 32 (0: 128); B is packed in
+                             // 128-row tiles, a narrower N tile reads a slice of one
 };
 void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, int total_tiles, const double* A,
                      const double* B, double* C, cudaStream_t s, const int64_t* row_off = nullptr);

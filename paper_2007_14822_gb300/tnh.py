@@ -30,7 +30,8 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
            "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
            "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag",
-           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout"]
+           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout", "tnh_heff_tuning",
+           "tnh_dmrg_checkpoint", "tnh_dmrg_resume", "tnh_dmrg_position"]
 
 
 class TnhError(RuntimeError):
@@ -96,6 +97,11 @@ def lib():
         "tnh_heff_flops": (i32, [vp, P(dbl)]),
         "tnh_heff_flops_detail": (i32, [vp, P(dbl), P(dbl), P(dbl)]),
         "tnh_heff_size": (i32, [vp, P(i64)]),
+        "tnh_heff_tuning": (i32, [vp, P(i32)]),
+        "tnh_dmrg_checkpoint": (i32, [vp, C.c_char_p, i32, i64]),
+        "tnh_dmrg_resume": (i32, [vp, i32, P(tnh_dmrg_problem), C.c_char_p, P(tnh_sweep_params), P(dbl),
+                                  P(tnh_sweep_stat)]),
+        "tnh_dmrg_position": (i32, [vp, P(i32), P(i32), P(i32), P(i32)]),
         "tnh_heff_free": (None, [vp]),
         "tnh_eigsolve": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
         "tnh_eigsolve_davidson": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
@@ -383,12 +389,13 @@ class Context:
         return res
 
     def dmrg(self, mpo, mps, start, done, maxdim, cutoff, mindim=1, krylov_dim=32, tol=1e-10,
-             prec=FP64, env_prec=FP64, ortho=(), weight=1.0, eigensolver="lanczos"):
+             prec=FP64, env_prec=FP64, ortho=(), weight=1.0, eigensolver="lanczos", resume=None):
         """Two-site DMRG sweeps. ``mpo`` is one MPO (list of site tensors) or,
         with ``start``/``done`` lists, a list of MPOs whose sum is H;
         ``ortho`` lists previous states (MPS) to stay orthogonal to, with the
-        energy penalty ``weight``. Returns (energy, per-sweep stats); the
-        final MPS is read with ``dmrg_mps``."""
+        energy penalty ``weight``. With ``resume`` (a checkpoint file) the run
+        continues from it and ``mps`` is ignored. Returns (energy, per-sweep
+        stats); the final MPS is read with ``dmrg_mps``."""
         keep = []
         ns = len(maxdim)
         md = (C.c_int32 * ns)(*maxdim)
@@ -400,8 +407,8 @@ class Context:
         e = C.c_double()
         terms = isinstance(start, (list, tuple))
         N = len(mpo[0]) if terms else len(mpo)
-        A = (tnh_tensor * N)(*[a._c(keep) for a in mps])
-        if not terms and not ortho:
+        A = (tnh_tensor * N)(*[a._c(keep) for a in mps]) if resume is None else None
+        if not terms and not ortho and resume is None:
             W = (tnh_tensor * N)(*[w._c(keep) for w in mpo])
             self.check(self._lib.tnh_dmrg(self.h, N, W, int(start), int(done), A, C.byref(p), C.byref(e), stats))
         else:
@@ -414,9 +421,26 @@ class Context:
             no = len(ortho)
             O = (tnh_tensor * max(1, no * N))(*[a._c(keep) for m in ortho for a in m])
             prob = tnh_dmrg_problem(len(mpos), W, st, dn, no, O, float(weight))
-            self.check(self._lib.tnh_dmrg_ex(self.h, N, C.byref(prob), A, C.byref(p), C.byref(e), stats))
+            if resume is None:
+                self.check(self._lib.tnh_dmrg_ex(self.h, N, C.byref(prob), A, C.byref(p), C.byref(e), stats))
+            else:
+                self.check(self._lib.tnh_dmrg_resume(self.h, N, C.byref(prob), os.fsencode(str(resume)),
+                                                     C.byref(p), C.byref(e), stats))
         return e.value, [dict(sweep=s.sweep, energy=s.energy, resid=s.resid, truncerr=s.truncerr,
                               maxlink=s.maxlink, matvecs=s.matvecs, seconds=s.seconds) for s in stats]
+
+    def dmrg_checkpoint(self, path, every=0, stop_after=0):
+        """Write checkpoints of later runs to ``path`` every ``every`` bonds
+        (0: at sweep ends) and stop a run after ``stop_after`` bonds (0:
+        never); ``path`` None turns checkpointing off."""
+        self.check(self._lib.tnh_dmrg_checkpoint(self.h, None if path is None else os.fsencode(str(path)),
+                                                 int(every), int(stop_after)))
+
+    def dmrg_position(self):
+        """(sweep, pass, step, finished) where the last run ended."""
+        a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self.check(self._lib.tnh_dmrg_position(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return a.value, b.value, c.value, bool(d.value)
 
     def dmrg_link(self, j):
         """Sectors [(qn, dim)] of link j of the MPS left by the last DMRG run."""
@@ -479,6 +503,14 @@ class Heff:
         n = C.c_int64()
         self.ctx.check(self.ctx._lib.tnh_heff_size(self.h, C.byref(n)))
         return n.value
+
+    @property
+    def tuning(self):
+        """The autotuner's GEMM choices: {'tiles_s1', 'split_s1', 'tiles_s4',
+        'split_s4', 'measured'} (see tnh_heff_tuning)."""
+        c = (C.c_int32 * 5)()
+        self.ctx.check(self.ctx._lib.tnh_heff_tuning(self.h, c))
+        return {"tiles_s1": c[0], "split_s1": c[1], "tiles_s4": c[2], "split_s4": c[3], "measured": bool(c[4])}
 
     def diag(self, out):
         """Diagonal of the MPO part of H_eff into ``out`` (CUDA float64 [n])."""

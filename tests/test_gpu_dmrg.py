@@ -292,3 +292,64 @@ def test_dmrg_splitblocks_mpo(ctx, qn):
     e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)))
     assert abs(Es - Ed) < 1e-12 * abs(Ed), (Es, Ed)
     assert abs(Es - e_ed) < 1e-9 * abs(e_ed)
+
+
+@pytest.mark.parametrize("stop,every", [(37, 1), (30, 0), (52, 7)])
+def test_dmrg_checkpoint_file_resume_inside_a_sweep(ctx, tmp_path, stop, every):
+    # a run that stops after `stop` bond updates (inside sweep 1, at the end of
+    # sweep 0, or inside the right-to-left pass of sweep 1), having written its
+    # checkpoint file, is resumed by a new context from that file: the energies
+    # of every sweep equal those of the uninterrupted run (FP64, deterministic
+    # kernels), the stopped run reports where it stopped, and the file holds
+    # the MPS, the environments and the position
+    from paper_2007_14822_gb300 import tnh
+    N = 16
+    host = pm.heisenberg(N)
+    W = pm.to_device(host, qn=True)
+    site = W[0].inds[3]
+    sweeps = [(8, 1e-12), (16, 1e-12), (32, 1e-12), (48, 1e-12)]
+    md, co = [m for m, _ in sweeps], [c for _, c in sweeps]
+    mk = lambda: pm.product_state(site, [0, 1] * (N // 2))
+    E4, st4 = ctx.dmrg(W, mk(), host.start, host.done, md, co, krylov_dim=32)
+    path = tmp_path / "run.ckpt"
+    c1 = tnh.Context(0)
+    c1.dmrg_checkpoint(path, every=every, stop_after=stop)
+    c1.dmrg(W, mk(), host.start, host.done, md, co, krylov_dim=32)
+    sw, pas, step, fin = c1.dmrg_position()
+    bonds_per_sweep = 2 * (N - 1)
+    assert not fin and sw == stop // bonds_per_sweep
+    rest = stop % bonds_per_sweep
+    assert (pas, step) == ((0, rest) if rest < N - 1 else (1, rest - (N - 1)))
+    assert path.exists() and path.read_bytes()[:8] == b"TNHCKPT1"
+    c1.close()
+    c2 = tnh.Context(0)
+    Er, str_ = c2.dmrg(W, None, host.start, host.done, md, co, krylov_dim=32, resume=path)
+    assert c2.dmrg_position()[3]
+    assert abs(Er - E4) < 1e-12 * abs(E4), (Er, E4)
+    for a, b in zip(str_, st4):
+        assert abs(a["energy"] - b["energy"]) < 1e-12 * abs(b["energy"]), (a, b)
+        assert a["maxlink"] == b["maxlink"]
+    c2.close()
+
+
+def test_dmrg_checkpoint_refuses_a_mismatched_problem(ctx, tmp_path):
+    from paper_2007_14822_gb300 import tnh
+    from paper_2007_14822_gb300.tnh import TnhError
+    N = 8
+    host = pm.heisenberg(N)
+    W = pm.to_device(host, qn=True)
+    site = W[0].inds[3]
+    path = tmp_path / "a.ckpt"
+    c1 = tnh.Context(0)
+    c1.dmrg_checkpoint(path, every=3, stop_after=5)
+    c1.dmrg(W, pm.product_state(site, [0, 1] * (N // 2)), host.start, host.done, [8, 8], [1e-12] * 2)
+    c1.close()
+    other = pm.to_device(pm.j1j2_chain(N, 1.0, 0.5), qn=True)    # another MPO link space
+    with pytest.raises(TnhError) as e:
+        ctx.dmrg(other, None, host.start, host.done, [8, 8], [1e-12] * 2, resume=path)
+    assert e.value.code == 5
+    bad = tmp_path / "junk.ckpt"
+    bad.write_bytes(b"not a checkpoint at all")
+    with pytest.raises(TnhError) as e:
+        ctx.dmrg(W, None, host.start, host.done, [8, 8], [1e-12] * 2, resume=bad)
+    assert e.value.code == 1

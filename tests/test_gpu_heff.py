@@ -190,6 +190,48 @@ def test_heff_k_split_matches_oracle(ctx, split, m, nsect, maxd, monkeypatch):
     assert err < TOL["bf16x6"], err
 
 
+@pytest.mark.parametrize("tiles,split", [("1,1", "1,1"), ("2,2", "1,1"), ("2,1", "2,4"), ("0,2", "1,2")])
+@pytest.mark.parametrize("m,nsect,maxd", [(300, 15, 60), (160, 9, 90), (70, 1, 70)])
+def test_heff_tile_widths_match_oracle(ctx, tiles, split, m, nsect, maxd, monkeypatch):
+    # N tiles of 64 and 32 columns (slices of the 128-row packed B tiles),
+    # alone and with K splits, on blocks of every width
+    monkeypatch.setenv("TNH_HEFF_TILES", tiles)
+    monkeypatch.setenv("TNH_HEFF_SPLIT", split)
+    err, plan = _heff_case(ctx, m, nsect, "bf16x6", maxd=maxd)
+    t = plan.tuning
+    assert (t["tiles_s1"], t["tiles_s4"]) == tuple(int(x) for x in tiles.split(",")) and not t["measured"]
+
+
+def test_heff_tuning_cache_file(ctx, tmp_path, monkeypatch):
+    # the autotuner's choices go to the TNH_TUNE_CACHE file; a new context
+    # reads them back for a plan of the same shapes instead of timing again
+    from paper_2007_14822_gb300 import tnh
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("TNH_TUNE_CACHE", str(path))
+    monkeypatch.delenv("TNH_HEFF_SPLIT", raising=False)
+    monkeypatch.delenv("TNH_HEFF_TILES", raising=False)
+    d = H.heff_inputs(96, None, 11, nsect=9, maxd=24)
+    c1 = tnh.Context(0)
+    p1 = c1.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec("bf16x6"))
+    t1 = p1.tuning
+    assert t1["measured"]
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("heff ")
+    c1.close()
+    c2 = tnh.Context(0)
+    p2 = c2.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec("bf16x6"))
+    t2 = p2.tuning
+    assert not t2["measured"] and {k: v for k, v in t2.items() if k != "measured"} == \
+        {k: v for k, v in t1.items() if k != "measured"}
+    y = __import__("torch").zeros_like(d["psi"].data)
+    p2.apply(d["psi"].data, y)
+    yt = d["psi"].with_inds(d["psi"].inds)
+    yt.data = y
+    want = D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    assert H.rel_err(H.to_oracle(yt), want) < TOL["bf16x6"]
+    c2.close()
+
+
 def test_heff_config2_full_size(ctx):
     # dense m=256, w=5, d=2: L/R (256,5,256), psi (256,2,2,256), Gaussian, seeded
     for p in ("fp64", "bf16x6"):
