@@ -290,6 +290,17 @@ tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_dim, double 
 tnh_status tnh_eigsolve_davidson(tnh_heff* plan, double* psi, int32_t krylov_dim, double tol,
                                  double* energy, double* resid, int32_t* matvecs);
 
+/* Lowest eigenpair of the symmetric tridiagonal matrix with diagonal
+ * alpha [k] and off-diagonal beta [k-1] (HOST arrays), by the kernel the
+ * Lanczos eigensolver runs after each step: float32 Sturm multisection, one
+ * float32 and one float64 twisted factorization with their Rayleigh
+ * quotients, a float64 Sturm check that nothing lies below the result (else
+ * float64 multisection). Writes theta and the normalised eigenvector v [k]
+ * (HOST; its sign is arbitrary). For testing the eigensolver's inner step;
+ * 1 <= k <= 255, TNH_ERR_NUMERIC for non-finite entries. Synchronous. */
+tnh_status tnh_tridiag_lowest(tnh_ctx* ctx, int32_t k, const double* alpha, const double* beta,
+                              double* theta, double* v);
+
 /* ---- environment update ------------------------------------------------ */
 
 /* dir = +1: E_out[b,w',b'] = sum E[a,w,a'] A[a,s,b] W[w,w',s,s'] A[a',s',b']
@@ -355,6 +366,10 @@ typedef struct {
     int32_t precision;       /* tnh_precision of the Lanczos matvecs */
     int32_t env_precision;   /* tnh_precision of theta and the environments */
     int32_t eigensolver;     /* 0: Lanczos (tnh_eigsolve), 1: Davidson (tnh_eigsolve_davidson) */
+    int32_t energy_mode;     /* 0: FP64 energy and residual (one FP64 H_eff product) at every bond;
+                              * 1: at the last bond of each sweep only, the other bonds report
+                              *    the eigensolver's Ritz value (the sweep statistics and the
+                              *    returned energy are always FP64). */
 } tnh_sweep_params;
 
 typedef struct {
@@ -371,7 +386,11 @@ typedef struct {
  * product state is) with MPO tensors W[j] [wl, wr, s, s'] (same arrows as
  * above). start/done are the MPO link states selected by the left and right
  * boundaries. A sweep is a left-to-right pass over the bonds followed by a
- * right-to-left pass; energy is the eigenvalue at the last bond. The final
+ * right-to-left pass; energy is the eigenvalue at the last bond. When the
+ * environments are built in a split precision (env_precision), the energy of
+ * the final sweep is evaluated again with FP64 environments rebuilt from the
+ * final MPS (right-orthogonal from site 2 on): <theta|H_eff|theta> at bond
+ * (0, 1) in FP64, the state's exact energy to float64 rounding. The final
  * MPS stays on the device inside the context (tnh_dmrg_mps_*). Synchronous. */
 tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, int64_t start,
                     int64_t done, const tnh_tensor* mps, const tnh_sweep_params* p,

@@ -348,6 +348,7 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
     TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad precision");
     TNH_REQUIRE(eprec == TNH_FP64 || planes_of(eprec) > 0, TNH_ERR_ARG, "tnh_dmrg: bad env precision");
     TNH_REQUIRE(p->eigensolver == 0 || p->eigensolver == 1, TNH_ERR_ARG, "tnh_dmrg: eigensolver %d", p->eigensolver);
+    TNH_REQUIRE(p->energy_mode == 0 || p->energy_mode == 1, TNH_ERR_ARG, "tnh_dmrg: energy_mode %d", p->energy_mode);
     CUDA_CHECK(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
     const int T = (int)pr.W.size();
@@ -517,8 +518,11 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
                     }
                     ph[1] += since(tp);
                     tp = clk::now();
-                    EigResult r = p->eigensolver == 1 ? davidson(*P, th.L.data, p->krylov_dim, p->lanczos_tol)
-                                                      : eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol);
+                    // the FP64 product for the energy: every bond, or the sweep's last one
+                    const bool fp64e = p->energy_mode == 0 || (pass == 1 && step == N - 2);
+                    EigResult r = p->eigensolver == 1
+                                      ? davidson(*P, th.L.data, p->krylov_dim, p->lanczos_tol, fp64e)
+                                      : eigsolve(*P, th.L.data, p->krylov_dim, p->lanczos_tol, fp64e);
                     ph[2] += since(tp);
                     E = r.energy;
                     resid = r.resid;
@@ -629,6 +633,34 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
                 return;
             }
         }
+    }
+    if (eprec != TNH_FP64) {
+        // the final state's energy with FP64 environments: R_N-1 .. R_2 again
+        // from the final MPS, then <theta|H_eff theta> / <theta|theta> at bond
+        // (0, 1) in FP64 (theta = A_0 A_1, sites 2.. right-orthogonal)
+        for (int j = N - 1; j >= 2; --j) {
+            const Layout& a = A[j].L;
+            Rs[j] = new_tensor({a.inds[0], W[j].inds[0], a.inds[0].dag()}, zero, s);
+            auto P = make_env(c, -1, Rs[j + 1].L, a, W[j], Rs[j].L);
+            run_env(c, *P, Rs[j + 1].L.data, a.data, W[j].data, Rs[j].L.data, TNH_FP64);
+            CUDA_CHECK(cudaStreamSynchronize(s));
+        }
+        Layout a1 = relabel(A[0].L, {1, 2, 3});
+        Layout a2 = relabel(A[1].L, {3, 4, 5});
+        DTensor th = new_tensor({a1.inds[0], a1.inds[1], a2.inds[1], a2.inds[2]}, fsum(a1.flux, a2.flux), s);
+        th.L = relabel(th.L, {1, 2, 4, 5});
+        contract64(c, a1, a2, th.L);
+        auto P = make_heff(c, Ls[0].L, W[0], W[1], Rs[2].L, th.L, TNH_FP64);
+        if (K) {
+            DevBuf phi((size_t)K * std::max<int64_t>(th.L.size, 1) * sizeof(double));
+            for (int i = 0; i < K; ++i)
+                projected_state(c, LO[i][0].L, pr.P[i][0], pr.P[i][1], RO[i][2].L, th.L,
+                                phi.as<double>() + (int64_t)i * th.L.size);
+            set_projectors(*P, K, phi.as<double>(), pr.weight);
+        }
+        const double ef = rayleigh_fp64(*P, th.L.data);
+        E = ef;
+        if (stats && p->nsweep > 0) stats[p->nsweep - 1].energy = ef;
     }
     c->pos_sweep = p->nsweep;
     c->pos_pass = c->pos_step = 0;

@@ -188,7 +188,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* w) {
 }
 
 template <class SrcT, bool kF64, int P>
-__global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restrict__ ctas,
+__global__ void __launch_bounds__(kW12Threads, 8) w12_kernel(const W12Cta* __restrict__ ctas,
                                                           const W12Cell* __restrict__ cells,
                                                           const W12In* __restrict__ ins,
                                                           const W12Out* __restrict__ outs,
@@ -202,23 +202,9 @@ __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restri
     const int q = T.q0 + (int)threadIdx.x;
     if (q >= C.Da * dbq) return;
     const int r = q / dbq, c = (q - r * dbq) * 4;
-    for (int o = 0; o < C.nout; ++o) {
-        const W12Out O = outs[C.out0 + o];
-        AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
-        for (int j = O.t0; j < O.t1; ++j) {
-            const W12Term t = terms[j];
-            const W12In in = ins[t.in];
-            // T1 rows are padded to multiples of 4 columns with zeros (S1
-            // multiplies zero rows of its psi operand there): four loads
-            // never leave the row's padded segment
-            SrcT x[4];
-            load4(src + in.base + (int64_t)r * in.ld + c, x);
-            const AccT cf = kF64 ? (AccT)t.coef : (AccT)t.coef32;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = fma(cf, (AccT)x[u], v[u]);
-        }
-        // the four columns lie inside one K piece of the S4 operand (padded to
-        // 4 columns): columns past Db are padding and are written as zero
+    // one output: its four columns lie inside one K piece of the S4 operand
+    // (padded to 4 columns): columns past Db are padding, written as zero
+    auto store = [&](const W12Out& O, const AccT* v) {
         const OpGeom G = geom[O.task];
         const int row = O.row0 + r, col = O.col0 + c;
         if constexpr (kF64) {
@@ -236,6 +222,37 @@ __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restri
             for (int pl = 0; pl < P; ++pl)
                 *reinterpret_cast<uint2*>(d + pl * kTcTileElems) = make_uint2(w0[pl], w1[pl]);
         }
+    };
+    // T1 rows are padded to multiples of 4 columns with zeros (S1 multiplies
+    // zero rows of its psi operand there): four loads never leave the row's
+    // padded segment
+    auto term = [&](int j, AccT* v) {
+        const W12Term t = terms[j];
+        const W12In in = ins[t.in];
+        SrcT x[4];
+        load4(src + in.base + (int64_t)r * in.ld + c, x);
+        const AccT cf = kF64 ? (AccT)t.coef : (AccT)t.coef32;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = fma(cf, (AccT)x[u], v[u]);
+    };
+    // two outputs at a time: the loads of both are in flight together
+    int o = 0;
+    for (; o + 1 < C.nout; o += 2) {
+        const W12Out O0 = outs[C.out0 + o], O1 = outs[C.out0 + o + 1];
+        AccT v0[4] = {AccT(0), AccT(0), AccT(0), AccT(0)}, v1[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
+        const int n0 = O0.t1 - O0.t0, n1 = O1.t1 - O1.t0;
+        for (int j = 0; j < max(n0, n1); ++j) {
+            if (j < n0) term(O0.t0 + j, v0);
+            if (j < n1) term(O1.t0 + j, v1);
+        }
+        store(O0, v0);
+        store(O1, v1);
+    }
+    if (o < C.nout) {
+        const W12Out O = outs[C.out0 + o];
+        AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
+        for (int j = O.t0; j < O.t1; ++j) term(j, v);
+        store(O, v);
     }
 }
 

@@ -373,19 +373,24 @@ __global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict_
     }
     __syncthreads();
     int lo = lo_s;
+    SplitRed R = reds[lo];   // a register copy, reloaded when the thread steps to the next reduction
+    int64_t next = lo + 1 < nred ? reds[lo + 1].e0 : INT64_MAX;
 #pragma unroll
     for (int k = 0; k < kRedPerBlock / 256; ++k) {
         const int64_t e = base + threadIdx.x + k * 256;
         if (e >= total) break;
-        while (lo + 1 < nred && reds[lo + 1].e0 <= e) ++lo;
-        const SplitRed& R = reds[lo];
+        if (e >= next) {
+            while (lo + 1 < nred && reds[lo + 1].e0 <= e) ++lo;
+            R = reds[lo];
+            next = lo + 1 < nred ? reds[lo + 1].e0 : INT64_MAX;
+        }
         const int loc = (int)(e - R.e0);   // < M * N < 2^31
         const int m = loc / R.N, n = loc - m * R.N;
         const int64_t mn = (int64_t)R.M * R.N;
         const PartT* p = part + R.part + loc;
         double acc = 0.0;
-        for (int j = 0; j < R.S; ++j) acc += (double)p[j * mn];
-        if (R.use_roff) static_cast<double*>(out)[row_off[R.roff + m] + n] = acc;
+        for (int j = 0; j < R.S; ++j) acc += (double)__ldg(p + j * mn);
+        if (R.use_roff) static_cast<double*>(out)[__ldg(row_off + R.roff + m) + n] = acc;
         else if (R.out_f32) static_cast<float*>(out)[R.c_base + (int64_t)m * R.ldc + n] = (float)acc;
         else static_cast<double*>(out)[R.c_base + (int64_t)m * R.ldc + n] = acc;
     }

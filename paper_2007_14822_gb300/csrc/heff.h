@@ -114,12 +114,16 @@ struct EigResult {
     double energy = 0, resid = 0;
     int matvecs = 0;
 };
-// Lanczos on the plan; psi (device, length P.n) in/out.
-EigResult eigsolve(HeffPlan& P, double* psi, int krylov_dim, double tol);
+// Lanczos on the plan; psi (device, length P.n) in/out. With fp64_energy
+// the energy and residual come from a final FP64 product with the Ritz
+// vector, else they are the Ritz value and residual estimate of the run.
+EigResult eigsolve(HeffPlan& P, double* psi, int krylov_dim, double tol, bool fp64_energy = true);
 // Davidson with the diagonal preconditioner; same contract as eigsolve.
-EigResult davidson(HeffPlan& P, double* psi, int krylov_dim, double tol);
+EigResult davidson(HeffPlan& P, double* psi, int krylov_dim, double tol, bool fp64_energy = true);
 
 void vdot(Ctx* ctx, VecWork& w, const double* x, const double* y, int64_t n, double* d_out);
+// <x|H x> / <x|x> with the plan's FP64 product (x device, length P.n).
+double rayleigh_fp64(HeffPlan& P, const double* x);
 void vscale_copy(Ctx* ctx, const double* x, double* y, int64_t n, const double* d_num, const double* d_den,
                  int mode);
 

@@ -126,50 +126,143 @@ __device__ int sturm_count(const double* a, const double* b2, int k, double x) {
 
 constexpr int kMaxKrylov = 256;
 
+// The same count in float32 (the float64 units of this GPU run at 1/64 of
+// the float32 rate), rescaling at 2^+-60: exact up to float32 rounding of
+// the minors, i.e. it may miscount only for x within float32 resolution of
+// an eigenvalue.
+__device__ int sturm_count_f32(const float* a, const float* b2, int k, float x) {
+    int c = 0;
+    float pm = 1.0f, p = a[0] - x;
+    if (p == 0.0f) p = 0x1p-100f;
+    if (p < 0.0f) ++c;
+    for (int i = 1; i < k; ++i) {
+        float pn = fmaf(a[i] - x, p, -b2[i - 1] * pm);
+        if (pn == 0.0f) pn = p * 0x1p-100f;
+        if ((pn < 0.0f) != (p < 0.0f)) ++c;
+        pm = p;
+        p = pn;
+        const float ap = fabsf(p);
+        if (ap > 0x1p60f) { p *= 0x1p-60f; pm *= 0x1p-60f; }
+        else if (ap < 0x1p-60f && fabsf(pm) < 0x1p-60f) { p *= 0x1p60f; pm *= 0x1p60f; }
+    }
+    return c;
+}
+
+// Eigenvector for theta by one twisted factorization of T - theta (the
+// twist r minimises |gamma_r|, v_r = 1, v recurred outwards), normalised;
+// returns the Rayleigh quotient v^T T v. T = (a, b), b2 = b^2, in type R for
+// the factorization; v and the quotient in float64. Called by the whole
+// block (uniform); threads 0 and 32 run the two directions concurrently.
+template <class R>
+__device__ double twisted_rq(const double* a, const double* b, const double* b2, int k, double theta, double tiny,
+                             R* dd, R* dl, double* v, int* twist) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        R d = (R)(a[0] - theta);
+        for (int i = 0; i < k; ++i) {
+            if (i > 0) d = (R)(a[i] - theta) - (R)b2[i - 1] / d;
+            if (fabs((double)d) < tiny) d = d < (R)0 ? (R)-tiny : (R)tiny;
+            dd[i] = d;   // D+
+        }
+    } else if (t == 32) {
+        R d = (R)(a[k - 1] - theta);
+        for (int i = k - 1; i >= 0; --i) {
+            if (i < k - 1) d = (R)(a[i] - theta) - (R)b2[i] / d;
+            if (fabs((double)d) < tiny) d = d < (R)0 ? (R)-tiny : (R)tiny;
+            dl[i] = d;   // D-
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        int r = 0;
+        double gbest = INFINITY;
+        for (int i = 0; i < k; ++i) {
+            const double g = fabs((double)dd[i] + (double)dl[i] - (a[i] - theta));
+            if (g < gbest) { gbest = g; r = i; }
+        }
+        *twist = r;
+    }
+    __syncthreads();
+    const int r = *twist;
+    if (t == 0) {   // v_r = 1 and the part above the twist
+        R vi = (R)1;
+        v[r] = 1.0;
+        for (int i = r - 1; i >= 0; --i) {
+            vi = -((R)b[i] / dd[i]) * vi;
+            v[i] = (double)vi;
+        }
+    } else if (t == 32) {   // the part below the twist (starts from v_r = 1 itself)
+        R vi = (R)1;
+        for (int i = r + 1; i < k; ++i) {
+            vi = -((R)b[i - 1] / dl[i]) * vi;
+            v[i] = (double)vi;
+        }
+    }
+    __syncthreads();
+    __shared__ double rq_s;
+    if (t == 0) {
+        double nrm = 0.0;
+        for (int i = 0; i < k; ++i) nrm = fma(v[i], v[i], nrm);
+        const double inv = 1.0 / sqrt(nrm);
+        for (int i = 0; i < k; ++i) v[i] *= inv;
+        double rq = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double tv = a[i] * v[i];
+            if (i > 0) tv += b[i - 1] * v[i - 1];
+            if (i + 1 < k) tv += b[i] * v[i + 1];
+            rq += v[i] * tv;
+        }
+        rq_s = rq;
+    }
+    __syncthreads();
+    return rq_s;
+}
+
 // Lowest eigenpair of T_k (alpha[0..k), beta[0..k-1)); beta2_last = |w|^2 of
 // the current step. out[0] = theta, out[1] = beta_k |s_k|, out[2] = beta_k,
 // beta[k-1] = beta_k is written, s[0..k) = normalised eigenvector.
+//   1. float32 multisection (32 Sturm probes per round, one warp) brackets
+//      the lowest eigenvalue to float32 resolution;
+//   2. a float32 twisted factorization at the bracket's midpoint gives an
+//      eigenvector accurate to about float32 precision; its float64
+//      Rayleigh quotient is then accurate to about its square;
+//   3. one float64 twisted factorization at that quotient and its Rayleigh
+//      quotient give the pair to float64 accuracy (Rayleigh quotient
+//      iteration, cubic convergence);
+//   4. a float64 Sturm count just below the result confirms that no
+//      eigenvalue lies below it; if one does (the float32 bracket missed a
+//      close pair) the float64 multisection of the whole spectrum's bottom
+//      decides instead, followed by one float64 twisted factorization.
 __global__ void tridiag_lowest(const double* __restrict__ alpha, double* __restrict__ beta, int k,
                                const double* __restrict__ beta2_last, double* __restrict__ out,
                                double* __restrict__ s) {
     __shared__ double a[kMaxKrylov], b[kMaxKrylov], b2[kMaxKrylov];
-    __shared__ double lo_s, hi_s, tiny_s;
-    __shared__ int first_s;
+    __shared__ float af[kMaxKrylov], b2f[kMaxKrylov];
+    __shared__ double lo_s, hi_s, tiny_s, th_s;
+    __shared__ int twist_s, bad_s;
     __shared__ double dd[kMaxKrylov], dl[kMaxKrylov], v[kMaxKrylov];
+    __shared__ float ddf[kMaxKrylov], dlf[kMaxKrylov];
     const int t = threadIdx.x, nt = blockDim.x;
-    for (int i = t; i < k; i += nt) a[i] = alpha[i];
-    for (int i = t; i + 1 < k; i += nt) { b[i] = beta[i]; b2[i] = beta[i] * beta[i]; }
+    for (int i = t; i < k; i += nt) { a[i] = alpha[i]; af[i] = (float)alpha[i]; }
+    for (int i = t; i + 1 < k; i += nt) {
+        b[i] = beta[i];
+        b2[i] = beta[i] * beta[i];
+        b2f[i] = (float)b2[i];
+    }
     __syncthreads();
     if (t == 0) {
-        double lo = a[0], hi = a[0];
+        double lo = a[0], hi = a[0], tn = 1e-300;
         for (int i = 0; i < k; ++i) {
             double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
             lo = fmin(lo, a[i] - r);
             hi = fmax(hi, a[i] + r);
+            tn = fmax(tn, fabs(a[i]) + r);
         }
         double pad = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
         lo_s = lo - pad;
         hi_s = hi + pad;
-    }
-    __syncthreads();
-    // multisection: 32 probes per round, by the first warp only (float64
-    // throughput of one SM bounds many probes; 5 bits per round suffice)
-    if (t < 32) {
-        double lo = lo_s, hi = hi_s;
-        for (int round = 0; round < 24; ++round) {
-            if (hi - lo <= 2e-16 * fmax(fabs(lo), fabs(hi))) break;
-            const double x = lo + (hi - lo) * (double)(t + 1) / 33.0;
-            const unsigned below = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x) >= 1);
-            const int f = below ? __ffs(below) - 1 : 32;   // first probe with an eigenvalue below it
-            const double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / 33.0;
-            const double nhi = f == 32 ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
-            lo = nlo;
-            hi = nhi;
-        }
-        if (t == 0) {
-            lo_s = lo;
-            hi_s = hi;
-        }
+        tiny_s = fmax(1e-15 * tn, 1e-200);
+        bad_s = 0;
     }
     __syncthreads();
     if (k == 1) {   // uniform branch: the other one has barriers
@@ -181,88 +274,66 @@ __global__ void tridiag_lowest(const double* __restrict__ alpha, double* __restr
             out[2] = bk;
             s[0] = 1.0;
         }
-    } else {
-        // eigenvector for theta by one twisted factorization of T - theta:
-        // D+ from the top (thread 0) and D- from the bottom (thread 1) run
-        // concurrently; the twist r minimises |gamma_r|, v_r = 1, and v is
-        // recurred outwards (threads 0 and 1 again)
-        const double theta = 0.5 * (lo_s + hi_s);
-        if (t == 0) {
-            double tn = 1e-300;
-            for (int i = 0; i < k; ++i)
-                tn = fmax(tn, fabs(a[i]) + (i + 1 < k ? fabs(b[i]) : 0.0) + (i > 0 ? fabs(b[i - 1]) : 0.0));
-            tiny_s = fmax(1e-15 * tn, 1e-200);
+        return;
+    }
+    const double tiny = tiny_s;
+    // 1. float32 multisection
+    if (t < 32) {
+        float lo = (float)lo_s, hi = (float)hi_s;
+        lo = nextafterf(lo, -INFINITY);
+        hi = nextafterf(hi, INFINITY);
+        for (int round = 0; round < 8; ++round) {
+            if (hi - lo <= 4e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+            const float x = lo + (hi - lo) * (float)(t + 1) / 33.0f;
+            const unsigned below = __ballot_sync(0xffffffffu, sturm_count_f32(af, b2f, k, x) >= 1);
+            const int f = below ? __ffs(below) - 1 : 32;
+            const float nlo = f == 0 ? lo : lo + (hi - lo) * (float)f / 33.0f;
+            const float nhi = f == 32 ? hi : lo + (hi - lo) * (float)(f + 1) / 33.0f;
+            lo = nlo;
+            hi = nhi;
+        }
+        if (t == 0) th_s = 0.5 * ((double)lo + (double)hi);
+    }
+    __syncthreads();
+    // 2. float32 twisted factorization, float64 Rayleigh quotient
+    const double tiny32 = fmax(1e-6 * (tiny * 1e15), 1e-30);
+    double theta = twisted_rq<float>(a, b, b2, k, th_s, tiny32, ddf, dlf, v, &twist_s);
+    // 3. float64 Rayleigh quotient iteration step
+    theta = twisted_rq<double>(a, b, b2, k, theta, tiny, dd, dl, v, &twist_s);
+    // 4. nothing below it
+    if (t == 0) {
+        const double delta = 1e-13 * fmax(1.0, tiny * 1e15);
+        bad_s = sturm_count(a, b2, k, theta - delta) > 0;
+    }
+    __syncthreads();
+    if (bad_s) {   // uniform: float64 multisection, then one twisted factorization
+        if (t < 32) {
+            double lo = lo_s, hi = hi_s;
+            for (int round = 0; round < 24; ++round) {
+                if (hi - lo <= 2e-16 * fmax(fabs(lo), fabs(hi))) break;
+                const double x = lo + (hi - lo) * (double)(t + 1) / 33.0;
+                const unsigned below = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x) >= 1);
+                const int f = below ? __ffs(below) - 1 : 32;
+                const double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / 33.0;
+                const double nhi = f == 32 ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+                lo = nlo;
+                hi = nhi;
+            }
+            if (t == 0) th_s = 0.5 * (lo + hi);
         }
         __syncthreads();
-        const double tiny = tiny_s;
-        if (t == 0) {
-            double d = a[0] - theta;
-            for (int i = 0; i < k; ++i) {
-                if (i > 0) d = (a[i] - theta) - b2[i - 1] / d;
-                if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
-                dd[i] = d;   // D+
-            }
-        } else if (t == 1) {
-            double d = a[k - 1] - theta;
-            for (int i = k - 1; i >= 0; --i) {
-                if (i < k - 1) d = (a[i] - theta) - b2[i] / d;
-                if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
-                dl[i] = d;   // D-
-            }
-        }
-        __syncthreads();
-        if (t == 0) {
-            int r = 0;
-            double gbest = INFINITY;
-            for (int i = 0; i < k; ++i) {
-                const double g = fabs(dd[i] + dl[i] - (a[i] - theta));
-                if (g < gbest) { gbest = g; r = i; }
-            }
-            first_s = r;
-        }
-        __syncthreads();
-        const int r = first_s;
-        if (t == 0) {   // v_r = 1 and the part above the twist
-            double vi = 1.0;
-            v[r] = 1.0;
-            for (int i = r - 1; i >= 0; --i) {
-                vi = -(b[i] / dd[i]) * vi;
-                v[i] = vi;
-            }
-        } else if (t == 1) {   // the part below the twist (starts from v_r = 1 itself)
-            double vi = 1.0;
-            for (int i = r + 1; i < k; ++i) {
-                vi = -(b[i - 1] / dl[i]) * vi;
-                v[i] = vi;
-            }
-        }
-        __syncthreads();
-        if (t == 0) {
-            double nrm = 0.0;
-            for (int i = 0; i < k; ++i) nrm = fma(v[i], v[i], nrm);
-            const double inv = 1.0 / sqrt(nrm);
-            for (int i = 0; i < k; ++i) v[i] *= inv;
-            // Rayleigh quotient refines theta to machine precision
-            double rq = 0.0;
-            for (int i = 0; i < k; ++i) {
-                double tv = a[i] * v[i];
-                if (i > 0) tv += b[i - 1] * v[i - 1];
-                if (i + 1 < k) tv += b[i] * v[i + 1];
-                rq += v[i] * tv;
-            }
-            double bk = sqrt(fmax(*beta2_last, 0.0));
-            beta[k - 1] = bk;
-            out[0] = rq;
-            out[1] = bk * fabs(v[k - 1]);
-            out[2] = bk;
-            for (int i = 0; i < k; ++i) s[i] = v[i];
-        }
+        theta = twisted_rq<double>(a, b, b2, k, th_s, tiny, dd, dl, v, &twist_s);
+    }
+    if (t == 0) {
+        double bk = sqrt(fmax(*beta2_last, 0.0));
+        beta[k - 1] = bk;
+        out[0] = theta;
+        out[1] = bk * fabs(v[k - 1]);
+        out[2] = bk;
+        for (int i = 0; i < k; ++i) s[i] = v[i];
     }
 }
 
-// Fixed-length runs (tol <= 0) need the tridiagonal eigenpair only at the
-// end: intermediate steps only record beta_j = |w| (and alpha_j as a scale
-// for the breakdown test).
 __global__ void set_beta(const double* __restrict__ alpha_j, const double* __restrict__ beta2_last,
                          double* __restrict__ beta_j, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -460,7 +531,7 @@ void add_projectors(HeffPlan& P, const double* x, double* y) {
     }
 }
 
-EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
+EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol, bool fp64_energy) {
     Ctx* ctx = P.ctx;
     cudaStream_t s = ctx->stream;
     const int64_t n = P.n;
@@ -547,6 +618,15 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
     { KScope ks_("scale_copy", s);
     scale_copy<<<g, 256, 0, s>>>(psi, psi, n, nullptr, misc, 1);
     }
+    res.matvecs = k;
+    if (!fp64_energy) {
+        // the Ritz value and its residual estimate (of the last solve)
+        CUDA_CHECK(cudaStreamSynchronize(s));
+        check_device_flag(ctx);
+        res.energy = host[0];
+        res.resid = host[1];
+        return res;
+    }
     // float64 energy and residual
     heff_apply(P, TNH_FP64, psi, yv.as<double>());
     vdot(ctx, vw, psi, yv.as<double>(), n, misc + 2);
@@ -564,7 +644,26 @@ EigResult eigsolve(HeffPlan& P, double* psi, int kmax, double tol) {
     return res;
 }
 
-EigResult davidson(HeffPlan& P, double* psi, int kmax, double tol) {
+double rayleigh_fp64(HeffPlan& P, const double* x) {
+    Ctx* ctx = P.ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P.n;
+    if (n == 0) return 0.0;
+    VecWork vw;
+    vw.ensure(ctx->num_sms);
+    DevBuf yv((size_t)n * sizeof(double)), sc(4 * sizeof(double));
+    heff_apply(P, TNH_FP64, x, yv.as<double>());
+    vdot(ctx, vw, x, yv.as<double>(), n, sc.as<double>());
+    vdot(ctx, vw, x, x, n, sc.as<double>() + 1);
+    double h[2];
+    CUDA_CHECK(cudaMemcpyAsync(h, sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_CHECK(cudaStreamSynchronize(s));
+    check_device_flag(ctx);
+    TNH_REQUIRE(std::isfinite(h[0]) && h[1] > 0.0, TNH_ERR_NUMERIC, "rayleigh quotient of a zero or non-finite vector");
+    return h[0] / h[1];
+}
+
+EigResult davidson(HeffPlan& P, double* psi, int kmax, double tol, bool fp64_energy) {
     Ctx* ctx = P.ctx;
     cudaStream_t s = ctx->stream;
     const int64_t n = P.n;
@@ -659,6 +758,17 @@ EigResult davidson(HeffPlan& P, double* psi, int kmax, double tol) {
     { KScope ks_("scale_copy", s);
     scale_copy<<<g, 256, 0, s>>>(psi, psi, n, nullptr, misc + 3, 1);
     }
+    res.matvecs = k;
+    if (!fp64_energy) {
+        // the Ritz value and residual of the last projected solve
+        double rr[2];
+        CUDA_CHECK(cudaMemcpyAsync(rr, misc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
+        check_device_flag(ctx);
+        res.energy = rr[0];
+        res.resid = std::sqrt(std::max(rr[1], 0.0));
+        return res;
+    }
     double* y = yv.as<double>();
     heff_apply(P, TNH_FP64, psi, y);
     vdot(ctx, vw, psi, y, n, misc + 4);
@@ -701,5 +811,37 @@ extern "C" tnh_status tnh_eigsolve(tnh_heff* plan, double* psi, int32_t krylov_d
         if (energy) *energy = r.energy;
         if (resid) *resid = r.resid;
         if (matvecs) *matvecs = r.matvecs;
+    });
+}
+
+extern "C" tnh_status tnh_tridiag_lowest(tnh_ctx* ctx, int32_t k, const double* alpha, const double* beta,
+                                         double* theta, double* v) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    return guard(c, [&] {
+        TNH_REQUIRE(c && alpha && theta && v && (k == 1 || beta), TNH_ERR_ARG, "tnh_tridiag_lowest: NULL argument");
+        TNH_REQUIRE(k >= 1 && k < kMaxKrylov, TNH_ERR_ARG, "tnh_tridiag_lowest: k = %d out of 1..%d", k,
+                    kMaxKrylov - 1);
+        for (int i = 0; i < k; ++i) TNH_REQUIRE(std::isfinite(alpha[i]), TNH_ERR_NUMERIC, "tnh_tridiag_lowest: alpha");
+        for (int i = 0; i + 1 < k; ++i) TNH_REQUIRE(std::isfinite(beta[i]), TNH_ERR_NUMERIC, "tnh_tridiag_lowest: beta");
+        CUDA_CHECK(cudaSetDevice(c->device));
+        cudaStream_t s = c->stream;
+        // device copies: alpha [k], beta [k] (beta[k-1] receives beta_k = 0), beta2_last, out[3], s[k]
+        DevBuf d((size_t)(3 * k + 4) * sizeof(double));
+        double* da = d.as<double>();
+        double* db = da + k;
+        double* dout = db + k;   // [0..2]
+        double* dz = dout + 3;   // beta2_last = 0
+        double* ds = dz + 1;
+        CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes, s));
+        CUDA_CHECK(cudaMemcpyAsync(da, alpha, (size_t)k * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (k > 1) CUDA_CHECK(cudaMemcpyAsync(db, beta, (size_t)(k - 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+        {
+            KScope ks_("tridiag_lowest", s);
+            tridiag_lowest<<<1, 256, 0, s>>>(da, db, k, dz, dout, ds);
+        }
+        CUDA_CHECK(cudaGetLastError());
+        CUDA_CHECK(cudaMemcpyAsync(theta, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaMemcpyAsync(v, ds, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_CHECK(cudaStreamSynchronize(s));
     });
 }

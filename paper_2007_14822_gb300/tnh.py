@@ -31,7 +31,7 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
            "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag",
            "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout", "tnh_heff_tuning",
-           "tnh_dmrg_checkpoint", "tnh_dmrg_resume", "tnh_dmrg_position"]
+           "tnh_dmrg_checkpoint", "tnh_dmrg_resume", "tnh_dmrg_position", "tnh_tridiag_lowest"]
 
 
 class TnhError(RuntimeError):
@@ -54,7 +54,8 @@ class tnh_tensor(C.Structure):
 class tnh_sweep_params(C.Structure):
     _fields_ = [("nsweep", C.c_int32), ("maxdim", C.POINTER(C.c_int32)), ("cutoff", C.POINTER(C.c_double)),
                 ("mindim", C.c_int32), ("krylov_dim", C.c_int32), ("lanczos_tol", C.c_double),
-                ("precision", C.c_int32), ("env_precision", C.c_int32), ("eigensolver", C.c_int32)]
+                ("precision", C.c_int32), ("env_precision", C.c_int32), ("eigensolver", C.c_int32),
+                ("energy_mode", C.c_int32)]
 
 
 class tnh_sweep_stat(C.Structure):
@@ -102,6 +103,7 @@ def lib():
         "tnh_dmrg_resume": (i32, [vp, i32, P(tnh_dmrg_problem), C.c_char_p, P(tnh_sweep_params), P(dbl),
                                   P(tnh_sweep_stat)]),
         "tnh_dmrg_position": (i32, [vp, P(i32), P(i32), P(i32), P(i32)]),
+        "tnh_tridiag_lowest": (i32, [vp, i32, P(dbl), P(dbl), P(dbl), P(dbl)]),
         "tnh_heff_free": (None, [vp]),
         "tnh_eigsolve": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
         "tnh_eigsolve_davidson": (i32, [vp, vp, i32, dbl, P(dbl), P(dbl), P(i32)]),
@@ -389,7 +391,8 @@ class Context:
         return res
 
     def dmrg(self, mpo, mps, start, done, maxdim, cutoff, mindim=1, krylov_dim=32, tol=1e-10,
-             prec=FP64, env_prec=FP64, ortho=(), weight=1.0, eigensolver="lanczos", resume=None):
+             prec=FP64, env_prec=FP64, ortho=(), weight=1.0, eigensolver="lanczos", resume=None,
+             energy_mode=0):
         """Two-site DMRG sweeps. ``mpo`` is one MPO (list of site tensors) or,
         with ``start``/``done`` lists, a list of MPOs whose sum is H;
         ``ortho`` lists previous states (MPS) to stay orthogonal to, with the
@@ -402,7 +405,7 @@ class Context:
         co = (C.c_double * ns)(*cutoff)
         p = tnh_sweep_params(ns, C.cast(md, C.POINTER(C.c_int32)), C.cast(co, C.POINTER(C.c_double)),
                              int(mindim), int(krylov_dim), float(tol), int(prec), int(env_prec),
-                             {"lanczos": 0, "davidson": 1}[eigensolver])
+                             {"lanczos": 0, "davidson": 1}[eigensolver], int(energy_mode))
         stats = (tnh_sweep_stat * ns)()
         e = C.c_double()
         terms = isinstance(start, (list, tuple))
@@ -428,6 +431,20 @@ class Context:
                                                      C.byref(p), C.byref(e), stats))
         return e.value, [dict(sweep=s.sweep, energy=s.energy, resid=s.resid, truncerr=s.truncerr,
                               maxlink=s.maxlink, matvecs=s.matvecs, seconds=s.seconds) for s in stats]
+
+    def tridiag_lowest(self, alpha, beta):
+        """Lowest eigenpair (theta, v) of the tridiagonal (alpha, beta) by the
+        eigensolver's device kernel (host float64 arrays in and out)."""
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        k = len(a)
+        th = C.c_double()
+        v = np.zeros(k)
+        P = C.POINTER(C.c_double)
+        self.check(self._lib.tnh_tridiag_lowest(self.h, k, a.ctypes.data_as(P),
+                                                b.ctypes.data_as(P) if k > 1 else None, C.byref(th),
+                                                v.ctypes.data_as(P)))
+        return th.value, v
 
     def dmrg_checkpoint(self, path, every=0, stop_after=0):
         """Write checkpoints of later runs to ``path`` every ``every`` bonds

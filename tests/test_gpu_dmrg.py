@@ -353,3 +353,36 @@ def test_dmrg_checkpoint_refuses_a_mismatched_problem(ctx, tmp_path):
     with pytest.raises(TnhError) as e:
         ctx.dmrg(W, None, host.start, host.done, [8, 8], [1e-12] * 2, resume=bad)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("model", ["heisenberg", "hubbard"])
+def test_dmrg_split_environments_with_fp64_final_energy(ctx, model):
+    # BF16x6 matvecs and BF16x6 environment updates, the FP64 energy product
+    # only at each sweep's last bond (energy_mode 1) and the final energy
+    # evaluated with FP64 environments rebuilt from the final MPS: the same
+    # energy as plain FP64 sweeps and exact diagonalisation to 1e-9; in FP64,
+    # energy_mode 1 returns the energy of energy_mode 0
+    from paper_2007_14822_gb300 import tnh
+    if model == "heisenberg":
+        N, d, host = 12, 2, pm.heisenberg(12)
+        states = [0, 1] * (N // 2)
+        sweeps = [(8, 1e-12), (32, 1e-12), (64, 1e-13), (64, 1e-13)]
+        e_ed = ed.ground_energy(N, 2, om.spin_pair_terms(om.heisenberg_pairs(N)), om.SPIN_QN, (0,))
+    else:
+        N, d, host = 6, 4, pm.hubbard(6, 1.0, 4.0)
+        states = [1, 2] * (N // 2)
+        sweeps = [(16, 1e-12), (64, 1e-13), (64, 1e-13), (64, 1e-13)]
+        e_ed = ed.ground_energy(N, 4, om.hubbard_terms(N, 1.0, 4.0), om.HUB_QN, (N, 0))
+    W = pm.to_device(host, qn=True)
+    site = W[0].inds[3]
+    md, co = [m for m, _ in sweeps], [c for _, c in sweeps]
+    run = lambda **kw: ctx.dmrg(W, pm.product_state(site, states), host.start, host.done, md, co,
+                                krylov_dim=64, **kw)
+    E0, st0 = run(tol=1e-10)
+    E1, st1 = run(tol=1e-10, energy_mode=1)
+    assert abs(E1 - E0) < 1e-13 * abs(E0), (E0, E1)
+    assert [s["maxlink"] for s in st1] == [s["maxlink"] for s in st0]
+    E2, st2 = run(tol=1e-7, prec=tnh.BF16x6, env_prec=tnh.BF16x6, energy_mode=1)
+    assert abs(E2 - E0) < 1e-9 * abs(E0), (E2, E0)
+    assert abs(E2 - e_ed) < 1e-9 * abs(e_ed), (E2, e_ed)
+    assert st2[-1]["energy"] == E2

@@ -490,3 +490,42 @@ def test_heff_qn_workloads_full_size(ctx, which):
         yt.data = y
         err, rep = H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
         print(name, p, "norm-wise", err, "worst block", rep["block"], "worst element", rep["elem"])
+
+
+# ------------------------------------------------- tridiagonal eigensolve
+def _tridiag_cases():
+    rng = np.random.default_rng(8)
+    cases = []
+    for k in (1, 2, 3, 17, 64, 255):
+        cases.append(("random", rng.standard_normal(k) * 10, rng.standard_normal(k - 1) * 3))
+    # Wilkinson W+ (pairs of eigenvalues close to rounding at the top; the
+    # bottom is simple), and its negative (close pairs at the bottom)
+    for m in (10, 30):
+        a = np.abs(np.arange(-m, m + 1, dtype=float))
+        cases.append(("wilkinson", a, np.ones(2 * m)))
+        cases.append(("-wilkinson", -a, np.ones(2 * m)))
+    # an exactly degenerate lowest pair: two copies of a block, split by b = 0
+    a1, b1 = rng.standard_normal(12), rng.standard_normal(11)
+    cases.append(("degenerate", np.concatenate([a1, a1]), np.concatenate([b1, [0.0], b1])))
+    # graded entries over sixteen decades and a Lanczos-like matrix of a
+    # converged run (tiny trailing beta)
+    g = 10.0 ** np.linspace(-8, 8, 40)
+    cases.append(("graded", g, np.sqrt(g[:-1] * g[1:]) * 0.3))
+    a = -40 + rng.standard_normal(48)
+    b = np.abs(rng.standard_normal(47)) * 5
+    b[-8:] = 1e-9
+    cases.append(("converged", a, b))
+    return cases
+
+
+@pytest.mark.parametrize("name,alpha,beta", _tridiag_cases(), ids=[c[0] + str(len(c[1])) for c in _tridiag_cases()])
+def test_tridiag_lowest_matches_lapack(ctx, name, alpha, beta):
+    # the Lanczos inner step on its own, against LAPACK's tridiagonal solver
+    from scipy.linalg import eigh_tridiagonal
+    th, v = ctx.tridiag_lowest(alpha, beta)
+    w, V = eigh_tridiagonal(alpha, beta) if len(alpha) > 1 else (alpha.copy(), np.ones((1, 1)))
+    scale = max(1.0, float(np.max(np.abs(alpha))) + (2 * float(np.max(np.abs(beta))) if len(beta) else 0.0))
+    assert abs(th - w[0]) < 1e-13 * scale, (th, w[0])
+    T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+    assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+    assert np.linalg.norm(T @ v - th * v) < 1e-10 * scale
