@@ -339,63 +339,143 @@ def sweep_reference():
         return json.load(f)
 
 
+def mixed_kw(tnh):
+    """Mixed-precision sweep settings: BF16x6 matvecs and environment updates,
+    the FP64 energy product at each sweep's last bond, the final energy
+    evaluated with FP64 environments."""
+    return dict(prec=tnh.BF16x6, env_prec=tnh.BF16x6, energy_mode=1)
+
+
+def sweep_record(E, st, t_run):
+    last = st[-1]
+    return {"energy": E, "last_sweep_s": last["seconds"], "maxlink": last["maxlink"],
+            "matvecs_last_sweep": last["matvecs"], "truncerr": last["truncerr"], "run_s": t_run,
+            "sweep_s": [x["seconds"] for x in st], "maxlink_per_sweep": [x["maxlink"] for x in st]}
+
+
 def bench_sweeps(ctx, tnh):
     from paper_2007_14822_gb300 import models as pm
     mpo = pm.heisenberg(SWEEP_N)
     res = {}
-    for name, prec, tol in (("bf16x6", tnh.BF16x6, 1e-7), ("fp64", tnh.FP64, 1e-9)):
+    for name, kw, tol in (("bf16x6", mixed_kw(tnh), 1e-7), ("fp64", {"prec": tnh.FP64}, 1e-9)):
         W = pm.to_device(mpo, qn=True)
         A = pm.product_state(W[0].inds[3], [0, 1] * (SWEEP_N // 2))
+        t0 = time.perf_counter()
         E, st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in SWEEP_SCHEDULE],
-                         [c for _, c in SWEEP_SCHEDULE], krylov_dim=16, tol=tol, prec=prec)
-        last = st[-1]
-        res[name] = {"energy": E, "last_sweep_s": last["seconds"], "maxlink": last["maxlink"],
-                     "matvecs_last_sweep": last["matvecs"], "truncerr": last["truncerr"],
-                     "sweep_s": [x["seconds"] for x in st]}
+                         [c for _, c in SWEEP_SCHEDULE], krylov_dim=16, tol=tol, **kw)
+        res[name] = sweep_record(E, st, time.perf_counter() - t0)
+        if name == "fp64":
+            final_mps = ctx.dmrg_mps(W[0].inds[3])
     e64 = res["fp64"]["energy"]
     res["dE_rel_mixed_vs_fp64"] = abs(res["bf16x6"]["energy"] - e64) / abs(e64)
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["last_sweep_s"] / res["bf16x6"]["last_sweep_s"]
     res["energy_per_bond_fp64"] = e64 / (SWEEP_N - 1)
     ref = sweep_reference()
     res["energy_oracle"] = ref["energy"]
     res["dE_rel_vs_oracle"] = {k: abs(res[k]["energy"] - ref["energy"]) / abs(ref["energy"]) for k in ("bf16x6", "fp64")}
-    res["oracle_last_sweep_s"] = {"value": ref["sweeps"][-1]["seconds"], "host": ref["host"],
-                                  "kind": "oracle, stored by tests/golden/make_heisenberg_n100.py"}
+    # the oracle's last sweep timed here, on this machine's cores: one sweep
+    # (maxdim 256, cutoff 1e-12, Lanczos <= 16) from the GPU run's final MPS
+    res["oracle_last_sweep"] = oracle_sweep_from(final_mps, SWEEP_N, SWEEP_SCHEDULE[-1])
+    res["oracle_last_sweep_stored"] = {"value": ref["sweeps"][-1]["seconds"], "host": ref["host"],
+                                       "kind": "oracle, stored by tests/golden/make_heisenberg_n100.py"}
     res["model"] = (f"U(1) Heisenberg chain N={SWEEP_N}, Neel start, maxdim "
                     f"{[m for m, _ in SWEEP_SCHEDULE]}, cutoff 1e-12, Lanczos <= 16 steps")
+    res["m1024"] = bench_heis_m1024(ctx, tnh)
     res["small"] = bench_small_sweeps(ctx, tnh)
-    res["cylinder_m2048"] = bench_cylinder_sweeps(ctx, tnh)
+    res["cylinder_6x4_m2048"] = bench_cylinder_sweeps(ctx, tnh)
+    res["cylinder_6x24_m2048"] = bench_large_sweeps(ctx, tnh, "cyl")
+    res["hubbard_n64_m4096"] = bench_large_sweeps(ctx, tnh, "hub")
     return res
 
 
-# J1-J2 cylinder (Ly=6 periodic, Lx=4 open, snake order, J2/J1=1/2, w=26) up
-# to m=2048: the bond dimension grows about fourfold per sweep from the Neel
-# state, so seven sweeps of maxdim 256, 512, 1024, 2048 x4 (cutoff 1e-10),
-# six Lanczos steps per bond in both precisions; the sweep time is the last
-# sweep's. Length 4 keeps the FP64 run within the bench's time.
-CYL_SCHEDULE = [(256, 1e-10), (512, 1e-10), (1024, 1e-10)] + [(2048, 1e-10)] * 4
+def oracle_sweep_from(mps, N, sweep):
+    """One oracle sweep (numpy FP64, this machine's cores) from a device MPS."""
+    from oracle import dmrg as D_, models as om
+    A = [oracle_tensor(T) for T in mps]
+    t0 = time.perf_counter()
+    E, _, st = D_.dmrg(om.heisenberg_mpo(N), A, [sweep], 16, 1e-9)
+    dt = time.perf_counter() - t0
+    return {"value": dt, "unit": "s", "energy": E, "cores": blas_threads(), "cpu": cpu_model(), "kind": "oracle",
+            "sample": f"one sweep, maxdim {sweep[0]}, cutoff {sweep[1]}, from the GPU run's final MPS"}
 
 
-def bench_cylinder_sweeps(ctx, tnh):
+def bench_heis_m1024(ctx, tnh):
+    """Config 3 at its stated maxdim: the N=100 chain with maxdim up to 1024
+    (cutoff 1e-12 decides the bond dimension the state needs)."""
     from paper_2007_14822_gb300 import models as pm
-    Lx, Ly = 4, 6
-    N = Lx * Ly
-    mpo = pm.spin_pairs(N, pm.cylinder_pairs(Lx, Ly, 1.0, 0.5))
+    mpo = pm.heisenberg(SWEEP_N)
+    sched = [(64, 1e-12), (256, 1e-12), (1024, 1e-12), (1024, 1e-12)]
     res = {}
-    for name, prec in (("bf16x6", tnh.BF16x6), ("fp64", tnh.FP64)):
+    for name, kw, tol in (("bf16x6", mixed_kw(tnh), 1e-7), ("fp64", {"prec": tnh.FP64}, 1e-9)):
         W = pm.to_device(mpo, qn=True)
-        A = pm.product_state(W[0].inds[3], [0, 1] * (N // 2))
+        A = pm.product_state(W[0].inds[3], [0, 1] * (SWEEP_N // 2))
         t0 = time.perf_counter()
-        E, st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in CYL_SCHEDULE], [c for _, c in CYL_SCHEDULE],
-                         krylov_dim=6, tol=0.0, prec=prec)
-        last = st[-1]
-        res[name] = {"energy": E, "last_sweep_s": last["seconds"], "maxlink": last["maxlink"],
-                     "matvecs_last_sweep": last["matvecs"], "truncerr": last["truncerr"],
-                     "run_s": time.perf_counter() - t0, "sweep_s": [x["seconds"] for x in st]}
+        E, st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in sched], [c for _, c in sched], krylov_dim=16,
+                         tol=tol, **kw)
+        res[name] = sweep_record(E, st, time.perf_counter() - t0)
     e64 = res["fp64"]["energy"]
     res["dE_rel_mixed_vs_fp64"] = abs(res["bf16x6"]["energy"] - e64) / abs(e64)
     res["speedup_mixed_vs_fp64"] = res["fp64"]["last_sweep_s"] / res["bf16x6"]["last_sweep_s"]
-    res["model"] = (f"U(1) J1-J2 cylinder Ly={Ly} x Lx={Lx} (N={N}, J2/J1=0.5, w={mpo.max_bond()}), Neel start, "
-                    f"maxdim {[m for m, _ in CYL_SCHEDULE]}, cutoff 1e-10, 6 Lanczos steps per bond")
+    res["model"] = (f"U(1) Heisenberg chain N={SWEEP_N}, Neel start, maxdim {[m for m, _ in sched]}, cutoff 1e-12, "
+                    "Lanczos <= 16 steps")
+    return res
+
+
+# The configurations at their stated size: the J1-J2 cylinder Ly=6 x Lx=24
+# (N=144, w=26) up to m=2048 and the Hubbard chain N=64 (U/t=4, half
+# filling, U(1)xU(1)) up to m=4096. The mixed-precision run goes the whole
+# schedule (the last sweep is timed); its checkpoint before the last sweep
+# is then resumed twice for LARGE_BONDS bond updates, in FP64 and in the
+# mixed precision, both with the FP64 energy at every bond: the per-bond
+# times and energies of the two precisions on the same state, and the FP64
+# sweep time estimated as per-bond time x bonds per sweep.
+LARGE = {
+    "cyl": dict(name="U(1) J1-J2 cylinder Ly=6 x Lx=24 (N=144, J2/J1=0.5, w=26, snake order), Neel start",
+                N=144, sched=[(256, 1e-10), (512, 1e-10), (1024, 1e-10), (2048, 1e-10), (2048, 1e-10),
+                              (2048, 1e-10)], krylov=6, states=[0, 1] * 72),
+    "hub": dict(name="U(1)xU(1) Hubbard chain N=64, U/t=4, half filling, alternating up/down start",
+                N=64, sched=[(256, 1e-12), (1024, 1e-12), (2048, 1e-12), (4096, 1e-12), (4096, 1e-12)],
+                krylov=6, states=[1, 2] * 32),
+}
+LARGE_BONDS = 24
+
+
+def bench_large_sweeps(ctx, tnh, kind):
+    import tempfile
+    from paper_2007_14822_gb300 import models as pm
+    cfg = LARGE[kind]
+    N = cfg["N"]
+    mpo = pm.spin_pairs(N, pm.cylinder_pairs(24, 6, 1.0, 0.5)) if kind == "cyl" else pm.hubbard(N, 1.0, 4.0)
+    W = pm.to_device(mpo, qn=True)
+    site = W[0].inds[3]
+    md, co = [m for m, _ in cfg["sched"]], [c for _, c in cfg["sched"]]
+    res = {"model": f"{cfg['name']}, maxdim {md}, cutoff {co[-1]}, {cfg['krylov']} Lanczos steps per bond"}
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "run.ckpt")
+        ctx.dmrg_checkpoint(path, 0, 0)      # a checkpoint at every sweep end but the last
+        t0 = time.perf_counter()
+        E, st = ctx.dmrg(W, pm.product_state(site, cfg["states"]), mpo.start, mpo.done, md, co,
+                         krylov_dim=cfg["krylov"], tol=0.0, **mixed_kw(tnh))
+        res["bf16x6"] = sweep_record(E, st, time.perf_counter() - t0)
+        bonds = 2 * (N - 1)
+        part = {}
+        for name, kw in (("bf16x6", dict(prec=tnh.BF16x6, env_prec=tnh.BF16x6)), ("fp64", dict(prec=tnh.FP64))):
+            ctx.dmrg_checkpoint(None, 0, LARGE_BONDS)
+            t0 = time.perf_counter()
+            Ep, _ = ctx.dmrg(W, None, mpo.start, mpo.done, md, co, krylov_dim=cfg["krylov"], tol=0.0, resume=path,
+                             **kw)
+            dt = time.perf_counter() - t0
+            part[name] = {"bonds": LARGE_BONDS, "s": dt, "s_per_bond": dt / LARGE_BONDS, "energy_at_stop": Ep,
+                          "sweep_s_estimate": dt / LARGE_BONDS * bonds}
+        ctx.dmrg_checkpoint(None, 0, 0)
+    part["dE_rel_at_stop"] = abs(part["bf16x6"]["energy_at_stop"] - part["fp64"]["energy_at_stop"]) / \
+        abs(part["fp64"]["energy_at_stop"])
+    part["speedup_per_bond"] = part["fp64"]["s_per_bond"] / part["bf16x6"]["s_per_bond"]
+    part["note"] = (f"both resumed from the checkpoint before the last sweep, {LARGE_BONDS} bond updates with "
+                    "the FP64 energy at every bond; the FP64 sweep time is per-bond time x bonds per sweep")
+    res["last_sweep_resumed"] = part
+    res["fp64_sweep_s_estimate"] = part["fp64"]["sweep_s_estimate"]
+    res["speedup_mixed_vs_fp64_estimate"] = part["fp64"]["sweep_s_estimate"] / res["bf16x6"]["last_sweep_s"]
     return res
 
 

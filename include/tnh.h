@@ -251,14 +251,20 @@ tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops);
  * would, although the plan applies them fused in one pass) and the S4 GEMM
  * (sum over w2, b with R). s1 + s23 + s4 is tnh_heff_flops. */
 tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, double* s4);
-/* The choices the plan's autotuner made for its two tcgen05 GEMMs (the
- * paper's Sec. 9.4 block-contraction strategies are fixed; this is GPU
- * tuning): choice[0] / choice[2] the N tile policy of S1 / S4 (0: 128-wide
- * tiles; 1: widths 128, 64 or 32 per output block, fewest operand bytes;
- * 2: the same, fewest MMA columns), choice[1] / choice[3] their K-split
- * factor (1, 2, 4, 8), choice[4] 1 when the plan timed the candidates itself
- * (0: reused from the context or the TNH_TUNE_CACHE file, or forced by
- * TNH_HEFF_SPLIT / TNH_HEFF_TILES). An FP64 plan reports 0 1 0 1 0. */
+/* The choices made for the plan (choice [7]):
+ * - choice[5]: the block-contraction strategy (Sec. 9.4: neither always
+ *   wins): 0 combines the blocks of a contracted sector into one GEMM task
+ *   (S1 one task per a-sector, S4 one per b'-sector), 1 contracts block pairs
+ *   (S1 one task per (L block, psi block) pair, S4 one per output block);
+ *   choice[6] = 1 when both were built and timed for this plan (0: the
+ *   context had timed this shape before, or TNH_HEFF_STRATEGY forced it);
+ * - for the two tcgen05 GEMMs (split-precision plans): choice[0] / choice[2]
+ *   the N tile policy of S1 / S4 (0: 128-wide tiles; 1: widths 128, 64 or 32
+ *   per output block, fewest operand bytes; 2: the same, fewest MMA
+ *   columns), choice[1] / choice[3] their K-split factor (1, 2, 4, 8),
+ *   choice[4] 1 when the plan timed the candidates itself (0: reused from
+ *   the context or the TNH_TUNE_CACHE file, or forced by TNH_HEFF_SPLIT /
+ *   TNH_HEFF_TILES). An FP64 plan reports 0 1 0 1 0 for these. */
 tnh_status tnh_heff_tuning(const tnh_heff* plan, int32_t* choice);
 /* Diagonal of the MPO part of H_eff (the projectors excluded), DEVICE
  * float64 [n] in the psi layout:

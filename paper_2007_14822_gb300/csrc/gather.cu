@@ -188,7 +188,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* w) {
 }
 
 template <class SrcT, bool kF64, int P>
-__global__ void __launch_bounds__(kW12Threads, 8) w12_kernel(const W12Cta* __restrict__ ctas,
+__global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restrict__ ctas,
                                                           const W12Cell* __restrict__ cells,
                                                           const W12In* __restrict__ ins,
                                                           const W12Out* __restrict__ outs,
@@ -235,20 +235,7 @@ __global__ void __launch_bounds__(kW12Threads, 8) w12_kernel(const W12Cta* __res
 #pragma unroll
         for (int u = 0; u < 4; ++u) v[u] = fma(cf, (AccT)x[u], v[u]);
     };
-    // two outputs at a time: the loads of both are in flight together
-    int o = 0;
-    for (; o + 1 < C.nout; o += 2) {
-        const W12Out O0 = outs[C.out0 + o], O1 = outs[C.out0 + o + 1];
-        AccT v0[4] = {AccT(0), AccT(0), AccT(0), AccT(0)}, v1[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
-        const int n0 = O0.t1 - O0.t0, n1 = O1.t1 - O1.t0;
-        for (int j = 0; j < max(n0, n1); ++j) {
-            if (j < n0) term(O0.t0 + j, v0);
-            if (j < n1) term(O1.t0 + j, v1);
-        }
-        store(O0, v0);
-        store(O1, v1);
-    }
-    if (o < C.nout) {
+    for (int o = 0; o < C.nout; ++o) {
         const W12Out O = outs[C.out0 + o];
         AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
         for (int j = O.t0; j < O.t1; ++j) term(j, v);

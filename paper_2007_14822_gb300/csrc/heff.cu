@@ -282,8 +282,8 @@ struct CellBuilder {
     }
 };
 
-GemmTask gemm_task(int64_t M, int64_t N, int64_t K, const HeffOperand& A, const HeffOperand& B, int t, bool tc,
-                   int tile0) {
+GemmTask gemm_task(int64_t M, int64_t N, int64_t K, const HeffOperand& A, int ta, const HeffOperand& B, int tb,
+                   bool tc, int tile0) {
     TNH_REQUIRE(M < (1 << 30) && N < (1 << 30) && K < (1 << 30), TNH_ERR_SHAPE, "heff_plan: block too large");
     GemmTask g{};
     g.M = (int)M;
@@ -293,16 +293,16 @@ GemmTask gemm_task(int64_t M, int64_t N, int64_t K, const HeffOperand& A, const 
         g.mt = (int)cdiv(M, kTcTileM);
         g.nt = (int)cdiv(N, kTcTileN);
         g.kt = (int)cdiv(K, kTcTileK);
-        g.a_base = A.gtc[t].base;
-        g.b_base = B.gtc[t].base;
+        g.a_base = A.gtc[ta].base;
+        g.b_base = B.gtc[tb].base;
     } else {
         g.mt = (int)cdiv(M, kF64TileM);
         g.nt = (int)cdiv(N, kF64TileN);
         g.kt = (int)cdiv(K, kF64TileK);
-        g.a_base = A.g64[t].base;
-        g.b_base = B.g64[t].base;
-        g.lda = A.g64[t].ld;
-        g.ldb = B.g64[t].ld;
+        g.a_base = A.g64[ta].base;
+        g.b_base = B.g64[tb].base;
+        g.lda = A.g64[ta].ld;
+        g.ldb = B.g64[tb].ld;
     }
     g.tile0 = tile0;
     return g;
@@ -558,9 +558,9 @@ void save_tune_line(const std::vector<int>& key, const std::array<int, 4>& c) {
 // (tile_width; 128-wide tiles against tiles fitted to the output blocks'
 // widths by two cost models), then the K-split factor (1, 2, 4, 8; only
 // splits that can fill the GPU better). Each candidate is timed with CUDA
-// events on the plan's own operands, one warm-up and three timed runs of the
-// GEMM and its reduction; a candidate replaces the incumbent only when it is
-// 3% faster. Choices are kept in the context by a coarse shape signature
+// events on the plan's own operands, one warm-up and the best of three timed
+// runs of the GEMM and its reduction; a candidate replaces the incumbent only
+// when it is 3% faster. Choices are kept in the context by a coarse shape signature
 // (tasks, tiles and mean K blocks per task, in half octaves), so the bonds
 // of a sweep at similar sizes reuse them, and in the TNH_TUNE_CACHE file
 // across processes. TNH_HEFF_SPLIT="s1,s4" and TNH_HEFF_TILES="p1,p4"
@@ -604,13 +604,19 @@ void tune_plan(HeffPlan& P) {
                 else launch_stage(G, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), ytmp.p, P.row_off.as<int64_t>(), s);
             };
             run();
-            CUDA_CHECK(cudaEventRecord(e0, s));
-            for (int r = 0; r < 3; ++r) run();
-            CUDA_CHECK(cudaEventRecord(e1, s));
-            CUDA_CHECK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-            return ms;
+            // the best of three separately timed runs (the first plans of a
+            // process run while clocks and caches settle)
+            float best = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                CUDA_CHECK(cudaEventRecord(e0, s));
+                run();
+                CUDA_CHECK(cudaEventRecord(e1, s));
+                CUDA_CHECK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+                best = std::min(best, ms);
+            }
+            return best;
         };
         HeffGemm* Gs[2] = {&P.g1, &P.g4};
         for (int g = 0; g < 2; ++g) {
@@ -699,8 +705,8 @@ struct PlanClock {
 };
 }  // namespace
 
-std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
-                                    const Layout& R, const Layout& X, tnh_precision prec) {
+std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
+                                             const Layout& R, const Layout& X, tnh_precision prec, int strategy) {
     TNH_REQUIRE(L.rank() == 3 && R.rank() == 3 && W1.rank() == 4 && W2.rank() == 4 && X.rank() == 4,
                 TNH_ERR_ARG, "heff_plan: ranks must be L 3, W 4, R 3, psi 4");
     TNH_REQUIRE(prec == TNH_FP64 || planes_of(prec) > 0, TNH_ERR_ARG, "heff_plan: bad precision");
@@ -751,14 +757,31 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     }
 
     clk.mark("flops");
-    // ---------------- S1: one task per a-sector A with L and psi blocks
+    // ---------------- S1: per a-sector A with L and psi blocks. Strategy 0
+    // (combine, then contract): one GEMM task per A, all L blocks of A along
+    // M and all psi blocks of A along N. Strategy 1 (block pairs): one task
+    // per (L block, psi block) pair, writing its sub-block of the same T1
+    // layout. Both read L and psi packed once.
     struct RowRef { int task; int64_t row; };
     std::map<std::pair<int, int>, std::vector<RowRef>> t1_rows;   // (w element, a'-sector) -> rows
     std::map<std::array<int, 4>, std::pair<int, int64_t>> t1_cols; // psi block sectors -> (task, first col)
     std::vector<int64_t> t1_base, t1_ld;
-    std::vector<int> t1_sector;   // a-sector of every S1 task
+    std::vector<int> t1_sector;   // a-sector of every T1 block row group
     JobBuilder bL, bX;
     int tf = 0, tt = 0;
+    auto add_s1 = [&](int64_t M, int64_t N, int64_t K, int ta, int tb, int64_t c_base, int64_t ldc) {
+        GemmTask g = gemm_task(M, N, K, P->oL, ta, P->oX, tb, false, tf);
+        g.c_base = c_base;
+        g.ldc = (int)ldc;
+        GemmTask h = gemm_task(M, N, K, P->oL, ta, P->oX, tb, true, tt);
+        h.c_base = c_base;
+        h.ldc = (int)ldc;
+        h.c_f32 = 1;
+        tf += g.mt * g.nt;
+        tt += h.mt * h.nt;
+        P->g1.f64.push_back(g);
+        P->g1.tc.push_back(h);
+    };
     for (int A = 0; A < ia.nsect; ++A) {
         std::vector<int> lb, xb;
         for (int b = 0; b < L.nblocks(); ++b)
@@ -774,46 +797,73 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         // multiple of 4, so that every T1 row segment the MPO step reads is
         // 16-byte aligned (the padding columns are zero)
         for (int b : xb) N += (int64_t)X.bdim(b, 1) * X.bdim(b, 2) * rup(X.bdim(b, 3), 4);
-        P->oL.add_task(M, K);
-        P->oX.add_task(N, K);
-        bL.task(M, K);
-        bX.task(N, K);
+        // operand tasks: one per A (strategy 0) or one per block (strategy 1)
+        std::vector<int> lt, xt;
+        if (strategy == 0) {
+            lt.assign(lb.size(), P->oL.count());
+            xt.assign(xb.size(), P->oX.count());
+            P->oL.add_task(M, K);
+            P->oX.add_task(N, K);
+            bL.task(M, K);
+            bX.task(N, K);
+        } else {
+            for (int b : lb) {
+                lt.push_back(P->oL.count());
+                P->oL.add_task((int64_t)L.bdim(b, 1) * L.bdim(b, 2), K);
+                bL.task((int64_t)L.bdim(b, 1) * L.bdim(b, 2), K);
+            }
+            for (int b : xb) {
+                const int64_t nbp = (int64_t)X.bdim(b, 1) * X.bdim(b, 2) * rup(X.bdim(b, 3), 4);
+                xt.push_back(P->oX.count());
+                P->oX.add_task(nbp, K);
+                bX.task(nbp, K);
+            }
+        }
         // rows (w, a'): operand A = L^T, element (r = a', c = a)
         int64_t row = 0;
-        for (int b : lb) {
+        std::vector<int64_t> lrow0;
+        for (size_t i = 0; i < lb.size(); ++i) {
+            const int b = lb[i];
             const int Sx = L.sect[(size_t)b * 3 + 1], Ap = L.sect[(size_t)b * 3 + 2];
             const int Dx = L.bdim(b, 1), Dap = L.bdim(b, 2);
+            lrow0.push_back(row);
+            const int64_t r0 = strategy == 0 ? row : 0;   // row inside the operand task
             for (int xl = 0; xl < Dx; ++xl) {
-                bL.rect(t, row, 0, Dap, K, {GatherTerm{1.0, L.off[b] + (int64_t)xl * Dap, 1, (int64_t)Dx * Dap, 1.0f}});
-                t1_rows[{(int)(iw.off[Sx] + xl), Ap}].push_back({t, row});
-                row += Dap;
+                bL.rect(lt[i], r0 + (int64_t)xl * Dap, 0, Dap, K,
+                        {GatherTerm{1.0, L.off[b] + (int64_t)xl * Dap, 1, (int64_t)Dx * Dap, 1.0f}});
+                t1_rows[{(int)(iw.off[Sx] + xl), Ap}].push_back({t, row + (int64_t)xl * Dap});
             }
+            row += (int64_t)Dx * Dap;
         }
         // columns (s1, s2, b): operand B = psi^T, element (r = (s1,s2,b), c = a);
         // group g = (s1, s2) of a block starts at column col + g * Dbp
         int64_t col = 0;
-        for (int b : xb) {
+        std::vector<int64_t> xcol0;
+        for (size_t i = 0; i < xb.size(); ++i) {
+            const int b = xb[i];
             const int64_t nb = X.belems(b) / K;
             const int Db = X.bdim(b, 3), Dbp = (int)rup(Db, 4), ng = X.bdim(b, 1) * X.bdim(b, 2);
+            xcol0.push_back(col);
+            const int64_t c0 = strategy == 0 ? col : 0;
             for (int g = 0; g < ng; ++g)
-                bX.rect(t, col + (int64_t)g * Dbp, 0, Db, K, {GatherTerm{1.0, X.off[b] + (int64_t)g * Db, 1, nb, 1.0f}});
+                bX.rect(xt[i], c0 + (int64_t)g * Dbp, 0, Db, K, {GatherTerm{1.0, X.off[b] + (int64_t)g * Db, 1, nb, 1.0f}});
             t1_cols[{A, X.sect[(size_t)b * 4 + 1], X.sect[(size_t)b * 4 + 2], X.sect[(size_t)b * 4 + 3]}] = {t, col};
             col += (int64_t)ng * Dbp;
         }
         t1_base.push_back(P->t1_elems);
         t1_ld.push_back(N);
         t1_sector.push_back(A);
-        GemmTask g = gemm_task(M, N, K, P->oL, P->oX, t, false, tf);
-        g.c_base = P->t1_elems;
-        g.ldc = (int)N;
-        GemmTask h = gemm_task(M, N, K, P->oL, P->oX, t, true, tt);
-        h.c_base = P->t1_elems;
-        h.ldc = (int)N;
-        h.c_f32 = 1;
-        tf += g.mt * g.nt;
-        tt += h.mt * h.nt;
-        P->g1.f64.push_back(g);
-        P->g1.tc.push_back(h);
+        if (strategy == 0) {
+            add_s1(M, N, K, lt[0], xt[0], P->t1_elems, N);
+        } else {
+            for (size_t i = 0; i < lb.size(); ++i)
+                for (size_t j = 0; j < xb.size(); ++j) {
+                    const int bl = lb[i], bx = xb[j];
+                    const int64_t Mi = (int64_t)L.bdim(bl, 1) * L.bdim(bl, 2);
+                    const int64_t Nj = (int64_t)X.bdim(bx, 1) * X.bdim(bx, 2) * rup(X.bdim(bx, 3), 4);
+                    add_s1(Mi, Nj, K, lt[i], xt[j], P->t1_elems + lrow0[i] * N + xcol0[j], N);
+                }
+        }
         P->t1_elems += rup(M * N, 4);
     }
     P->g1.tiles64 = tf;
@@ -899,7 +949,11 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     }
 
     clk.mark("diag");
-    // ---------------- S4: one task per b'-sector; fused S2+S3 fills operand A
+    // ---------------- S4: per b'-sector; the fused S2+S3 step fills operand A.
+    // Strategy 0: one GEMM task per b'-sector, the rows of all its psi blocks
+    // along M. Strategy 1: one task per psi block (its rows), all tasks of a
+    // b'-sector reading the same packed R. K is the same: every (w2 element,
+    // b-sector) piece of R for that b'.
     JobBuilder bR;
     CellBuilder bW;
     std::vector<int64_t> roff;
@@ -913,16 +967,26 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
         for (int b = 0; b < R.nblocks(); ++b)
             if (R.sect[(size_t)b * 3 + 2] == Bp) rb.push_back(b);
         if (yb.empty() || rb.empty()) continue;
-        const int t = (int)P->g4.f64.size();
+        const int tr = P->oR.count();
         const int64_t N = ibp.dim[Bp];
         int64_t M = 0, K = 0;
         for (int b : yb) M += X.belems(b) / N;
         // K pieces (w2 element, b-sector) of Db columns each start at a multiple
         // of 4, so the MPO step writes four columns with one store per plane
         for (int b : rb) K += rup(R.bdim(b, 0), 4) * R.bdim(b, 1);
-        P->oT.add_task(M, K);
         P->oR.add_task(N, K);
         bR.task(N, K);
+        // operand A tasks: one per b'-sector, or one per psi block
+        std::vector<int> at;
+        if (strategy == 0) {
+            at.assign(yb.size(), P->oT.count());
+            P->oT.add_task(M, K);
+        } else {
+            for (int b : yb) {
+                at.push_back(P->oT.count());
+                P->oT.add_task(X.belems(b) / N, K);
+            }
+        }
         // K pieces (w2 element z, b-sector B): operand B = R^T, element (r = b', c = b)
         struct KPiece { int z, B; int64_t col; int Db; };
         std::vector<KPiece> kp;
@@ -931,18 +995,20 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
             const int B = R.sect[(size_t)b * 3], Sz = R.sect[(size_t)b * 3 + 1];
             const int Db = R.bdim(b, 0), Dz = R.bdim(b, 1);
             for (int zl = 0; zl < Dz; ++zl) {
-                bR.rect(t, 0, col, N, Db, {GatherTerm{1.0, R.off[b] + (int64_t)zl * N, 1, (int64_t)Dz * N, 1.0f}});
+                bR.rect(tr, 0, col, N, Db, {GatherTerm{1.0, R.off[b] + (int64_t)zl * N, 1, (int64_t)Dz * N, 1.0f}});
                 kp.push_back({(int)(iz.off[Sz] + zl), B, col, Db});
                 col += rup(Db, 4);
             }
         }
         // row pieces (s1', s2', a'): every row of every psi block of this b'-sector
         int64_t row = 0;
-        const int64_t roff0 = (int64_t)roff.size();
-        for (int b : yb) {
+        for (size_t yi = 0; yi < yb.size(); ++yi) {
+            const int b = yb[yi];
             covered[b] = 1;
             const int Ap = X.sect[(size_t)b * 4], S1p = X.sect[(size_t)b * 4 + 1], S2p = X.sect[(size_t)b * 4 + 2];
             const int Dap = X.bdim(b, 0), d1 = X.bdim(b, 1), d2 = X.bdim(b, 2);
+            const int64_t roff0 = (int64_t)roff.size();
+            const int64_t brow0 = row;   // first row of this block in the b'-sector's rows
             for (int u1 = 0; u1 < d1; ++u1)
                 for (int u2 = 0; u2 < d2; ++u2) {
                     const int s1p = (int)(is1.off[S1p] + u1), s2p = (int)(is2.off[S2p] + u2);
@@ -967,19 +1033,32 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
                                 tm.push_back({t1_base[ref.task] + ref.row * ld + c0, ld, e.v});
                             }
                         }
-                        bW.add(Ap, k.B, Dap, k.Db, t, row, k.col, std::move(tm));
+                        bW.add(Ap, k.B, Dap, k.Db, at[yi], strategy == 0 ? row : row - brow0, k.col, std::move(tm));
                     }
                     row += Dap;
                 }
+            if (strategy == 1) {
+                const int64_t Mb = X.belems(b) / N;
+                GemmTask g = gemm_task(Mb, N, K, P->oT, at[yi], P->oR, tr, false, tf);
+                GemmTask h = gemm_task(Mb, N, K, P->oT, at[yi], P->oR, tr, true, tt);
+                g.use_roff = h.use_roff = 1;
+                g.roff = h.roff = roff0;
+                tf += g.mt * g.nt;
+                tt += h.mt * h.nt;
+                P->g4.f64.push_back(g);
+                P->g4.tc.push_back(h);
+            }
         }
-        GemmTask g = gemm_task(M, N, K, P->oT, P->oR, t, false, tf);
-        GemmTask h = gemm_task(M, N, K, P->oT, P->oR, t, true, tt);
-        g.use_roff = h.use_roff = 1;
-        g.roff = h.roff = roff0;
-        tf += g.mt * g.nt;
-        tt += h.mt * h.nt;
-        P->g4.f64.push_back(g);
-        P->g4.tc.push_back(h);
+        if (strategy == 0) {
+            GemmTask g = gemm_task(M, N, K, P->oT, at[0], P->oR, tr, false, tf);
+            GemmTask h = gemm_task(M, N, K, P->oT, at[0], P->oR, tr, true, tt);
+            g.use_roff = h.use_roff = 1;
+            g.roff = h.roff = (int64_t)roff.size() - M;
+            tf += g.mt * g.nt;
+            tt += h.mt * h.nt;
+            P->g4.f64.push_back(g);
+            P->g4.tc.push_back(h);
+        }
     }
     P->g4.tiles64 = tf;
     P->g4.tilestc = tt;
@@ -1041,6 +1120,78 @@ std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1,
     // the host tables and the caller's L, R must stay alive until these ran
     CUDA_CHECK(cudaStreamSynchronize(s));
     return P;
+}
+
+namespace {
+
+// Device time of one application of a plan (the best of three, after one
+// untimed), in its own precision, on zero vectors.
+float time_plan(HeffPlan& P) {
+    cudaStream_t s = P.stream;
+    DevBuf x((size_t)std::max<int64_t>(P.n, 1) * sizeof(double)), y((size_t)std::max<int64_t>(P.n, 1) * sizeof(double));
+    CUDA_CHECK(cudaMemsetAsync(x.p, 0, x.bytes, s));
+    cudaEvent_t e0, e1;
+    CUDA_CHECK(cudaEventCreate(&e0));
+    CUDA_CHECK(cudaEventCreate(&e1));
+    heff_apply(P, P.prec, x.as<double>(), y.as<double>());
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        CUDA_CHECK(cudaEventRecord(e0, s));
+        heff_apply(P, P.prec, x.as<double>(), y.as<double>());
+        CUDA_CHECK(cudaEventRecord(e1, s));
+        CUDA_CHECK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    check_device_flag(P.ctx);
+    return best;
+}
+
+}  // namespace
+
+// The block-contraction strategy is chosen per shape (the paper notes that
+// neither combining blocks before contracting nor contracting block pairs
+// always wins, Sec. 9.4): both plans are built and timed once for a shape
+// signature (precision, psi size, block counts and mean sector dimension of
+// psi, in half octaves), the faster one (block pairs only when 3% faster)
+// is kept in the context for later plans of the same signature.
+// TNH_HEFF_STRATEGY=0 / 1 forces combine-then-contract / block pairs.
+std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
+                                    const Layout& R, const Layout& X, tnh_precision prec) {
+    if (const char* f = std::getenv("TNH_HEFF_STRATEGY")) {
+        const int st = std::atoi(f) == 1 ? 1 : 0;
+        auto P = make_heff_strategy(ctx, L, W1, W2, R, X, prec, st);
+        P->strategy = st;
+        return P;
+    }
+    auto bucket = [](double x) { return (int)std::lround(2.0 * std::log2(std::max(1.0, x))); };
+    double dsum = 0.0;
+    for (int b = 0; b < X.nblocks(); ++b) dsum += X.bdim(b, 0) + X.bdim(b, 3);
+    std::vector<int> key{-1, (int)prec, bucket((double)X.size), bucket((double)X.nblocks()), bucket((double)L.nblocks()),
+                         bucket((double)R.nblocks()), bucket(dsum / std::max(1, 2 * X.nblocks()))};
+    auto it = ctx->heff_strategy.find(key);
+    if (it != ctx->heff_strategy.end()) {
+        auto P = make_heff_strategy(ctx, L, W1, W2, R, X, prec, it->second);
+        P->strategy = it->second;
+        return P;
+    }
+    auto P0 = make_heff_strategy(ctx, L, W1, W2, R, X, prec, 0);
+    auto P1 = make_heff_strategy(ctx, L, W1, W2, R, X, prec, 1);
+    const float t0 = time_plan(*P0), t1 = time_plan(*P1);   // per product
+    const int st = t1 < 0.97f * t0 ? 1 : 0;
+    ctx->heff_strategy[key] = st;
+    auto& P = st == 1 ? P1 : P0;
+    P->strategy = st;
+    P->strategy_measured = true;
+    P->strategy_ms[0] = t0;
+    P->strategy_ms[1] = t1;
+    if (std::getenv("TNH_DEBUG"))
+        std::fprintf(stderr, "heff_plan: strategy %s (combine %.3f ms, block pairs %.3f ms per product)\n",
+                     st == 1 ? "block pairs" : "combine", t0, t1);
+    return std::move(P);
 }
 
 namespace {
@@ -1313,6 +1464,8 @@ tnh_status tnh_heff_tuning(const tnh_heff* plan, int32_t* choice) {
         TNH_REQUIRE(P && choice, TNH_ERR_ARG, "tnh_heff_tuning: NULL argument");
         for (int k = 0; k < 4; ++k) choice[k] = P->tune[k];
         choice[4] = P->tune_measured ? 1 : 0;
+        choice[5] = P->strategy;
+        choice[6] = P->strategy_measured ? 1 : 0;
     });
 }
 

@@ -15,6 +15,7 @@ struct HeffOperand {
     int64_t elems64 = 0, tiles = 0;
     DevBuf d_g64, d_gtc;
     void add_task(int64_t rows, int64_t K);
+    int count() const { return (int)gtc.size(); }
 };
 // One GEMM of the plan. The tcgen05 tasks are launched as given in tc: the
 // block tasks of tc_base, or, with split > 1, every block task cut into up
@@ -69,6 +70,9 @@ struct HeffPlan {
     bool zero_y = false;    // some output rows are written by no S4 task
     std::array<int, 4> tune{0, 1, 0, 1};   // tile policy / K split of S1, then of S4
     bool tune_measured = false;            // chosen by timing in this plan (not cached or forced)
+    int strategy = 0;                      // 0: combine, then contract; 1: block pairs (make_heff)
+    bool strategy_measured = false;        // both strategies were timed for this plan
+    float strategy_ms[2] = {0.f, 0.f};     // their times per product when measured
     // one CUDA graph per format (float64, split): the four launches of an
     // application, replayed with the x and y arguments patched in
     struct Graph {
@@ -99,6 +103,13 @@ struct HeffPlan {
 };
 
 // L, W1, W2, R are read while the plan is made and not referenced after.
+// strategy 0: combine the blocks of a contracted sector into one GEMM task
+// (S1 per a-sector, S4 per b'-sector); 1: one task per block pair (S1) or
+// per output block (S4).
+std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
+                                             const Layout& R, const Layout& psi, tnh_precision prec, int strategy);
+// The same with the strategy chosen per shape by timing both (cached in the
+// context), or forced by TNH_HEFF_STRATEGY.
 std::unique_ptr<HeffPlan> make_heff(Ctx* ctx, const Layout& L, const Layout& W1, const Layout& W2,
                                     const Layout& R, const Layout& psi, tnh_precision prec);
 // H_eff (of the plan's MPO terms) plus the projectors, if any.

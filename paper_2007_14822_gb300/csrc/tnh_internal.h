@@ -175,6 +175,8 @@ struct Ctx {
     // then of S4) by shape signature; loaded from TNH_TUNE_CACHE once
     std::map<std::vector<int>, std::array<int, 4>> heff_tune;
     bool tune_loaded = false;
+    // H_eff block-contraction strategy (0 combine, 1 block pairs) by shape
+    std::map<std::vector<int>, int> heff_strategy;
     // the MPS left by the last DMRG run
     std::vector<OwnedTensor> mps;
     // checkpointing of DMRG runs (tnh_dmrg_checkpoint) and where the last

@@ -523,11 +523,12 @@ class Heff:
 
     @property
     def tuning(self):
-        """The autotuner's GEMM choices: {'tiles_s1', 'split_s1', 'tiles_s4',
-        'split_s4', 'measured'} (see tnh_heff_tuning)."""
-        c = (C.c_int32 * 5)()
+        """The plan's choices: {'tiles_s1', 'split_s1', 'tiles_s4', 'split_s4',
+        'measured', 'strategy', 'strategy_measured'} (see tnh_heff_tuning)."""
+        c = (C.c_int32 * 7)()
         self.ctx.check(self.ctx._lib.tnh_heff_tuning(self.h, c))
-        return {"tiles_s1": c[0], "split_s1": c[1], "tiles_s4": c[2], "split_s4": c[3], "measured": bool(c[4])}
+        return {"tiles_s1": c[0], "split_s1": c[1], "tiles_s4": c[2], "split_s4": c[3], "measured": bool(c[4]),
+                "strategy": c[5], "strategy_measured": bool(c[6])}
 
     def diag(self, out):
         """Diagonal of the MPO part of H_eff into ``out`` (CUDA float64 [n])."""

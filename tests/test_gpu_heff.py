@@ -208,6 +208,7 @@ def test_heff_tuning_cache_file(ctx, tmp_path, monkeypatch):
     from paper_2007_14822_gb300 import tnh
     path = tmp_path / "tune.txt"
     monkeypatch.setenv("TNH_TUNE_CACHE", str(path))
+    monkeypatch.setenv("TNH_HEFF_STRATEGY", "0")
     monkeypatch.delenv("TNH_HEFF_SPLIT", raising=False)
     monkeypatch.delenv("TNH_HEFF_TILES", raising=False)
     d = H.heff_inputs(96, None, 11, nsect=9, maxd=24)
@@ -490,6 +491,39 @@ def test_heff_qn_workloads_full_size(ctx, which):
         yt.data = y
         err, rep = H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
         print(name, p, "norm-wise", err, "worst block", rep["block"], "worst element", rep["elem"])
+
+
+@pytest.mark.parametrize("strategy", ["0", "1"])
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("m,nsect,maxd", [(64, 9, 16), (300, 15, 60), (40, 1, 40)])
+def test_heff_block_strategies_match_oracle(ctx, strategy, p, m, nsect, maxd, monkeypatch):
+    # combine-then-contract and block pairs (Sec. 9.4), each forced, against
+    # the oracle: norm-wise, per block and per element
+    monkeypatch.setenv("TNH_HEFF_STRATEGY", strategy)
+    err, plan = _heff_case(ctx, m, nsect, p, maxd=maxd)
+    t = plan.tuning
+    assert t["strategy"] == int(strategy) and not t["strategy_measured"]
+
+
+@pytest.mark.parametrize("model,j", [("j1j2", 3), ("hubbard", 2)])
+def test_heff_block_pairs_distinct_mpo_tensors(ctx, model, j, monkeypatch):
+    monkeypatch.setenv("TNH_HEFF_STRATEGY", "1")
+    test_heff_distinct_mpo_tensors(ctx, model, j, "bf16x6")
+    test_heff_distinct_mpo_tensors(ctx, model, j, "fp64")
+
+
+def test_heff_strategy_timed_once_per_shape(ctx, monkeypatch):
+    # without TNH_HEFF_STRATEGY both strategies are timed for a new shape and
+    # the choice is reused for the next plan of that shape
+    from paper_2007_14822_gb300 import tnh
+    monkeypatch.delenv("TNH_HEFF_STRATEGY", raising=False)
+    c = tnh.Context(0)
+    d = H.heff_inputs(80, None, 4, nsect=9, maxd=20)
+    p1 = c.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec("bf16x6"))
+    p2 = c.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec("bf16x6"))
+    t1, t2 = p1.tuning, p2.tuning
+    assert t1["strategy_measured"] and not t2["strategy_measured"] and t1["strategy"] == t2["strategy"]
+    c.close()
 
 
 # ------------------------------------------------- tridiagonal eigensolve
