@@ -479,6 +479,35 @@ def bench_large_sweeps(ctx, tnh, kind):
     return res
 
 
+# J1-J2 cylinder (Ly=6 periodic, Lx=4 open, snake order, J2/J1=1/2, w=26) up
+# to m=2048: the bond dimension grows about fourfold per sweep from the Neel
+# state, so seven sweeps of maxdim 256, 512, 1024, 2048 x4 (cutoff 1e-10),
+# six Lanczos steps per bond in both precisions; the sweep time is the last
+# sweep's. Length 4 keeps the FP64 run within the bench's time.
+CYL_SCHEDULE = [(256, 1e-10), (512, 1e-10), (1024, 1e-10)] + [(2048, 1e-10)] * 4
+
+
+def bench_cylinder_sweeps(ctx, tnh):
+    from paper_2007_14822_gb300 import models as pm
+    Lx, Ly = 4, 6
+    N = Lx * Ly
+    mpo = pm.spin_pairs(N, pm.cylinder_pairs(Lx, Ly, 1.0, 0.5))
+    res = {}
+    for name, kw in (("bf16x6", mixed_kw(tnh)), ("fp64", {"prec": tnh.FP64})):
+        W = pm.to_device(mpo, qn=True)
+        A = pm.product_state(W[0].inds[3], [0, 1] * (N // 2))
+        t0 = time.perf_counter()
+        E, st = ctx.dmrg(W, A, mpo.start, mpo.done, [m for m, _ in CYL_SCHEDULE], [c for _, c in CYL_SCHEDULE],
+                         krylov_dim=6, tol=0.0, **kw)
+        res[name] = sweep_record(E, st, time.perf_counter() - t0)
+    e64 = res["fp64"]["energy"]
+    res["dE_rel_mixed_vs_fp64"] = abs(res["bf16x6"]["energy"] - e64) / abs(e64)
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["last_sweep_s"] / res["bf16x6"]["last_sweep_s"]
+    res["model"] = (f"U(1) J1-J2 cylinder Ly={Ly} x Lx={Lx} (N={N}, J2/J1=0.5, w={mpo.max_bond()}), Neel start, "
+                    f"maxdim {[m for m, _ in CYL_SCHEDULE]}, cutoff 1e-10, 6 Lanczos steps per bond")
+    return res
+
+
 def bench_small_sweeps(ctx, tnh):
     """Dense Heisenberg N=20, m=32, cutoff 1e-10, 5 sweeps from a seeded random
     product state: the whole run on the GPU (FP64) and by the oracle."""

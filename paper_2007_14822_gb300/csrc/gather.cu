@@ -1,8 +1,8 @@
 // Tile gather: build GEMM operand tiles from weighted sums of strided
 // sub-blocks.
 //
-// One CTA owns one 128-row x 64-column tile of a GEMM operand (K-major).
-// The tile is assembled in shared memory from its segments; a segment is a
+// Two CTAs own one 128-row x 64-column tile of a GEMM operand (K-major),
+// 64 rows each. The tile is assembled in shared memory from its segments; a segment is a
 // rectangle of the tile whose every element is
 //     sum_j coef_j * src[off_j + r * rs_j + c * cs_j]
 // (r, c relative to the segment). Elements covered by no segment are zero,
@@ -38,7 +38,7 @@ namespace tnh {
 namespace {
 
 constexpr int kPitch = kGatherCols + 1;   // padded smem row (doubles)
-constexpr int kSmemBytes = kGatherRows * kPitch * 8;
+constexpr int kSmemBytes = (kGatherRows / 2) * kPitch * 8;
 
 // x = hi + mid + lo, each part rounded to nearest bfloat16; float32
 // arithmetic (exact residuals), the float64 units of this GPU being scarce
@@ -65,6 +65,10 @@ __device__ __forceinline__ typename Acc<kF64>::T coef_of(const GatherTerm& g) {
     if constexpr (kF64) return g.coef; else return g.coef32;
 }
 
+// One CTA builds one half (64 rows) of a 128 x 64 tile: CTA 2t + h owns
+// rows [64 h, 64 h + 64) of tile t.
+constexpr int kHalfRows = kGatherRows / 2;
+
 template <class SrcT, bool kF64, int P>
 __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restrict__ tiles,
                                                      const GatherSeg* __restrict__ segs,
@@ -73,13 +77,18 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
                                                      const SrcT* __restrict__ src, void* __restrict__ dst) {
     using AccT = typename Acc<kF64>::T;
     extern __shared__ double tile_raw[];
-    AccT* tile_s = reinterpret_cast<AccT*>(tile_raw);
-    const GatherTile T = tiles[blockIdx.x];
-    for (int e = threadIdx.x; e < kGatherRows * kPitch; e += blockDim.x) tile_s[e] = AccT(0);
+    AccT* tile_s = reinterpret_cast<AccT*>(tile_raw);   // [kHalfRows][kPitch]
+    const GatherTile T = tiles[blockIdx.x >> 1];
+    const int h0 = (blockIdx.x & 1) * kHalfRows;         // first tile row of this CTA
+    for (int e = threadIdx.x; e < kHalfRows * kPitch; e += blockDim.x) tile_s[e] = AccT(0);
     __syncthreads();
     for (int si = T.seg0; si < T.seg1; ++si) {
         const GatherSeg S = segs[si];
-        const int n = S.nr * S.nc;
+        // rows of the segment inside this half
+        const int rb = max(0, h0 - S.r0), re = min(S.nr, h0 + kHalfRows - S.r0);
+        if (rb >= re) continue;
+        const int nr = re - rb;
+        const int n = nr * S.nc;
         const bool cfast = terms[S.t0].cs == 1;
         if (S.t1 - S.t0 == 1) {
             // one term (a copy): eight independent loads in flight per thread
@@ -94,9 +103,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
                     int r = 0, c = 0;
                     if (e < n) {
                         if (cfast) { r = e / S.nc; c = e - r * S.nc; }
-                        else { c = e / S.nr; r = e - c * S.nr; }
+                        else { c = e / nr; r = e - c * nr; }
                     }
-                    pos[u] = e < n ? (S.r0 + r) * kPitch + S.c0 + c : -1;
+                    r += rb;
+                    pos[u] = e < n ? (S.r0 + r - h0) * kPitch + S.c0 + c : -1;
                     v[u] = e < n ? cf * (AccT)src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs] : AccT(0);
                 }
 #pragma unroll
@@ -108,21 +118,22 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
             int r, c;
             if (cfast) { r = e / S.nc; c = e - r * S.nc; }
-            else { c = e / S.nr; r = e - c * S.nr; }
+            else { c = e / nr; r = e - c * nr; }
+            r += rb;
             AccT v = AccT(0);
             for (int j = S.t0; j < S.t1; ++j) {
                 const GatherTerm& g = terms[j];
                 v += coef_of<kF64>(g) * (AccT)src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs];
             }
-            tile_s[(S.r0 + r) * kPitch + S.c0 + c] = v;
+            tile_s[(S.r0 + r - h0) * kPitch + S.c0 + c] = v;
         }
     }
     __syncthreads();
     const OpGeom G = geom[T.task];
     if constexpr (kF64) {
-        double* d = static_cast<double*>(dst) + G.base + (int64_t)T.mi * kGatherRows * G.ld +
+        double* d = static_cast<double*>(dst) + G.base + ((int64_t)T.mi * kGatherRows + h0) * G.ld +
                     (int64_t)T.ki * kGatherCols;
-        for (int e = threadIdx.x; e < kGatherRows * kGatherCols; e += blockDim.x) {
+        for (int e = threadIdx.x; e < kHalfRows * kGatherCols; e += blockDim.x) {
             const int r = e / kGatherCols, c = e - r * kGatherCols;
             d[(int64_t)r * G.ld + c] = tile_s[r * kPitch + c];
         }
@@ -131,22 +142,23 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
         // 16-byte chunk j of row r holds k-group j ^ (r & 7) (128-byte swizzle)
         uint16_t* d = static_cast<uint16_t*>(dst) +
                       (G.base + (int64_t)T.mi * G.ld + T.ki) * (int64_t)(P * kTcTileElems);
-        for (int ci = threadIdx.x; ci < kGatherRows * 8; ci += blockDim.x) {
-            const int r = ci >> 3, j = ci & 7;
+        for (int ci = threadIdx.x; ci < kHalfRows * 8; ci += blockDim.x) {
+            const int rl = ci >> 3, j = ci & 7, r = h0 + rl;
             const int kg = j ^ (r & 7);
-            const float* v = tile_s + r * kPitch + kg * 8;
+            const float* v = tile_s + rl * kPitch + kg * 8;
             uint32_t w[3][4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
+            for (int hh = 0; hh < 4; ++hh) {
                 uint16_t a[3], b[3];
-                split_bf16<P>(v[2 * h], a);
-                split_bf16<P>(v[2 * h + 1], b);
+                split_bf16<P>(v[2 * hh], a);
+                split_bf16<P>(v[2 * hh + 1], b);
 #pragma unroll
-                for (int p = 0; p < P; ++p) w[p][h] = (uint32_t)a[p] | ((uint32_t)b[p] << 16);
+                for (int p = 0; p < P; ++p) w[p][hh] = (uint32_t)a[p] | ((uint32_t)b[p] << 16);
             }
 #pragma unroll
             for (int p = 0; p < P; ++p)
-                *reinterpret_cast<uint4*>(d + p * kTcTileElems + ci * 8) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+                *reinterpret_cast<uint4*>(d + p * kTcTileElems + (r * 8 + j) * 8) =
+                    make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
         }
     }
 }
@@ -228,9 +240,8 @@ __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restri
     // padded segment
     auto term = [&](int j, AccT* v) {
         const W12Term t = terms[j];
-        const W12In in = ins[t.in];
         SrcT x[4];
-        load4(src + in.base + (int64_t)r * in.ld + c, x);
+        load4(src + t.base + (int64_t)r * t.ld + c, x);
         const AccT cf = kF64 ? (AccT)t.coef : (AccT)t.coef32;
 #pragma unroll
         for (int u = 0; u < 4; ++u) v[u] = fma(cf, (AccT)x[u], v[u]);
@@ -268,7 +279,7 @@ void launch_one(const GatherJob& J, const OpGeom* geom, const SrcT* src, void* d
                                         kSmemBytes));
         configured = true;
     }
-    gather_kernel<SrcT, kF64, P><<<J.ntiles, 256, kSmemBytes, s>>>(
+    gather_kernel<SrcT, kF64, P><<<2 * J.ntiles, 256, kSmemBytes, s>>>(
         J.d_tiles.as<GatherTile>(), J.d_segs.as<GatherSeg>(), J.d_terms.as<GatherTerm>(), geom, src, dst);
 }
 

@@ -45,7 +45,7 @@ constexpr int kW12Threads = 128;
 struct W12Cell { int in0, nin, out0, nout, Da, Db; };
 struct W12In { int64_t base; int64_t ld; };
 struct W12Out { int task, row0, col0, t0, t1; };
-struct W12Term { double coef; float coef32; int in; };
+struct W12Term { int64_t base; double coef; float coef32; int ld; };   // input T1 sub-block (base, row pitch)
 struct W12Cta { int cell, q0; };
 struct W12Job {
     std::vector<W12Cell> cells;

@@ -264,7 +264,11 @@ struct CellBuilder {
                 TNH_REQUIRE(out.row0 < INT32_MAX && out.col0 < INT32_MAX && (out.col0 & 3) == 0, TNH_ERR_SHAPE,
                             "heff_plan: MPO step output out of range");
                 W12Out o{out.task, (int)out.row0, (int)out.col0, (int)J.terms.size(), 0};
-                for (auto& a : acc) J.terms.push_back({a.second, (float)a.second, a.first});
+                for (auto& a : acc) {
+                    const W12In& in = J.ins[(size_t)a.first];
+                    TNH_REQUIRE(in.ld < INT32_MAX, TNH_ERR_SHAPE, "heff_plan: T1 row pitch too large");
+                    J.terms.push_back({in.base, a.second, (float)a.second, (int)in.ld});
+                }
                 o.t1 = (int)J.terms.size();
                 J.outs.push_back(o);
             }
