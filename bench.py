@@ -468,11 +468,12 @@ def bench_large_sweeps(ctx, tnh, kind):
             part[name] = {"bonds": LARGE_BONDS, "s": dt, "s_per_bond": dt / LARGE_BONDS, "energy_at_stop": Ep,
                           "sweep_s_estimate": dt / LARGE_BONDS * bonds}
         ctx.dmrg_checkpoint(None, 0, 0)
-    part["dE_rel_at_stop"] = abs(part["bf16x6"]["energy_at_stop"] - part["fp64"]["energy_at_stop"]) / \
-        abs(part["fp64"]["energy_at_stop"])
     part["speedup_per_bond"] = part["fp64"]["s_per_bond"] / part["bf16x6"]["s_per_bond"]
     part["note"] = (f"both resumed from the checkpoint before the last sweep, {LARGE_BONDS} bond updates with "
-                    "the FP64 energy at every bond; the FP64 sweep time is per-bond time x bonds per sweep")
+                    "the FP64 energy at every bond; the FP64 sweep time is per-bond time x bonds per sweep. The "
+                    "energies at the stop are those of part of a sweep with six Lanczos steps per bond, not "
+                    "converged states, so they are no precision comparison (the full runs of the 6x4 cylinder "
+                    "and of the N=100 chain are)")
     res["last_sweep_resumed"] = part
     res["fp64_sweep_s_estimate"] = part["fp64"]["sweep_s_estimate"]
     res["speedup_mixed_vs_fp64_estimate"] = part["fp64"]["sweep_s_estimate"] / res["bf16x6"]["last_sweep_s"]

@@ -539,8 +539,9 @@ void run_dmrg(Ctx* c, int N, const Problem& pr, const tnh_tensor* mps, const tnh
                     if (dbg) {
                         int kept = 0;
                         for (int d : sh.dims) kept += d;
-                        std::fprintf(stderr, "dmrg: sweep %d bond %d dir %+d E %.14f kept %d in %zu sectors truncerr %.3e\n",
-                                     sw, j, dir, E, kept, sh.dims.size(), sh.truncerr);
+                        std::fprintf(stderr, "dmrg: sweep %d bond %d dir %+d E %.14f kept %d in %zu sectors truncerr %.3e "
+                                     "(so far: theta %.3f plan %.3f eig %.3f svd %.3f s)\n",
+                                     sw, j, dir, E, kept, sh.dims.size(), sh.truncerr, ph[0], ph[1], ph[2], ph[3]);
                     }
                     Index link;
                     link.nsect = (int)sh.dims.size();

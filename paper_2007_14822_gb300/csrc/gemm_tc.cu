@@ -382,44 +382,22 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
     gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err, row_off);
 }
 
-// K-split reduction: element e of the concatenated outputs belongs to the
-// reduction R with R.e0 <= e < R.e0 + M*N. Block b owns elements
-// [1024 b, 1024 b + 1024), four per thread with a stride of 256; the block
-// looks up the reduction of its first element once, every thread steps on
-// from there (its elements ascend).
-constexpr int kRedPerBlock = 1024;
-
+// K-split reduction: block b sums rows [m0, m1) of one reduction R over its
+// S float32 (or float64) partial slabs [S][M][N], in slab order, and writes
+// them to the output rows (scattered by row_off, or at c_base + m ldc).
 template <class PartT>
-__global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds, int nred, int64_t total,
+__global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds,
+                                                     const RedBlock* __restrict__ blocks,
                                                      const PartT* __restrict__ part, void* __restrict__ out,
                                                      const int64_t* __restrict__ row_off) {
-    __shared__ int lo_s;
-    const int64_t base = (int64_t)blockIdx.x * kRedPerBlock;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = nred - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (reds[mid].e0 <= base) lo = mid; else hi = mid - 1;
-        }
-        lo_s = lo;
-    }
-    __syncthreads();
-    int lo = lo_s;
-    SplitRed R = reds[lo];   // a register copy, reloaded when the thread steps to the next reduction
-    int64_t next = lo + 1 < nred ? reds[lo + 1].e0 : INT64_MAX;
-#pragma unroll
-    for (int k = 0; k < kRedPerBlock / 256; ++k) {
-        const int64_t e = base + threadIdx.x + k * 256;
-        if (e >= total) break;
-        if (e >= next) {
-            while (lo + 1 < nred && reds[lo + 1].e0 <= e) ++lo;
-            R = reds[lo];
-            next = lo + 1 < nred ? reds[lo + 1].e0 : INT64_MAX;
-        }
-        const int loc = (int)(e - R.e0);   // < M * N < 2^31
-        const int m = loc / R.N, n = loc - m * R.N;
-        const int64_t mn = (int64_t)R.M * R.N;
-        const PartT* p = part + R.part + loc;
+    const RedBlock b = blocks[blockIdx.x];
+    const SplitRed R = reds[b.red];
+    const int64_t mn = (int64_t)R.M * R.N;
+    const int nel = (b.m1 - b.m0) * R.N;
+    const PartT* p0 = part + R.part + (int64_t)b.m0 * R.N;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+        const int ml = e / R.N, n = e - ml * R.N, m = b.m0 + ml;
+        const PartT* p = p0 + e;
         double acc = 0.0;
         for (int j = 0; j < R.S; ++j) acc += (double)__ldg(p + j * mn);
         if (R.use_roff) static_cast<double*>(out)[__ldg(row_off + R.roff + m) + n] = acc;
@@ -445,22 +423,27 @@ void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const 
 
 namespace tnh {
 
-void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const float* part, void* out,
-                          const int64_t* row_off, int num_sms, cudaStream_t s) {
-    if (total == 0 || nred == 0) return;
-    KScope ks("splitk_reduce", s);
-    const int64_t grid = (total + kRedPerBlock - 1) / kRedPerBlock;
-    TNH_REQUIRE(grid < INT32_MAX, TNH_ERR_SHAPE, "splitk_reduce: %lld elements", (long long)total);
-    splitk_reduce<float><<<(unsigned)grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
+std::vector<RedBlock> reduction_blocks(const std::vector<SplitRed>& reds) {
+    std::vector<RedBlock> out;
+    for (int r = 0; r < (int)reds.size(); ++r) {
+        const int rpb = std::max(1, 2048 / std::max(1, reds[r].N));
+        for (int m0 = 0; m0 < reds[r].M; m0 += rpb) out.push_back({r, m0, std::min(reds[r].M, m0 + rpb)});
+    }
+    return out;
 }
 
-void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const double* part, void* out,
-                          const int64_t* row_off, int num_sms, cudaStream_t s) {
-    if (total == 0 || nred == 0) return;
+void launch_splitk_reduce(const SplitRed* d_reds, const RedBlock* d_blocks, int nblocks, const float* part,
+                          void* out, const int64_t* row_off, cudaStream_t s) {
+    if (nblocks == 0) return;
+    KScope ks("splitk_reduce", s);
+    splitk_reduce<float><<<nblocks, 256, 0, s>>>(d_reds, d_blocks, part, out, row_off);
+}
+
+void launch_splitk_reduce(const SplitRed* d_reds, const RedBlock* d_blocks, int nblocks, const double* part,
+                          void* out, const int64_t* row_off, cudaStream_t s) {
+    if (nblocks == 0) return;
     KScope ks("splitk_reduce_f64", s);
-    const int64_t grid = (total + kRedPerBlock - 1) / kRedPerBlock;
-    TNH_REQUIRE(grid < INT32_MAX, TNH_ERR_SHAPE, "splitk_reduce: %lld elements", (long long)total);
-    splitk_reduce<double><<<(unsigned)grid, 256, 0, s>>>(d_reds, nred, total, part, out, row_off);
+    splitk_reduce<double><<<nblocks, 256, 0, s>>>(d_reds, d_blocks, part, out, row_off);
 }
 
 }  // namespace tnh

@@ -368,6 +368,8 @@ void set_split64(HeffGemm& G, int num_sms, cudaStream_t s) {
     }
     G.d_f64run = upload(G.f64run, s);
     G.d_reds64 = upload(G.reds64, s);
+    G.red64_blocks = reduction_blocks(G.reds64);
+    G.d_red64_blocks = upload(G.red64_blocks, s);
 }
 
 // Rebuild the launched tcgen05 tasks of G for a K-split factor (1: the block
@@ -425,6 +427,8 @@ void set_split(HeffGemm& G, int split, cudaStream_t s) {
     G.tilestc = tile0;
     G.d_tc = upload(G.tc, s);
     G.d_reds = upload(G.reds, s);
+    G.red_blocks = reduction_blocks(G.reds);
+    G.d_red_blocks = upload(G.red_blocks, s);
     // (pageable uploads are staged before they return: the host vectors may change)
 }
 
@@ -439,8 +443,8 @@ void launch_stage(const HeffGemm& G, const HeffPlan& P, const uint16_t* A, const
     } else {
         launch_gemm_tc(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, A, B, P.part.as<double>(), P.planes,
                        ctx->num_sms, err, s, nullptr);
-        launch_splitk_reduce(G.d_reds.as<SplitRed>(), (int)G.reds.size(), G.red_total, P.part.as<float>(), out,
-                             row_off, ctx->num_sms, s);
+        launch_splitk_reduce(G.d_reds.as<SplitRed>(), G.d_red_blocks.as<RedBlock>(), (int)G.red_blocks.size(),
+                             P.part.as<float>(), out, row_off, s);
     }
 }
 
@@ -1215,8 +1219,8 @@ cudaGraphNode_t last_node(cudaStream_t s) {
 // gather_kernel(tiles, segs, terms, geom, src, dst) reads x as argument 4;
 // y is written by gemm_f64_kernel(tasks, ntasks, A, B, C, row_off) as
 // argument 4, gemm_tc_kernel(tasks, ntasks, tiles, A, B, C, err, row_off) as
-// argument 5, or splitk_reduce(reds, nred, total, part, out, row_off) as
-// argument 4.
+// argument 5, or splitk_reduce(reds, blocks, part, out, row_off) as
+// argument 3.
 void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_t s, HeffPlan::Graph* G) {
     const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
     if (f64) {
@@ -1226,8 +1230,8 @@ void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_
             if (Gm.split64 > 1) {
                 launch_gemm_f64(Gm.d_f64run.as<GemmTask>(), (int)Gm.f64run.size(), Gm.tiles64run, A, B,
                                 P.part64.as<double>(), s);
-                launch_splitk_reduce(Gm.d_reds64.as<SplitRed>(), (int)Gm.reds64.size(), Gm.red64_total,
-                                     P.part64.as<double>(), out, roff, P.ctx->num_sms, s);
+                launch_splitk_reduce(Gm.d_reds64.as<SplitRed>(), Gm.d_red64_blocks.as<RedBlock>(),
+                                     (int)Gm.red64_blocks.size(), P.part64.as<double>(), out, roff, s);
             } else {
                 launch_gemm_f64(Gm.d_f64.as<GemmTask>(), ntasks, Gm.tiles64, A, B, out, s, roff);
             }
@@ -1238,11 +1242,9 @@ void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_
         launch_w12(P.jW, P.oT.d_g64.as<OpGeom>(), P.t1.as<double>(), P.opT64.p, 0, s);
         f64_stage(P.g4, n4, P.opT64.as<double>(), P.R64.as<double>(), y, P.row_off.as<int64_t>());
         if (G) {
-            // gemm_f64_kernel(tasks, ntasks, A, B, C, row_off) and
-            // splitk_reduce(reds, nred, total, part, out, row_off) both take y as argument 4
             G->ny = last_node(s);
-            G->iy = 4;
-            G->ny_args = 6;
+            G->iy = P.g4.split64 > 1 ? 3 : 4;
+            G->ny_args = P.g4.split64 > 1 ? 5 : 6;
         }
     } else {
         launch_gather(P.jX, P.oX.d_gtc.as<OpGeom>(), x, P.opX.p, P.planes, s, "heff_pack_x");
@@ -1252,8 +1254,8 @@ void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_
         launch_stage(P.g4, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y, P.row_off.as<int64_t>(), s);
         if (G) {
             G->ny = last_node(s);
-            G->iy = P.g4.split > 1 ? 4 : 5;
-            G->ny_args = P.g4.split > 1 ? 6 : 8;
+            G->iy = P.g4.split > 1 ? 3 : 5;
+            G->ny_args = P.g4.split > 1 ? 5 : 8;
         }
     }
 }

@@ -27,15 +27,17 @@ struct HeffGemm {
     int split = 1;
     int tile_policy = 0;   // N tile widths of the tcgen05 tasks (see tile_width)
     std::vector<SplitRed> reds;
+    std::vector<RedBlock> red_blocks;
     int64_t red_total = 0, part_elems = 0;
-    DevBuf d_f64, d_tc, d_reds;
+    DevBuf d_f64, d_tc, d_reds, d_red_blocks;
     // the FP64 GEMM: with split64 > 1 the tasks of f64run write float64
     // partial slabs (K slices of 16-multiples), summed by reds64 in order
     int split64 = 1, tiles64run = 0;
     std::vector<GemmTask> f64run;
     std::vector<SplitRed> reds64;
+    std::vector<RedBlock> red64_blocks;
     int64_t red64_total = 0, part64_elems = 0;
-    DevBuf d_f64run, d_reds64;
+    DevBuf d_f64run, d_reds64, d_red64_blocks;
 };
 
 // ---- device vector helpers (float64, deterministic reductions) -----------

@@ -187,8 +187,7 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
                                                                        int ngroups, int total_pairs, int max_rounds,
                                                                        float* __restrict__ X, float* __restrict__ V,
                                                                        int* smax, int* state, GridBar* bar, int* err,
-                                                                       int stride, const double* __restrict__ fro2,
-                                                                       long long* tdbg) {
+                                                                       int stride, const double* __restrict__ fro2) {
     constexpr int NC = 2 * B;
     extern __shared__ __align__(16) float sm[];   // [2B][stride] X columns, then Q [2B][2B]
     __shared__ int skip;
@@ -196,9 +195,7 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned epoch = 0;
     int t = 0;
-#define STAMP(j) if (tdbg && blockIdx.x == 0 && threadIdx.x == 0 && t >= 64 && t < 96) tdbg[(t - 64) * 8 + (j)] = clock64();
     for (; t < max_rounds; ++t) {
-        STAMP(0)
         for (int item = blockIdx.x; item < total_pairs; item += gridDim.x) {
             int lo = 0, hi = ngroups - 1;
             while (lo < hi) {
@@ -216,7 +213,6 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
             __syncthreads();
             const int sk = skip;
             __syncthreads();   // every thread has read skip before thread 0 rewrites it
-            STAMP(1)
             if (sk) continue;
             const int bp = rr_pos(i, k, R), bq = rr_pos(G.nblk - 1 - i, k, R);
             // local column list: block bp then block bq (clipped to n)
@@ -231,7 +227,6 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
             }
             for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) Qs[e] = e / NC == e % NC ? 1.f : 0.f;
             __syncthreads();
-            STAMP(2)
             const int ne = nc + (nc & 1), Ri = ne - 1;
             const float null2 = (float)(1e-12 * fro2[lo]);
             // stop test, per column pair: float32 rotations leave every column
@@ -287,7 +282,6 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
                 }
                 __syncthreads();
             }
-            STAMP(3)
             for (int c = warp; c < nc; c += nwarp) {
                 const int col = c < np ? p0 + c : q0 + (c - np);
                 stage_out(X + G.x_off + (int64_t)col * L, sm + (size_t)c * stride, L, lane, 32);
@@ -354,16 +348,12 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
             }
             if (lane == 0 && wmax > 0.f) atomicMax(&smax[3 * lo + (t / R) % 3], __float_as_int(wmax));
             __syncthreads();
-            STAMP(4)
         }
         if (!grid_barrier(bar, gridDim.x, epoch, err)) break;
-        STAMP(5)
         if (all_done(groups, ngroups, smax, t + 1, 1.0f)) { ++t; break; }
-        STAMP(6)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[1] = t;
 }
-#undef STAMP
 
 // ------------------------------------------------ stage b: float64 pairs
 struct JGroup {
@@ -998,13 +988,8 @@ int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg
     int* smaxp = d_smax.as<int>();
     int* statep = d_state.as<int>();
     GridBar* barp = d_bar.as<GridBar>();
-    const bool tr = std::getenv("TNH_ROUND_TIMES") != nullptr;
-    DevBuf d_t(tr ? 32 * 8 * 8 : 16);
-    if (tr) CUDA_CHECK(cudaMemsetAsync(d_t.p, 0, 32 * 8 * 8, s));
-    long long* tp = tr ? d_t.as<long long>() : nullptr;
     void* args[] = {(void*)&gp,    (void*)&ng,     (void*)&bpairs, (void*)&max_rounds, (void*)&X,      (void*)&V,
-                    (void*)&smaxp, (void*)&statep, (void*)&barp,   (void*)&errp,       (void*)&stride, (void*)&fro2,
-                    (void*)&tp};
+                    (void*)&smaxp, (void*)&statep, (void*)&barp,   (void*)&errp,       (void*)&stride, (void*)&fro2};
     {
         KScope ks("svd_jacobi_f32", s);
         CUDA_CHECK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, s));
@@ -1012,19 +997,6 @@ int run_block_jacobi(Ctx* ctx, const std::vector<BGroup>& bg, const DevBuf& d_bg
     int st[2];
     CUDA_CHECK(cudaMemcpyAsync(st, d_state.p, 8, cudaMemcpyDeviceToHost, s));
     CUDA_CHECK(cudaStreamSynchronize(s));   // bookkeeping buffers are freed on return
-    if (tr && st[1] >= 96) {
-        std::vector<long long> h(32 * 8);
-        CUDA_CHECK(cudaMemcpy(h.data(), d_t.p, h.size() * 8, cudaMemcpyDeviceToHost));
-        double acc[7] = {0};
-        for (int r = 0; r < 32; ++r) {
-            for (int j = 0; j < 6; ++j) acc[j] += (double)(h[r * 8 + j + 1] - h[r * 8 + j]);
-            if (r + 1 < 32) acc[6] += (double)(h[(r + 1) * 8] - h[r * 8 + 6]);
-        }
-        std::fprintf(stderr, "svd f32 round phases (cycles, mean of 32 rounds): skip %.0f stage_in %.0f inner %.0f "
-                     "stage_out %.0f barrier %.0f all_done %.0f loop %.0f, round %.0f\n", acc[0] / 32, acc[1] / 32,
-                     acc[2] / 32, acc[3] / 32, acc[4] / 32, acc[5] / 32, acc[6] / 31,
-                     (double)(h[31 * 8] - h[0]) / 31);
-    }
     if (std::getenv("TNH_DEBUG"))
         std::fprintf(stderr, "svd: float32 block Jacobi%s %d rounds (max %d, per sweep %d, grid %d, b %d)\n", what,
                      st[1], max_rounds, rmax, grid, bmax);

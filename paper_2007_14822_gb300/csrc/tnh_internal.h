@@ -266,11 +266,15 @@ struct SplitRed {
     int64_t c_base;  // else: row m starts at c_base + m * ldc
     int64_t e0;      // prefix of M * N over the reductions of one launch
 };
-void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const float* part, void* out,
-                          const int64_t* row_off, int num_sms, cudaStream_t s);
+// One block of the reduction launch: rows [m0, m1) of reduction red.
+struct RedBlock { int red, m0, m1; };
+// The blocks of a list of reductions, about 2048 elements each.
+std::vector<RedBlock> reduction_blocks(const std::vector<SplitRed>& reds);
+void launch_splitk_reduce(const SplitRed* d_reds, const RedBlock* d_blocks, int nblocks, const float* part,
+                          void* out, const int64_t* row_off, cudaStream_t s);
 // The same with float64 partial slabs (K-split FP64 GEMMs).
-void launch_splitk_reduce(const SplitRed* d_reds, int nred, int64_t total, const double* part, void* out,
-                          const int64_t* row_off, int num_sms, cudaStream_t s);
+void launch_splitk_reduce(const SplitRed* d_reds, const RedBlock* d_blocks, int nblocks, const double* part,
+                          void* out, const int64_t* row_off, cudaStream_t s);
 constexpr int kF64TileM = 64, kF64TileN = 64, kF64TileK = 16;
 constexpr int kTcTileM = 128, kTcTileN = 128, kTcTileK = 64;
 constexpr int kTcTileElems = kTcTileM * kTcTileK;   // 8192 bf16 per plane tile

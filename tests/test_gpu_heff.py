@@ -156,12 +156,17 @@ def test_heff_qn(ctx, m, nsect, maxd, p):
 
 
 @pytest.mark.parametrize("p", ["fp64", "bf16x6"])
-def test_heff_graph_replay_with_new_buffers(ctx, p):
+@pytest.mark.parametrize("m,nsect,maxd,split", [(40, 7, 12, None), (300, 3, 200, "2,4")])
+def test_heff_graph_replay_with_new_buffers(ctx, p, m, nsect, maxd, split, monkeypatch):
     # the first application launches directly, the second captures a CUDA
     # graph, later ones replay it with the x / y arguments patched: every
-    # call must give the oracle's result for its own input
+    # call must give the oracle's result for its own input (also when the
+    # last launch is a K-split reduction: forced here for the split modes;
+    # the FP64 GEMM splits the long K of the few-tile m=300 case itself)
     import torch
-    d = H.heff_inputs(40, None, 5, nsect=7, maxd=12)
+    if split:
+        monkeypatch.setenv("TNH_HEFF_SPLIT", split)
+    d = H.heff_inputs(m, None, 5, nsect=nsect, maxd=maxd)
     plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
     from oracle.blocksparse import BlockTensor
     xs = [d["psi"].data.clone() * (1.0 + 0.5 * i) for i in range(3)]
