@@ -251,7 +251,7 @@ tnh_status tnh_heff_flops(const tnh_heff* plan, double* flops);
  * would, although the plan applies them fused in one pass) and the S4 GEMM
  * (sum over w2, b with R). s1 + s23 + s4 is tnh_heff_flops. */
 tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, double* s4);
-/* The choices made for the plan (choice [7]):
+/* The choices made for the plan (choice [8]):
  * - choice[5]: the block-contraction strategy (Sec. 9.4: neither always
  *   wins): 0 combines the blocks of a contracted sector into one GEMM task
  *   (S1 one task per a-sector, S4 one per b'-sector), 1 contracts block pairs
@@ -264,7 +264,10 @@ tnh_status tnh_heff_flops_detail(const tnh_heff* plan, double* s1, double* s23, 
  *   columns), choice[1] / choice[3] their K-split factor (1, 2, 4, 8),
  *   choice[4] 1 when the plan timed the candidates itself (0: reused from
  *   the context or the TNH_TUNE_CACHE file, or forced by TNH_HEFF_SPLIT /
- *   TNH_HEFF_TILES). An FP64 plan reports 0 1 0 1 0 for these. */
+ *   TNH_HEFF_TILES). An FP64 plan reports 0 1 0 1 0 for these;
+ * - choice[7]: 1 when the S4 GEMM forms its operand A itself from T1 (the
+ *   W1.W2 step inside the GEMM, no separate pass; chosen by timing both, or
+ *   forced by TNH_HEFF_FUSED=0/1), 0 otherwise. */
 tnh_status tnh_heff_tuning(const tnh_heff* plan, int32_t* choice);
 /* Diagonal of the MPO part of H_eff (the projectors excluded), DEVICE
  * float64 [n] in the psi layout:

@@ -32,6 +32,7 @@
 
 #include "gather.h"
 #include "prof.h"
+#include "split.cuh"
 
 namespace tnh {
 
@@ -163,11 +164,6 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
     }
 }
 
-// Offset of element (row, k) inside a 128 x 64 bfloat16 operand tile in the
-// 128-byte-swizzled K-major layout of the tcgen05 shared-memory descriptor.
-__device__ __forceinline__ int swz(int row, int k) {
-    return row * 64 + ((((k >> 3) ^ (row & 7))) << 3) + (k & 7);
-}
 
 // four consecutive source elements (16-byte aligned for float, 32 for double)
 __device__ __forceinline__ void load4(const float* p, float* v) {
@@ -178,25 +174,6 @@ __device__ __forceinline__ void load4(const double* p, double* v) {
     const double2 x = __ldg(reinterpret_cast<const double2*>(p));
     const double2 y = __ldg(reinterpret_cast<const double2*>(p) + 1);
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-}
-
-// hi / mid / lo bfloat16 parts (round to nearest each) of two float32
-// values, packed in pairs: plane p holds (part p of a) | (part p of b) << 16
-template <int P>
-__device__ __forceinline__ void split2(float a, float b, uint32_t* w) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    w[0] = *reinterpret_cast<uint32_t*>(&h);
-    if (P > 1) {
-        const float2 hf = __bfloat1622float2(h);
-        const float ra = a - hf.x, rb = b - hf.y;
-        __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
-        w[1] = *reinterpret_cast<uint32_t*>(&m);
-        if (P > 2) {
-            const float2 mf = __bfloat1622float2(m);
-            __nv_bfloat162 l = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
-            w[2] = *reinterpret_cast<uint32_t*>(&l);
-        }
-    }
 }
 
 template <class SrcT, bool kF64, int P>

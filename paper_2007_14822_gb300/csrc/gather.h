@@ -56,6 +56,13 @@ struct W12Job {
     DevBuf d_cells, d_ins, d_outs, d_terms, d_ctas;
     void upload_all(cudaStream_t s);
 };
+// The S4 GEMM with its operand A formed in the kernel from T1 (float32) by
+// the gather job (atiles, asegs, aterms) over the operand's tile numbering,
+// three-plane split; B packed. Same output conventions as launch_gemm_tc.
+void launch_gemm_tc_fused(const GemmTask* d_tasks, int ntasks, int total_tiles, const GatherTile* atiles,
+                          const GatherSeg* asegs, const GatherTerm* aterms, const float* asrc, const uint16_t* B,
+                          double* C, int num_sms, int* err, cudaStream_t s, const int64_t* row_off);
+
 // src: T1 (float64 or float32); dst: S4 operand A in the format of planes.
 void launch_w12(const W12Job& J, const OpGeom* d_geom, const double* src, void* dst, int planes, cudaStream_t s);
 void launch_w12(const W12Job& J, const OpGeom* d_geom, const float* src, void* dst, int planes, cudaStream_t s);

@@ -31,8 +31,10 @@
 // Every wait is bounded (ptx::mbar_wait); a timeout sets the device error flag.
 #include <cuda_bf16.h>
 
+#include "gather.h"
 #include "prof.h"
 #include "ptx.cuh"
+#include "split.cuh"
 #include "tnh_internal.h"
 
 namespace tnh {
@@ -42,6 +44,10 @@ namespace {
 constexpr int kTileBytes = kTcTileM * kTcTileK * 2;   // 16384, A and B tiles alike
 constexpr int kThreads = 320;   // producer, MMA, 8 epilogue warps
 constexpr int kEpiWarps = 8;
+// with the A operand formed in the kernel: 4 more warps (warps 10-13) that
+// build each A stage from its gather segments
+constexpr int kAWarps = 4;
+constexpr int kThreadsFused = kThreads + 32 * kAWarps;
 
 // epilogue staging: per epilogue warp 32 rows x 33 words (a 32 x 32 float or
 // 32 x 16 double block, one padding word per row against bank conflicts)
@@ -73,11 +79,20 @@ __device__ __forceinline__ int find_task(const GemmTask* __restrict__ tasks, int
     return lo;
 }
 
-template <int P>
-__global__ void __launch_bounds__(kThreads, 1)
+// kFusedA: operand A is not read pre-packed but formed in the kernel, tile
+// by tile, from float32 source rows: A tile (task, mi, kb) is the gather tile
+// a_base + mi * kstride + kb of (atiles, asegs, aterms), every segment of it
+// a rectangle whose elements are sums of coef * asrc[off + r rs + c] (the
+// W1.W2 step of the effective Hamiltonian feeding S4 directly). Segments
+// cover every row below M and every column of the tile; four warps write the
+// split-bfloat16 planes into the stage and arrive on its barrier.
+template <int P, bool kFusedA>
+__global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
     gemm_tc_kernel(const GemmTask* __restrict__ tasks, int ntasks, int total_tiles,
                    const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, double* __restrict__ C,
-                   int* err, const int64_t* __restrict__ row_off) {
+                   int* err, const int64_t* __restrict__ row_off, const GatherTile* __restrict__ atiles,
+                   const GatherSeg* __restrict__ asegs, const GatherTerm* __restrict__ aterms,
+                   const float* __restrict__ asrc) {
     using Cfg = TcCfg<P>;
     constexpr int S = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
@@ -96,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&full[s], kFusedA ? 1 + kAWarps : 1);
             ptx::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -137,9 +152,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ks = pt->kstride ? pt->kstride : pt->kt;
                 const int tn = pt->tn ? pt->tn : kTcTileN;
                 const int bt = (ni * tn) >> 7, boff = ((ni * tn) & 127) * 64;
-                const uint16_t* a = A + (pt->a_base + (int64_t)mi * ks + pkb) * P * kTcTileElems;
                 const uint16_t* b = B + (pt->b_base + (int64_t)bt * ks + pkb) * P * kTcTileElems + boff;
-                ptx::bulk_prefetch_l2(a, P * kTileBytes);
+                if (!kFusedA) ptx::bulk_prefetch_l2(A + (pt->a_base + (int64_t)mi * ks + pkb) * P * kTcTileElems,
+                                                    P * kTileBytes);
 #pragma unroll
                 for (int p = 0; p < P; ++p) ptx::bulk_prefetch_l2(b + (int64_t)p * kTcTileElems, (uint32_t)tn * 128u);
                 if (++pkb == pkt) {
@@ -166,11 +181,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = 0; kb < t.kt; ++kb) {
                     pf_step();
                     if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, err, 1)) { ok = false; break; }
-                    ptx::mbar_expect_tx(&full[stage], P * (kTileBytes + bbytes));
+                    ptx::mbar_expect_tx(&full[stage], P * ((kFusedA ? 0u : (uint32_t)kTileBytes) + bbytes));
+                    if (!kFusedA) {
 #pragma unroll
-                    for (int p = 0; p < P; ++p)
-                        ptx::bulk_g2s(sA + (stage * P + p) * kTileBytes,
-                                      a + ((int64_t)kb * P + p) * kTcTileElems, kTileBytes, &full[stage]);
+                        for (int p = 0; p < P; ++p)
+                            ptx::bulk_g2s(sA + (stage * P + p) * kTileBytes,
+                                          a + ((int64_t)kb * P + p) * kTcTileElems, kTileBytes, &full[stage]);
+                    }
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         ptx::bulk_g2s(sB + (stage * P + p) * kTileBytes,
@@ -229,6 +246,51 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mma_commit(fin);
             ptx::mbar_wait(fin, 0, err, 4, /*watch_flag=*/false);
         }
+    } else if (kFusedA && warp >= 2 + kEpiWarps) {
+        // ---------------- A producers: form each A stage from its segments
+        const int ptid = threadIdx.x - 32 * (2 + kEpiWarps);
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
+            const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
+            const int mi = (tile - t.tile0) / t.nt;
+            const int ks = t.kstride ? t.kstride : t.kt;
+            for (int kb = 0; kb < t.kt; ++kb) {
+                if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, err, 6)) { ok = false; break; }
+                const GatherTile g = atiles[t.a_base + (int64_t)mi * ks + kb];
+                uint8_t* sa = sA + stage * P * kTileBytes;
+                for (int si = g.seg0; si < g.seg1; ++si) {
+                    const GatherSeg sg = asegs[si];
+                    const int ncq = sg.nc >> 2, nq = sg.nr * ncq;
+                    for (int e = ptid; e < nq; e += 32 * kAWarps) {
+                        const int r = e / ncq, cq = e - r * ncq;
+                        float v[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (int j = sg.t0; j < sg.t1; ++j) {
+                            const GatherTerm gt = aterms[j];
+                            const float4 x =
+                                __ldg(reinterpret_cast<const float4*>(asrc + gt.off + (int64_t)r * gt.rs + 4 * cq));
+                            v[0] = fmaf(gt.coef32, x.x, v[0]);
+                            v[1] = fmaf(gt.coef32, x.y, v[1]);
+                            v[2] = fmaf(gt.coef32, x.z, v[2]);
+                            v[3] = fmaf(gt.coef32, x.w, v[3]);
+                        }
+                        uint32_t w0[3], w1[3];
+                        split2<P>(v[0], v[1], w0);
+                        split2<P>(v[2], v[3], w1);
+                        const int off = swz(sg.r0 + r, sg.c0 + 4 * cq);
+#pragma unroll
+                        for (int p = 0; p < P; ++p)
+                            *reinterpret_cast<uint2*>(sa + p * kTileBytes + off * 2) = make_uint2(w0[p], w1[p]);
+                    }
+                }
+                // the tensor core (async proxy) reads what these threads wrote
+                ptx::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&full[stage]);
+                if (++stage == S) { stage = 0; phase ^= 1u; }
+            }
+        }
     } else {
         // ---------------- epilogue: warp w owns TMEM lane quarter (w % 4) and
         // the column half (w - 2) / 4 of the tile
@@ -259,15 +321,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int c0 = 0; c0 < kCols; c0 += 32) {
                     if (c0 >= ncols) break;
-                    uint32_t rh[32], rx[32];
-                    ptx::tmem_ld32(row_addr + c0, rh);
-                    if (P > 1) ptx::tmem_ld32(row_addr + 128 + c0, rx);
-                    ptx::tmem_wait_ld();
+                    if constexpr (kFusedA) {
+                        // one 32-column buffer at a time (the 14-warp launch
+                        // leaves fewer registers per thread): the chunk's hh
+                        // and cross sums are added to the running sum in turn
+                        uint32_t r[32];
+                        ptx::tmem_ld32(row_addr + c0, r);
+                        ptx::tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float v = __uint_as_float(rh[j]);
-                        if (P > 1) v += __uint_as_float(rx[j]);
-                        acc[c0 + j] += v;
+                        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+                        if (P > 1) {
+                            ptx::tmem_ld32(row_addr + 128 + c0, r);
+                            ptx::tmem_wait_ld();
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+                        }
+                    } else {
+                        uint32_t rh[32], rx[32];
+                        ptx::tmem_ld32(row_addr + c0, rh);
+                        if (P > 1) ptx::tmem_ld32(row_addr + 128 + c0, rx);
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            float v = __uint_as_float(rh[j]);
+                            if (P > 1) v += __uint_as_float(rx[j]);
+                            acc[c0 + j] += v;
+                        }
                     }
                 }
                 ptx::tc_fence_before();
@@ -368,18 +447,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int P>
+template <int P, bool kFusedA>
 void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16_t* A, const uint16_t* B,
-              double* C, int num_sms, int* err, cudaStream_t s, const int64_t* row_off) {
+              double* C, int num_sms, int* err, cudaStream_t s, const int64_t* row_off, const GatherTile* atiles,
+              const GatherSeg* asegs, const GatherTerm* aterms, const float* asrc) {
     static bool configured = false;
     if (!configured) {
-        CUDA_CHECK(cudaFuncSetAttribute(gemm_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CUDA_CHECK(cudaFuncSetAttribute(gemm_tc_kernel<P, kFusedA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         TcCfg<P>::kSmem));
         configured = true;
     }
     int grid = std::min(total_tiles, num_sms > 0 ? num_sms : 148);
-    KScope ks(P == 3 ? "gemm_tc_bf16x6" : (P == 2 ? "gemm_tc_bf16x3" : "gemm_tc_bf16"), s);
-    gemm_tc_kernel<P><<<grid, kThreads, TcCfg<P>::kSmem, s>>>(d_tasks, ntasks, total_tiles, A, B, C, err, row_off);
+    KScope ks(kFusedA ? "gemm_tc_bf16x6_w12" : (P == 3 ? "gemm_tc_bf16x6" : (P == 2 ? "gemm_tc_bf16x3" : "gemm_tc_bf16")),
+              s);
+    gemm_tc_kernel<P, kFusedA><<<grid, kFusedA ? kThreadsFused : kThreads, TcCfg<P>::kSmem, s>>>(
+        d_tasks, ntasks, total_tiles, A, B, C, err, row_off, atiles, asegs, aterms, asrc);
 }
 
 // K-split reduction: block b sums rows [m0, m1) of one reduction R over its
@@ -412,11 +494,22 @@ void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const 
                     double* C, int planes, int num_sms, int* err, cudaStream_t s, const int64_t* row_off) {
     if (total_tiles == 0) return;
     if (planes == 3)
-        launch_p<3>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
+        launch_p<3, false>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off, nullptr, nullptr, nullptr,
+                           nullptr);
     else if (planes == 2)
-        launch_p<2>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
+        launch_p<2, false>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off, nullptr, nullptr, nullptr,
+                           nullptr);
     else
-        launch_p<1>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off);
+        launch_p<1, false>(d_tasks, ntasks, total_tiles, A, B, C, num_sms, err, s, row_off, nullptr, nullptr, nullptr,
+                           nullptr);
+}
+
+void launch_gemm_tc_fused(const GemmTask* d_tasks, int ntasks, int total_tiles, const GatherTile* atiles,
+                          const GatherSeg* asegs, const GatherTerm* aterms, const float* asrc, const uint16_t* B,
+                          double* C, int num_sms, int* err, cudaStream_t s, const int64_t* row_off) {
+    if (total_tiles == 0) return;
+    launch_p<3, true>(d_tasks, ntasks, total_tiles, nullptr, B, C, num_sms, err, s, row_off, atiles, asegs, aterms,
+                      asrc);
 }
 
 }  // namespace tnh

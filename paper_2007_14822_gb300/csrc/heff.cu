@@ -35,6 +35,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <set>
 #include <string>
 
 #include "heff.h"
@@ -178,8 +179,9 @@ struct JobBuilder {
     }
     // rows [row0, row0+nr) x cols [col0, col0+nc) of task t: element (r, c)
     // is sum over terms of coef * src[off + r rs + c cs]
-    void rect(int t, int64_t row0, int64_t col0, int64_t nr, int64_t nc, const std::vector<GatherTerm>& tm) {
-        if (tm.empty() || nr <= 0 || nc <= 0) return;
+    void rect(int t, int64_t row0, int64_t col0, int64_t nr, int64_t nc, const std::vector<GatherTerm>& tm,
+              bool keep_empty = false) {
+        if ((tm.empty() && !keep_empty) || nr <= 0 || nc <= 0) return;
         const Task& T = tasks[t];
         for (int64_t R = row0; R < row0 + nr;) {
             const int64_t mi = R / kGatherRows, Re = std::min(row0 + nr, (mi + 1) * kGatherRows);
@@ -432,17 +434,22 @@ void set_split(HeffGemm& G, int split, cudaStream_t s) {
     // (pageable uploads are staged before they return: the host vectors may change)
 }
 
-// One tcgen05 GEMM of the plan, and its reduction when K is split.
+// One tcgen05 GEMM of the plan, and its reduction when K is split. With
+// fusedA the GEMM (S4) forms its operand A from T1 by the plan's job jT.
 void launch_stage(const HeffGemm& G, const HeffPlan& P, const uint16_t* A, const uint16_t* B, void* out,
-                  const int64_t* row_off, cudaStream_t s) {
+                  const int64_t* row_off, cudaStream_t s, bool fusedA = false) {
     Ctx* ctx = P.ctx;
     int* err = ctx->d_flag.as<int>();
-    if (G.split <= 1) {
-        launch_gemm_tc(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, A, B, static_cast<double*>(out), P.planes,
-                       ctx->num_sms, err, s, row_off);
-    } else {
-        launch_gemm_tc(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, A, B, P.part.as<double>(), P.planes,
-                       ctx->num_sms, err, s, nullptr);
+    double* C = G.split <= 1 ? static_cast<double*>(out) : P.part.as<double>();
+    const int64_t* ro = G.split <= 1 ? row_off : nullptr;
+    if (fusedA)
+        launch_gemm_tc_fused(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, P.jT.d_tiles.as<GatherTile>(),
+                             P.jT.d_segs.as<GatherSeg>(), P.jT.d_terms.as<GatherTerm>(), P.t1.as<float>(), B, C,
+                             ctx->num_sms, err, s, ro);
+    else
+        launch_gemm_tc(G.d_tc.as<GemmTask>(), (int)G.tc.size(), G.tilestc, A, B, C, P.planes, ctx->num_sms, err, s,
+                       ro);
+    if (G.split > 1) {
         launch_splitk_reduce(G.d_reds.as<SplitRed>(), G.d_red_blocks.as<RedBlock>(), (int)G.red_blocks.size(),
                              P.part.as<float>(), out, row_off, s);
     }
@@ -505,11 +512,11 @@ void set_tiles(HeffGemm& G, int policy) {
 }
 
 // ---- tuning cache on disk: one line per shape signature,
-//   "heff <key values...> : <tiles S1> <split S1> <tiles S4> <split S4>"
+//   "heff <key values...> : <tiles S1> <split S1> <tiles S4> <split S4> <S4 fused>"
 // read when a context first tunes, appended to after every measurement.
 // The file is named by TNH_TUNE_CACHE (no file: the choices live as long as
 // the context).
-std::string tune_line(const std::vector<int>& key, const std::array<int, 4>& c) {
+std::string tune_line(const std::vector<int>& key, const std::array<int, 5>& c) {
     std::string l = "heff";
     for (int k : key) l += " " + std::to_string(k);
     l += " :";
@@ -531,7 +538,7 @@ void load_tune_file(Ctx* ctx) {
         const size_t colon = l.find(':');
         if (colon == std::string::npos) continue;
         std::vector<int> key;
-        std::array<int, 4> c{};
+        std::array<int, 5> c{};
         int v, pos = 5, n = 0;
         const std::string a = l.substr(5, colon - 5), b = l.substr(colon + 1);
         const char* p = a.c_str();
@@ -541,19 +548,19 @@ void load_tune_file(Ctx* ctx) {
         }
         p = b.c_str();
         int k = 0;
-        while (k < 4 && std::sscanf(p, "%d%n", &v, &n) == 1) {
+        while (k < 5 && std::sscanf(p, "%d%n", &v, &n) == 1) {
             c[k++] = v;
             p += n;
         }
         (void)pos;
-        const bool valid = k == 4 && c[0] >= 0 && c[0] <= 2 && c[2] >= 0 && c[2] <= 2 && c[1] >= 1 && c[1] <= 8 &&
-                           c[3] >= 1 && c[3] <= 8;
+        const bool valid = k == 5 && c[0] >= 0 && c[0] <= 2 && c[2] >= 0 && c[2] <= 2 && c[1] >= 1 && c[1] <= 8 &&
+                           c[3] >= 1 && c[3] <= 8 && (c[4] == 0 || c[4] == 1);
         if (valid && !key.empty()) ctx->heff_tune[key] = c;
     }
     std::fclose(f);
 }
 
-void save_tune_line(const std::vector<int>& key, const std::array<int, 4>& c) {
+void save_tune_line(const std::vector<int>& key, const std::array<int, 5>& c) {
     const char* path = std::getenv("TNH_TUNE_CACHE");
     if (!path || !*path) return;
     if (FILE* f = std::fopen(path, "a")) {
@@ -588,15 +595,19 @@ void tune_plan(HeffPlan& P) {
         key.push_back(bucket((double)kt / std::max<size_t>(1, G->tc_base.size())));
     }
     load_tune_file(ctx);
-    std::array<int, 4> choice{0, 1, 0, 1};   // tiles S1, split S1, tiles S4, split S4
+    // tiles S1, split S1, tiles S4, split S4, S4 forms its operand itself
+    std::array<int, 5> choice{0, 1, 0, 1, 0};
     bool measured = false;
+    const bool can_fuse = P.planes == 3 && P.jT.ntiles > 0;
     const char* fs = std::getenv("TNH_HEFF_SPLIT");
     const char* ft = std::getenv("TNH_HEFF_TILES");
-    if (fs || ft) {
+    const char* ff = std::getenv("TNH_HEFF_FUSED");
+    if (fs || ft || ff) {
         int a = 1, b = 1, c = 0, d = 0;
         if (fs && std::sscanf(fs, "%d,%d", &a, &b) != 2) a = b = 1;
         if (ft && std::sscanf(ft, "%d,%d", &c, &d) != 2) c = d = 0;
-        choice = {std::min(std::max(c, 0), 2), std::max(1, a), std::min(std::max(d, 0), 2), std::max(1, b)};
+        const int f = ff && std::atoi(ff) == 1 && can_fuse ? 1 : 0;
+        choice = {std::min(std::max(c, 0), 2), std::max(1, a), std::min(std::max(d, 0), 2), std::max(1, b), f};
     } else if (ctx->heff_tune.count(key)) {
         choice = ctx->heff_tune[key];
     } else {
@@ -604,13 +615,8 @@ void tune_plan(HeffPlan& P) {
         cudaEvent_t e0, e1;
         CUDA_CHECK(cudaEventCreate(&e0));
         CUDA_CHECK(cudaEventCreate(&e1));
-        auto time_run = [&](HeffGemm& G, bool s1, int split) {
-            set_split(G, split, s);
-            ensure_part(P, G.part_elems);
-            auto run = [&] {
-                if (s1) launch_stage(G, P, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(), P.t1.p, nullptr, s);
-                else launch_stage(G, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), ytmp.p, P.row_off.as<int64_t>(), s);
-            };
+        bool fused = false;
+        auto best_of_3 = [&](auto&& run) {
             run();
             // the best of three separately timed runs (the first plans of a
             // process run while clocks and caches settle)
@@ -626,9 +632,32 @@ void tune_plan(HeffPlan& P) {
             }
             return best;
         };
+        auto time_run = [&](HeffGemm& G, bool s1, int split) {
+            set_split(G, split, s);
+            ensure_part(P, G.part_elems);
+            auto run = [&] {
+                if (s1) launch_stage(G, P, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(), P.t1.p, nullptr, s);
+                else launch_stage(G, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), ytmp.p, P.row_off.as<int64_t>(),
+                                  s, fused);
+            };
+            return best_of_3(run);
+        };
         HeffGemm* Gs[2] = {&P.g1, &P.g4};
         for (int g = 0; g < 2; ++g) {
             HeffGemm& G = *Gs[g];
+            // S4: the W1.W2 pass then the GEMM, or the GEMM forming its own
+            // operand A from T1 (128-wide tiles, no split)
+            if (g == 1 && can_fuse) {
+                fused = false;
+                const float tw = best_of_3([&] {
+                    launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, P.planes, s);
+                });
+                const float tu = tw + time_run(G, false, 1);
+                fused = true;
+                const float tf = time_run(G, false, 1);
+                fused = tf < 0.97f * tu;
+                choice[4] = fused ? 1 : 0;
+            }
             // tile policy at split 1
             std::vector<int> widths0;
             for (const GemmTask& t : G.tc_base) widths0.push_back(t.tn);
@@ -675,12 +704,13 @@ void tune_plan(HeffPlan& P) {
     set_tiles(P.g4, choice[2]);
     set_split(P.g1, choice[1], s);
     set_split(P.g4, choice[3], s);
+    P.fusedS4 = choice[4] == 1 && can_fuse;
     ensure_part(P, std::max(P.g1.part_elems, P.g4.part_elems));
     P.tune = choice;
     P.tune_measured = measured;
     if (std::getenv("TNH_DEBUG"))
-        std::fprintf(stderr, "heff_plan: S1 tiles %d split %d, S4 tiles %d split %d (%s; S1 %lld tiles, S4 %lld tiles)\n",
-                     choice[0], choice[1], choice[2], choice[3], measured ? "measured" : "cached or forced",
+        std::fprintf(stderr, "heff_plan: S1 tiles %d split %d, S4 tiles %d split %d fused %d (%s; S1 %lld tiles, S4 %lld tiles)\n",
+                     choice[0], choice[1], choice[2], choice[3], choice[4], measured ? "measured" : "cached or forced",
                      (long long)base_tiles(P.g1), (long long)base_tiles(P.g4));
 }
 
@@ -965,6 +995,10 @@ std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const La
     JobBuilder bR;
     CellBuilder bW;
     std::vector<int64_t> roff;
+    // per operand-A task of S4: rows, K, row pieces (row0, rows) and K pieces
+    // (col0, columns): the grid every W1.W2 output fills one cell of
+    std::vector<int64_t> tM, tK;
+    std::vector<std::vector<std::pair<int64_t, int>>> trows, tkp;
     std::vector<char> covered(X.nblocks(), 0);
     tf = tt = 0;
     const Index& ibp = R.inds[2];
@@ -989,12 +1023,18 @@ std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const La
         if (strategy == 0) {
             at.assign(yb.size(), P->oT.count());
             P->oT.add_task(M, K);
+            tM.push_back(M);
+            tK.push_back(K);
         } else {
             for (int b : yb) {
                 at.push_back(P->oT.count());
                 P->oT.add_task(X.belems(b) / N, K);
+                tM.push_back(X.belems(b) / N);
+                tK.push_back(K);
             }
         }
+        trows.resize(tM.size());
+        tkp.resize(tM.size());
         // K pieces (w2 element z, b-sector B): operand B = R^T, element (r = b', c = b)
         struct KPiece { int z, B; int64_t col; int Db; };
         std::vector<KPiece> kp;
@@ -1008,6 +1048,8 @@ std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const La
                 col += rup(Db, 4);
             }
         }
+        for (int a : std::vector<int>(at.begin(), strategy == 0 ? at.begin() + 1 : at.end()))
+            for (const KPiece& k : kp) tkp[a].push_back({k.col, (int)rup(k.Db, 4)});
         // row pieces (s1', s2', a'): every row of every psi block of this b'-sector
         int64_t row = 0;
         for (size_t yi = 0; yi < yb.size(); ++yi) {
@@ -1022,6 +1064,7 @@ std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const La
                     const int s1p = (int)(is1.off[S1p] + u1), s2p = (int)(is2.off[S2p] + u2);
                     for (int al = 0; al < Dap; ++al)
                         roff.push_back(X.off[b] + (((int64_t)al * d1 + u1) * d2 + u2) * N);
+                    trows[at[yi]].push_back({strategy == 0 ? row : row - brow0, Dap});
                     for (const KPiece& k : kp) {
                         auto it = w12.find({k.z, s1p, s2p});
                         if (it == w12.end()) continue;
@@ -1077,6 +1120,35 @@ std::unique_ptr<HeffPlan> make_heff_strategy(Ctx* ctx, const Layout& L, const La
     // ---------------- device side
     bX.finish(P->jX, s);
     bW.finish(P->jW, s);
+    // the W1.W2 step as gather segments of S4's operand A (split formats):
+    // every cell (row piece, K piece) of every task is one output rectangle
+    // (its terms) or zero, and the K tail of the last K tile is zero, so the
+    // GEMM that forms A itself writes every element it multiplies
+    if (P->planes == 3) {
+        JobBuilder bT;
+        for (size_t t = 0; t < tM.size(); ++t) bT.task(tM[t], tK[t]);
+        std::vector<std::set<std::pair<int64_t, int64_t>>> covered_cells(tM.size());
+        for (const W12Cell& cell : P->jW.cells)
+            for (int o = cell.out0; o < cell.out0 + cell.nout; ++o) {
+                const W12Out& out = P->jW.outs[(size_t)o];
+                std::vector<GatherTerm> tm;
+                for (int j = out.t0; j < out.t1; ++j) {
+                    const tnh::W12Term& w = P->jW.terms[(size_t)j];
+                    tm.push_back(GatherTerm{w.coef, w.base, w.ld, 1, w.coef32});
+                }
+                bT.rect(out.task, out.row0, out.col0, cell.Da, rup(cell.Db, 4), tm);
+                covered_cells[(size_t)out.task].insert({out.row0, out.col0});
+            }
+        for (size_t t = 0; t < tM.size(); ++t) {
+            for (const auto& rp : trows[t])
+                for (const auto& kq : tkp[t])
+                    if (!covered_cells[t].count({rp.first, kq.first}))
+                        bT.rect((int)t, rp.first, kq.first, rp.second, kq.second, {}, true);
+            const int64_t Kp = rup(tK[t], kGatherCols);
+            if (Kp > tK[t]) bT.rect((int)t, 0, tK[t], tM[t], Kp - tK[t], {}, true);
+        }
+        bT.finish(P->jT, s);
+    }
     GatherJob jL, jR;
     bL.finish(jL, s);
     bR.finish(jR, s);
@@ -1218,9 +1290,9 @@ cudaGraphNode_t last_node(cudaStream_t s) {
 // recorded with the position of that pointer among their arguments:
 // gather_kernel(tiles, segs, terms, geom, src, dst) reads x as argument 4;
 // y is written by gemm_f64_kernel(tasks, ntasks, A, B, C, row_off) as
-// argument 4, gemm_tc_kernel(tasks, ntasks, tiles, A, B, C, err, row_off) as
-// argument 5, or splitk_reduce(reds, blocks, part, out, row_off) as
-// argument 3.
+// argument 4, gemm_tc_kernel(tasks, ntasks, tiles, A, B, C, err, row_off,
+// atiles, asegs, aterms, asrc) as argument 5, or splitk_reduce(reds, blocks,
+// part, out, row_off) as argument 3.
 void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_t s, HeffPlan::Graph* G) {
     const int n1 = (int)P.g1.f64.size(), n4 = (int)P.g4.f64.size();
     if (f64) {
@@ -1250,12 +1322,13 @@ void launch_chain(HeffPlan& P, bool f64, const double* x, double* y, cudaStream_
         launch_gather(P.jX, P.oX.d_gtc.as<OpGeom>(), x, P.opX.p, P.planes, s, "heff_pack_x");
         if (G) G->nx = last_node(s);
         launch_stage(P.g1, P, P.Ltc.as<uint16_t>(), P.opX.as<uint16_t>(), P.t1.p, nullptr, s);
-        launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, P.planes, s);
-        launch_stage(P.g4, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y, P.row_off.as<int64_t>(), s);
+        if (!P.fusedS4) launch_w12(P.jW, P.oT.d_gtc.as<OpGeom>(), P.t1.as<float>(), P.opTtc.p, P.planes, s);
+        launch_stage(P.g4, P, P.opTtc.as<uint16_t>(), P.Rtc.as<uint16_t>(), y, P.row_off.as<int64_t>(), s,
+                     P.fusedS4);
         if (G) {
             G->ny = last_node(s);
             G->iy = P.g4.split > 1 ? 3 : 5;
-            G->ny_args = P.g4.split > 1 ? 5 : 8;
+            G->ny_args = P.g4.split > 1 ? 5 : 12;
         }
     }
 }
@@ -1472,6 +1545,7 @@ tnh_status tnh_heff_tuning(const tnh_heff* plan, int32_t* choice) {
         choice[4] = P->tune_measured ? 1 : 0;
         choice[5] = P->strategy;
         choice[6] = P->strategy_measured ? 1 : 0;
+        choice[7] = P->fusedS4 ? 1 : 0;
     });
 }
 

@@ -60,6 +60,8 @@ struct HeffPlan {
     HeffOperand oL, oX, oT, oR;
     GatherJob jX;           // per application: pack psi
     W12Job jW;              // per application: fused S2+S3
+    GatherJob jT;           // the same step as segments of S4's operand A tiles, formed inside S4 (three planes)
+    bool fusedS4 = false;   // S4 forms its operand A from T1 itself (no separate W1.W2 pass)
     HeffGemm g1, g4;
     DevBuf L64, Ltc, R64, Rtc;   // L and R packed once
     DevBuf opX;             // operand B of S1 (either format)
@@ -70,7 +72,7 @@ struct HeffPlan {
     DevBuf part64;          // float64 partial slabs of K-split FP64 GEMMs
     int64_t t1_elems = 0;
     bool zero_y = false;    // some output rows are written by no S4 task
-    std::array<int, 4> tune{0, 1, 0, 1};   // tile policy / K split of S1, then of S4
+    std::array<int, 5> tune{0, 1, 0, 1, 0};   // tile policy / K split of S1, then of S4; S4 fused
     bool tune_measured = false;            // chosen by timing in this plan (not cached or forced)
     int strategy = 0;                      // 0: combine, then contract; 1: block pairs (make_heff)
     bool strategy_measured = false;        // both strategies were timed for this plan

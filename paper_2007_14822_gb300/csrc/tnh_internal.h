@@ -173,7 +173,7 @@ struct Ctx {
     std::unique_ptr<Profiler> prof;
     // H_eff GEMM choices of the plan autotuner (tile policy and K split of S1,
     // then of S4) by shape signature; loaded from TNH_TUNE_CACHE once
-    std::map<std::vector<int>, std::array<int, 4>> heff_tune;
+    std::map<std::vector<int>, std::array<int, 5>> heff_tune;
     bool tune_loaded = false;
     // H_eff block-contraction strategy (0 combine, 1 block pairs) by shape
     std::map<std::vector<int>, int> heff_strategy;

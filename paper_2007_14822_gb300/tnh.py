@@ -524,11 +524,11 @@ class Heff:
     @property
     def tuning(self):
         """The plan's choices: {'tiles_s1', 'split_s1', 'tiles_s4', 'split_s4',
-        'measured', 'strategy', 'strategy_measured'} (see tnh_heff_tuning)."""
-        c = (C.c_int32 * 7)()
+        'measured', 'strategy', 'strategy_measured', 'fused_s4'} (see tnh_heff_tuning)."""
+        c = (C.c_int32 * 8)()
         self.ctx.check(self.ctx._lib.tnh_heff_tuning(self.h, c))
         return {"tiles_s1": c[0], "split_s1": c[1], "tiles_s4": c[2], "split_s4": c[3], "measured": bool(c[4]),
-                "strategy": c[5], "strategy_measured": bool(c[6])}
+                "strategy": c[5], "strategy_measured": bool(c[6]), "fused_s4": bool(c[7])}
 
     def diag(self, out):
         """Diagonal of the MPO part of H_eff into ``out`` (CUDA float64 [n])."""

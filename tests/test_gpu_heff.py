@@ -491,7 +491,20 @@ def test_heff_qn_workloads_full_size(ctx, which):
         assert plan.flops == pytest.approx(bench.chain_flops(*args, H.to_oracle(psi)), rel=1e-12)
     want = D.heff_apply(*args, H.to_oracle(psi))
     scale = heff_scale(*args, H.to_oracle(psi))
-    for p, y in (("fp64", y64), ("bf16x6", ymx)):
+    results = [("fp64", y64), ("bf16x6", ymx)]
+    # the other S4 form of the split precision (the tuned plan used one)
+    import os
+    os.environ["TNH_HEFF_FUSED"] = "0" if plan.tuning["fused_s4"] else "1"
+    try:
+        plan2 = ctx.heff_plan(L, W1, W2, R, psi, prec("bf16x6"))
+    finally:
+        del os.environ["TNH_HEFF_FUSED"]
+    assert plan2.tuning["fused_s4"] != plan.tuning["fused_s4"]
+    y2 = torch.zeros_like(x)
+    for _ in range(3):
+        plan2.apply(x, y2)
+    results.append(("bf16x6", y2))
+    for p, y in results:
         yt = psi.with_inds(psi.inds)
         yt.data = y
         err, rep = H.assert_parity(H.to_oracle(yt), want, scale, p, TOL[p])
@@ -508,6 +521,31 @@ def test_heff_block_strategies_match_oracle(ctx, strategy, p, m, nsect, maxd, mo
     err, plan = _heff_case(ctx, m, nsect, p, maxd=maxd)
     t = plan.tuning
     assert t["strategy"] == int(strategy) and not t["strategy_measured"]
+
+
+@pytest.mark.parametrize("strategy", ["0", "1"])
+@pytest.mark.parametrize("split", ["1,1", "1,3", "2,8"])
+@pytest.mark.parametrize("m,nsect,maxd", [(64, 9, 16), (300, 15, 60), (70, 1, 70), (200, 5, 90)])
+def test_heff_s4_forming_its_operand_matches_oracle(ctx, strategy, split, m, nsect, maxd, monkeypatch):
+    # S4 forms its operand A from T1 inside the GEMM (the W1.W2 step fused),
+    # alone, with K splits and with both block strategies, against the oracle
+    monkeypatch.setenv("TNH_HEFF_FUSED", "1")
+    monkeypatch.setenv("TNH_HEFF_SPLIT", split)
+    monkeypatch.setenv("TNH_HEFF_STRATEGY", strategy)
+    err, plan = _heff_case(ctx, m, nsect, "bf16x6", maxd=maxd)
+    assert plan.tuning["fused_s4"]
+
+
+@pytest.mark.parametrize("model,j", [("j1j2", 0), ("j1j2", 3), ("hubbard", 2)])
+def test_heff_s4_forming_its_operand_distinct_mpo_tensors(ctx, model, j, monkeypatch):
+    monkeypatch.setenv("TNH_HEFF_FUSED", "1")
+    test_heff_distinct_mpo_tensors(ctx, model, j, "bf16x6")
+
+
+def test_heff_s4_forming_its_operand_graph_replay(ctx, monkeypatch):
+    monkeypatch.setenv("TNH_HEFF_FUSED", "1")
+    test_heff_graph_replay_with_new_buffers(ctx, "bf16x6", 40, 7, 12, None, monkeypatch)
+    test_heff_graph_replay_with_new_buffers(ctx, "bf16x6", 300, 3, 200, "2,4", monkeypatch)
 
 
 @pytest.mark.parametrize("model,j", [("j1j2", 3), ("hubbard", 2)])
