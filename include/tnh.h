@@ -152,6 +152,16 @@ tnh_status tnh_debug_fail_alloc(int64_t k);
 tnh_status tnh_debug_pool_used(tnh_ctx* ctx, uint64_t* bytes);
 tnh_status tnh_debug_wait_timeout(tnh_ctx* ctx, uint64_t limit_ns);
 
+/* tnh_debug_convert_check (test support): the packers round float64 inputs to
+ * float32, and the epilogues widen float32 results to float64, with integer
+ * operations (IEEE 754 binary32/binary64 formats; round to nearest, ties to
+ * even) instead of the float64 pipe. This call runs both on n bit patterns
+ * from a SplitMix64 counter generator seeded with seed (uniform patterns,
+ * exponents across and beyond the float32 range, exact ties, the top binade)
+ * and writes to *mismatches how many results differ in their bits from the
+ * GPU's own conversion (NaN equals NaN). Synchronises the stream. */
+tnh_status tnh_debug_convert_check(tnh_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* mismatches);
+
 /* ---- layout helper (host only, no device work) ------------------------- */
 
 /* Enumerate the blocks of a tensor with the given indices and flux (Sec. 8.3:

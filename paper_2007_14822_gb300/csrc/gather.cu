@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gather.h"
 #include "prof.h"
@@ -39,7 +40,11 @@ namespace tnh {
 namespace {
 
 constexpr int kPitch = kGatherCols + 1;   // padded smem row (doubles)
-constexpr int kSmemBytes = (kGatherRows / 2) * kPitch * 8;
+// one CTA builds a quarter (32 rows) of a tile: four times the CTAs of one
+// per tile, so that the few tiles of a ψ pack still fill the SMs
+constexpr int kTileParts = 4;
+constexpr int kPartRows = kGatherRows / kTileParts;
+constexpr int kSmemBytes = kPartRows * kPitch * 8;
 
 // x = hi + mid + lo, each part rounded to nearest bfloat16; float32
 // arithmetic (exact residuals), the float64 units of this GPU being scarce
@@ -66,9 +71,15 @@ __device__ __forceinline__ typename Acc<kF64>::T coef_of(const GatherTerm& g) {
     if constexpr (kF64) return g.coef; else return g.coef32;
 }
 
-// One CTA builds one half (64 rows) of a 128 x 64 tile: CTA 2t + h owns
-// rows [64 h, 64 h + 64) of tile t.
-constexpr int kHalfRows = kGatherRows / 2;
+// source element -> accumulation type; float64 sources are rounded to float32
+// on the integer pipes
+template <class AccT, class SrcT>
+__device__ __forceinline__ AccT to_acc(SrcT x) {
+    if constexpr (std::is_same<AccT, float>::value && std::is_same<SrcT, double>::value) return f64_to_f32_rn(x);
+    else return (AccT)x;
+}
+
+// CTA kTileParts t + h builds rows [kPartRows h, kPartRows (h + 1)) of tile t.
 
 template <class SrcT, bool kF64, int P>
 __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restrict__ tiles,
@@ -78,15 +89,15 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
                                                      const SrcT* __restrict__ src, void* __restrict__ dst) {
     using AccT = typename Acc<kF64>::T;
     extern __shared__ double tile_raw[];
-    AccT* tile_s = reinterpret_cast<AccT*>(tile_raw);   // [kHalfRows][kPitch]
-    const GatherTile T = tiles[blockIdx.x >> 1];
-    const int h0 = (blockIdx.x & 1) * kHalfRows;         // first tile row of this CTA
-    for (int e = threadIdx.x; e < kHalfRows * kPitch; e += blockDim.x) tile_s[e] = AccT(0);
+    AccT* tile_s = reinterpret_cast<AccT*>(tile_raw);   // [kPartRows][kPitch]
+    const GatherTile T = tiles[blockIdx.x / kTileParts];
+    const int h0 = (blockIdx.x % kTileParts) * kPartRows;   // first tile row of this CTA
+    for (int e = threadIdx.x; e < kPartRows * kPitch; e += blockDim.x) tile_s[e] = AccT(0);
     __syncthreads();
     for (int si = T.seg0; si < T.seg1; ++si) {
         const GatherSeg S = segs[si];
         // rows of the segment inside this half
-        const int rb = max(0, h0 - S.r0), re = min(S.nr, h0 + kHalfRows - S.r0);
+        const int rb = max(0, h0 - S.r0), re = min(S.nr, h0 + kPartRows - S.r0);
         if (rb >= re) continue;
         const int nr = re - rb;
         const int n = nr * S.nc;
@@ -108,7 +119,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
                     }
                     r += rb;
                     pos[u] = e < n ? (S.r0 + r - h0) * kPitch + S.c0 + c : -1;
-                    v[u] = e < n ? cf * (AccT)src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs] : AccT(0);
+                    v[u] = e < n ? cf * to_acc<AccT>(src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs]) : AccT(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
@@ -124,7 +135,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
             AccT v = AccT(0);
             for (int j = S.t0; j < S.t1; ++j) {
                 const GatherTerm& g = terms[j];
-                v += coef_of<kF64>(g) * (AccT)src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs];
+                v += coef_of<kF64>(g) * to_acc<AccT>(src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs]);
             }
             tile_s[(S.r0 + r - h0) * kPitch + S.c0 + c] = v;
         }
@@ -134,7 +145,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
     if constexpr (kF64) {
         double* d = static_cast<double*>(dst) + G.base + ((int64_t)T.mi * kGatherRows + h0) * G.ld +
                     (int64_t)T.ki * kGatherCols;
-        for (int e = threadIdx.x; e < kHalfRows * kGatherCols; e += blockDim.x) {
+        for (int e = threadIdx.x; e < kPartRows * kGatherCols; e += blockDim.x) {
             const int r = e / kGatherCols, c = e - r * kGatherCols;
             d[(int64_t)r * G.ld + c] = tile_s[r * kPitch + c];
         }
@@ -143,7 +154,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTile* __restric
         // 16-byte chunk j of row r holds k-group j ^ (r & 7) (128-byte swizzle)
         uint16_t* d = static_cast<uint16_t*>(dst) +
                       (G.base + (int64_t)T.mi * G.ld + T.ki) * (int64_t)(P * kTcTileElems);
-        for (int ci = threadIdx.x; ci < kHalfRows * 8; ci += blockDim.x) {
+        for (int ci = threadIdx.x; ci < kPartRows * 8; ci += blockDim.x) {
             const int rl = ci >> 3, j = ci & 7, r = h0 + rl;
             const int kg = j ^ (r & 7);
             const float* v = tile_s + rl * kPitch + kg * 8;
@@ -176,6 +187,11 @@ __device__ __forceinline__ void load4(const double* p, double* v) {
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
 }
 
+// outputs and terms of one cell staged in shared memory (cells with more read
+// them from global memory)
+constexpr int kW12StageOuts = 96;
+constexpr int kW12StageTerms = 384;
+
 template <class SrcT, bool kF64, int P>
 __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restrict__ ctas,
                                                           const W12Cell* __restrict__ cells,
@@ -185,8 +201,21 @@ __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restri
                                                           const OpGeom* __restrict__ geom,
                                                           const SrcT* __restrict__ src, void* __restrict__ dst) {
     using AccT = typename Acc<kF64>::T;
+    __shared__ W12Out s_out[kW12StageOuts];
+    __shared__ W12Term s_term[kW12StageTerms];
     const W12Cta T = ctas[blockIdx.x];
     const W12Cell C = cells[T.cell];
+    // the terms of a cell's outputs are contiguous, in output order
+    const int tb = C.nout > 0 ? outs[C.out0].t0 : 0;
+    const int nterm = C.nout > 0 ? outs[C.out0 + C.nout - 1].t1 - tb : 0;
+    const bool staged = C.nout <= kW12StageOuts && nterm <= kW12StageTerms;
+    if (staged) {
+        for (int k = threadIdx.x; k < C.nout; k += blockDim.x) s_out[k] = outs[C.out0 + k];
+        for (int k = threadIdx.x; k < nterm; k += blockDim.x) s_term[k] = terms[tb + k];
+    }
+    __syncthreads();
+    const W12Out* po = staged ? s_out : outs + C.out0;
+    const W12Term* pt = staged ? s_term : terms + tb;
     const int dbq = (C.Db + 3) >> 2;
     const int q = T.q0 + (int)threadIdx.x;
     if (q >= C.Da * dbq) return;
@@ -214,19 +243,31 @@ __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restri
     };
     // T1 rows are padded to multiples of 4 columns with zeros (S1 multiplies
     // zero rows of its psi operand there): four loads never leave the row's
-    // padded segment
-    auto term = [&](int j, AccT* v) {
-        const W12Term t = terms[j];
-        SrcT x[4];
-        load4(src + t.base + (int64_t)r * t.ld + c, x);
-        const AccT cf = kF64 ? (AccT)t.coef : (AccT)t.coef32;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = fma(cf, (AccT)x[u], v[u]);
-    };
+    // padded segment. The loads of up to kB terms are issued together; the
+    // sums run in term order.
+    constexpr int kB = 4;
     for (int o = 0; o < C.nout; ++o) {
-        const W12Out O = outs[C.out0 + o];
+        const W12Out O = po[o];
         AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
-        for (int j = O.t0; j < O.t1; ++j) term(j, v);
+        for (int j0 = O.t0 - tb; j0 < O.t1 - tb; j0 += kB) {
+            const int nb = min(kB, O.t1 - tb - j0);
+            SrcT x[kB][4];
+            AccT cf[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                if (u < nb) {
+                    const W12Term& t = pt[j0 + u];
+                    load4(src + t.base + (int64_t)r * t.ld + c, x[u]);
+                    cf[u] = kF64 ? (AccT)t.coef : (AccT)t.coef32;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                if (u < nb) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) v[k] = fma(cf[u], (AccT)x[u][k], v[k]);
+                }
+        }
         store(O, v);
     }
 }
@@ -256,7 +297,7 @@ void launch_one(const GatherJob& J, const OpGeom* geom, const SrcT* src, void* d
                                         kSmemBytes));
         configured = true;
     }
-    gather_kernel<SrcT, kF64, P><<<2 * J.ntiles, 256, kSmemBytes, s>>>(
+    gather_kernel<SrcT, kF64, P><<<kTileParts * J.ntiles, 256, kSmemBytes, s>>>(
         J.d_tiles.as<GatherTile>(), J.d_segs.as<GatherSeg>(), J.d_terms.as<GatherTerm>(), geom, src, dst);
 }
 

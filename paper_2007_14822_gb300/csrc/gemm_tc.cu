@@ -31,6 +31,8 @@
 // Every wait is bounded (ptx::mbar_wait); a timeout sets the device error flag.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "gather.h"
 #include "prof.h"
 #include "ptx.cuh"
@@ -420,9 +422,7 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
                     if (nv <= 0) break;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const double v = (double)acc[pass * 16 + j];
-                        buf[lane * 33 + 2 * j] = (uint32_t)__double2loint(v);
-                        buf[lane * 33 + 2 * j + 1] = (uint32_t)__double2hiint(v);
+                        f32_to_f64_words(acc[pass * 16 + j], buf[lane * 33 + 2 * j + 1], buf[lane * 33 + 2 * j]);
                     }
                     __syncwarp();
                     const int j = lane & 15;
@@ -465,26 +465,61 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
 }
 
 // K-split reduction: block b sums rows [m0, m1) of one reduction R over its
-// S float32 (or float64) partial slabs [S][M][N], in slab order, and writes
-// them to the output rows (scattered by row_off, or at c_base + m ldc).
+// S partial slabs [S][M][N], in slab order, and writes them to the output rows
+// (scattered by row_off, or at c_base + m ldc). float32 partials (the
+// split-bfloat16 GEMM, itself accumulating in float32) are summed in float32
+// and widened to float64 on the integer pipes; float64 partials in float64. A
+// thread takes kE elements and issues their loads of one slab together, so a
+// block waits S load latencies, not S times its element count.
 template <class PartT>
 __global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds,
                                                      const RedBlock* __restrict__ blocks,
                                                      const PartT* __restrict__ part, void* __restrict__ out,
                                                      const int64_t* __restrict__ row_off) {
+    constexpr int kE = 8;
     const RedBlock b = blocks[blockIdx.x];
     const SplitRed R = reds[b.red];
     const int64_t mn = (int64_t)R.M * R.N;
     const int nel = (b.m1 - b.m0) * R.N;
+    if (nel <= 0) return;
     const PartT* p0 = part + R.part + (int64_t)b.m0 * R.N;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-        const int ml = e / R.N, n = e - ml * R.N, m = b.m0 + ml;
-        const PartT* p = p0 + e;
-        double acc = 0.0;
-        for (int j = 0; j < R.S; ++j) acc += (double)__ldg(p + j * mn);
-        if (R.use_roff) static_cast<double*>(out)[__ldg(row_off + R.roff + m) + n] = acc;
-        else if (R.out_f32) static_cast<float*>(out)[R.c_base + (int64_t)m * R.ldc + n] = (float)acc;
-        else static_cast<double*>(out)[R.c_base + (int64_t)m * R.ldc + n] = acc;
+    // (row, column) of this thread's first element and the step between its
+    // elements (256 apart), without a division per element
+    const int dm = 256 / R.N, dn = 256 - dm * R.N;
+    for (int base = 0; base < nel; base += kE * 256) {
+        int ml = (base + (int)threadIdx.x) / R.N, n = base + (int)threadIdx.x - ml * R.N;
+        int64_t dst[kE];
+        PartT acc[kE];
+#pragma unroll
+        for (int i = 0; i < kE; ++i) {
+            const int e = base + i * 256 + threadIdx.x;
+            acc[i] = PartT(0);
+            dst[i] = -1;
+            if (e < nel) {
+                const int m = b.m0 + ml;
+                dst[i] = R.use_roff ? __ldg(row_off + R.roff + m) + n : R.c_base + (int64_t)m * R.ldc + n;
+            }
+            ml += dm;
+            n += dn;
+            if (n >= R.N) { n -= R.N; ++ml; }
+        }
+        for (int j = 0; j < R.S; ++j) {
+            PartT v[kE];
+#pragma unroll
+            for (int i = 0; i < kE; ++i) {
+                const int e = base + i * 256 + threadIdx.x;
+                v[i] = e < nel ? __ldg(p0 + j * mn + e) : PartT(0);
+            }
+#pragma unroll
+            for (int i = 0; i < kE; ++i) acc[i] += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kE; ++i) {
+            if (dst[i] < 0) continue;
+            if (R.out_f32) static_cast<float*>(out)[dst[i]] = (float)acc[i];
+            else if constexpr (std::is_same<PartT, float>::value) static_cast<double*>(out)[dst[i]] = f32_to_f64(acc[i]);
+            else static_cast<double*>(out)[dst[i]] = acc[i];
+        }
     }
 }
 

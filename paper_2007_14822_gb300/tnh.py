@@ -30,7 +30,7 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
            "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
            "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag",
-           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout", "tnh_heff_tuning",
+           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout", "tnh_debug_convert_check", "tnh_heff_tuning",
            "tnh_dmrg_checkpoint", "tnh_dmrg_resume", "tnh_dmrg_position", "tnh_tridiag_lowest"]
 
 
@@ -130,6 +130,7 @@ def lib():
         "tnh_debug_fail_alloc": (i32, [i64]),
         "tnh_debug_pool_used": (i32, [vp, P(C.c_uint64)]),
         "tnh_debug_wait_timeout": (i32, [vp, C.c_uint64]),
+        "tnh_debug_convert_check": (i32, [vp, C.c_uint64, C.c_uint64, P(C.c_uint64)]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -322,6 +323,13 @@ class Context:
     def debug_wait_timeout(self, limit_ns):
         """A bounded device wait that nothing completes: raises TNH_ERR_TIMEOUT."""
         self.check(self._lib.tnh_debug_wait_timeout(self.h, int(limit_ns)))
+
+    def debug_convert_check(self, n, seed=0):
+        """Mismatches of the integer-path float32/float64 conversions against
+        the GPU's own conversion on n generated bit patterns (syncs)."""
+        v = C.c_uint64()
+        self.check(self._lib.tnh_debug_convert_check(self.h, int(n), int(seed), C.byref(v)))
+        return v.value
 
     def profile_begin(self):
         self.check(self._lib.tnh_profile_begin(self.h))
