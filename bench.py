@@ -686,7 +686,7 @@ def source_sha(files):
     return h.hexdigest()
 
 
-KERNEL_SOURCES = {"gemm_tc": ["gemm_tc.cu", "ptx.cuh", "tnh_internal.h"],
+KERNEL_SOURCES = {"gemm_tc": ["gemm_tc.cu", "ptx.cuh", "split.cuh", "tnh_internal.h"],
                   "heff_w12": ["gather.cu", "gather.h"], "heff_pack_x": ["gather.cu", "gather.h"]}
 
 

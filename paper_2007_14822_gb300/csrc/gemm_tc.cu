@@ -11,9 +11,7 @@
 //   warp 0      producer: bulk-copies the P A-tiles and P B-tiles of one
 //               64-wide K block into a shared-memory stage (TMA engine,
 //               mbarrier complete_tx); operands arrive pre-tiled and
-//               pre-swizzled from the packer, one 16 KB copy per tile. It
-//               prefetches the K blocks three steps ahead into L2, so the
-//               two stages are refilled from L2 rather than from HBM.
+//               pre-swizzled from the packer, one 16 KB copy per tile.
 //   warp 1      MMA issuer: one thread issues tcgen05.mma (M=128, N=128,
 //               K=16) into tensor memory; hh goes to its own accumulator,
 //               the cross products to a second one, so the large partial
@@ -138,35 +136,6 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            // L2 prefetch kPrefetch K blocks ahead of the copies (along this
-            // CTA's own sequence of tiles), so that the copies into the two
-            // stages are served from L2
-            int ptile = blockIdx.x, pkb = 0, pkt = 0;
-            const GemmTask* pt = nullptr;
-            auto pf_step = [&]() {
-                if (ptile >= total_tiles) return;
-                if (pt == nullptr) {
-                    pt = &tasks[find_task(tasks, ntasks, ptile)];
-                    pkt = pt->kt;
-                }
-                const int local = ptile - pt->tile0;
-                const int mi = local / pt->nt, ni = local - mi * pt->nt;
-                const int ks = pt->kstride ? pt->kstride : pt->kt;
-                const int tn = pt->tn ? pt->tn : kTcTileN;
-                const int bt = (ni * tn) >> 7, boff = ((ni * tn) & 127) * 64;
-                const uint16_t* b = B + (pt->b_base + (int64_t)bt * ks + pkb) * P * kTcTileElems + boff;
-                if (!kFusedA) ptx::bulk_prefetch_l2(A + (pt->a_base + (int64_t)mi * ks + pkb) * P * kTcTileElems,
-                                                    P * kTileBytes);
-#pragma unroll
-                for (int p = 0; p < P; ++p) ptx::bulk_prefetch_l2(b + (int64_t)p * kTcTileElems, (uint32_t)tn * 128u);
-                if (++pkb == pkt) {
-                    pkb = 0;
-                    ptile += gridDim.x;
-                    pt = nullptr;
-                }
-            };
-            constexpr int kPrefetch = 3;
-            for (int i = 0; i < kPrefetch; ++i) pf_step();
             for (int tile = blockIdx.x; ok && tile < total_tiles; tile += gridDim.x) {
                 const GemmTask& t = tasks[find_task(tasks, ntasks, tile)];
                 const int local = tile - t.tile0;
@@ -181,7 +150,6 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
                 const uint16_t* a = A + (t.a_base + (int64_t)mi * ks) * P * kTcTileElems;
                 const uint16_t* b = B + (t.b_base + (int64_t)bt * ks) * P * kTcTileElems + boff;
                 for (int kb = 0; kb < t.kt; ++kb) {
-                    pf_step();
                     if (!ptx::mbar_wait(&empty[stage], phase ^ 1u, err, 1)) { ok = false; break; }
                     ptx::mbar_expect_tx(&full[stage], P * ((kFusedA ? 0u : (uint32_t)kTileBytes) + bbytes));
                     if (!kFusedA) {

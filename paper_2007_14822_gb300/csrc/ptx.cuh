@@ -79,11 +79,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// Prefetch bytes (16-byte aligned, a multiple of 16) of global memory into L2.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // Bulk copy shared -> global on the TMA engine, in this thread's bulk async
 // group; both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
