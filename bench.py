@@ -674,7 +674,11 @@ def max_over_ranks(x, dist, device):
 # from one ncu capture of the headline workload, with the SHA-256 of the
 # kernel's sources at capture time: the figure is reported only while the
 # sources are unchanged.
-TRAFFIC = {}
+TRAFFIC = {
+    # S1 79.04 + 96.38 MB, S4 324.23 + 15.82 MB (profiles/heff_cylinder_m2048_bf16x6.md): the mean of the two
+    "gemm_tc_bf16x6": {"bytes_per_launch": (79.040256 + 96.377856 + 324.230656 + 15.819776) / 2 * 1e6,
+                       "source_sha": "86845ec4d1d176bb8f18993336cf6fed96cab92d90634093883be0cdbb23de78"},
+}
 
 
 def source_sha(files):
@@ -701,6 +705,7 @@ def kernel_traffic(name):
 
 
 HEAD = QN_CONFIGS[1]   # the J1-J2 cylinder, m = 2048
+HEAD_CHOICES = {"cylinder": QN_CONFIGS[1], "u1": QN_CONFIGS[0], "hubbard": QN_CONFIGS[2]}
 
 
 def time_heff_steps(torch, plan, x, y, steps, flush, host=None):
@@ -751,15 +756,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads and the sweeps")
+    ap.add_argument("--heff-workload", default="cylinder", choices=list(HEAD_CHOICES),
+                    help="the block-sparse H_eff workload of the headline line (default: the J1-J2 cylinder at "
+                         "m=2048, the configuration the metric is quoted on; the others are for profiling)")
     ap.add_argument("--oracle-matvec", default="heis,hub",
                     help="extra block-sparse workloads whose H_eff product is also timed on the oracle (comma "
                          "list of heis, hub; the Hubbard one takes tens of seconds on the host)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
-    wname, wkind, wm, wrecipe, wseed = HEAD
-    config = {"workload": f"H_eff.psi, {wname} (bulk sites 62/63 of the 6x24 cylinder, seeded N(0,1) blocks, "
-                          f"seed {wseed})",
+    head = HEAD_CHOICES[args.heff_workload]
+    wname, wkind, wm, wrecipe, wseed = head
+    where = "bulk sites 62/63 of the 6x24 cylinder, " if wkind == "cyl" else ""
+    config = {"workload": f"H_eff.psi, {wname} ({where}seeded N(0,1) blocks, seed {wseed})",
               "step": "one BF16x6 application y = H_eff x (graph replay: pack psi, S1, fused W1.W2, S4)",
               "l2": "flushed before every timed step (256 MB write)",
               "parallelism": f"replicas x{world}"}
