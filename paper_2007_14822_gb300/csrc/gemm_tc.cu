@@ -334,38 +334,37 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
             uint32_t* buf = stage_all + (warp - 2) * kStageWords;
             // float32 rows that start on 16-byte boundaries and end on them
             // (every row of a float32 result without scatter whose base,
-            // pitch and width are multiples of 4) leave by bulk copies
-            const bool bulk = t.c_f32 && !t.use_roff && ((t.c_base | (int64_t)t.ldc | (int64_t)t.N) & 3) == 0;
-            // the previous tile's bulk copies must have read the stage
-            ptx::bulk_wait_read();
-            __syncwarp();
+            // pitch and width are multiples of 4) leave by 16-byte stores
+            const bool vec4 = t.c_f32 && !t.use_roff && ((t.c_base | (int64_t)t.ldc | (int64_t)t.N) & 3) == 0;
             if (ncols == 0) {
                 // nothing to store for this warp
-            } else if (bulk) {
-                // 16 rows at a time (lanes 0-15, then 16-31) go to the stage
-                // as 16-byte rows of 36 words; every lane copies its own row
+            } else if (vec4) {
+                // aligned float32 rows: the 32 x 32 block goes through the
+                // stage (a row per lane), then every lane stores 16 bytes of
+                // one of four rows per step: eight 128-byte row segments per
+                // store instruction, and no wait on a copy engine
                 float* Cf = reinterpret_cast<float*>(C);
-                float* sb = reinterpret_cast<float*>(buf) + (lane & 15) * 36;
+                const int cq = (lane & 7) * 4, rsub = lane >> 3;
 #pragma unroll
                 for (int pass = 0; pass < kCols / 32; ++pass) {
                     const int c0 = n0 + pass * 32, nv = nend - c0;
                     if (nv <= 0) break;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        ptx::bulk_wait_read();
-                        __syncwarp();
-                        if ((lane >> 4) == h) {
-                            float4* row = reinterpret_cast<float4*>(sb);
+                    for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __float_as_uint(acc[pass * 32 + j]);
+                    __syncwarp();
 #pragma unroll
-                            for (int q4 = 0; q4 < 8; ++q4)
-                                row[q4] = make_float4(acc[pass * 32 + 4 * q4], acc[pass * 32 + 4 * q4 + 1],
-                                                      acc[pass * 32 + 4 * q4 + 2], acc[pass * 32 + 4 * q4 + 3]);
-                            ptx::fence_proxy_async_smem();
-                            if (mrow) ptx::bulk_s2g(Cf + rb + c0, sb, (uint32_t)min(nv, 32) * 4u);
-                            ptx::bulk_commit();
+                    for (int k = 0; k < 8; ++k) {
+                        const int row = 4 * k + rsub;
+                        const int64_t rbr = __shfl_sync(0xffffffffu, rb, row);
+                        const int ok = __shfl_sync(0xffffffffu, mrow, row);
+                        if (ok && cq < nv) {
+                            const uint32_t* b = buf + row * 33 + cq;
+                            *reinterpret_cast<float4*>(Cf + rbr + c0 + cq) =
+                                make_float4(__uint_as_float(b[0]), __uint_as_float(b[1]), __uint_as_float(b[2]),
+                                            __uint_as_float(b[3]));
                         }
-                        __syncwarp();
                     }
+                    __syncwarp();
                 }
             } else if (t.c_f32) {
                 float* Cf = reinterpret_cast<float*>(C);
@@ -406,8 +405,6 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
             }
         }
     }
-    // the bulk copies of the epilogue have completed before the CTA ends
-    if (warp >= 2) ptx::bulk_wait();
     __syncthreads();
     if (warp == 0) {
         ptx::tc_fence_after();
