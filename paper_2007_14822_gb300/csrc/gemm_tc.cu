@@ -334,8 +334,10 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
             uint32_t* buf = stage_all + (warp - 2) * kStageWords;
             // float32 rows that start on 16-byte boundaries and end on them
             // (every row of a float32 result without scatter whose base,
-            // pitch and width are multiples of 4) leave by 16-byte stores
-            const bool vec4 = t.c_f32 && !t.use_roff && ((t.c_base | (int64_t)t.ldc | (int64_t)t.N) & 3) == 0;
+            // pitch and width are multiples of 4, in a 16-byte-aligned
+            // output) leave by 16-byte stores
+            const bool vec4 = t.c_f32 && !t.use_roff && ((t.c_base | (int64_t)t.ldc | (int64_t)t.N) & 3) == 0 &&
+                              (reinterpret_cast<uintptr_t>(C) & 15) == 0;
             if (ncols == 0) {
                 // nothing to store for this warp
             } else if (vec4) {
@@ -392,13 +394,28 @@ __global__ void __launch_bounds__(kFusedA ? kThreadsFused : kThreads, 1)
                         f32_to_f64_words(acc[pass * 16 + j], buf[lane * 33 + 2 * j + 1], buf[lane * 33 + 2 * j]);
                     }
                     __syncwarp();
-                    const int j = lane & 15;
-                    for (int r = 0; r < 32; r += 2) {
-                        const int rr = r + (lane >> 4);
-                        const int64_t rbr = __shfl_sync(0xffffffffu, rb, rr);
-                        const int ok = __shfl_sync(0xffffffffu, mrow, rr);
-                        if (ok && j < nv)
-                            C[rbr + c0 + j] = __hiloint2double((int)buf[rr * 33 + 2 * j + 1], (int)buf[rr * 33 + 2 * j]);
+                    // four rows per step, a lane two consecutive doubles of one
+                    // row: one 16-byte store where the pair's address is on a
+                    // 16-byte boundary (scattered rows start anywhere, and the
+                    // output itself may start on any 8-byte boundary), else two
+                    const int j0 = 2 * (lane & 7);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int row = 4 * k + (lane >> 3);
+                        const int64_t rbr = __shfl_sync(0xffffffffu, rb, row);
+                        const int ok = __shfl_sync(0xffffffffu, mrow, row);
+                        if (ok && j0 < nv) {
+                            const uint32_t* b = buf + row * 33 + 2 * j0;
+                            const double d0 = __hiloint2double((int)b[1], (int)b[0]);
+                            const double d1 = __hiloint2double((int)b[3], (int)b[2]);
+                            double* p = C + rbr + c0 + j0;
+                            if (j0 + 1 < nv && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+                                *reinterpret_cast<double2*>(p) = make_double2(d0, d1);
+                            } else {
+                                p[0] = d0;
+                                if (j0 + 1 < nv) p[1] = d1;
+                            }
+                        }
                     }
                     __syncwarp();
                 }
