@@ -249,6 +249,14 @@ tnh_status tnh_heff_set_projectors(tnh_heff* plan, int32_t k, const double* phi,
 /* y = H_eff . x; x and y are DEVICE float64 vectors in the psi layout of the
  * plan (they must not alias). Asynchronous on the plan's context stream. */
 tnh_status tnh_heff_apply(tnh_heff* plan, const double* x, double* y);
+/* y = H_eff . x for HOST vectors (float64, n elements in the psi layout): x is
+ * copied to the device, the product runs in the plan's precision, y is copied
+ * back, and the call returns when y is on the host (it synchronises the
+ * plan's stream). x and y may be the same array. Page-locked host memory
+ * makes the copies asynchronous DMA; pageable memory works, slower. The
+ * first call on a plan allocates the plan's two device vectors (freed with
+ * the plan). */
+tnh_status tnh_heff_apply_host(tnh_heff* plan, const double* x, double* y);
 /* Same product in another precision than the plan's (FP64 is always
  * available; a split mode is available when the plan was made with it). */
 tnh_status tnh_heff_apply_prec(tnh_heff* plan, tnh_precision prec,

@@ -1508,6 +1508,27 @@ tnh_status tnh_heff_apply_prec(tnh_heff* plan, tnh_precision prec, const double*
     });
 }
 
+tnh_status tnh_heff_apply_host(tnh_heff* plan, const double* x, double* y) {
+    auto* P = reinterpret_cast<HeffPlan*>(plan);
+    return guard(P ? P->ctx : nullptr, [&] {
+        TNH_REQUIRE(P && x && y, TNH_ERR_ARG, "tnh_heff_apply_host: NULL argument");
+        CUDA_CHECK(cudaSetDevice(P->ctx->device));
+        const size_t bytes = (size_t)P->n * sizeof(double);
+        if (P->n > 0 && !P->hx.p) {
+            AllocScope scope(P->stream);
+            P->hx.alloc(bytes);
+            P->hy.alloc(bytes);
+        }
+        if (P->n > 0) {
+            CUDA_CHECK(cudaMemcpyAsync(P->hx.p, x, bytes, cudaMemcpyHostToDevice, P->stream));
+            heff_apply(*P, P->prec, P->hx.as<double>(), P->hy.as<double>());
+            CUDA_CHECK(cudaMemcpyAsync(y, P->hy.p, bytes, cudaMemcpyDeviceToHost, P->stream));
+        }
+        CUDA_CHECK(cudaStreamSynchronize(P->stream));
+        check_device_flag(P->ctx);
+    });
+}
+
 tnh_status tnh_heff_diag(tnh_heff* plan, double* d) {
     auto* P = reinterpret_cast<HeffPlan*>(plan);
     return guard(P ? P->ctx : nullptr, [&] {

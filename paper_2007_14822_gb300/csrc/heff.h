@@ -103,6 +103,7 @@ struct HeffPlan {
     DevBuf Ld, Rd, d_dblocks, d_dstart, d_dterms, diag;
     int dg_wdim = 0, dg_zdim = 0, dg_d2 = 0, dg_nblocks = 0;
     int64_t dg_maxblock = 0;
+    DevBuf hx, hy;          // device vectors of tnh_heff_apply_host (made on its first call)
     ~HeffPlan();
 };
 

@@ -30,7 +30,8 @@ SYMBOLS = ["tnh_create", "tnh_destroy", "tnh_last_error", "tnh_sync", "tnh_layou
            "tnh_svd_stats", "tnh_svd_get", "tnh_svd_free", "tnh_dmrg", "tnh_profile_begin", "tnh_profile_end",
            "tnh_contract_dense_noalloc", "tnh_heff_plan_sum", "tnh_heff_set_projectors", "tnh_dmrg_ex",
            "tnh_dmrg_mps_size", "tnh_dmrg_mps_link", "tnh_dmrg_mps_get", "tnh_eigsolve_davidson", "tnh_heff_diag",
-           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout", "tnh_debug_convert_check", "tnh_heff_tuning",
+           "tnh_debug_fail_alloc", "tnh_debug_pool_used", "tnh_debug_wait_timeout", "tnh_debug_convert_check",
+           "tnh_heff_apply_host", "tnh_heff_tuning",
            "tnh_dmrg_checkpoint", "tnh_dmrg_resume", "tnh_dmrg_position", "tnh_tridiag_lowest"]
 
 
@@ -94,6 +95,7 @@ def lib():
         "tnh_heff_plan": (i32, [vp, P(tnh_tensor), P(tnh_tensor), P(tnh_tensor), P(tnh_tensor),
                                 P(tnh_tensor), C.c_int, P(vp)]),
         "tnh_heff_apply": (i32, [vp, vp, vp]),
+        "tnh_heff_apply_host": (i32, [vp, vp, vp]),
         "tnh_heff_apply_prec": (i32, [vp, C.c_int, vp, vp]),
         "tnh_heff_flops": (i32, [vp, P(dbl)]),
         "tnh_heff_flops_detail": (i32, [vp, P(dbl), P(dbl), P(dbl)]),
@@ -508,6 +510,19 @@ class Heff:
             self.ctx.check(self.ctx._lib.tnh_heff_apply(self.h, _ptr(x), _ptr(y)))
         else:
             self.ctx.check(self.ctx._lib.tnh_heff_apply_prec(self.h, int(prec), _ptr(x), _ptr(y)))
+        return y
+
+    def apply_host(self, x, y):
+        """y = H_eff x for CPU float64 tensors (page-locked for asynchronous
+        copies): the library copies x in and y out; returns when y is ready."""
+        import torch
+        for t in (x, y):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous():
+                raise TypeError("apply_host takes contiguous CPU float64 tensors")
+            if t.numel() != self.size:
+                raise ValueError(f"apply_host: {t.numel()} elements, the plan has {self.size}")
+        self.ctx.check(self.ctx._lib.tnh_heff_apply_host(self.h, C.c_void_p(x.data_ptr()),
+                                                         C.c_void_p(y.data_ptr())))
         return y
 
     @property

@@ -156,6 +156,37 @@ def test_heff_qn(ctx, m, nsect, maxd, p):
 
 
 @pytest.mark.parametrize("p", ["fp64", "bf16x6"])
+def test_heff_apply_host_buffers(ctx, p):
+    # the host-buffer entry point: x copied in, product, y copied out; the
+    # result is the device product's, bit for bit, within the oracle bound,
+    # in pinned and pageable memory, and with y the same array as x
+    import torch
+    d = H.heff_inputs(64, None, 11, nsect=9, maxd=16)
+    plan = ctx.heff_plan(d["L"], d["W"], d["W"], d["R"], d["psi"], prec(p))
+    ydev = torch.zeros_like(d["psi"].data)
+    plan.apply(d["psi"].data, ydev)
+    want = ydev.cpu()
+    for pinned in (True, False):
+        xh = d["psi"].data.cpu()
+        yh = torch.full_like(xh, float("nan"))
+        if pinned:
+            xh, yh = xh.pin_memory(), yh.pin_memory()
+        for _ in range(2):
+            plan.apply_host(xh, yh)
+            assert torch.equal(yh, want)
+        inplace = xh.clone()
+        plan.apply_host(inplace, inplace)
+        assert torch.equal(inplace, want)
+    ytens = d["psi"].with_inds(d["psi"].inds)
+    ytens.data = yh.cuda()
+    scale = heff_scale(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"])
+    H.assert_parity(H.to_oracle(ytens), D.heff_apply(d["Lo"], d["Wo"], d["Wo"], d["Ro"], d["psio"]), scale, p,
+                    TOL[p])
+    with pytest.raises(TypeError):
+        plan.apply_host(d["psi"].data, yh)
+
+
+@pytest.mark.parametrize("p", ["fp64", "bf16x6"])
 @pytest.mark.parametrize("m,nsect,maxd,split", [(40, 7, 12, None), (300, 3, 200, "2,4")])
 def test_heff_graph_replay_with_new_buffers(ctx, p, m, nsect, maxd, split, monkeypatch):
     # the first application launches directly, the second captures a CUDA
