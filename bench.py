@@ -14,7 +14,8 @@ the allowed block pairs of S1..S4; the extra products of the bf16 split are
 not counted) divided by the step time.
 
 More measurements go on the same JSON line (skip with --no-extra):
-  heff_qn          H_eff TFLOP/s, BF16x6 and FP64, on three block-sparse
+  heff_qn          H_eff TFLOP/s, BF16x6 and FP64, and the matvec error of
+                   every split mode (BF16x6, BF16x3, BF16) against FP64, on three block-sparse
                    workloads (U(1) m=1024, the cylinder m=2048, U(1)xU(1)
                    Hubbard m=4096); flops are the plan's block-pair sum
   bond_update_m256 one full bond update of the dense Heisenberg chain at
@@ -312,6 +313,24 @@ def bench_qn_heff(ctx, torch, tnh, oracle_kinds=()):
                     "fp64": {"ms": t_64 * 1e3, "tflops": f / t_64 / 1e12},
                     "plan_ms": t_plan * 1e3,
                     "kernels_bf16x6": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}})
+        # measured matvec error of every split mode against the FP64 product
+        # on the same inputs (which matches the oracle to 1e-12 in the tests):
+        # |y_mode - y_fp64|_2 / |y_fp64|_2 and the largest element deviation
+        # over |y_fp64|_inf
+        y64 = torch.empty_like(psi.data)
+        plan.apply(psi.data, y64, tnh.FP64)
+        errs = {}
+        for mode in ("bf16x6", "bf16x3", "bf16"):
+            pm_ = plan if mode == "bf16x6" else ctx.heff_plan(L, W1, W2, R, psi, tnh.PRECISION[mode])
+            ym = torch.empty_like(psi.data)
+            pm_.apply(psi.data, ym)
+            errs[mode] = {"norm": float(torch.linalg.vector_norm(ym - y64) / torch.linalg.vector_norm(y64)),
+                          "max_elem": float((ym - y64).abs().max() / y64.abs().max())}
+            if pm_ is not plan:
+                pm_.free()
+            del ym
+        out[-1]["matvec_rel_err_vs_fp64"] = errs
+        del y64
         if kind in oracle_kinds:
             t_or = oracle_matvec_seconds(L, W1, W2, R, psi)
             out[-1]["oracle_matvec"] = {"s": t_or, "tflops": f / t_or / 1e12, "cores": blas_threads(),
@@ -675,9 +694,9 @@ def max_over_ranks(x, dist, device):
 # kernel's sources at capture time: the figure is reported only while the
 # sources are unchanged.
 TRAFFIC = {
-    # S1 79.04 + 96.38 MB, S4 324.23 + 15.82 MB (profiles/heff_cylinder_m2048_bf16x6.md): the mean of the two
-    "gemm_tc_bf16x6": {"bytes_per_launch": (79.040256 + 96.377856 + 324.230656 + 15.819776) / 2 * 1e6,
-                       "source_sha": "86845ec4d1d176bb8f18993336cf6fed96cab92d90634093883be0cdbb23de78"},
+    # S1 79.04 + 96.33 MB, S4 324.22 + 15.84 MB (profiles/heff_cylinder_m2048_bf16x6.md): the mean of the two
+    "gemm_tc_bf16x6": {"bytes_per_launch": (79.038976 + 96.333312 + 324.219904 + 15.840768) / 2 * 1e6,
+                       "source_sha": "52dd38bfcc736377904f084cf79967759ac20add8dad90281b0e76755760625d"},
 }
 
 
