@@ -167,7 +167,7 @@ struct BGroup {
     int pair0;       // first global block-pair index
 };
 
-constexpr int kBJMaxB = 16;            // columns per block (a block pair has <= 32)
+constexpr int kBJMaxB = 8;             // columns per block (a block pair has <= 16)
 constexpr float kTol32 = 1e-5f;    // float32 rotation threshold
 constexpr float kDone32 = 2e-3f;   // float32 stop (the float64 polish finishes)
 
@@ -1116,7 +1116,7 @@ std::unique_ptr<SvdResult> run_svd(Ctx* ctx, const Layout& T, int nrow, double c
     }
     const int ng = (int)bg.size();
     if (ng == 0) return R;
-    // one block width for all groups: up to 16 columns while a block pair's
+    // one block width for all groups: up to 8 columns while a block pair's
     // X and V columns together would fit in 200 KB of shared memory (the
     // rule the widths were measured with; the kernel stages X only and
     // keeps V in global memory). An inner step moves about
