@@ -91,6 +91,17 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// the group whose block pairs include `item` (groups ascending by pair0)
+template <class GroupT>
+__device__ __forceinline__ int find_group(const GroupT* __restrict__ groups, int ngroups, int item) {
+    int lo = 0, hi = ngroups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (groups[mid].pair0 <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // round-robin (circle) schedule: slot j of round k among R+1 slots
 __device__ __forceinline__ int rr_pos(int j, int k, int R) { return j == 0 ? 0 : 1 + (j - 1 + k) % R; }
 
@@ -194,13 +205,12 @@ __global__ void __launch_bounds__(32 * (B < 4 ? 4 : B)) block_jacobi_f32(const B
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned epoch = 0;
     int t = 0;
+    // the group of this CTA's first block pair, found once (it is the same
+    // in every round; a CTA with more pairs looks the others up each round)
+    const int lo0 = blockIdx.x < total_pairs ? find_group(groups, ngroups, (int)blockIdx.x) : 0;
     for (; t < max_rounds; ++t) {
         for (int item = blockIdx.x; item < total_pairs; item += gridDim.x) {
-            int lo = 0, hi = ngroups - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (groups[mid].pair0 <= item) lo = mid; else hi = mid - 1;
-            }
+            const int lo = item == (int)blockIdx.x ? lo0 : find_group(groups, ngroups, item);
             const BGroup G = groups[lo];
             const int R = G.rounds;
             const int i = item - G.pair0, k = t % R;
@@ -389,13 +399,12 @@ __global__ void __launch_bounds__(kJ64Threads) jacobi_f64(const JGroup* __restri
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned epoch = 0;
     int t = 0;
+    // the group of this CTA's first block pair, found once (it is the same
+    // in every round; a CTA with more pairs looks the others up each round)
+    const int lo0 = blockIdx.x < total_pairs ? find_group(groups, ngroups, (int)blockIdx.x) : 0;
     for (; t < max_rounds; ++t) {
         for (int item = blockIdx.x; item < total_pairs; item += gridDim.x) {
-            int lo = 0, hi = ngroups - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (groups[mid].pair0 <= item) lo = mid; else hi = mid - 1;
-            }
+            const int lo = item == (int)blockIdx.x ? lo0 : find_group(groups, ngroups, item);
             const JGroup G = groups[lo];
             const int R = G.rounds;
             const int i = item - G.pair0, k = t % R;
