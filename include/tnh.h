@@ -203,10 +203,9 @@ tnh_status tnh_contract(tnh_ctx* ctx, const tnh_tensor* A, const tnh_tensor* B,
  * with TNH_ERR_ARG (use tnh_contract). The launch descriptors are written
  * into that array by a kernel that gets them as launch arguments: no host
  * buffer is copied. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it: make that first call before
- * any stream capture. Every call reuses the same array, so calls whose work
- * overlaps on the GPU (other streams, other contexts on the same device)
- * race and must be serialised by the caller. Asynchronous on the context's
+ * address (cudaGetSymbolAddress) and caches it. Every call reuses the same
+ * array, so calls whose work overlaps on the GPU (other streams, other
+ * contexts on the same device) race and must be serialised by the caller. Asynchronous on the context's
  * stream. Errors, all raised before anything is launched: TNH_ERR_LABEL for
  * a label repeated within A, B or C, or a free label missing in C;
  * TNH_ERR_SHAPE when a C index differs from the A or B index of its label
