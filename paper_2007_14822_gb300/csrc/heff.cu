@@ -1524,7 +1524,8 @@ tnh_status tnh_heff_apply_host(tnh_heff* plan, const double* x, double* y) {
             heff_apply(*P, P->prec, P->hx.as<double>(), P->hy.as<double>());
             CUDA_CHECK(cudaMemcpyAsync(y, P->hy.p, bytes, cudaMemcpyDeviceToHost, P->stream));
         }
-        CUDA_CHECK(cudaStreamSynchronize(P->stream));
+        // the plan's stream is the context's: reading the error flag after y
+        // is the one synchronisation of the call
         check_device_flag(P->ctx);
     });
 }

@@ -256,7 +256,8 @@ void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int total_tiles, const 
                     const uint16_t* B, double* C, int planes, int num_sms, int* err,
                     cudaStream_t s, const int64_t* row_off = nullptr);
 // K-split reduction: out = sum over S float32 partial slabs [S][M][N]
-// (summed in float64, fixed order), written to float32 or float64 rows.
+// (float32 partials summed in float32, float64 ones in float64, slab order),
+// written to float32 or float64 rows.
 struct SplitRed {
     int M, N, S;
     int use_roff, out_f32;
