@@ -691,21 +691,28 @@ def max_over_ranks(x, dist, device):
 
 # DRAM bytes (read + write) per launch of the headline's dominant kernel,
 # from one ncu capture of the headline workload, with the SHA-256 of the
-# kernel's sources at capture time: the figure is reported only while the
-# sources are unchanged.
+# kernel's sources (comments removed) at capture time: the figure is reported
+# only while the sources' code is unchanged.
 TRAFFIC = {
-    # S1 79.04 + 96.33 MB, S4 324.22 + 15.84 MB (profiles/heff_cylinder_m2048_bf16x6.md): the mean of the two
+    # S1 79.04 + 96.33 MB, S4 324.22 + 15.84 MB (dram__bytes_read.sum + dram__bytes_write.sum of one
+    # application of the headline workload): the mean of the two launches
     "gemm_tc_bf16x6": {"bytes_per_launch": (79.038976 + 96.333312 + 324.219904 + 15.840768) / 2 * 1e6,
-                       "source_sha": "52dd38bfcc736377904f084cf79967759ac20add8dad90281b0e76755760625d"},
+                       "source_sha": "80894296b271849ff345517fb72f1a8d44cc03ea684ef130fb69c6eb0bf4dc4d"},
 }
 
 
 def source_sha(files):
+    """SHA-256 of the sources' code: comments, blank lines and trailing
+    blanks removed, so that editing a comment keeps the captured figures."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2007_14822_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2007_14822_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()
 
 

@@ -71,3 +71,21 @@ def test_chain_flops_equal_the_counted_heff_contractions(counted, kind, m, recip
     f = bench.chain_flops(L, W1, W2, R, psi)
     D.heff_apply(L, W1, W2, R, psi)
     assert counted[0] == f and f > 0
+
+
+def test_kernel_traffic_is_keyed_on_code_not_comments(tmp_path, monkeypatch):
+    """The stored DRAM traffic of a kernel stays valid across comment edits of
+    its sources and is dropped (None) after a change to their code."""
+    src = tmp_path / "paper_2007_14822_gb300" / "csrc"
+    src.mkdir(parents=True)
+    code = "// a kernel\nint f(int x) {\n    return x + 1;   /* one */\n}\n"
+    (src / "k.cu").write_text(code)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.KERNEL_SOURCES, "kern", ["k.cu"])
+    monkeypatch.setitem(bench.TRAFFIC, "kern_x", {"bytes_per_launch": 123.0,
+                                                  "source_sha": bench.source_sha(["k.cu"])})
+    assert bench.kernel_traffic("kern_x") == 123.0
+    (src / "k.cu").write_text("// the kernel, reworded\n\nint f(int x) {\n    return x + 1;\n}   // end\n")
+    assert bench.kernel_traffic("kern_x") == 123.0
+    (src / "k.cu").write_text(code.replace("x + 1", "x + 2"))
+    assert bench.kernel_traffic("kern_x") is None
