@@ -243,32 +243,40 @@ __global__ void __launch_bounds__(kW12Threads) w12_kernel(const W12Cta* __restri
     };
     // T1 rows are padded to multiples of 4 columns with zeros (S1 multiplies
     // zero rows of its psi operand there): four loads never leave the row's
-    // padded segment. The loads of up to kB terms are issued together; the
-    // sums run in term order.
+    // padded segment. The cell's terms are walked in chunks of kB in their
+    // stored order (each output's terms contiguous, output after output, at
+    // least one per output): a chunk's loads are issued together even where
+    // it spans several outputs (most outputs have one or two terms), and an
+    // output is stored as soon as its last term is added. Each output's sum
+    // runs in term order.
     constexpr int kB = 4;
-    for (int o = 0; o < C.nout; ++o) {
-        const W12Out O = po[o];
-        AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
-        for (int j0 = O.t0 - tb; j0 < O.t1 - tb; j0 += kB) {
-            const int nb = min(kB, O.t1 - tb - j0);
-            SrcT x[kB][4];
-            AccT cf[kB];
+    int o = 0;
+    int oend = C.nout > 0 ? po[0].t1 - tb : 0;   // end of output o's terms, relative to tb
+    AccT v[4] = {AccT(0), AccT(0), AccT(0), AccT(0)};
+    for (int j0 = 0; j0 < nterm; j0 += kB) {
+        const int nb = min(kB, nterm - j0);
+        SrcT x[kB][4];
+        AccT cf[kB];
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                if (u < nb) {
-                    const W12Term& t = pt[j0 + u];
-                    load4(src + t.base + (int64_t)r * t.ld + c, x[u]);
-                    cf[u] = kF64 ? (AccT)t.coef : (AccT)t.coef32;
+        for (int u = 0; u < kB; ++u) {
+            if (u < nb) {
+                const W12Term& t = pt[j0 + u];
+                load4(src + t.base + (int64_t)r * t.ld + c, x[u]);
+                cf[u] = kF64 ? (AccT)t.coef : (AccT)t.coef32;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (u < nb) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = fma(cf[u], (AccT)x[u][k], v[k]);
+                if (j0 + u + 1 == oend) {
+                    store(po[o], v);
+                    v[0] = v[1] = v[2] = v[3] = AccT(0);
+                    if (++o < C.nout) oend = po[o].t1 - tb;
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kB; ++u)
-                if (u < nb) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) v[k] = fma(cf[u], (AccT)x[u][k], v[k]);
-                }
         }
-        store(O, v);
     }
 }
 
