@@ -454,10 +454,10 @@ void launch_p(const GemmTask* d_tasks, int ntasks, int total_tiles, const uint16
 // thread takes kE elements and issues their loads of one slab together, so a
 // block waits S load latencies, not S times its element count.
 template <class PartT>
-__global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict__ reds,
-                                                     const RedBlock* __restrict__ blocks,
-                                                     const PartT* __restrict__ part, void* __restrict__ out,
-                                                     const int64_t* __restrict__ row_off) {
+__global__ void __launch_bounds__(256, 6) splitk_reduce(const SplitRed* __restrict__ reds,
+                                                        const RedBlock* __restrict__ blocks,
+                                                        const PartT* __restrict__ part, void* __restrict__ out,
+                                                        const int64_t* __restrict__ row_off) {
     constexpr int kE = 8;
     const RedBlock b = blocks[blockIdx.x];
     const SplitRed R = reds[b.red];
@@ -469,22 +469,9 @@ __global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict_
     // elements (256 apart), without a division per element
     const int dm = 256 / R.N, dn = 256 - dm * R.N;
     for (int base = 0; base < nel; base += kE * 256) {
-        int ml = (base + (int)threadIdx.x) / R.N, n = base + (int)threadIdx.x - ml * R.N;
-        int64_t dst[kE];
         PartT acc[kE];
 #pragma unroll
-        for (int i = 0; i < kE; ++i) {
-            const int e = base + i * 256 + threadIdx.x;
-            acc[i] = PartT(0);
-            dst[i] = -1;
-            if (e < nel) {
-                const int m = b.m0 + ml;
-                dst[i] = R.use_roff ? __ldg(row_off + R.roff + m) + n : R.c_base + (int64_t)m * R.ldc + n;
-            }
-            ml += dm;
-            n += dn;
-            if (n >= R.N) { n -= R.N; ++ml; }
-        }
+        for (int i = 0; i < kE; ++i) acc[i] = PartT(0);
         for (int j = 0; j < R.S; ++j) {
             PartT v[kE];
 #pragma unroll
@@ -495,12 +482,22 @@ __global__ void __launch_bounds__(256) splitk_reduce(const SplitRed* __restrict_
 #pragma unroll
             for (int i = 0; i < kE; ++i) acc[i] += v[i];
         }
+        // destinations are formed after the sums, so that they hold no
+        // registers while the slices load (six blocks of 256 threads fit an SM)
+        int ml = (base + (int)threadIdx.x) / R.N, n = base + (int)threadIdx.x - ml * R.N;
 #pragma unroll
         for (int i = 0; i < kE; ++i) {
-            if (dst[i] < 0) continue;
-            if (R.out_f32) static_cast<float*>(out)[dst[i]] = (float)acc[i];
-            else if constexpr (std::is_same<PartT, float>::value) static_cast<double*>(out)[dst[i]] = f32_to_f64(acc[i]);
-            else static_cast<double*>(out)[dst[i]] = acc[i];
+            const int e = base + i * 256 + threadIdx.x;
+            if (e < nel) {
+                const int m = b.m0 + ml;
+                const int64_t d = R.use_roff ? __ldg(row_off + R.roff + m) + n : R.c_base + (int64_t)m * R.ldc + n;
+                if (R.out_f32) static_cast<float*>(out)[d] = (float)acc[i];
+                else if constexpr (std::is_same<PartT, float>::value) static_cast<double*>(out)[d] = f32_to_f64(acc[i]);
+                else static_cast<double*>(out)[d] = acc[i];
+            }
+            ml += dm;
+            n += dn;
+            if (n >= R.N) { n -= R.N; ++ml; }
         }
     }
 }
