@@ -694,10 +694,10 @@ def max_over_ranks(x, dist, device):
 # kernel's sources (comments removed) at capture time: the figure is reported
 # only while the sources' code is unchanged.
 TRAFFIC = {
-    # S1 79.04 + 96.33 MB, S4 324.22 + 15.84 MB (dram__bytes_read.sum + dram__bytes_write.sum of one
+    # S1 79.02 + 96.44 MB, S4 324.22 + 16.00 MB (dram__bytes_read.sum + dram__bytes_write.sum of one
     # application of the headline workload): the mean of the two launches
-    "gemm_tc_bf16x6": {"bytes_per_launch": (79.038976 + 96.333312 + 324.219904 + 15.840768) / 2 * 1e6,
-                       "source_sha": "80894296b271849ff345517fb72f1a8d44cc03ea684ef130fb69c6eb0bf4dc4d"},
+    "gemm_tc_bf16x6": {"bytes_per_launch": (79.024128 + 96.43776 + 324.224 + 16.000256) / 2 * 1e6,
+                       "source_sha": "da7071d557175e7db89371e98863734bd6f5f5beea36a42a5b877773c6f8222c"},
 }
 
 
