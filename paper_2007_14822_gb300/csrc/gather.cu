@@ -105,24 +105,30 @@ __global__ void __launch_bounds__(256, kF64 ? 6 : 7) gather_kernel(const GatherT
         const int nr = re - rb;
         const int n = nr * S.nc;
         const bool cfast = terms[S.t0].cs == 1;
+        // element e of the segment part is (row, column) = (e / nc, e % nc)
+        // when the source runs along columns, else (e % nr, e / nr): with
+        // minor = nc or nr, e = major * minor + minor index. A thread's
+        // elements are blockDim.x apart, so it steps (major, minor) instead
+        // of dividing per element.
+        const int minor = cfast ? S.nc : nr;
+        const int dmaj = (int)blockDim.x / minor, dmin = (int)blockDim.x - dmaj * minor;
         if (S.t1 - S.t0 == 1) {
             // one term (a copy): eight independent loads in flight per thread
             const GatherTerm g = terms[S.t0];
             const AccT cf = coef_of<kF64>(g);
             for (int e0 = threadIdx.x; e0 < n; e0 += 8 * blockDim.x) {
+                int maj = e0 / minor, mnr = e0 - maj * minor;
                 AccT v[8];
                 int pos[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int e = e0 + u * blockDim.x;
-                    int r = 0, c = 0;
-                    if (e < n) {
-                        if (cfast) { r = e / S.nc; c = e - r * S.nc; }
-                        else { c = e / nr; r = e - c * nr; }
-                    }
-                    r += rb;
+                    const int r = (cfast ? maj : mnr) + rb, c = cfast ? mnr : maj;
                     pos[u] = e < n ? (S.r0 + r - h0) * kPitch + S.c0 + c : -1;
                     v[u] = e < n ? cf * to_acc<AccT>(src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs]) : AccT(0);
+                    maj += dmaj;
+                    mnr += dmin;
+                    if (mnr >= minor) { mnr -= minor; ++maj; }
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
@@ -130,17 +136,18 @@ __global__ void __launch_bounds__(256, kF64 ? 6 : 7) gather_kernel(const GatherT
             }
             continue;
         }
+        int maj = (int)threadIdx.x / minor, mnr = (int)threadIdx.x - maj * minor;
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            int r, c;
-            if (cfast) { r = e / S.nc; c = e - r * S.nc; }
-            else { c = e / nr; r = e - c * nr; }
-            r += rb;
+            const int r = (cfast ? maj : mnr) + rb, c = cfast ? mnr : maj;
             AccT v = AccT(0);
             for (int j = S.t0; j < S.t1; ++j) {
                 const GatherTerm& g = terms[j];
                 v += coef_of<kF64>(g) * to_acc<AccT>(src[g.off + (int64_t)r * g.rs + (int64_t)c * g.cs]);
             }
             tile_s[(S.r0 + r - h0) * kPitch + S.c0 + c] = v;
+            maj += dmaj;
+            mnr += dmin;
+            if (mnr >= minor) { mnr -= minor; ++maj; }
         }
     }
     __syncthreads();
