@@ -272,6 +272,8 @@ struct CellBuilder {
                     J.terms.push_back({in.base, a.second, (float)a.second, (int)in.ld});
                 }
                 o.t1 = (int)J.terms.size();
+                // the MPO step stores an output with its last term: none may be empty
+                TNH_REQUIRE(o.t1 > o.t0, TNH_ERR_SHAPE, "heff_plan: MPO step output without terms");
                 J.outs.push_back(o);
             }
             cell.nin = (int)J.ins.size() - cell.in0;
