@@ -161,6 +161,38 @@ CASES = [
     ("product state: link charges subtracted", "oracle.dmrg",
      "        q = qn_add(q, qs)", "        q = qn_add(q, tuple(-x for x in qs))",
      TD.test_dmrg_hubbard_vs_ed, ()),
+    ("theta: second tensor joined at its right link", "oracle.dmrg",
+     '    A2 = A2.relabel(["c", "s2", "b"])', '    A2 = A2.relabel(["b", "s2", "c"])',
+     TD.test_dmrg_heisenberg_dense_vs_ed, ()),
+    ("sweep: right-to-left step drops S from the new centre", "oracle.dmrg",
+     "                A[j] = scale_link(U, S, 2)", "                A[j] = U",
+     TD.test_dmrg_excited_states_tfim, ()),
+    ("sweep: every sweep truncated to the first sweep's maxdim", "oracle.dmrg",
+     "            U, S, V, err = svd_trunc(th, 2, cutoff, maxdim, mindim)",
+     "            U, S, V, err = svd_trunc(th, 2, cutoff, sweeps[0][0], mindim)",
+     TD.test_dmrg_heisenberg_dense_vs_ed, ()),
+    ("residual: E x added instead of subtracted", "oracle.dmrg",
+     "    r = y.axpy(-E, x).norm()", "    r = y.axpy(E, x).norm()",
+     TD.test_energy_residual_rayleigh_quotient, ()),
+    ("ED: highest eigenvalue returned", "oracle.ed",
+     "        w = np.linalg.eigh(H.toarray())[0]\n        return w[:k] if k > 1 else float(w[0])",
+     "        w = np.linalg.eigh(H.toarray())[0]\n        return w[:k] if k > 1 else float(w[-1])",
+     TM.test_heisenberg_small_closed_forms, (4, -0.75 - math.sqrt(3) / 2)),
+    ("ED: sector test on any one charge component", "oracle.ed",
+     "np.all(ch == np.asarray(sector)[None, :], axis=1)", "np.any(ch == np.asarray(sector)[None, :], axis=1)",
+     TD.test_dmrg_hubbard_vs_ed, ()),
+    ("permutation: block keys moved, data not transposed", "oracle.blocksparse",
+     "        blocks = {tuple(k[p] for p in perm): np.transpose(v, perm)",
+     "        blocks = {tuple(k[p] for p in perm): v",
+     TB.test_index_order_independence, ()),
+    ("contraction: free sectors of B before those of A", "oracle.blocksparse",
+     "            kc = tuple(ka[p] for p in fa) + tuple(kb[q] for q in fb)",
+     "            kc = tuple(kb[q] for q in fb) + tuple(ka[p] for p in fa)",
+     TB.test_blocksparse_contract_equals_dense, ()),
+    ("contraction: contracted axes paired in reverse", "oracle.blocksparse",
+     "            prod = np.tensordot(va, vb, axes=(ia, ib))",
+     "            prod = np.tensordot(va, vb, axes=(ia, ib[::-1]))",
+     TB.test_blocksparse_contract_equals_dense, ()),
 ]
 
 
