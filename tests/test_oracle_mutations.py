@@ -193,6 +193,16 @@ CASES = [
      "            prod = np.tensordot(va, vb, axes=(ia, ib))",
      "            prod = np.tensordot(va, vb, axes=(ia, ib[::-1]))",
      TB.test_blocksparse_contract_equals_dense, ()),
+    ("Lanczos: Ritz vector from shifted coefficients", "oracle.dmrg",
+     "    for qi, si in zip(q[1:len(s)], s[1:]):", "    for qi, si in zip(q[1:len(s)], s[:-1]):",
+     TD.test_lanczos_matches_eigh, ()),
+    ("SVD: U columns out of order", "oracle.dmrg",
+     "            Ut.blocks[rk + (ci,)] = U[roff[rk]:roff[rk] + rr, idx].reshape(shp + (len(idx),))",
+     "            Ut.blocks[rk + (ci,)] = U[roff[rk]:roff[rk] + rr, idx[::-1]].reshape(shp + (len(idx),))",
+     TD.test_svd_trunc_eckart_young_and_predicted_count, ()),
+    ("SVD: a group's singular values in reverse", "oracle.dmrg",
+     "        S[Q] = s[idx]", "        S[Q] = s[idx][::-1]",
+     TD.test_svd_trunc_eckart_young_and_predicted_count, ()),
 ]
 
 
