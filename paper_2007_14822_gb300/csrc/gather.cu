@@ -80,9 +80,10 @@ __device__ __forceinline__ AccT to_acc(SrcT x) {
 }
 
 // CTA kTileParts t + h builds rows [kPartRows h, kPartRows (h + 1)) of tile t.
-// The split formats run seven CTAs per SM (32 registers, no spills): more
-// loads in flight for packs of many small tiles (the U(1)xU(1) Hubbard ψ,
-// m = 4096: 43 -> 38 us).
+// The split formats run seven CTAs per SM (32 registers; no spills for the
+// float64 sources that the effective-Hamiltonian plan packs): more loads in
+// flight for packs of many small tiles (the U(1)xU(1) Hubbard ψ, m = 4096:
+// 43 -> 38 us).
 template <class SrcT, bool kF64, int P>
 __global__ void __launch_bounds__(256, kF64 ? 6 : 7) gather_kernel(const GatherTile* __restrict__ tiles,
                                                                    const GatherSeg* __restrict__ segs,
