@@ -21,6 +21,14 @@
  *     of the last error of a context is returned by tnh_last_error().
  *   - Nothing falls back to the CPU: when the device or the kernels are not
  *     usable the call fails with TNH_ERR_CUDA.
+ *   - Errors any call may return besides those listed with it: TNH_ERR_ARG
+ *     for a NULL handle or output pointer, a negative size or an unknown
+ *     enum value; TNH_ERR_OOM when a device allocation fails (everything the
+ *     call had allocated is released first); TNH_ERR_TIMEOUT when a bounded
+ *     device wait gave up (the call that finds the context's device error
+ *     flag set reports it and clears it; the context stays usable);
+ *     TNH_ERR_CUDA for a failed CUDA call, named in tnh_last_error(). The
+ *     functions that free a handle accept NULL and do nothing.
  */
 #ifndef TNH_H
 #define TNH_H
@@ -107,13 +115,19 @@ typedef struct {
 
 /* Create a context on CUDA device `device` using `stream` (a cudaStream_t,
  * NULL for the legacy default stream). The library keeps the stream handle;
- * the caller keeps ownership of the stream. */
+ * the caller keeps ownership of the stream. TNH_ERR_ARG for a device index
+ * out of range; TNH_ERR_CUDA when there is no device or it is not an sm_103
+ * GPU (the library is built for sm_103a only). */
 tnh_status tnh_create(tnh_ctx** ctx, int device, void* stream);
+/* Synchronise the context's stream and free the context. Plans and SVD
+ * results made on it must not be used afterwards (they refer to it); they
+ * may still be freed. NULL does nothing. */
 void tnh_destroy(tnh_ctx* ctx);
 /* Text of the last error raised on `ctx` (or of the last context-free error
  * when ctx is NULL). Valid until the next call on the same context. */
 const char* tnh_last_error(const tnh_ctx* ctx);
-/* Block until all work queued by the context has finished. */
+/* Block until all work queued by the context has finished; reports a
+ * bounded device wait that gave up in that work (TNH_ERR_TIMEOUT). */
 tnh_status tnh_sync(tnh_ctx* ctx);
 
 /* Kernel profiling (no counterpart in the paper; measurement support).
