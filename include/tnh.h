@@ -240,7 +240,12 @@ tnh_status tnh_contract_dense_noalloc(tnh_ctx* ctx, const tnh_tensor* A, const t
  *   psi [a, s1, s2, b]    layout of the two-site state (data ignored).
  * Labels are taken from the position, not from the index labels. L, R and
  * the W's are read during the call (the plan keeps packed copies; the
- * caller may free them afterwards). Synchronises the context's stream. */
+ * caller may free them afterwards). Synchronises the context's stream.
+ * Errors: TNH_ERR_ARG for other ranks or an unknown precision;
+ * TNH_ERR_SHAPE when two contracted indices have different sectors, an
+ * output index differs from psi's, or psi's storage is smaller than its
+ * blocks; TNH_ERR_ARROW for contracted indices with equal arrows;
+ * TNH_ERR_FLUX when L, W1, W2 and R together do not conserve psi's flux. */
 tnh_status tnh_heff_plan(tnh_ctx* ctx, const tnh_tensor* L, const tnh_tensor* W1,
                          const tnh_tensor* W2, const tnh_tensor* R,
                          const tnh_tensor* psi, tnh_precision prec, tnh_heff** plan);
