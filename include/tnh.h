@@ -265,7 +265,8 @@ tnh_status tnh_heff_plan_sum(tnh_ctx* ctx, int32_t nterm, const tnh_tensor* L, c
  * removes them), in float64 with deterministic reductions. k <= 256. */
 tnh_status tnh_heff_set_projectors(tnh_heff* plan, int32_t k, const double* phi, double weight);
 /* y = H_eff . x; x and y are DEVICE float64 vectors in the psi layout of the
- * plan (they must not alias). Asynchronous on the plan's context stream. */
+ * plan (they must not alias: TNH_ERR_ARG). Asynchronous on the plan's
+ * context stream. */
 tnh_status tnh_heff_apply(tnh_heff* plan, const double* x, double* y);
 /* y = H_eff . x for HOST vectors (float64, n elements in the psi layout): x is
  * copied to the device, the product runs in the plan's precision, y is copied
@@ -276,7 +277,8 @@ tnh_status tnh_heff_apply(tnh_heff* plan, const double* x, double* y);
  * the plan). */
 tnh_status tnh_heff_apply_host(tnh_heff* plan, const double* x, double* y);
 /* Same product in another precision than the plan's (FP64 is always
- * available; a split mode is available when the plan was made with it). */
+ * available; a split mode is available when the plan was made with it,
+ * else TNH_ERR_ARG). x and y must not alias (TNH_ERR_ARG). */
 tnh_status tnh_heff_apply_prec(tnh_heff* plan, tnh_precision prec,
                                const double* x, double* y);
 /* Algorithmic flops of one product: 2 M N K summed over every block GEMM of
