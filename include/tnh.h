@@ -438,7 +438,13 @@ typedef struct {
  * the final sweep is evaluated again with FP64 environments rebuilt from the
  * final MPS (right-orthogonal from site 2 on): <theta|H_eff|theta> at bond
  * (0, 1) in FP64, the state's exact energy to float64 rounding. The final
- * MPS stays on the device inside the context (tnh_dmrg_mps_*). Synchronous. */
+ * MPS stays on the device inside the context (tnh_dmrg_mps_*). Synchronous.
+ * Errors: TNH_ERR_ARG for N < 2, an empty schedule, an unknown precision,
+ * eigensolver or energy mode, tensors of the wrong rank or start/done
+ * outside the boundary links; TNH_ERR_FLUX for an MPS block with another
+ * flux than its site's or a boundary state in a forbidden block;
+ * TNH_ERR_SHAPE, TNH_ERR_ARROW as for the contractions of a bond;
+ * TNH_ERR_NUMERIC when a start vector is zero or not finite. */
 tnh_status tnh_dmrg(tnh_ctx* ctx, int32_t N, const tnh_tensor* mpo, int64_t start,
                     int64_t done, const tnh_tensor* mps, const tnh_sweep_params* p,
                     double* energy, tnh_sweep_stat* stats);
